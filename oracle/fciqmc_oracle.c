@@ -1,0 +1,870 @@
+/*
+ * Plain CPU oracle for the FCIQMC walker cycle (Booth, Smart, Alavi,
+ * "Linear-scaling and parallelizable algorithms for stochastic quantum
+ * chemistry").
+ *
+ * TEST INFRASTRUCTURE ONLY. Nothing in the product path may call, link or
+ * load this file; it exists so that tests, the smoke check and the CPU
+ * baseline of the benchmark can compare the CUDA library against a slow,
+ * obviously correct restatement of the method. It shares no code, header or
+ * constant table with the CUDA side: every constant of the random-number
+ * contract is written out again here.
+ *
+ * Build: gcc -O2 -ffp-contract=off -fopenmp -fPIC -shared (no FMA contraction,
+ * so every floating-point expression below is evaluated exactly as written).
+ *
+ * What is computed, per iteration (Sec. II, Eqs. 1, 3, 4; Sec. V; Sec. VI):
+ *   1. for every walker on every occupied determinant D_i (populations taken
+ *      at the start of the iteration, Sec. II "walkers spawned, cloned or
+ *      killed within an iteration do not contribute"): draw an excitation
+ *      D_j with normalised probability P_gen(j|i) (Sec. VI A/B), evaluate
+ *      H_ij by the Slater-Condon rules, and spawn floor(p) + Bernoulli(frac p)
+ *      walkers with p = tau |H_ij| / P_gen and sign -sign(C_i) sign(H_ij)
+ *      (Eq. 3);
+ *   2. death/cloning on every determinant with p_death = tau C_i (H_ii-E0-S)
+ *      (Eq. 4);
+ *   3. sort and compress the spawned list (Sec. V A), i.e. merge duplicate
+ *      determinants, summing signed amounts and OR-ing initiator flags;
+ *   4. annihilate the merged list against the post-death main list: add to
+ *      occupied determinants, insert unoccupied ones only if the initiator
+ *      flag is set (or the initiator approximation is off), computing the
+ *      stored diagonal H_ii on insertion (Sec. V B);
+ *   5. record the estimators (shift S, projected energy Eq. 2) and update S.
+ *
+ * Readings where the paper is silent (each one also fixed on the CUDA side):
+ *   - random numbers: counter-based Philox4x32-10 (Salmon et al., SC'11) in
+ *     place of the Mersenne twister, keyed by (seed, iteration) with counter
+ *     (attempt, tag, fingerprint lo, fingerprint hi); fingerprint = Algorithm 1
+ *     (p = 1099511628211, uint64 wraparound, no abs/mod) over the ascending
+ *     occupied spin orbitals with a Philox-generated orbital map;
+ *   - random choices among n options by rank selection, k = floor(r n / 2^64),
+ *     instead of redraw loops (same distribution, fixed draw count);
+ *   - single/double choice: double iff (r0 >> 11) < floor(P_double 2^53), and
+ *     P_double itself is the double/single ratio of the reference rounded to a
+ *     multiple of 2^-53 so that the draw realises it exactly;
+ *   - initiator: |C_i| > threshold, or D_i is the reference;
+ *   - shift: S <- S - zeta/(A tau) ln(N_w(n) / N_w(n-A)) every A iterations
+ *     once N_w first reaches the target.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OQ_MAXW 2
+#define OQ_MAXSO 128
+
+/* ------------------------------------------------------------------------- */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy
+ * as 1, 2, 3", SC'11): 10 rounds of two 32x32->64 multiplications with the
+ * published multipliers and Weyl key increments. */
+void oq_philox(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; ++round) {
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Two 64-bit words from one Philox block: (out0 | out1 << 32, out2 | out3 << 32). */
+static void draw2(uint32_t a, uint32_t tag, uint64_t fp, uint32_t seed, uint32_t iter,
+                  uint64_t *w0, uint64_t *w1)
+{
+    uint32_t ctr[4] = {a, tag, (uint32_t)fp, (uint32_t)(fp >> 32)};
+    uint32_t key[2] = {seed, iter};
+    uint32_t o[4];
+    oq_philox(ctr, key, o);
+    *w0 = (uint64_t)o[0] | ((uint64_t)o[1] << 32);
+    *w1 = (uint64_t)o[2] | ((uint64_t)o[3] << 32);
+}
+
+/* k = floor(r * n / 2^64): uniform choice in [0, n) from a 64-bit word. */
+static uint64_t rank_of(uint64_t r, uint64_t n)
+{
+    return (uint64_t)(((unsigned __int128)r * (unsigned __int128)n) >> 64);
+}
+
+/* u = (r >> 11) * 2^-53, exactly representable, in [0, 1). */
+static double unit53(uint64_t r)
+{
+    return (double)(r >> 11) * 0x1.0p-53;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Natural logarithm written from the mathematics (used by the shift update).
+ * x = m 2^e with m in [sqrt(1/2), sqrt(2)); s = (m-1)/(m+1);
+ * ln m = 2 atanh(s) = 2 s sum_{k>=0} s^{2k}/(2k+1), truncated after k = 11
+ * (|s| <= 0.1716, so the first omitted term is below 1e-19 relative);
+ * ln x = e*LN2_HI + (ln m + e*LN2_LO) with ln 2 split so that e*LN2_HI is exact. */
+double oq_log(double x)
+{
+    const double LN2_HI = 0x1.62e42fe800000p-1;
+    const double LN2_LO = 0x1.e8e7bcd5e4f1ep-31;
+    const double SQRT2 = 0x1.6a09e667f3bcdp+0;
+    if (!(x > 0.0)) return x == 0.0 ? -INFINITY : NAN;
+    if (isinf(x)) return x;
+    int e = 0;
+    if (x < 0x1.0p-1022) { x = x * 0x1.0p54; e = -54; }
+    uint64_t bits;
+    memcpy(&bits, &x, 8);
+    e += (int)((bits >> 52) & 0x7FF) - 1023;
+    bits = (bits & 0x000FFFFFFFFFFFFFull) | 0x3FF0000000000000ull;
+    double m;
+    memcpy(&m, &bits, 8);
+    if (m > SQRT2) { m = m * 0.5; e += 1; }
+    double s = (m - 1.0) / (m + 1.0);
+    double z = s * s;
+    double poly = 1.0 / 23.0;
+    for (int k = 10; k >= 0; --k) poly = poly * z + 1.0 / (double)(2 * k + 1);
+    double t = s * poly;
+    double lnm = t + t;
+    double de = (double)e;
+    double r = lnm + de * LN2_LO;
+    return de * LN2_HI + r;
+}
+
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    int64_t iter;
+    double shift;
+    int64_t nw_in, nd_in, c0_in;
+    double num_in;
+    int64_t nw_out, nd_out;
+    int64_t attempts, nulls, spawn_events, spawned_walkers;
+    int64_t death_walkers, clone_walkers, merged_entries, aborted_walkers, inserted_dets;
+} oq_row;
+
+typedef struct {
+    uint64_t d[OQ_MAXW];
+    int64_t amt;
+    int flag;
+} spawn_t;
+
+typedef struct {
+    int n_orb, n_elec, n_so, W, n_alpha, n_beta;
+    double *h, *eri, e_core;
+    int64_t npair_sp;          /* spatial pairs M(M+1)/2 */
+    int irrep[OQ_MAXSO / 2];
+    int has_sym;
+    uint64_t ref[OQ_MAXW];
+    double E0;                 /* H_00 without e_core */
+    double tau;
+    int32_t init_thr;
+    int64_t target;
+    double zeta;
+    int32_t period;
+    double c_shift;            /* zeta / (A tau) */
+    uint32_t seed;
+    uint64_t map1[OQ_MAXSO];
+    int64_t n_single_ref, n_double_ref;
+    uint64_t d53;              /* double iff (r0 >> 11) < d53 */
+    double p_double, p_single, cs, cd;
+    /* state */
+    int64_t n, cap;
+    uint64_t *det;             /* n * W, sorted ascending (lexicographic on words) */
+    int32_t *pop;
+    double *hd;                /* H_ii - E0 */
+    uint32_t iter;
+    double shift;
+    int vary;
+    int64_t nw_prev;
+    int n_since;
+    int error;                 /* 0 ok, nonzero: numeric overflow */
+} oq_t;
+
+/* ---------------- bit-string helpers ---------------- */
+static int det_bit(const oq_t *q, const uint64_t *d, int k) { (void)q; return (int)((d[k >> 6] >> (k & 63)) & 1u); }
+static void det_flip(uint64_t *d, int k) { d[k >> 6] ^= (uint64_t)1 << (k & 63); }
+static int det_eq(const oq_t *q, const uint64_t *a, const uint64_t *b)
+{
+    for (int w = 0; w < q->W; ++w) if (a[w] != b[w]) return 0;
+    return 1;
+}
+static int det_cmp(int W, const uint64_t *a, const uint64_t *b)
+{
+    for (int w = W - 1; w >= 0; --w) {
+        if (a[w] < b[w]) return -1;
+        if (a[w] > b[w]) return 1;
+    }
+    return 0;
+}
+/* ascending occupied spin orbitals */
+static int decode(const oq_t *q, const uint64_t *d, int *occ)
+{
+    int n = 0;
+    for (int k = 0; k < q->n_so; ++k) if (det_bit(q, d, k)) occ[n++] = k;
+    return n;
+}
+static int spin_of(int k) { return k & 1; }
+static int spat_of(int k) { return k >> 1; }
+static int class_of(const oq_t *q, int k) { return q->irrep[spat_of(k)] * 2 + spin_of(k); }
+static int class_make(int irrep, int spin) { return irrep * 2 + spin; }
+
+/* ---------------- integrals ---------------- */
+static double h1(const oq_t *q, int p, int r) { return q->h[(int64_t)p * q->n_orb + r]; }
+static int64_t pair_index(int64_t p, int64_t r) { return p >= r ? p * (p + 1) / 2 + r : r * (r + 1) / 2 + p; }
+/* chemists' (pq|rs) over spatial orbitals, 8-fold packed */
+static double eri4(const oq_t *q, int p, int r, int s, int t)
+{
+    int64_t a = pair_index(p, r), b = pair_index(s, t);
+    return q->eri[pair_index(a, b)];
+}
+
+/* Algorithm 1 (Sec. V): hash = p*hash + map(det(i))*i over electrons i = 1..N. */
+uint64_t oq_fingerprint(const oq_t *q, const uint64_t *d)
+{
+    int occ[OQ_MAXSO];
+    int n = decode(q, d, occ);
+    uint64_t hsh = 0;
+    for (int i = 1; i <= n; ++i) hsh = 1099511628211ull * hsh + q->map1[occ[i - 1]] * (uint64_t)i;
+    return hsh;
+}
+
+/* number of occupied spin orbitals strictly between k and l */
+static int occ_between(const oq_t *q, const uint64_t *d, int k, int l)
+{
+    int lo = k < l ? k : l, hi = k < l ? l : k, c = 0;
+    for (int m = lo + 1; m < hi; ++m) c += det_bit(q, d, m);
+    return c;
+}
+
+/* ---------------- Slater-Condon rules (Sec. II) ---------------- */
+/* Diagonal: sum_p h_pp + sum_{p<q} [(pp|qq) - delta_spin (pq|qp)], ascending order. */
+double oq_hdiag(const oq_t *q, const uint64_t *d)
+{
+    int occ[OQ_MAXSO];
+    int n = decode(q, d, occ);
+    double v = 0.0;
+    for (int x = 0; x < n; ++x) v = v + h1(q, spat_of(occ[x]), spat_of(occ[x]));
+    for (int x = 0; x < n; ++x) {
+        for (int y = x + 1; y < n; ++y) {
+            int p = spat_of(occ[x]), r = spat_of(occ[y]);
+            v = v + eri4(q, p, p, r, r);
+            if (spin_of(occ[x]) == spin_of(occ[y])) v = v - eri4(q, p, r, r, p);
+        }
+    }
+    return v;
+}
+
+/* Single i -> a from source d: sign * [h_ia + sum_{j occ, j != i} ((ia|jj) - delta (ij|ja))]. */
+static double hij_single(const oq_t *q, const uint64_t *d, int i, int a)
+{
+    int occ[OQ_MAXSO];
+    int n = decode(q, d, occ);
+    int I = spat_of(i), A = spat_of(a);
+    double v = h1(q, I, A);
+    for (int x = 0; x < n; ++x) {
+        int j = occ[x];
+        if (j == i) continue;
+        int J = spat_of(j);
+        v = v + eri4(q, I, A, J, J);
+        if (spin_of(j) == spin_of(i)) v = v - eri4(q, I, J, J, A);
+    }
+    int par = occ_between(q, d, i, a) & 1;
+    return par ? -v : v;
+}
+
+/* Double (i<j) -> (a<b) from source d. */
+static double hij_double(const oq_t *q, const uint64_t *d, int i, int j, int a, int b)
+{
+    double v = 0.0;
+    if (spin_of(i) == spin_of(a) && spin_of(j) == spin_of(b))
+        v = v + eri4(q, spat_of(i), spat_of(a), spat_of(j), spat_of(b));
+    if (spin_of(i) == spin_of(b) && spin_of(j) == spin_of(a))
+        v = v - eri4(q, spat_of(i), spat_of(b), spat_of(j), spat_of(a));
+    uint64_t t[OQ_MAXW];
+    memcpy(t, d, sizeof(uint64_t) * q->W);
+    int par = occ_between(q, t, i, a);
+    det_flip(t, i);
+    det_flip(t, a);
+    par += occ_between(q, t, j, b);
+    return (par & 1) ? -v : v;
+}
+
+/* Canonical matrix element <dst|H|src> evaluated from the source side (0 beyond doubles).
+ * The diagonal case returns H_ii without e_core. */
+double oq_hij(const oq_t *q, const uint64_t *src, const uint64_t *dst)
+{
+    int nd = 0;
+    for (int w = 0; w < q->W; ++w) nd += __builtin_popcountll(src[w] ^ dst[w]);
+    if (nd == 0) return oq_hdiag(q, src);
+    if (nd != 2 && nd != 4) return 0.0;
+    int holes[2], parts[2], nh = 0, np = 0;
+    for (int k = 0; k < q->n_so; ++k) {
+        int s = det_bit(q, src, k), t = det_bit(q, dst, k);
+        if (s && !t) holes[nh++] = k;
+        if (!s && t) parts[np++] = k;
+    }
+    if (nd == 2) return hij_single(q, src, holes[0], parts[0]);
+    return hij_double(q, src, holes[0], holes[1], parts[0], parts[1]);
+}
+
+/* ---------------- excitation generator (Sec. VI) ---------------- */
+static void unocc_counts(const oq_t *q, const uint64_t *d, int *cnt)
+{
+    for (int c = 0; c < 16; ++c) cnt[c] = 0;
+    for (int k = 0; k < q->n_so; ++k) if (!det_bit(q, d, k)) cnt[class_of(q, k)]++;
+}
+
+/* Outcome of one excitation with explicit rank choices.
+ * info[0] = kind (0 null, 1 single, 2 double)
+ * info[1..3] = number of options at stage 1 (|E_ok| or N(N-1)/2), stage 2 (M_allow or
+ *              M^a - delta_d, for the stage-1 choice) and stage 3 (M^(b|a), doubles)
+ * info[4], info[5] = P_gen / P_type as the rational num/den
+ * info[6..9] = orbitals i, j, a, b (j, b = -1 for singles; a < b for doubles). */
+int oq_excite_ranks(const oq_t *q, const uint64_t *d, int type, uint64_t k1, uint64_t k2, uint64_t k3,
+                    uint64_t *child, int64_t *info)
+{
+    int occ[OQ_MAXSO], cnt[16];
+    int n = decode(q, d, occ);
+    unocc_counts(q, d, cnt);
+    for (int x = 0; x < 10; ++x) info[x] = 0;
+    info[6] = info[7] = info[8] = info[9] = -1;
+    memcpy(child, d, sizeof(uint64_t) * q->W);
+    if (type == 1) {
+        /* Sec. VI A: electrons with no symmetry-allowed a are removed from the choice
+         * (delta_s renormalisation); i uniform over the rest, a uniform over M_allow. */
+        int eok[OQ_MAXSO], nok = 0;
+        for (int x = 0; x < n; ++x) if (cnt[class_of(q, occ[x])] > 0) eok[nok++] = occ[x];
+        info[1] = nok;
+        if (nok == 0 || k1 >= (uint64_t)nok) return 0;
+        int i = eok[k1];
+        int c = class_of(q, i);
+        int mallow = cnt[c];
+        info[2] = mallow;
+        int seen = 0, a = -1;
+        for (int k = 0; k < q->n_so; ++k) {
+            if (!det_bit(q, d, k) && class_of(q, k) == c) {
+                if ((uint64_t)seen == k2) { a = k; break; }
+                seen++;
+            }
+        }
+        if (a < 0) return 0;
+        det_flip(child, i);
+        det_flip(child, a);
+        info[0] = 1;
+        info[4] = 1;
+        info[5] = (int64_t)mallow * (int64_t)nok;   /* M_allow (N - delta_s) */
+        info[6] = i; info[8] = a;
+        return 1;
+    }
+    /* Sec. VI B: unique pair {i,j} by inverse triangular index k = j(j-1)/2 + i. */
+    int64_t npairs = (int64_t)n * (n - 1) / 2;
+    info[1] = npairs;
+    if (npairs == 0 || k1 >= (uint64_t)npairs) return 0;
+    int ej = 1;
+    while ((int64_t)ej * (ej + 1) / 2 <= (int64_t)k1) ej++;
+    int ei = (int)((int64_t)k1 - (int64_t)ej * (ej - 1) / 2);
+    int i = occ[ei], j = occ[ej];
+    int si = spin_of(i), sj = spin_of(j);
+    int gij = q->irrep[spat_of(i)] ^ q->irrep[spat_of(j)];
+    /* a must carry an allowed spin and leave at least one symmetry/spin-allowed b */
+    int good[OQ_MAXSO], ngood = 0;
+    for (int k = 0; k < q->n_so; ++k) {
+        if (det_bit(q, d, k)) continue;
+        int sa = spin_of(k);
+        if (si == sj && sa != si) continue;
+        int ca = class_of(q, k);
+        int cb = class_make(gij ^ q->irrep[spat_of(k)], si + sj - sa);
+        int avail = cnt[cb] - (cb == ca ? 1 : 0);
+        if (avail >= 1) good[ngood++] = k;
+    }
+    info[2] = ngood;
+    if (ngood == 0 || k2 >= (uint64_t)ngood) return 0;
+    int a = good[k2];
+    int ca = class_of(q, a);
+    int cb = class_make(gij ^ q->irrep[spat_of(a)], si + sj - spin_of(a));
+    int cand[OQ_MAXSO], ncand = 0;
+    for (int k = 0; k < q->n_so; ++k)
+        if (!det_bit(q, d, k) && k != a && class_of(q, k) == cb) cand[ncand++] = k;
+    info[3] = ncand;
+    if (ncand == 0 || k3 >= (uint64_t)ncand) return 0;
+    int b = cand[k3];
+    int64_t m_ba = ncand;
+    int64_t m_ab = cnt[ca] - (ca == cb ? 1 : 0);
+    det_flip(child, i); det_flip(child, j); det_flip(child, a); det_flip(child, b);
+    info[0] = 2;
+    info[4] = m_ba + m_ab;
+    info[5] = npairs * (int64_t)ngood * m_ba * m_ab;
+    info[6] = i; info[7] = j;
+    info[8] = a < b ? a : b;
+    info[9] = a < b ? b : a;
+    return 2;
+}
+
+/* ---------------- setup ---------------- */
+static void count_ref_excitations(oq_t *q)
+{
+    int occ[OQ_MAXSO];
+    int n = decode(q, q->ref, occ);
+    int64_t ns = 0, ndb = 0;
+    for (int x = 0; x < n; ++x)
+        for (int a = 0; a < q->n_so; ++a)
+            if (!det_bit(q, q->ref, a) && class_of(q, a) == class_of(q, occ[x])) ns++;
+    for (int x = 0; x < n; ++x)
+        for (int y = x + 1; y < n; ++y) {
+            int i = occ[x], j = occ[y];
+            int gij = q->irrep[spat_of(i)] ^ q->irrep[spat_of(j)];
+            for (int a = 0; a < q->n_so; ++a) {
+                if (det_bit(q, q->ref, a)) continue;
+                for (int b = a + 1; b < q->n_so; ++b) {
+                    if (det_bit(q, q->ref, b)) continue;
+                    if (spin_of(a) + spin_of(b) != spin_of(i) + spin_of(j)) continue;
+                    if ((q->irrep[spat_of(a)] ^ q->irrep[spat_of(b)]) != gij) continue;
+                    ndb++;
+                }
+            }
+        }
+    q->n_single_ref = ns;
+    q->n_double_ref = ndb;
+}
+
+void oq_destroy(oq_t *q)
+{
+    if (!q) return;
+    free(q->h); free(q->eri); free(q->det); free(q->pop); free(q->hd);
+    free(q);
+}
+
+static int ensure_cap(oq_t *q, int64_t need)
+{
+    if (need <= q->cap) return 0;
+    int64_t nc = q->cap ? q->cap : 1024;
+    while (nc < need) nc *= 2;
+    uint64_t *d = realloc(q->det, sizeof(uint64_t) * q->W * nc);
+    if (!d) return -1;
+    q->det = d;
+    int32_t *p = realloc(q->pop, sizeof(int32_t) * nc);
+    if (!p) return -1;
+    q->pop = p;
+    double *hd = realloc(q->hd, sizeof(double) * nc);
+    if (!hd) return -1;
+    q->hd = hd;
+    q->cap = nc;
+    return 0;
+}
+
+oq_t *oq_create(const double *h, const double *eri_s8, double e_core, int n_elec, int n_orb, int ms2,
+                const int32_t *orb_irrep, double tau, int32_t initiator_threshold, int64_t target_walkers,
+                double shift_damping, int32_t shift_period, double initial_shift, int32_t initial_population,
+                uint64_t seed, double p_double_override, const uint64_t *reference)
+{
+    if (n_orb < 1 || 2 * n_orb > OQ_MAXSO || n_elec < 1 || n_elec >= 2 * n_orb) return NULL;
+    if ((n_elec + ms2) % 2 != 0 || ms2 < -n_elec || ms2 > n_elec) return NULL;
+    oq_t *q = calloc(1, sizeof(oq_t));
+    if (!q) return NULL;
+    q->n_orb = n_orb; q->n_elec = n_elec; q->n_so = 2 * n_orb; q->W = (2 * n_orb + 63) / 64;
+    q->n_alpha = (n_elec + ms2) / 2; q->n_beta = (n_elec - ms2) / 2;
+    if (q->n_alpha > n_orb || q->n_beta > n_orb) { free(q); return NULL; }
+    q->npair_sp = (int64_t)n_orb * (n_orb + 1) / 2;
+    int64_t neri = q->npair_sp * (q->npair_sp + 1) / 2;
+    q->h = malloc(sizeof(double) * n_orb * n_orb);
+    q->eri = malloc(sizeof(double) * neri);
+    memcpy(q->h, h, sizeof(double) * n_orb * n_orb);
+    memcpy(q->eri, eri_s8, sizeof(double) * neri);
+    q->e_core = e_core;
+    q->has_sym = orb_irrep != NULL;
+    for (int p = 0; p < n_orb; ++p) {
+        q->irrep[p] = orb_irrep ? orb_irrep[p] : 0;
+        if (q->irrep[p] < 0 || q->irrep[p] > 7) { oq_destroy(q); return NULL; }
+    }
+    if (reference) {
+        memcpy(q->ref, reference, sizeof(uint64_t) * q->W);
+    } else {
+        memset(q->ref, 0, sizeof(q->ref));
+        for (int p = 0; p < q->n_alpha; ++p) det_flip(q->ref, 2 * p);
+        for (int p = 0; p < q->n_beta; ++p) det_flip(q->ref, 2 * p + 1);
+    }
+    q->tau = tau; q->init_thr = initiator_threshold; q->target = target_walkers;
+    q->zeta = shift_damping; q->period = shift_period;
+    q->c_shift = shift_damping / ((double)shift_period * tau);
+    q->seed = (uint32_t)seed;
+    /* orbital map for Algorithm 1: Philox with key ("FCIQ", "MAP1"), counter (k, 0, 0, 0) */
+    for (int k = 0; k < q->n_so; ++k) {
+        uint32_t ctr[4] = {(uint32_t)k, 0u, 0u, 0u}, key[2] = {0x46434951u, 0x4D415031u}, o[4];
+        oq_philox(ctr, key, o);
+        q->map1[k] = (uint64_t)o[0] | ((uint64_t)o[1] << 32);
+    }
+    q->E0 = oq_hdiag(q, q->ref);
+    count_ref_excitations(q);
+    double pd = p_double_override > 0.0 ? p_double_override
+              : (double)q->n_double_ref / (double)(q->n_single_ref + q->n_double_ref);
+    if (pd > 1.0) pd = 1.0;
+    q->d53 = (uint64_t)(pd * 0x1.0p53);
+    q->p_double = (double)q->d53 * 0x1.0p-53;
+    q->p_single = 1.0 - q->p_double;
+    q->cs = tau / q->p_single;
+    q->cd = tau / q->p_double;
+    q->shift = initial_shift;
+    if (ensure_cap(q, 1024)) { oq_destroy(q); return NULL; }
+    q->n = 1;
+    memcpy(q->det, q->ref, sizeof(uint64_t) * q->W);
+    q->pop[0] = initial_population;
+    q->hd[0] = 0.0;
+    return q;
+}
+
+/* ---------------- one spawning attempt and death (Eqs. 3, 4) ---------------- */
+typedef struct {
+    spawn_t *s;
+    int64_t n, cap;
+    int64_t nulls, events, walkers;
+    int err;
+    char pad[128];   /* keeps per-thread buffers on separate cache lines */
+} sbuf_t;
+
+static void sbuf_push(sbuf_t *b, int W, const uint64_t *d, int64_t amt, int flag)
+{
+    if (b->n == b->cap) {
+        int64_t nc = b->cap ? 2 * b->cap : 1024;
+        spawn_t *ns = realloc(b->s, sizeof(spawn_t) * nc);
+        if (!ns) { b->err = 1; return; }
+        b->s = ns; b->cap = nc;
+    }
+    memset(&b->s[b->n], 0, sizeof(spawn_t));
+    memcpy(b->s[b->n].d, d, sizeof(uint64_t) * W);
+    b->s[b->n].amt = amt;
+    b->s[b->n].flag = flag;
+    b->n++;
+}
+
+/* One spawning attempt a on determinant d (population c, fingerprint fp).
+ * Returns the signed number of walkers spawned onto *child (0: none); *is_null = 1 when the
+ * excitation generator returned a null excitation. Sets *err on a population overflow. */
+static int64_t attempt_one(const oq_t *q, const uint64_t *d, int32_t c, uint64_t fp, uint32_t a,
+                           uint64_t *child, int *is_null, int *err)
+{
+    uint64_t r0, r1, r2, r3, r4, r5;
+    *is_null = 0;
+    draw2(a, 0u, fp, q->seed, q->iter, &r0, &r1);
+    draw2(a, 1u, fp, q->seed, q->iter, &r2, &r3);
+    int type = (r0 >> 11) < q->d53 ? 2 : 1;
+    int64_t info[10];
+    /* stage option counts depend on the earlier choices, so the generator is queried stage by stage */
+    oq_excite_ranks(q, d, type, 0, 0, 0, child, info);
+    if (info[1] == 0) { *is_null = 1; return 0; }
+    uint64_t k1 = rank_of(r1, (uint64_t)info[1]);
+    oq_excite_ranks(q, d, type, k1, 0, 0, child, info);
+    if (info[2] == 0) { *is_null = 1; return 0; }
+    uint64_t k2 = rank_of(r2, (uint64_t)info[2]);
+    uint64_t k3 = 0;
+    if (type == 2) {
+        oq_excite_ranks(q, d, type, k1, k2, 0, child, info);
+        if (info[3] == 0) { *is_null = 1; return 0; }
+        k3 = rank_of(r3, (uint64_t)info[3]);
+    }
+    int kind = oq_excite_ranks(q, d, type, k1, k2, k3, child, info);
+    if (kind == 0) { *is_null = 1; return 0; }
+    double hv = kind == 1 ? hij_single(q, d, (int)info[6], (int)info[8])
+                          : hij_double(q, d, (int)info[6], (int)info[7], (int)info[8], (int)info[9]);
+    if (hv == 0.0) return 0;
+    /* p = tau |H| / P_gen (Eq. 3), evaluated in the fixed order
+     *   single: (|H| * (tau/P_single)) * (M_allow (N - delta_s))
+     *   double: ((|H| * (tau/P_double)) * (npairs G M^(b|a) M^(a|b))) * (1 / (M^(b|a) + M^(a|b))) */
+    double p;
+    if (kind == 1) p = (fabs(hv) * q->cs) * (double)info[5];
+    else p = ((fabs(hv) * q->cd) * (double)info[5]) * (1.0 / (double)info[4]);
+    draw2(a, 2u, fp, q->seed, q->iter, &r4, &r5);
+    double fl = floor(p);
+    if (fl >= 2147483647.0) { *err = 1; return 0; }
+    int64_t nsp = (int64_t)fl + (unit53(r4) < p - fl ? 1 : 0);
+    if (nsp == 0) return 0;
+    int sgn_c = c > 0 ? 1 : -1, sgn_h = hv > 0.0 ? 1 : -1;
+    return -(int64_t)sgn_c * sgn_h * nsp;
+}
+
+static void spawn_from(const oq_t *q, const uint64_t *d, int32_t c, uint64_t fp, int flag, sbuf_t *b)
+{
+    uint32_t na = (uint32_t)(c < 0 ? -(int64_t)c : c);
+    for (uint32_t a = 0; a < na; ++a) {
+        uint64_t child[OQ_MAXW];
+        int is_null = 0;
+        int64_t amt = attempt_one(q, d, c, fp, a, child, &is_null, &b->err);
+        if (is_null) b->nulls++;
+        if (amt == 0) continue;
+        sbuf_push(b, q->W, child, amt, flag);
+        b->events++;
+        b->walkers += amt < 0 ? -amt : amt;
+    }
+}
+
+static int cmp_spawn_w1(const void *x, const void *y)
+{
+    const spawn_t *a = x, *b = y;
+    return det_cmp(1, a->d, b->d);
+}
+static int cmp_spawn_w2(const void *x, const void *y)
+{
+    const spawn_t *a = x, *b = y;
+    return det_cmp(2, a->d, b->d);
+}
+
+/* estimators of the current list: N_w, N_d, C_0 and sum_{i != 0} H_0i C_i (ascending det order) */
+void oq_estimate(const oq_t *q, int64_t *nw, int64_t *nd, int64_t *c0, double *num)
+{
+    int64_t w = 0, dd = 0, cz = 0;
+    double s = 0.0;
+    for (int64_t x = 0; x < q->n; ++x) {
+        const uint64_t *d = q->det + x * q->W;
+        int32_t c = q->pop[x];
+        if (c == 0) continue;
+        w += c < 0 ? -(int64_t)c : c;
+        dd++;
+        if (det_eq(q, d, q->ref)) { cz = c; continue; }
+        int nx = 0;
+        for (int k = 0; k < q->W; ++k) nx += __builtin_popcountll(d[k] ^ q->ref[k]);
+        if (nx == 2 || nx == 4) s = s + oq_hij(q, q->ref, d) * (double)c;
+    }
+    *nw = w; *nd = dd; *c0 = cz; *num = s;
+}
+
+int oq_iterate(oq_t *q, int n_iter, oq_row *rows)
+{
+    const int W = q->W;
+    for (int it = 0; it < n_iter; ++it) {
+        oq_row *row = &rows[it];
+        memset(row, 0, sizeof(*row));
+        row->iter = q->iter;
+        row->shift = q->shift;
+        oq_estimate(q, &row->nw_in, &row->nd_in, &row->c0_in, &row->num_in);
+        row->attempts = row->nw_in;
+
+        /* spawning from start-of-iteration populations (thread-local buffers, merged by sorting) */
+        int nthreads = 1;
+#ifdef _OPENMP
+        nthreads = omp_get_max_threads();
+#endif
+        sbuf_t *bufs = calloc((size_t)nthreads, sizeof(sbuf_t));
+        int32_t *newpop = malloc(sizeof(int32_t) * (q->n ? q->n : 1));
+        int64_t death_w = 0, clone_w = 0;
+        int numeric = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : death_w, clone_w) reduction(| : numeric)
+        for (int64_t x = 0; x < q->n; ++x) {
+            int tid = 0;
+#ifdef _OPENMP
+            tid = omp_get_thread_num();
+#endif
+            const uint64_t *d = q->det + x * W;
+            int32_t c = q->pop[x];
+            newpop[x] = c;
+            if (c == 0) continue;
+            uint64_t fp = oq_fingerprint(q, d);
+            int64_t ac = c < 0 ? -(int64_t)c : c;
+            int flag = q->init_thr < 0 || ac > q->init_thr || det_eq(q, d, q->ref);
+            spawn_from(q, d, c, fp, flag, &bufs[tid]);
+            /* death / cloning, Eq. 4: r = tau (H_ii - E0 - S) |C_i| */
+            double r = (q->tau * (q->hd[x] - q->shift)) * (double)ac;
+            double ar = fabs(r);
+            double fl = floor(ar);
+            if (fl >= 2147483647.0) { numeric = 1; continue; }
+            uint64_t u, unused;
+            draw2(0u, 3u, fp, q->seed, q->iter, &u, &unused);
+            int64_t nd = (int64_t)fl + (unit53(u) < ar - fl ? 1 : 0);
+            int64_t sc = c > 0 ? 1 : -1;
+            int64_t nc;
+            if (r >= 0.0) { nc = (int64_t)c - sc * nd; death_w += nd; }
+            else { nc = (int64_t)c + sc * nd; clone_w += nd; }
+            if (nc > 2147483647LL || nc < -2147483647LL) { numeric = 1; continue; }
+            newpop[x] = (int32_t)nc;
+        }
+        /* concatenate, sort and compress the spawned list (Sec. V A) */
+        int64_t ns = 0;
+        for (int t = 0; t < nthreads; ++t) {
+            ns += bufs[t].n;
+            row->nulls += bufs[t].nulls;
+            row->spawn_events += bufs[t].events;
+            row->spawned_walkers += bufs[t].walkers;
+            if (bufs[t].err) numeric = 1;
+        }
+        spawn_t *sp = malloc(sizeof(spawn_t) * (ns ? ns : 1));
+        int64_t off = 0;
+        for (int t = 0; t < nthreads; ++t) {
+            if (bufs[t].n) memcpy(sp + off, bufs[t].s, sizeof(spawn_t) * bufs[t].n);
+            off += bufs[t].n;
+            free(bufs[t].s);
+        }
+        free(bufs);
+        qsort(sp, (size_t)ns, sizeof(spawn_t), W == 1 ? cmp_spawn_w1 : cmp_spawn_w2);
+        int64_t nm = 0;
+        for (int64_t x = 0; x < ns; ) {
+            int64_t y = x;
+            spawn_t m = sp[x];
+            for (y = x + 1; y < ns && det_cmp(W, sp[y].d, m.d) == 0; ++y) {
+                m.amt += sp[y].amt;
+                m.flag |= sp[y].flag;
+            }
+            sp[nm++] = m;
+            x = y;
+        }
+        row->death_walkers = death_w;
+        row->clone_walkers = clone_w;
+        row->merged_entries = nm;
+        /* annihilation: merge the sorted merged list into the sorted post-death list */
+        int64_t cap_new = q->n + nm;
+        uint64_t *nd_det = malloc(sizeof(uint64_t) * W * (cap_new ? cap_new : 1));
+        int32_t *nd_pop = malloc(sizeof(int32_t) * (cap_new ? cap_new : 1));
+        double *nd_hd = malloc(sizeof(double) * (cap_new ? cap_new : 1));
+        int64_t a = 0, bidx = 0, out = 0;
+        while (a < q->n || bidx < nm) {
+            int take;  /* 0: main only, 1: spawn only, 2: both */
+            if (a >= q->n) take = 1;
+            else if (bidx >= nm) take = 0;
+            else {
+                int cmp = det_cmp(W, q->det + a * W, sp[bidx].d);
+                take = cmp < 0 ? 0 : (cmp > 0 ? 1 : 2);
+            }
+            if (take == 0) {
+                if (newpop[a] != 0) {
+                    memcpy(nd_det + out * W, q->det + a * W, sizeof(uint64_t) * W);
+                    nd_pop[out] = newpop[a];
+                    nd_hd[out] = q->hd[a];
+                    out++;
+                }
+                a++;
+            } else {
+                const spawn_t *m = &sp[bidx];
+                int occupied = take == 2 && newpop[a] != 0;
+                if (occupied) {
+                    int64_t v = (int64_t)newpop[a] + m->amt;
+                    if (v > 2147483647LL || v < -2147483647LL) numeric = 1;
+                    if (v != 0) {
+                        memcpy(nd_det + out * W, q->det + a * W, sizeof(uint64_t) * W);
+                        nd_pop[out] = (int32_t)v;
+                        nd_hd[out] = q->hd[a];
+                        out++;
+                    }
+                } else if (m->amt != 0) {
+                    if (q->init_thr < 0 || m->flag) {
+                        if (m->amt > 2147483647LL || m->amt < -2147483647LL) numeric = 1;
+                        memcpy(nd_det + out * W, m->d, sizeof(uint64_t) * W);
+                        nd_pop[out] = (int32_t)m->amt;
+                        nd_hd[out] = oq_hdiag(q, m->d) - q->E0;
+                        out++;
+                        row->inserted_dets++;
+                    } else {
+                        row->aborted_walkers += m->amt < 0 ? -m->amt : m->amt;
+                    }
+                }
+                if (take == 2) a++;
+                bidx++;
+            }
+        }
+        free(sp);
+        free(newpop);
+        free(q->det); free(q->pop); free(q->hd);
+        q->det = nd_det; q->pop = nd_pop; q->hd = nd_hd;
+        q->n = out; q->cap = cap_new ? cap_new : 1;
+        if (numeric) q->error = 1;
+
+        int64_t nw_out = 0;
+        for (int64_t x = 0; x < q->n; ++x) nw_out += q->pop[x] < 0 ? -(int64_t)q->pop[x] : q->pop[x];
+        row->nw_out = nw_out;
+        row->nd_out = q->n;
+        /* shift update (reading stated in the header) */
+        if (!q->vary) {
+            if (nw_out >= q->target) { q->vary = 1; q->nw_prev = nw_out; q->n_since = 0; }
+        } else {
+            q->n_since++;
+            if (q->n_since == q->period) {
+                double ratio = (double)nw_out / (double)q->nw_prev;
+                q->shift = q->shift - q->c_shift * oq_log(ratio);
+                q->nw_prev = nw_out;
+                q->n_since = 0;
+            }
+        }
+        q->iter++;
+        if (q->error) return -1;
+    }
+    return 0;
+}
+
+/* ---------------- accessors ---------------- */
+int64_t oq_n_dets(const oq_t *q) { return q->n; }
+int oq_words(const oq_t *q) { return q->W; }
+void oq_get_walkers(const oq_t *q, uint64_t *dets, int32_t *pops, double *hd)
+{
+    memcpy(dets, q->det, sizeof(uint64_t) * q->W * q->n);
+    memcpy(pops, q->pop, sizeof(int32_t) * q->n);
+    if (hd) memcpy(hd, q->hd, sizeof(double) * q->n);
+}
+static const uint64_t *g_sort_base;
+static int g_sort_w;
+static int cmp_index(const void *x, const void *y)
+{
+    int64_t a = *(const int64_t *)x, b = *(const int64_t *)y;
+    return det_cmp(g_sort_w, g_sort_base + a * g_sort_w, g_sort_base + b * g_sort_w);
+}
+/* Replace the walker list (any order, nonzero populations, distinct determinants) and the
+ * dynamic state. H_ii is recomputed. Returns -1 on duplicates. */
+int oq_set_walkers(oq_t *q, const uint64_t *dets, const int32_t *pops, int64_t n, uint32_t iter,
+                   double shift, int vary, int64_t nw_prev, int n_since)
+{
+    int64_t *idx = malloc(sizeof(int64_t) * (n ? n : 1));
+    for (int64_t x = 0; x < n; ++x) idx[x] = x;
+    g_sort_base = dets; g_sort_w = q->W;
+    qsort(idx, (size_t)n, sizeof(int64_t), cmp_index);
+    free(q->det); free(q->pop); free(q->hd);
+    q->det = NULL; q->pop = NULL; q->hd = NULL; q->cap = 0;
+    if (ensure_cap(q, n ? n : 1)) { free(idx); return -2; }
+    int64_t m = 0;
+    for (int64_t x = 0; x < n; ++x) {
+        const uint64_t *d = dets + idx[x] * q->W;
+        if (pops[idx[x]] == 0) continue;
+        if (m > 0 && det_cmp(q->W, q->det + (m - 1) * q->W, d) == 0) { free(idx); return -1; }
+        memcpy(q->det + m * q->W, d, sizeof(uint64_t) * q->W);
+        q->pop[m] = pops[idx[x]];
+        q->hd[m] = oq_hdiag(q, d) - q->E0;
+        m++;
+    }
+    free(idx);
+    q->n = m;
+    q->iter = iter; q->shift = shift; q->vary = vary; q->nw_prev = nw_prev; q->n_since = n_since;
+    return 0;
+}
+void oq_get_state(const oq_t *q, int64_t *iter, double *shift, int64_t *vary, int64_t *nw_prev, int64_t *n_since)
+{
+    *iter = q->iter; *shift = q->shift; *vary = q->vary; *nw_prev = q->nw_prev; *n_since = q->n_since;
+}
+/* scalar facts of the system: E0, P_double, n_single_ref, n_double_ref, d53 */
+void oq_info(const oq_t *q, double *e0, double *pdouble, int64_t *ns, int64_t *nd, uint64_t *d53, uint64_t *ref)
+{
+    *e0 = q->E0; *pdouble = q->p_double; *ns = q->n_single_ref; *nd = q->n_double_ref; *d53 = q->d53;
+    memcpy(ref, q->ref, sizeof(uint64_t) * q->W);
+}
+/* map1 table of the fingerprint */
+void oq_map1(const oq_t *q, uint64_t *out) { memcpy(out, q->map1, sizeof(uint64_t) * q->n_so); }
+
+/* H over an explicit determinant list: out[x*n+y] = <dets[y]|H|dets[x]> from source x (no e_core). */
+void oq_hmatrix(const oq_t *q, const uint64_t *dets, int64_t n, double *out)
+{
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t x = 0; x < n; ++x)
+        for (int64_t y = 0; y < n; ++y)
+            out[x * n + y] = oq_hij(q, dets + x * q->W, dets + y * q->W);
+}
+
+/* One full spawn attempt with the random-number contract, for tests: returns the signed
+ * number of walkers spawned onto *child by attempt a of determinant d with population c
+ * at the current iteration (0 when none; *is_null = 1 for a null excitation). */
+int64_t oq_attempt(const oq_t *q, const uint64_t *d, int32_t c, uint32_t a, uint64_t *child, int *is_null)
+{
+    int err = 0;
+    uint64_t fp = oq_fingerprint(q, d);
+    memcpy(child, d, sizeof(uint64_t) * q->W);
+    return attempt_one(q, d, c, fp, a, child, is_null, &err);
+}

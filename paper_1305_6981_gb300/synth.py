@@ -1,0 +1,178 @@
+"""Seeded synthetic inputs for the FCIQMC walker cycle.
+
+This module only draws inputs: one- and two-electron integral tables, orbital
+symmetry labels and the multi-system batches built from them. It holds none of
+the method's arithmetic (no matrix elements, excitations or walker dynamics),
+so both the CUDA path and the CPU oracle may take their inputs from it.
+
+The paper's own molecules (Be2 cc-pVQZ, Cr2 SV basis; Sec. VI-VII) need
+quantum-chemistry integral files that are not available, so the integrals are
+synthetic real tables with the shapes, permutational symmetry (8-fold, Sec. II
+footnote on double-triangular packing) and abelian point-group structure
+(Sec. II, XOR product of D2h-like irreps) of those workloads:
+
+* orbital energies e_p (optionally with a near-degenerate frontier window),
+  read as the diagonal Fock energies of the aufbau reference (n_elec/2 lowest
+  spatial orbitals doubly occupied), which is what "orbital energy" means in
+  the Hartree-Fock picture the paper's reference determinant comes from:
+  h_pp = e_p - sum_{j occ} [2 (pp|jj) - (pj|jp)], so f_pp = e_p,
+* h_pq = (the diagonal above) + sym(N(0, sigma_h) exp(-|p-q|/2)),
+* (pq|rs) = sum_k L^k_pq L^k_rs with L^k symmetric, which makes the ERI
+  tensor 8-fold symmetric and positive semidefinite.
+
+With symmetry labels Gamma_p, h_pq is zero unless Gamma_p == Gamma_q and
+Cholesky vector k carries irrep k mod 8 (L^k_pq = 0 unless
+Gamma_p ^ Gamma_q == k mod 8), so (pq|rs) vanishes unless
+Gamma_p ^ Gamma_q == Gamma_r ^ Gamma_s.
+"""
+from __future__ import annotations
+
+import dataclasses
+import hashlib
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class System:
+    """A synthetic Hamiltonian in the layout the C ABI takes."""
+    n_orb: int
+    n_elec: int
+    h: np.ndarray            # (n_orb, n_orb) float64, symmetric, row-major
+    eri_s8: np.ndarray       # packed (pq|rs), length npair*(npair+1)/2
+    irrep: np.ndarray | None  # (n_orb,) int32 labels 0..7, or None (no symmetry)
+    e_core: float = 0.0
+    name: str = ""
+
+    @property
+    def npair(self) -> int:
+        return self.n_orb * (self.n_orb + 1) // 2
+
+    def digest(self) -> str:
+        m = hashlib.sha256()
+        m.update(self.h.tobytes())
+        m.update(self.eri_s8.tobytes())
+        if self.irrep is not None:
+            m.update(self.irrep.tobytes())
+        return m.hexdigest()[:16]
+
+
+def pack_pairs(n_orb: int) -> tuple[np.ndarray, np.ndarray]:
+    """Lists (p, q) with p >= q in packed order pq = p(p+1)/2 + q."""
+    ps, qs = [], []
+    for p in range(n_orb):
+        for q in range(p + 1):
+            ps.append(p)
+            qs.append(q)
+    return np.array(ps), np.array(qs)
+
+
+def _sym(x: np.ndarray) -> np.ndarray:
+    return 0.5 * (x + x.T)
+
+
+def make_system(n_orb: int, n_elec: int, *, seed: int, n_chol: int,
+                symmetry: bool = False, sigma_h: float = 0.1,
+                chol_amp: float = 0.3, chol_decay_len: float = 1.0,
+                chol_k_decay: float | None = None,
+                energies: np.ndarray | None = None, fock_diagonal: bool = True,
+                name: str = "") -> System:
+    """Draw h and packed ERIs from Generator(PCG64(seed)).
+
+    chol_decay_len: L^k_pq ~ N(0, chol_amp) exp(-|p-q| / chol_decay_len).
+    chol_k_decay:   optional extra factor exp(-k / chol_k_decay) per vector.
+    energies:       orbital energies e_p (default -2 + 0.5 p).
+    fock_diagonal:  shift h_pp so that the aufbau reference's diagonal Fock energies are e_p.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    p = np.arange(n_orb)
+    dist = np.abs(p[:, None] - p[None, :])
+    e = (-2.0 + 0.5 * p) if energies is None else np.asarray(energies, dtype=np.float64)
+    irrep = (p % 8).astype(np.int32) if symmetry else None
+
+    noise = _sym(rng.normal(0.0, sigma_h, size=(n_orb, n_orb)) * np.exp(-dist / 2.0))
+    h = np.diag(e) + noise
+    if irrep is not None:
+        h = h * (irrep[:, None] == irrep[None, :])
+    h = _sym(h)  # exact symmetry
+
+    ps, qs = pack_pairs(n_orb)
+    lp = np.zeros((n_chol, len(ps)))
+    for k in range(n_chol):
+        x = _sym(rng.normal(0.0, chol_amp, size=(n_orb, n_orb))) * np.exp(-dist / chol_decay_len)
+        if chol_k_decay is not None:
+            x = x * np.exp(-k / chol_k_decay)
+        if irrep is not None:
+            x = x * ((irrep[:, None] ^ irrep[None, :]) == (k % 8))
+        lp[k] = x[ps, qs]
+    v = lp.T @ lp                      # (npair, npair), symmetric PSD
+    iu = np.tril_indices(len(ps))      # row >= col: packed index pq(pq+1)/2 + rs
+    eri = np.ascontiguousarray(v[iu])
+    if fock_diagonal:
+        def pidx(a, b):
+            return max(a, b) * (max(a, b) + 1) // 2 + min(a, b)
+        n_occ = n_elec // 2
+        for q in range(n_orb):
+            mf = 0.0
+            for j in range(n_occ):
+                mf += 2.0 * v[pidx(q, q), pidx(j, j)] - v[pidx(q, j), pidx(q, j)]
+            h[q, q] -= mf
+    return System(n_orb=n_orb, n_elec=n_elec, h=np.ascontiguousarray(h), eri_s8=eri,
+                  irrep=irrep, name=name)
+
+
+def frontier_energies(n_orb: int, lo: int = 8, hi: int = 15, gap: float = 0.05) -> np.ndarray:
+    """Orbital energies -2 + 0.5 p with a near-degenerate window [lo, hi] of spacing `gap`."""
+    e = np.empty(n_orb)
+    for p in range(n_orb):
+        if p < lo:
+            e[p] = -2.0 + 0.5 * p
+        elif p <= hi:
+            e[p] = (-2.0 + 0.5 * lo) + gap * (p - lo)
+        else:
+            e[p] = (-2.0 + 0.5 * lo) + gap * (hi - lo) + 0.5 * (p - hi)
+    return e
+
+
+# Workloads with the shapes of the five benchmark configurations.
+
+def tiny_8e8o() -> System:
+    """8 electrons in 8 spatial orbitals, no symmetry, 16 Cholesky vectors (Hilbert dim 4900)."""
+    return make_system(8, 8, seed=0, n_chol=16, name="8e8o")
+
+
+def init_12e24o() -> System:
+    """12 electrons in 24 spatial orbitals, 8 irreps round-robin, 32 Cholesky vectors."""
+    return make_system(24, 12, seed=1, n_chol=32, symmetry=True, name="12e24o")
+
+
+def large_24e60o() -> System:
+    """24 electrons in 60 spatial orbitals (two uint64 words), 8 irreps, decaying Cholesky
+    vectors and a near-degenerate frontier window around the Fermi level (HOMO = spatial 11)."""
+    return make_system(60, 24, seed=2, n_chol=120, symmetry=True, chol_decay_len=4.0,
+                       chol_k_decay=24.0, energies=frontier_energies(60), name="24e60o")
+
+
+def rdm_16e40o() -> System:
+    """16 electrons in 40 spatial orbitals, no symmetry, 32 Cholesky vectors."""
+    return make_system(40, 16, seed=4, n_chol=32, name="16e40o")
+
+
+def small_system(n_orb: int, n_elec: int, seed: int, symmetry: bool = False, n_chol: int = 8) -> System:
+    """Small random systems for exhaustive checks."""
+    return make_system(n_orb, n_elec, seed=seed, n_chol=n_chol, symmetry=symmetry,
+                       name=f"{n_elec}e{n_orb}o-s{seed}")
+
+
+def batch_systems(n_runs: int = 64, seed: int = 3) -> list[dict]:
+    """Uneven independent runs: n_elec even in [8, 16], n_orb in [max(16, n_elec), 40],
+    no symmetry, target walkers log-uniform in [1e4, 2e6], Philox seed 1000 + r."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    runs = []
+    for r in range(n_runs):
+        n_elec = int(rng.integers(4, 9)) * 2
+        n_orb = int(rng.integers(max(16, n_elec), 41))
+        target = int(round(10 ** rng.uniform(4.0, np.log10(2e6))))
+        runs.append(dict(n_elec=n_elec, n_orb=n_orb, target=target, seed=1000 + r,
+                         sys_seed=int(rng.integers(0, 2**31))))
+    return runs

@@ -1,0 +1,58 @@
+"""The oracle's pins have teeth: plant plausible mistakes in a copy of the oracle (on the CPU)
+and check that the pin suite rejects every mutant."""
+from __future__ import annotations
+
+import os
+import subprocess
+import sys
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "fciqmc_oracle.c")
+
+# (name, original text, planted mistake)
+MUTANTS = [
+    ("philox_multiplier", "0xD2511F53u * (uint64_t)c0", "0xD2511F55u * (uint64_t)c0"),
+    ("single_drops_exchange", "if (spin_of(j) == spin_of(i)) v = v - eri4(q, I, J, J, A);", ""),
+    ("diag_drops_coulomb", "v = v + eri4(q, p, p, r, r);", ""),
+    ("double_wrong_index", "v = v - eri4(q, spat_of(i), spat_of(b), spat_of(j), spat_of(a));",
+     "v = v - eri4(q, spat_of(i), spat_of(j), spat_of(b), spat_of(a));"),
+    ("parity_inclusive", "for (int m = lo + 1; m < hi; ++m)", "for (int m = lo; m < hi; ++m)"),
+    ("pgen_drops_reverse_order", "info[4] = m_ba + m_ab;", "info[4] = m_ba + m_ba;"),
+    ("singles_not_renormalised", "info[5] = (int64_t)mallow * (int64_t)nok;", "info[5] = (int64_t)mallow * (int64_t)n;"),
+    ("spawn_sign", "return -(int64_t)sgn_c * sgn_h * nsp;", "return (int64_t)sgn_c * sgn_h * nsp;"),
+    ("death_sign", "if (r >= 0.0) { nc = (int64_t)c - sc * nd;", "if (r >= 0.0) { nc = (int64_t)c + sc * nd;"),
+    ("initiator_flag_and", "m.flag |= sp[y].flag;", "m.flag &= sp[y].flag;"),
+    ("spin_rule_double", "if (si == sj && sa != si) continue;", "if (sa != si) continue;"),
+]
+
+FAST_PINS = ("philox or own_log or second_quantisation or symmetry_and_spin or two_words and hamiltonian "
+             "or pdouble or normalised or eq1 or initiator_rule")
+
+
+@pytest.mark.slow
+def test_every_planted_mistake_is_caught():
+    src = open(SRC).read()
+    tmp = tempfile.mkdtemp(prefix="oracle_mutants_")
+    procs = {}
+    for name, old, new in MUTANTS:
+        assert src.count(old) == 1, name
+        path_c = os.path.join(tmp, f"{name}.c")
+        path_so = os.path.join(tmp, f"{name}.so")
+        with open(path_c, "w") as f:
+            f.write(src.replace(old, new))
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
+                               "-o", path_so, path_c, "-lm"])
+        env = dict(os.environ, FCIQMC_ORACLE_LIB=path_so, OMP_NUM_THREADS="1")
+        procs[name] = subprocess.Popen(
+            [sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_pins.py"), "-x", "-q",
+             "-p", "no:cacheprovider", "-k", FAST_PINS],
+            env=env, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, cwd=ROOT)
+    survivors = []
+    for name, p in procs.items():
+        out, _ = p.communicate(timeout=600)
+        if p.returncode == 0:
+            survivors.append((name, out.decode()[-400:]))
+    assert not survivors, survivors
