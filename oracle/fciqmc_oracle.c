@@ -244,7 +244,8 @@ static int occ_between(const oq_t *q, const uint64_t *d, int k, int l)
 }
 
 /* ---------------- Slater-Condon rules (Sec. II) ---------------- */
-/* Diagonal: sum_p h_pp + sum_{p<q} [(pp|qq) - delta_spin (pq|qp)], ascending order. */
+/* Diagonal: sum_p h_pp + sum_{p<q} [(pp|qq) - delta_spin (pq|qp)], ascending order; each pair
+ * term (Coulomb minus exchange) is formed first and then added to the running sum. */
 double oq_hdiag(const oq_t *q, const uint64_t *d)
 {
     int occ[OQ_MAXSO];
@@ -254,8 +255,9 @@ double oq_hdiag(const oq_t *q, const uint64_t *d)
     for (int x = 0; x < n; ++x) {
         for (int y = x + 1; y < n; ++y) {
             int p = spat_of(occ[x]), r = spat_of(occ[y]);
-            v = v + eri4(q, p, p, r, r);
-            if (spin_of(occ[x]) == spin_of(occ[y])) v = v - eri4(q, p, r, r, p);
+            double t = eri4(q, p, p, r, r);
+            if (spin_of(occ[x]) == spin_of(occ[y])) t = t - eri4(q, p, r, r, p);
+            v = v + t;
         }
     }
     return v;

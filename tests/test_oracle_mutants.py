@@ -16,7 +16,7 @@ SRC = os.path.join(ROOT, "oracle", "fciqmc_oracle.c")
 MUTANTS = [
     ("philox_multiplier", "0xD2511F53u * (uint64_t)c0", "0xD2511F55u * (uint64_t)c0"),
     ("single_drops_exchange", "if (spin_of(j) == spin_of(i)) v = v - eri4(q, I, J, J, A);", ""),
-    ("diag_drops_coulomb", "v = v + eri4(q, p, p, r, r);", ""),
+    ("diag_drops_exchange", "if (spin_of(occ[x]) == spin_of(occ[y])) t = t - eri4(q, p, r, r, p);", ""),
     ("double_wrong_index", "v = v - eri4(q, spat_of(i), spat_of(b), spat_of(j), spat_of(a));",
      "v = v - eri4(q, spat_of(i), spat_of(j), spat_of(b), spat_of(a));"),
     ("parity_inclusive", "for (int m = lo + 1; m < hi; ++m)", "for (int m = lo; m < hi; ++m)"),
