@@ -1,0 +1,374 @@
+#!/usr/bin/env python
+"""Benchmark of the FCIQMC walker cycle: spawn attempts/s and iterations/s at 1e8 walkers.
+
+Workload (default "24e60o"): 24 electrons in 60 spatial orbitals (two uint64 words per
+determinant), 8 irreps, synthetic decaying-Cholesky integrals with a near-degenerate frontier,
+initiator threshold 3, tau = 0.001, 1e8 target walkers, main list of 2e8 slots. The walker
+population is grown on the GPU from the reference (untimed), the shift starts varying at the
+target, and after warm-up iterations K iterations are timed with CUDA events on the run's stream.
+One "step" is one full iteration: spawning, death, annihilation with the initiator filter,
+estimators and shift. The main list (GBs) is far larger than L2, so no L2 flush is needed.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload NAME]
+
+N > 1 runs under torchrun: each rank advances an independent replica (its own seed), the
+timed region is bracketed by barriers, the time is the maximum over ranks and the value is the
+total number of attempts of all ranks divided by that time (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import ctypes
+import io
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1305_6981_gb300 import synth  # noqa: E402
+
+METRIC = "spawn attempts/s at 1e8 walkers (24e/60o, initiator, tau 0.001)"
+
+WORKLOADS = {
+    "24e60o": dict(system=synth.large_24e60o, tau=0.001, thr=3, target=100_000_000, main_capacity=200_000_000,
+                   spawn_capacity=1 << 27, initial_population=20_000, initial_shift=3.0, max_growth=40_000,
+                   equilibrate=50,
+                   desc="24e/60o (W=2), 8 irreps, initiator 3, tau 0.001, 1e8 target walkers, 2e8-slot main list"),
+    "12e24o": dict(system=synth.init_12e24o, tau=0.005, thr=3, target=1_000_000, main_capacity=4_000_000,
+                   spawn_capacity=1 << 22, initial_population=2_000, initial_shift=1.0, max_growth=20_000,
+                   equilibrate=50, desc="12e/24o (W=1), 8 irreps, initiator 3, tau 0.005, 1e6 target walkers"),
+    "8e8o": dict(system=synth.tiny_8e8o, tau=0.01, thr=-1, target=1 << 14, main_capacity=1 << 14,
+                 spawn_capacity=1 << 14, initial_population=1_000, initial_shift=0.5, max_growth=5_000,
+                 equilibrate=50, desc="8e/8o (W=1), no symmetry, plain FCIQMC, tau 0.01, 2^14 target walkers"),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default="24e60o", choices=sorted(WORKLOADS))
+    ap.add_argument("--target", type=int, default=0, help="override target walkers (smaller runs)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle baseline")
+    ap.add_argument("--growth-log", default="")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------- clocks
+class Clocks:
+    """nvidia-smi samples during the timed region (clocks, power, throttle reasons)."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for r in csv.reader(f):
+                if len(r) >= 9:
+                    rows.append([x.strip() for x in r])
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
+
+
+# ---------------------------------------------------------------------------- oracle baseline
+def oracle_rate(system, wl, dets, pops, seconds: float, seed: int = 1):
+    """The CPU oracle as it stands on this host's cores: spawn attempts/s of whole iterations on a
+    bounded sample of the workload's walker list."""
+    from oracle.oracle import Oracle, lib
+    lib()
+    q = Oracle(system, tau=wl["tau"], initiator_threshold=wl["thr"], seed=seed)
+    att, it, elapsed = 0, 0, 0.0
+    while elapsed < seconds and it < 1000:
+        q.set_walkers(dets, pops, iteration=1000 + it, shift=0.0)
+        t1 = time.perf_counter()
+        rows = q.iterate(1)
+        elapsed += time.perf_counter() - t1
+        att += rows[0]["attempts"]
+        it += 1
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return att / elapsed, cores, it, att
+
+
+def sample_list(dets, pops, n_walkers, seed=0):
+    """Uniform sample of determinants holding about n_walkers walkers (populations unchanged)."""
+    rng = np.random.default_rng(seed)
+    tot = int(np.abs(pops).sum())
+    p = min(1.0, n_walkers / max(tot, 1))
+    keep = rng.random(len(pops)) < p
+    return dets[keep], pops[keep]
+
+
+# ---------------------------------------------------------------------------- reference arm
+def run_reference(args, wl, rank, world):
+    if rank != 0:
+        return
+    system = wl["system"]()
+    n_sample = 200_000 if args.workload == "24e60o" else 50_000
+    dets, pops = synth.walker_snapshot(system, n_sample, seed=7)
+    from oracle.oracle import Oracle, lib
+    lib()
+    q = Oracle(system, tau=wl["tau"], initiator_threshold=wl["thr"], seed=1)
+    for k in range(args.warmup):
+        q.set_walkers(dets, pops, iteration=k, shift=0.0)
+        q.iterate(1)
+    att, tsum = 0, 0.0
+    for k in range(args.steps):
+        q.set_walkers(dets, pops, iteration=args.warmup + k, shift=0.0)
+        t0 = time.perf_counter()
+        rows = q.iterate(1)
+        tsum += time.perf_counter() - t0
+        att += rows[0]["attempts"]
+    value = att / tsum
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "attempts/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tsum / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "system": wl["desc"],
+                   "sample": f"{len(pops)} determinants / {int(np.abs(pops).sum())} walkers of a synthetic "
+                             f"snapshot (reference + random symmetry-conserving excitations)"},
+        "cpu_baseline": {"value": value, "unit": "attempts/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} oracle iterations on a {int(np.abs(pops).sum())}-walker sample"},
+        "e2e": {"value": value, "unit": "attempts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------------------- GPU arm
+def algorithmic_bytes(W, nd, slots, merged, inserted):
+    """HBM bytes one iteration must move: per occupied determinant its words, population
+    and float diagonal read plus the new population written; per vacated slot its population read and
+    written; per distinct spawned determinant the merge entry written and read back with its position,
+    one index entry and one population read-modify-write; per insertion the new slot and index entry."""
+    entry = 8 * W + 8
+    sweep = nd * (8 * W + 4 + 4 + 4) + (slots - nd) * 8 + merged * (entry + 4)
+    annih = merged * (entry + 4) + merged * (entry + 8) + inserted * (8 * W + 8 + 4 + 4 + entry)
+    return sweep, annih
+
+
+def run_gpu(args, wl, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1305_6981_gb300 import Fciqmc
+
+    torch.cuda.set_device(local_rank)
+    system = wl["system"]()
+    target = args.target or wl["target"]
+    cap = wl["main_capacity"] if not args.target else max(4 * args.target, 1 << 16)
+    scap = wl["spawn_capacity"] if not args.target else max(1 << 14, 1 << int(np.ceil(np.log2(2 * args.target))))
+    g = Fciqmc(system, wl["tau"], wl["thr"], target_walkers=target, initial_population=wl["initial_population"],
+               initial_shift=wl["initial_shift"], seed=1 + rank, main_capacity=cap, spawn_capacity=scap)
+    info = g.info()
+    # growth (untimed)
+    t_grow = time.perf_counter()
+    grown, chunk = 0, 50
+    log = []
+    while True:
+        g.step(chunk)
+        grown += chunk
+        e = g.estimates()
+        log.append((grown, e["n_walkers"], e["n_dets"], e["shift"], e["list_slots"]))
+        if e["status"] != 0:
+            raise RuntimeError(f"device status {e['status']} during growth at {grown}: {log[-1]}")
+        if e["vary_shift"] or grown >= wl["max_growth"]:
+            break
+    g.step(wl["equilibrate"])
+    grown += wl["equilibrate"]
+    t_grow = time.perf_counter() - t_grow
+    if args.growth_log and rank == 0:
+        with open(args.growth_log, "w") as f:
+            json.dump(log, f)
+    # warm-up
+    g.step(args.warmup)
+    g.sync()
+    stream = g.stream
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = Clocks(local_rank)
+    e_before = g.estimates()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    torch.cuda.nvtx.range_push("timed")
+    ev0.record(stream)
+    g.step(args.steps)
+    ev1.record(stream)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    st = g.sync()
+    rows = g.history(args.steps)
+    attempts = sum(r["attempts"] for r in rows)
+    nd_mean = float(np.mean([r["nd_in"] for r in rows]))
+    nw_mean = float(np.mean([r["nw_in"] for r in rows]))
+    merged_mean = float(np.mean([r["merged_entries"] for r in rows]))
+    inserted_mean = float(np.mean([r["inserted_dets"] for r in rows]))
+    t = torch.tensor([ms, float(attempts)], dtype=torch.float64, device="cuda")
+    if world > 1:
+        tt = t.clone()
+        dist.all_reduce(tt[0:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(tt[1:2], op=dist.ReduceOp.SUM)
+        t = tt
+    ms_max, att_all = float(t[0]), float(t[1])
+    # per-kernel times (same iterations, kernels launched one by one between events)
+    est = g.estimates()
+    exact = {"spawn_per_iter": (est["exact_spawns"] - e_before["exact_spawns"]) / args.steps,
+             "death_per_iter": (est["exact_deaths"] - e_before["exact_deaths"]) / args.steps}
+    prof = g.profile(5)
+    slots = est["list_slots"]
+    sweep_b, annih_b = algorithmic_bytes(info["words"], nd_mean, slots, merged_mean, inserted_mean)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    dom = max(("sweep", "heavy", "annihilate"), key=lambda k: prof[k])
+    dom_ms = prof[dom] / 5.0
+    dom_bytes = {"sweep": sweep_b, "annihilate": annih_b, "heavy": merged_mean * (8 * info["words"] + 12)}[dom]
+    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
+    out = None
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": att_all / (ms_max * 1e-3), "unit": "attempts/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "iterations_per_s": args.steps / (ms_max * 1e-3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "system": wl["desc"], "walkers_mean": nw_mean,
+                       "dets_mean": nd_mean, "list_slots": slots, "merged_per_iter": merged_mean,
+                       "inserted_per_iter": inserted_mean, "growth_iterations": grown,
+                       "growth_seconds": round(t_grow, 1), "l2": "inputs larger than L2 (main list ~GBs)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak, "traffic": None, "peak_source": peak_src,
+                         "algorithmic_bytes_per_launch": dom_bytes, "launch_ms": dom_ms},
+            "kernel_ms_per_iter": {k: v / 5.0 for k, v in prof.items()},
+            "cycle_hbm_gbs": (sweep_b + annih_b) / (ms_max / args.steps * 1e-3) / 1e9,
+            "clocks": clk,
+            "status": st,
+            "exact_path": exact,
+            "gpu_launches": 8 * args.steps,
+        }
+    return g, out, info
+
+
+def e2e_rate(g, args, info, world):
+    """Same metric through the C ABI with host buffers: per step the walker list (determinants,
+    populations, diagonal elements) goes host->device from pinned memory, one iteration runs, and the
+    resulting list comes back device->host into pinned memory."""
+    import torch
+    n0 = g.estimates()["n_dets"]
+    cap = int(n0 * 1.5) + 1024
+    W = info["words"]
+    dets = torch.empty((cap, W), dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
+    pops = torch.empty(cap, dtype=torch.int32, pin_memory=True).numpy()
+    hd = torch.empty(cap, dtype=torch.float64, pin_memory=True).numpy()
+    n = g.walkers_into(dets, pops, hd)
+    st = g.state()
+    K = max(1, min(args.steps, 10))
+    h2d = d2h = 0
+    att = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(K):
+        g.set_walkers(dets[:n], pops[:n], hd[:n], iteration=st["iteration"] + k, shift=st["shift"],
+                      vary=st["vary_shift"], shift_counter=st["shift_counter"], nw_last_update=st["nw_last_update"])
+        h2d += n * (8 * W + 4 + 8)
+        g.step(1)
+        n = g.walkers_into(dets, pops, hd)
+        d2h += n * (8 * W + 4 + 8)
+        att += int(np.abs(pops[:n]).sum())
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return {"value": att / dt, "unit": "attempts/s", "h2d_bytes_per_step": h2d // K, "d2h_bytes_per_step": d2h // K,
+            "steps": K}, dets[:n].copy(), pops[:n].copy()
+
+
+def main():
+    args = parse()
+    wl = WORKLOADS[args.workload]
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        run_reference(args, wl, rank, world)
+        return
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl")
+    g, out, info = run_gpu(args, wl, rank, world, local_rank)
+    if rank == 0:
+        if not args.no_e2e and world == 1:
+            e2e, dets, pops = e2e_rate(g, args, info, world)
+            out["e2e"] = e2e
+        else:
+            dets, pops, _ = g.walkers()
+            out["e2e"] = None
+        if not args.no_cpu_baseline and world == 1:
+            system = wl["system"]()
+            sd, sp = sample_list(dets, pops, 300_000 if args.workload == "24e60o" else 50_000)
+            rate, cores, its, att = oracle_rate(system, wl, sd, sp, args.cpu_seconds)
+            out["cpu_baseline"] = {"value": rate, "unit": "attempts/s", "cores": cores, "kind": "oracle",
+                                   "sample": f"{its} oracle iterations on {len(sp)} determinants / "
+                                             f"{int(np.abs(sp).sum())} walkers sampled uniformly from the "
+                                             f"GPU list ({att} attempts)"}
+        print(json.dumps(out), flush=True)
+    g.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

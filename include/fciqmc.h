@@ -1,0 +1,239 @@
+/*
+ * fciqmc.h - C ABI of the GB300 FCIQMC walker cycle.
+ *
+ * The library advances a population of signed integer walkers on Slater
+ * determinants by the FCIQMC master equation (Booth, Smart, Alavi,
+ * "Linear-scaling and parallelizable algorithms for stochastic quantum
+ * chemistry", Sec. II, Eq. 1):
+ *
+ *   C_i(n+1) = [1 - tau (H_ii - E0 - S)] C_i(n) - tau sum_{j != i} H_ij C_j(n)
+ *
+ * realised each iteration by spawning (Eq. 3) with a normalised random
+ * excitation generator (Sec. VI), diagonal death/cloning (Eq. 4), and
+ * annihilation of the spawned list into the main list with the initiator
+ * filter (Sec. V, Sec. V B), followed by the shift and projected-energy
+ * (Eq. 2) estimators. Every step runs in CUDA kernels for sm_103a.
+ *
+ * Conventions shared by all calls
+ *   - Spin orbital k holds spatial orbital k >> 1 with spin k & 1 (0 = alpha).
+ *     A determinant is W = ceil(2 n_orb / 64) uint64 words; bit k of word
+ *     k >> 6 set means spin orbital k is occupied (Sec. III bit strings).
+ *   - Integrals are real: h is n_orb x n_orb row-major and symmetric; ERIs are
+ *     chemists' (pq|rs) packed 8-fold (Sec. II footnote): pair index
+ *     pq = p(p+1)/2 + q for p >= q, element index pq(pq+1)/2 + rs for pq >= rs.
+ *   - Orbital symmetry labels are 0..7 with the XOR direct product (abelian
+ *     D2h-like groups, Sec. II); NULL means no spatial symmetry.
+ *   - Limits: n_orb <= 64 (W <= 2), 1 <= n_elec <= 64, n_elec < 2 n_orb.
+ *   - Every call returns an int status (0 = FCIQMC_OK, < 0 = error); no
+ *     exception or abort crosses the ABI. fciqmc_strerror names a status.
+ *   - Device memory comes only from the caller: fciqmc_workspace_bytes() says
+ *     how much, and fciqmc_create() carves all device state out of that one
+ *     buffer. The handle never allocates device memory and frees nothing the
+ *     caller owns. Inputs are copied at creation; the caller keeps ownership
+ *     of every array it passes.
+ *   - One handle is driven from one host thread and one CUDA stream; there is
+ *     no internal locking. Kernels are enqueued asynchronously on that stream;
+ *     calls documented as synchronising wait for it.
+ *   - Errors detected on the device (capacity, numeric overflow) stop the
+ *     iteration in which they occur before it changes the committed walker
+ *     list; later iterations already enqueued do nothing. The error stays set
+ *     (sticky) until fciqmc_set_walkers; fciqmc_sync and fciqmc_estimators
+ *     return it. The read-back calls (history, walkers, state, n_dets) still
+ *     succeed and return the state of the last completed iteration, so a run
+ *     can be restarted with larger capacities without changing its trajectory
+ *     (the random numbers are keyed by iteration, not by history).
+ */
+#ifndef FCIQMC_H
+#define FCIQMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    FCIQMC_OK = 0,
+    FCIQMC_ERR_INVALID_ARG = -1,   /* bad argument or inconsistent input */
+    FCIQMC_ERR_CAPACITY = -2,      /* main list, hash index or spawn table full */
+    FCIQMC_ERR_NUMERIC = -3,       /* a population or spawn count left int32 */
+    FCIQMC_ERR_TIMEOUT = -4,       /* a bounded device wait gave up */
+    FCIQMC_ERR_CUDA = -5,          /* a CUDA runtime call failed */
+    FCIQMC_ERR_UNSUPPORTED = -6,   /* size beyond the limits above */
+    FCIQMC_ERR_WORKSPACE = -7      /* workspace too small or misaligned (256 B) */
+};
+
+typedef struct fciqmc_handle fciqmc_handle;
+
+/* Run options. Zero-initialise and set what you need; fciqmc_default_options
+ * fills the documented defaults. */
+typedef struct {
+    double shift_damping;        /* zeta of the shift update, default 0.05 */
+    int32_t shift_period;        /* A: iterations between shift updates, default 10 */
+    int32_t initial_population;  /* walkers placed on the reference, default 10 */
+    double initial_shift;        /* S (relative to E0) until N_w first reaches target, default 0 */
+    int64_t target_walkers;      /* vary-shift starts once N_w >= target, default 2^62 (never) */
+    uint64_t seed;               /* low 32 bits key the random numbers, default 1 */
+    double p_double;             /* > 0: fixed P_double; <= 0: from the reference (Sec. VI), default 0 */
+    int64_t main_capacity;       /* determinant slots of the main list, default 1 << 20 */
+    int64_t spawn_capacity;      /* entries of the spawn merge table (rounded up to a power of two),
+                                    default main_capacity / 2 */
+    int64_t history_capacity;    /* per-iteration estimator rows kept (ring), default 1 << 16 */
+    const uint64_t *reference;   /* W words, NULL: aufbau (lowest orbitals of each spin filled) */
+} fciqmc_options;
+
+/* Per-iteration record. The estimators (nw_in .. num_in) describe the list at
+ * the start of the iteration; nw_out / nd_out the list after it. */
+typedef struct {
+    int64_t iteration;        /* index of the iteration (0-based) */
+    double shift;             /* S used in this iteration (relative to E0) */
+    int64_t nw_in, nd_in;     /* sum |C_i|, number of occupied determinants */
+    int64_t c0_in;            /* population of the reference determinant */
+    double num_in;            /* sum_{i != 0} <D_i|H|D_0> C_i (Eq. 2 numerator) */
+    int64_t nw_out, nd_out;
+    int64_t attempts;         /* spawning attempts (= nw_in) */
+    int64_t nulls;            /* attempts that drew a null excitation */
+    int64_t spawn_events;     /* attempts that spawned at least one walker */
+    int64_t spawned_walkers;  /* walkers spawned */
+    int64_t death_walkers;    /* walkers removed by death */
+    int64_t clone_walkers;    /* walkers added by cloning */
+    int64_t merged_entries;   /* distinct determinants spawned onto */
+    int64_t aborted_walkers;  /* spawned walkers discarded by the initiator rule */
+    int64_t inserted_dets;    /* determinants newly occupied by spawning */
+} fciqmc_row;
+
+/* Estimators of the current list (Sec. II, Eq. 2). Energies include e_core. */
+typedef struct {
+    int64_t iteration;        /* iterations completed */
+    double shift;             /* S */
+    double e_ref;             /* E0 + e_core, E0 = H_00 of the reference */
+    double e_shift;           /* e_ref + S */
+    double e_proj;            /* e_ref + proj_num / c0 (NaN if c0 == 0) */
+    double proj_num;
+    int64_t c0, n_walkers, n_dets;
+    int32_t vary_shift;       /* 1 once the shift is being varied */
+    int32_t status;           /* sticky device status (0 = OK) */
+    int64_t list_slots;       /* slots in use in the main list (occupied + vacated) */
+    int64_t compactions;      /* main-list compactions so far */
+    int64_t exact_spawns;     /* spawn decisions taken by the exact FP64 path (diagnostic) */
+    int64_t exact_deaths;     /* death decisions taken by the exact FP64 path (diagnostic) */
+} fciqmc_estimates;
+
+/* Dynamic state needed, together with the walker list, to resume a run. */
+typedef struct {
+    int64_t iteration;
+    double shift;
+    int32_t vary_shift;
+    int32_t shift_counter;    /* iterations since the last shift update */
+    int64_t nw_last_update;   /* N_w at the last shift update */
+} fciqmc_state;
+
+/* Facts fixed at creation. */
+typedef struct {
+    int32_t n_elec, n_orb, words;
+    double e0;                /* H_00 without e_core */
+    double e_core;
+    double p_double;          /* as realised by the draw: d53 / 2^53 */
+    uint64_t d53;             /* a spawn attempt is a double iff (r0 >> 11) < d53 */
+    int64_t n_single_ref, n_double_ref;
+    uint64_t reference[2];
+    int64_t main_capacity, index_capacity, spawn_capacity, history_capacity;
+    size_t workspace_bytes;
+    int32_t grid_blocks;      /* persistent grid of the sweep kernels */
+    int32_t num_sms;
+} fciqmc_info;
+
+/* Fills the defaults listed in fciqmc_options. */
+void fciqmc_default_options(fciqmc_options *opt);
+
+/* Device bytes fciqmc_create needs for this problem and these options
+ * (opt may be NULL: defaults). Returns 0 for unsupported sizes. */
+size_t fciqmc_workspace_bytes(int n_elec, int n_orb, const fciqmc_options *opt);
+
+/* Creates a run (Sec. II problem statement).
+ *   h, eri_s8       host arrays, layout above; copied.
+ *   e_core          constant added to reported energies.
+ *   n_elec, n_orb   electrons and spatial orbitals.
+ *   ms2             2 S_z of the aufbau reference (ignored when opt->reference is set).
+ *   orb_irrep       n_orb labels 0..7 (host), or NULL.
+ *   tau             time step (> 0).
+ *   initiator_threshold  < 0: plain FCIQMC; >= 0: a determinant is an initiator
+ *                   iff |C_i| > threshold, the reference always (Sec. V B).
+ *   opt             may be NULL.
+ *   workspace       device pointer, 256-byte aligned, of workspace_bytes >=
+ *                   fciqmc_workspace_bytes(); owned by the caller, must outlive the handle.
+ *   cuda_stream     cudaStream_t (NULL: legacy default stream) all work is enqueued on.
+ * Synchronising. On success *out receives the handle. */
+int fciqmc_create(const double *h, const double *eri_s8, double e_core, int n_elec, int n_orb, int ms2,
+                  const int32_t *orb_irrep, double tau, int32_t initiator_threshold,
+                  const fciqmc_options *opt, void *workspace, size_t workspace_bytes, void *cuda_stream,
+                  fciqmc_handle **out);
+
+/* Enqueues n_iterations iterations (spawn + death, annihilation with the
+ * initiator filter, estimators and shift) on the stream. Asynchronous: device
+ * errors surface at the next synchronising call. */
+int fciqmc_step(fciqmc_handle *h, int32_t n_iterations);
+
+/* Waits for the stream; returns the sticky device status. */
+int fciqmc_sync(fciqmc_handle *h);
+
+/* Synchronising: estimators of the current list into *out (host struct).
+ * Returns the sticky device status (also in out->status). */
+int fciqmc_estimators(fciqmc_handle *h, fciqmc_estimates *out);
+
+/* Synchronising: copies up to max_rows of the most recent per-iteration rows,
+ * oldest first, into rows (host); *n_rows receives the count. */
+int fciqmc_history(fciqmc_handle *h, fciqmc_row *rows, int64_t max_rows, int64_t *n_rows);
+
+/* Synchronising: number of occupied determinants of the current list. */
+int fciqmc_n_dets(fciqmc_handle *h, int64_t *n_dets);
+
+/* Synchronising: copies the occupied determinants (W words each), their
+ * populations and, if hdiag is not NULL, their stored H_ii - E0, into host
+ * arrays of capacity cap entries, in unspecified order; *n receives the count.
+ * Host arrays may be pinned or pageable. Returns FCIQMC_ERR_CAPACITY (with *n
+ * set) if cap is too small. */
+int fciqmc_get_walkers(fciqmc_handle *h, uint64_t *dets, int32_t *pops, double *hdiag, int64_t cap,
+                       int64_t *n);
+
+/* Synchronising: replaces the walker list and, if st is not NULL, the
+ * dynamic state. dets: n x W words (host); pops: n nonzero populations;
+ * hdiag: H_ii - E0 per determinant as returned by fciqmc_get_walkers, or NULL
+ * to compute it. Determinants must be distinct and carry the run's electron
+ * count. Clears the history and the device status. */
+int fciqmc_set_walkers(fciqmc_handle *h, const uint64_t *dets, const int32_t *pops, const double *hdiag,
+                       int64_t n, const fciqmc_state *st);
+
+/* Synchronising: dynamic state of the run. */
+int fciqmc_get_state(fciqmc_handle *h, fciqmc_state *st);
+
+/* Facts fixed at creation. Not synchronising. */
+int fciqmc_get_info(const fciqmc_handle *h, fciqmc_info *info);
+
+/* Kernels of one iteration, in launch order (indices into the kernel_ms array
+ * of fciqmc_profile). */
+#define FCIQMC_N_KERNELS 8
+/* 0 compact_copy, 1 index_clear, 2 index_fill, 3 compact_finish (no-ops unless
+ * a compaction is due), 4 sweep (estimators, death, spawning), 5 heavy
+ * (spawning from determinants with more than 1024 walkers), 6 annihilate,
+ * 7 finish (reductions, shift). */
+
+/* Synchronising: runs n_iterations iterations exactly as fciqmc_step does, but
+ * launching each kernel individually between CUDA events on the run's stream,
+ * and adds each kernel's elapsed milliseconds, summed over the iterations,
+ * into kernel_ms[FCIQMC_N_KERNELS] (host array, not cleared). */
+int fciqmc_profile(fciqmc_handle *h, int32_t n_iterations, double *kernel_ms);
+
+/* Releases host-side resources (graphs, events). Synchronising. The
+ * workspace stays the caller's. Accepts NULL. */
+void fciqmc_destroy(fciqmc_handle *h);
+
+/* Static text for a status code. */
+const char *fciqmc_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FCIQMC_H */

@@ -1,0 +1,161 @@
+"""Build and load the CUDA library (libfciqmc.so) and declare its C ABI for ctypes.
+
+The library is compiled in-tree for sm_103a with nvcc. There is no fallback: if
+the library cannot be built or loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(HERE, "csrc")
+INCLUDE = os.path.join(ROOT, "include")
+BUILD = os.path.join(HERE, "_build")
+LIB = os.path.join(BUILD, "libfciqmc.so")
+SOURCES = ["fciqmc.cu"]
+DEPS = ["fciqmc.cu", "fciqmc_kernels.cuh", "fciqmc_device.cuh"]
+ARCH = "-gencode=arch=compute_103a,code=sm_103a"
+NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
+              "-Xcompiler", "-ffp-contract=off", "-fmad=false"]
+
+
+def nvcc() -> str:
+    for c in (os.environ.get("NVCC"), "/usr/local/cuda/bin/nvcc", "nvcc"):
+        if c and (os.path.isabs(c) and os.path.exists(c) or not os.path.isabs(c)):
+            return c
+    return "nvcc"
+
+
+def _stale() -> bool:
+    if not os.path.exists(LIB):
+        return True
+    t = os.path.getmtime(LIB)
+    deps = [os.path.join(CSRC, d) for d in DEPS] + [os.path.join(INCLUDE, "fciqmc.h")]
+    return any(os.path.getmtime(d) > t for d in deps)
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile libfciqmc.so for sm_103a (only when sources changed)."""
+    if not force and not _stale():
+        return LIB
+    os.makedirs(BUILD, exist_ok=True)
+    tmp = LIB + f".tmp{os.getpid()}"
+    cmd = [nvcc(), ARCH, *NVCC_FLAGS, "-I" + INCLUDE, "-o", tmp] + [os.path.join(CSRC, s) for s in SOURCES]
+    if verbose:
+        print(" ".join(cmd))
+    subprocess.check_call(cmd)
+    os.replace(tmp, LIB)
+    return LIB
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("shift_damping", ctypes.c_double), ("shift_period", ctypes.c_int32),
+                ("initial_population", ctypes.c_int32), ("initial_shift", ctypes.c_double),
+                ("target_walkers", ctypes.c_int64), ("seed", ctypes.c_uint64), ("p_double", ctypes.c_double),
+                ("main_capacity", ctypes.c_int64), ("spawn_capacity", ctypes.c_int64),
+                ("history_capacity", ctypes.c_int64), ("reference", ctypes.POINTER(ctypes.c_uint64))]
+
+
+ROW_FIELDS = ["iteration", "shift", "nw_in", "nd_in", "c0_in", "num_in", "nw_out", "nd_out", "attempts", "nulls",
+              "spawn_events", "spawned_walkers", "death_walkers", "clone_walkers", "merged_entries",
+              "aborted_walkers", "inserted_dets"]
+
+
+class Row(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_double if f in ("shift", "num_in") else ctypes.c_int64) for f in ROW_FIELDS]
+
+
+class Estimates(ctypes.Structure):
+    _fields_ = [("iteration", ctypes.c_int64), ("shift", ctypes.c_double), ("e_ref", ctypes.c_double),
+                ("e_shift", ctypes.c_double), ("e_proj", ctypes.c_double), ("proj_num", ctypes.c_double),
+                ("c0", ctypes.c_int64), ("n_walkers", ctypes.c_int64), ("n_dets", ctypes.c_int64),
+                ("vary_shift", ctypes.c_int32), ("status", ctypes.c_int32), ("list_slots", ctypes.c_int64),
+                ("compactions", ctypes.c_int64), ("exact_spawns", ctypes.c_int64), ("exact_deaths", ctypes.c_int64)]
+
+
+class State(ctypes.Structure):
+    _fields_ = [("iteration", ctypes.c_int64), ("shift", ctypes.c_double), ("vary_shift", ctypes.c_int32),
+                ("shift_counter", ctypes.c_int32), ("nw_last_update", ctypes.c_int64)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n_elec", ctypes.c_int32), ("n_orb", ctypes.c_int32), ("words", ctypes.c_int32),
+                ("e0", ctypes.c_double), ("e_core", ctypes.c_double), ("p_double", ctypes.c_double),
+                ("d53", ctypes.c_uint64), ("n_single_ref", ctypes.c_int64), ("n_double_ref", ctypes.c_int64),
+                ("reference", ctypes.c_uint64 * 2), ("main_capacity", ctypes.c_int64),
+                ("index_capacity", ctypes.c_int64), ("spawn_capacity", ctypes.c_int64),
+                ("history_capacity", ctypes.c_int64), ("workspace_bytes", ctypes.c_size_t),
+                ("grid_blocks", ctypes.c_int32), ("num_sms", ctypes.c_int32)]
+
+
+# every symbol declared in include/fciqmc.h
+SYMBOLS = ["fciqmc_default_options", "fciqmc_workspace_bytes", "fciqmc_create", "fciqmc_step", "fciqmc_sync",
+           "fciqmc_estimators", "fciqmc_history", "fciqmc_n_dets", "fciqmc_get_walkers", "fciqmc_set_walkers",
+           "fciqmc_get_state", "fciqmc_get_info", "fciqmc_profile", "fciqmc_destroy", "fciqmc_strerror"]
+N_KERNELS = 8
+KERNEL_NAMES = ["compact_copy", "index_clear", "index_fill", "compact_finish", "sweep", "heavy", "annihilate",
+                "finish"]
+
+_lock = threading.Lock()
+_lib = None
+
+
+def _declare(L):
+    P = ctypes.POINTER
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    u64p, i32p, f64p = P(ctypes.c_uint64), P(ctypes.c_int32), P(ctypes.c_double)
+    L.fciqmc_default_options.argtypes = [P(Options)]
+    L.fciqmc_default_options.restype = None
+    L.fciqmc_workspace_bytes.argtypes = [ctypes.c_int, ctypes.c_int, P(Options)]
+    L.fciqmc_workspace_bytes.restype = ctypes.c_size_t
+    L.fciqmc_create.argtypes = [f64p, f64p, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, i32p,
+                                ctypes.c_double, i32, P(Options), vp, ctypes.c_size_t, vp, P(vp)]
+    L.fciqmc_step.argtypes = [vp, i32]
+    L.fciqmc_sync.argtypes = [vp]
+    L.fciqmc_estimators.argtypes = [vp, P(Estimates)]
+    L.fciqmc_history.argtypes = [vp, P(Row), i64, P(i64)]
+    L.fciqmc_n_dets.argtypes = [vp, P(i64)]
+    L.fciqmc_get_walkers.argtypes = [vp, u64p, i32p, f64p, i64, P(i64)]
+    L.fciqmc_set_walkers.argtypes = [vp, u64p, i32p, f64p, i64, P(State)]
+    L.fciqmc_get_state.argtypes = [vp, P(State)]
+    L.fciqmc_get_info.argtypes = [vp, P(Info)]
+    L.fciqmc_profile.argtypes = [vp, i32, f64p]
+    L.fciqmc_destroy.argtypes = [vp]
+    L.fciqmc_destroy.restype = None
+    L.fciqmc_strerror.argtypes = [ctypes.c_int]
+    L.fciqmc_strerror.restype = ctypes.c_char_p
+    for name in ("fciqmc_create", "fciqmc_step", "fciqmc_sync", "fciqmc_estimators", "fciqmc_history",
+                 "fciqmc_n_dets", "fciqmc_get_walkers", "fciqmc_set_walkers", "fciqmc_get_state", "fciqmc_get_info",
+                 "fciqmc_profile"):
+        getattr(L, name).restype = ctypes.c_int
+
+
+def load(build_if_needed: bool = True):
+    """The loaded library; raises if it cannot be built or loaded."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = build() if build_if_needed else LIB
+            if not os.path.exists(path):
+                raise RuntimeError(f"libfciqmc.so not built ({path}); run __graft_entry__.build()")
+            L = ctypes.CDLL(path)
+            _declare(L)
+            _lib = L
+    return _lib
+
+
+class FciqmcError(RuntimeError):
+    def __init__(self, status: int, where: str = ""):
+        self.status = status
+        msg = load(False).fciqmc_strerror(status).decode() if _lib is not None else str(status)
+        super().__init__(f"{where}: {msg} (status {status})")
+
+
+def check(status: int, where: str = "") -> int:
+    if status != 0:
+        raise FciqmcError(status, where)
+    return status

@@ -1,0 +1,712 @@
+// C ABI of the FCIQMC walker cycle: workspace layout, setup, iteration launch, read-back.
+// The declarations and the contract of every entry point are in include/fciqmc.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstddef>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "fciqmc.h"
+#include "fciqmc_kernels.cuh"
+
+using fq::DevState;
+using fq::Params;
+
+namespace {
+
+#define FQ_CUDA(call)                                     \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return FCIQMC_ERR_CUDA;    \
+    } while (0)
+
+constexpr size_t kAlign = 256;
+constexpr int kMaxGrid = 4096;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+long long next_pow2(long long x) {
+    long long p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+int log2_exact(long long x) {
+    int b = 0;
+    while ((1LL << b) < x) ++b;
+    return b;
+}
+
+struct Sizes {
+    int W, n_so, npairs;
+    long long n_eri, cap, idx_cap, mt_cap, chunk_cap, hist_cap;
+};
+
+bool sizes_of(int n_elec, int n_orb, const fciqmc_options &o, Sizes &z) {
+    if (n_orb < 1 || n_orb > 64 || n_elec < 1 || n_elec > fq::MAXN || n_elec >= 2 * n_orb) return false;
+    z.W = (2 * n_orb + 63) / 64;
+    z.n_so = 2 * n_orb;
+    z.npairs = n_elec * (n_elec - 1) / 2;
+    long long npair = (long long)n_orb * (n_orb + 1) / 2;
+    z.n_eri = npair * (npair + 1) / 2;
+    z.cap = std::max<long long>(o.main_capacity > 0 ? o.main_capacity : (1LL << 20), 1024);
+    if (z.cap > (1LL << 31) - 2) return false;
+    z.idx_cap = next_pow2(std::max<long long>(2 * z.cap, 1 << 12));
+    z.mt_cap = next_pow2(std::max<long long>(o.spawn_capacity > 0 ? o.spawn_capacity : z.cap / 2, 1 << 12));
+    if (z.mt_cap > (1LL << 32)) return false;
+    z.chunk_cap = std::max<long long>(1 << 16, z.cap / 16);
+    z.hist_cap = std::max<long long>(o.history_capacity > 0 ? o.history_capacity : (1LL << 16), 16);
+    return true;
+}
+
+struct Layout {
+    size_t state, h, eri, eri_f, wpair, map1, cmask, irrep, pairs, recip, ref_occ, facts, e0;
+    size_t det[2], hd[2], hdf[2], pop[2][2], idx, mt, merged, chunks, partial, hist;
+    size_t total;
+};
+
+Layout layout_of(const Sizes &z, int n_orb) {
+    Layout L{};
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = align_up(off + bytes);
+        return o;
+    };
+    L.state = take(sizeof(DevState));
+    L.h = take(sizeof(double) * n_orb * n_orb);
+    L.eri = take(sizeof(double) * z.n_eri);
+    L.eri_f = take(sizeof(float) * z.n_eri);
+    L.wpair = take(sizeof(double) * 2 * n_orb * n_orb);
+    L.map1 = take(sizeof(unsigned long long) * fq::MAXSO);
+    L.cmask = take(sizeof(unsigned long long) * fq::NCLASS * fq::MAXW);
+    L.irrep = take(fq::MAXSO);
+    L.pairs = take(sizeof(unsigned short) * std::max(z.npairs, 1));
+    L.recip = take(sizeof(double) * (2 * fq::MAXSO + 2));
+    L.ref_occ = take(fq::MAXN);
+    L.facts = take(sizeof(long long) * 4);
+    L.e0 = take(sizeof(double));
+    for (int b = 0; b < 2; ++b) {
+        L.det[b] = take(sizeof(unsigned long long) * z.W * z.cap);
+        L.hd[b] = take(sizeof(double) * z.cap);
+        L.hdf[b] = take(sizeof(float) * z.cap);
+        L.pop[b][0] = take(sizeof(int) * z.cap);
+        L.pop[b][1] = take(sizeof(int) * z.cap);
+    }
+    const int stride = z.W == 1 ? 2 : 4;
+    L.idx = take(sizeof(unsigned long long) * stride * z.idx_cap);
+    L.mt = take(sizeof(unsigned long long) * stride * z.mt_cap);
+    L.merged = take(sizeof(unsigned) * z.mt_cap);
+    L.chunks = take(sizeof(uint4) * z.chunk_cap);
+    L.partial = take(sizeof(double) * kMaxGrid);
+    L.hist = take(sizeof(fciqmc_row) * z.hist_cap);
+    L.total = off;
+    return L;
+}
+
+float f32_down(double x) {
+    float f = (float)x;
+    if ((double)f > x) f = std::nextafter(f, -INFINITY);
+    return f;
+}
+float f32_up(double x) {
+    float f = (float)x;
+    if ((double)f < x) f = std::nextafter(f, INFINITY);
+    return f;
+}
+
+}  // namespace
+
+struct fciqmc_handle {
+    Params P;
+    Sizes z;
+    Layout L;
+    char *ws;
+    cudaStream_t stream;
+    fciqmc_info info;
+    int sweep_grid, heavy_grid, ann_grid, small_grid;
+    size_t smem_w;
+    double e_core;
+    cudaGraphExec_t graph;
+    bool graph_ready;
+};
+
+namespace {
+
+template <typename T>
+T *at(fciqmc_handle *h, size_t off) {
+    return reinterpret_cast<T *>(h->ws + off);
+}
+
+template <int W>
+int configure_kernels(fciqmc_handle *h) {
+    FQ_CUDA(cudaFuncSetAttribute(fq::k_annihilate<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem_w));
+    FQ_CUDA(cudaFuncSetAttribute(fq::k_prepare_list<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem_w));
+    FQ_CUDA(cudaFuncSetAttribute(fq::k_reference_energy<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem_w));
+    int dev = 0, sms = 0, per_sm = 0;
+    FQ_CUDA(cudaGetDevice(&dev));
+    FQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    FQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fq::k_sweep<W>, fq::kTile, 0));
+    h->sweep_grid = std::min(kMaxGrid, std::max(1, sms * std::max(per_sm, 1)));
+    FQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fq::k_annihilate<W>, 256, h->smem_w));
+    h->ann_grid = std::min(kMaxGrid, std::max(1, sms * std::max(per_sm, 1)));
+    h->heavy_grid = std::min(kMaxGrid, sms * 4);
+    h->small_grid = std::min(kMaxGrid, sms * 8);
+    h->info.num_sms = sms;
+    h->info.grid_blocks = h->sweep_grid;
+    h->P.sweep_grid = h->sweep_grid;
+    return FCIQMC_OK;
+}
+
+template <int W>
+void enqueue_iteration(fciqmc_handle *h, cudaStream_t s) {
+    const Params &P = h->P;
+    fq::k_compact_copy<W><<<h->small_grid, 256, 0, s>>>(P);
+    fq::k_index_clear<<<h->small_grid, 256, 0, s>>>(P, 0);
+    fq::k_index_fill<W><<<h->small_grid, 256, 0, s>>>(P, 0);
+    fq::k_compact_finish<<<1, 32, 0, s>>>(P);
+    fq::k_sweep<W><<<h->sweep_grid, fq::kTile, 0, s>>>(P);
+    fq::k_heavy<W><<<h->heavy_grid, fq::kTile, 0, s>>>(P);
+    fq::k_annihilate<W><<<h->ann_grid, 256, h->smem_w, s>>>(P);
+    fq::k_finish<<<1, 32, 0, s>>>(P);
+}
+
+void enqueue(fciqmc_handle *h, cudaStream_t s) {
+    if (h->z.W == 1) enqueue_iteration<1>(h, s);
+    else enqueue_iteration<2>(h, s);
+}
+
+int build_graph(fciqmc_handle *h) {
+    cudaStream_t cs;
+    FQ_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        enqueue(h, cs);
+        e = cudaStreamEndCapture(cs, &g);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&h->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    h->graph_ready = (e == cudaSuccess);
+    cudaGetLastError();
+    return FCIQMC_OK;
+}
+
+template <int W>
+void launch_index_rebuild(fciqmc_handle *h) {
+    fq::k_index_clear<<<h->small_grid, 256, 0, h->stream>>>(h->P, 1);
+    fq::k_index_fill<W><<<h->small_grid, 256, 0, h->stream>>>(h->P, 1);
+}
+
+template <int W>
+void launch_prepare(fciqmc_handle *h, long long n, int compute) {
+    long long blocks = std::min<long long>((n + 255) / 256, h->small_grid);
+    if (blocks < 1) blocks = 1;
+    fq::k_prepare_list<W><<<(unsigned)blocks, 256, h->smem_w, h->stream>>>(h->P, n, compute);
+}
+
+int read_state(fciqmc_handle *h, DevState &st) {
+    FQ_CUDA(cudaMemcpyAsync(&st, h->P.st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+    FQ_CUDA(cudaStreamSynchronize(h->stream));
+    return FCIQMC_OK;
+}
+
+int check_det(const fciqmc_handle *h, const uint64_t *d) {
+    int n = 0;
+    for (int w = 0; w < h->z.W; ++w) {
+        uint64_t x = d[w];
+        int hi_bits = h->z.n_so - 64 * w;
+        if (hi_bits < 64 && (x >> hi_bits) != 0) return 0;
+        n += __builtin_popcountll(x);
+    }
+    return n == h->P.n_elec;
+}
+
+}  // namespace
+
+extern "C" {
+
+void fciqmc_default_options(fciqmc_options *opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->shift_damping = 0.05;
+    opt->shift_period = 10;
+    opt->initial_population = 10;
+    opt->initial_shift = 0.0;
+    opt->target_walkers = 1LL << 62;
+    opt->seed = 1;
+    opt->p_double = 0.0;
+    opt->main_capacity = 1LL << 20;
+    opt->spawn_capacity = 0;
+    opt->history_capacity = 1LL << 16;
+    opt->reference = nullptr;
+}
+
+size_t fciqmc_workspace_bytes(int n_elec, int n_orb, const fciqmc_options *opt) {
+    fciqmc_options o;
+    if (opt) o = *opt;
+    else fciqmc_default_options(&o);
+    Sizes z;
+    if (!sizes_of(n_elec, n_orb, o, z)) return 0;
+    return layout_of(z, n_orb).total;
+}
+
+const char *fciqmc_strerror(int status) {
+    switch (status) {
+        case FCIQMC_OK: return "ok";
+        case FCIQMC_ERR_INVALID_ARG: return "invalid argument";
+        case FCIQMC_ERR_CAPACITY: return "capacity exceeded (main list, hash index or spawn table)";
+        case FCIQMC_ERR_NUMERIC: return "population or spawn count outside int32";
+        case FCIQMC_ERR_TIMEOUT: return "bounded device wait timed out";
+        case FCIQMC_ERR_CUDA: return "CUDA runtime error";
+        case FCIQMC_ERR_UNSUPPORTED: return "unsupported size (n_orb <= 64, n_elec <= 64)";
+        case FCIQMC_ERR_WORKSPACE: return "workspace too small or not 256-byte aligned";
+        default: return "unknown status";
+    }
+}
+
+int fciqmc_create(const double *h1, const double *eri_s8, double e_core, int n_elec, int n_orb, int ms2,
+                  const int32_t *orb_irrep, double tau, int32_t initiator_threshold, const fciqmc_options *opt,
+                  void *workspace, size_t workspace_bytes, void *cuda_stream, fciqmc_handle **out) {
+    if (!out) return FCIQMC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!h1 || !eri_s8 || !(tau > 0.0) || !std::isfinite(tau)) return FCIQMC_ERR_INVALID_ARG;
+    fciqmc_options o;
+    if (opt) o = *opt;
+    else fciqmc_default_options(&o);
+    if (o.shift_period < 1 || o.initial_population == 0 || o.target_walkers < 0) return FCIQMC_ERR_INVALID_ARG;
+    Sizes z;
+    if (!sizes_of(n_elec, n_orb, o, z)) return FCIQMC_ERR_UNSUPPORTED;
+    Layout L = layout_of(z, n_orb);
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0 || workspace_bytes < L.total)
+        return FCIQMC_ERR_WORKSPACE;
+    // reference determinant
+    uint64_t ref[2] = {0, 0};
+    if (o.reference) {
+        ref[0] = o.reference[0];
+        if (z.W == 2) ref[1] = o.reference[1];
+    } else {
+        if ((n_elec + ms2) % 2 != 0 || ms2 < -n_elec || ms2 > n_elec) return FCIQMC_ERR_INVALID_ARG;
+        int na = (n_elec + ms2) / 2, nb = (n_elec - ms2) / 2;
+        if (na > n_orb || nb > n_orb) return FCIQMC_ERR_INVALID_ARG;
+        for (int p = 0; p < na; ++p) ref[(2 * p) >> 6] |= 1ull << ((2 * p) & 63);
+        for (int p = 0; p < nb; ++p) ref[(2 * p + 1) >> 6] |= 1ull << ((2 * p + 1) & 63);
+    }
+    int max_irrep = 0;
+    if (orb_irrep) {
+        for (int p = 0; p < n_orb; ++p) {
+            if (orb_irrep[p] < 0 || orb_irrep[p] > 7) return FCIQMC_ERR_INVALID_ARG;
+            max_irrep = std::max(max_irrep, (int)orb_irrep[p]);
+        }
+    }
+
+    fciqmc_handle *h = new (std::nothrow) fciqmc_handle();
+    if (!h) return FCIQMC_ERR_INVALID_ARG;
+    h->z = z;
+    h->L = L;
+    h->ws = static_cast<char *>(workspace);
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    h->e_core = e_core;
+    h->graph_ready = false;
+    h->smem_w = sizeof(double) * (2 * n_orb * n_orb + n_orb);
+
+    Params &P = h->P;
+    std::memset(&P, 0, sizeof(P));
+    P.n_elec = n_elec;
+    P.n_orb = n_orb;
+    P.n_so = z.n_so;
+    P.npairs = z.npairs;
+    P.n_irrep_used = max_irrep + 1;
+    P.init_thr = initiator_threshold < 0 ? -1 : initiator_threshold;
+    P.seed = (unsigned)(o.seed & 0xFFFFFFFFull);
+    P.tau = tau;
+    P.period = o.shift_period;
+    P.target = o.target_walkers;
+    P.c_shift = o.shift_damping / ((double)o.shift_period * tau);
+    P.tau_lo = f32_down(tau);
+    P.tau_hi = f32_up(tau);
+    P.h = at<double>(h, L.h);
+    P.eri = at<double>(h, L.eri);
+    P.eri_f = at<float>(h, L.eri_f);
+    P.wpair = at<double>(h, L.wpair);
+    P.map1 = at<unsigned long long>(h, L.map1);
+    P.cmask = at<unsigned long long>(h, L.cmask);
+    P.irrep = at<unsigned char>(h, L.irrep);
+    P.pairs = at<unsigned short>(h, L.pairs);
+    P.recip = at<double>(h, L.recip);
+    P.ref[0] = ref[0];
+    P.ref[1] = ref[1];
+    P.ref_occ = at<unsigned char>(h, L.ref_occ);
+    for (int b = 0; b < 2; ++b) {
+        P.det[b] = at<unsigned long long>(h, L.det[b]);
+        P.hd[b] = at<double>(h, L.hd[b]);
+        P.hdf[b] = at<float>(h, L.hdf[b]);
+        P.pop[b][0] = at<int>(h, L.pop[b][0]);
+        P.pop[b][1] = at<int>(h, L.pop[b][1]);
+    }
+    P.cap = z.cap;
+    P.idx = at<unsigned long long>(h, L.idx);
+    P.idx_cap = z.idx_cap;
+    P.idx_bits = log2_exact(z.idx_cap);
+    P.idx_stride = z.W == 1 ? 2 : 4;
+    P.mt = at<unsigned long long>(h, L.mt);
+    P.mt_cap = z.mt_cap;
+    P.mt_bits = log2_exact(z.mt_cap);
+    P.merged = at<unsigned>(h, L.merged);
+    P.chunks = at<uint4>(h, L.chunks);
+    P.chunk_cap = z.chunk_cap;
+    P.partial = at<double>(h, L.partial);
+    P.hist = at<fciqmc_row>(h, L.hist);
+    P.hist_cap = z.hist_cap;
+    P.st = at<DevState>(h, L.state);
+
+    int rc = FCIQMC_OK;
+    cudaStream_t s = h->stream;
+    // host-side tables: class masks, irreps, electron pairs, reference occupations
+    std::vector<unsigned long long> cmask(fq::NCLASS * fq::MAXW, 0ull);
+    std::vector<unsigned char> irr(fq::MAXSO, 0);
+    for (int k = 0; k < z.n_so; ++k) {
+        int g = orb_irrep ? orb_irrep[k >> 1] : 0;
+        int cl = g * 2 + (k & 1);
+        cmask[cl * fq::MAXW + (k >> 6)] |= 1ull << (k & 63);
+    }
+    for (int p = 0; p < n_orb; ++p) irr[p] = orb_irrep ? (unsigned char)orb_irrep[p] : 0;
+    std::vector<unsigned short> pairs(std::max(z.npairs, 1), 0);
+    for (int j = 1, k = 0; j < n_elec; ++j)
+        for (int i = 0; i < j; ++i) pairs[k++] = (unsigned short)(i | (j << 8));
+    std::vector<unsigned char> ref_occ(fq::MAXN, 0);
+    {
+        int n = 0;
+        for (int k = 0; k < z.n_so; ++k)
+            if ((ref[k >> 6] >> (k & 63)) & 1ull) {
+                if (n < fq::MAXN) ref_occ[n] = (unsigned char)k;
+                ++n;
+            }
+        if (n != n_elec) { delete h; return FCIQMC_ERR_INVALID_ARG; }
+    }
+    if (z.W == 1 && ref[1] != 0) { delete h; return FCIQMC_ERR_INVALID_ARG; }
+
+#define FQ_TRY(call)                               \
+    do {                                           \
+        if ((call) != cudaSuccess) {               \
+            rc = FCIQMC_ERR_CUDA;                  \
+            goto fail;                             \
+        }                                          \
+    } while (0)
+    {
+        FQ_TRY(cudaMemsetAsync(P.st, 0, sizeof(DevState), s));
+        FQ_TRY(cudaMemcpyAsync(const_cast<double *>(P.h), h1, sizeof(double) * n_orb * n_orb, cudaMemcpyHostToDevice, s));
+        FQ_TRY(cudaMemcpyAsync(const_cast<double *>(P.eri), eri_s8, sizeof(double) * z.n_eri, cudaMemcpyHostToDevice, s));
+        FQ_TRY(cudaMemcpyAsync(const_cast<unsigned long long *>(P.cmask), cmask.data(), sizeof(unsigned long long) * cmask.size(), cudaMemcpyHostToDevice, s));
+        FQ_TRY(cudaMemcpyAsync(const_cast<unsigned char *>(P.irrep), irr.data(), irr.size(), cudaMemcpyHostToDevice, s));
+        FQ_TRY(cudaMemcpyAsync(const_cast<unsigned short *>(P.pairs), pairs.data(), sizeof(unsigned short) * pairs.size(), cudaMemcpyHostToDevice, s));
+        FQ_TRY(cudaMemcpyAsync(const_cast<unsigned char *>(P.ref_occ), ref_occ.data(), ref_occ.size(), cudaMemcpyHostToDevice, s));
+        long long *facts = at<long long>(h, L.facts);
+        double *e0 = at<double>(h, L.e0);
+        if (z.W == 1) {
+            if (configure_kernels<1>(h) != FCIQMC_OK) { rc = FCIQMC_ERR_CUDA; goto fail; }
+            fq::k_setup<1><<<1, 256, 0, s>>>(P, z.n_eri, const_cast<unsigned long long *>(P.map1), const_cast<double *>(P.wpair),
+                                             const_cast<float *>(P.eri_f), const_cast<double *>(P.recip), facts, e0);
+            fq::k_reference_energy<1><<<1, 256, h->smem_w, s>>>(P, e0);
+        } else {
+            if (configure_kernels<2>(h) != FCIQMC_OK) { rc = FCIQMC_ERR_CUDA; goto fail; }
+            fq::k_setup<2><<<1, 256, 0, s>>>(P, z.n_eri, const_cast<unsigned long long *>(P.map1), const_cast<double *>(P.wpair),
+                                             const_cast<float *>(P.eri_f), const_cast<double *>(P.recip), facts, e0);
+            fq::k_reference_energy<2><<<1, 256, h->smem_w, s>>>(P, e0);
+        }
+        FQ_TRY(cudaGetLastError());
+        long long hf[4];
+        double E0;
+        FQ_TRY(cudaMemcpyAsync(hf, facts, sizeof(hf), cudaMemcpyDeviceToHost, s));
+        FQ_TRY(cudaMemcpyAsync(&E0, e0, sizeof(double), cudaMemcpyDeviceToHost, s));
+        FQ_TRY(cudaStreamSynchronize(s));
+        // P_double from the reference's allowed excitations (Sec. VI), realised exactly by the draw
+        double pd = o.p_double > 0.0 ? o.p_double : (double)hf[1] / (double)(hf[0] + hf[1]);
+        if (pd > 1.0) pd = 1.0;
+        unsigned long long d53 = (unsigned long long)(pd * 0x1.0p53);
+        double p_double = (double)d53 * 0x1.0p-53;
+        double p_single = 1.0 - p_double;
+        P.d53 = d53;
+        P.E0 = E0;
+        P.cs = tau / p_single;
+        P.cd = tau / p_double;
+        P.cd_lo = f32_down(P.cd);
+        P.cd_hi = f32_up(P.cd);
+        // initial state: the reference with the initial population
+        DevState st0;
+        std::memset(&st0, 0, sizeof(st0));
+        st0.iter = 0;
+        st0.shift = o.initial_shift;
+        st0.list_len = 1;
+        st0.claim = 1;
+        FQ_TRY(cudaMemcpyAsync(P.st, &st0, sizeof(st0), cudaMemcpyHostToDevice, s));
+        FQ_TRY(cudaMemcpyAsync(P.det[0], ref, sizeof(uint64_t) * z.W, cudaMemcpyHostToDevice, s));
+        int p0 = o.initial_population;
+        FQ_TRY(cudaMemcpyAsync(P.pop[0][0], &p0, sizeof(int), cudaMemcpyHostToDevice, s));
+        if (z.W == 1) {
+            launch_prepare<1>(h, 1, 1);
+            launch_index_rebuild<1>(h);
+        } else {
+            launch_prepare<2>(h, 1, 1);
+            launch_index_rebuild<2>(h);
+        }
+        FQ_TRY(cudaGetLastError());
+        // empty spawn table: EMPTY keys, zero payloads
+        fq::k_mt_clear<<<h->small_grid, 256, 0, s>>>(P, z.W);
+        FQ_TRY(cudaGetLastError());
+        DevState chk;
+        if (read_state(h, chk) != FCIQMC_OK) { rc = FCIQMC_ERR_CUDA; goto fail; }
+        if (chk.status != 0) { rc = chk.status; goto fail; }
+
+        fciqmc_info &I = h->info;
+        I.n_elec = n_elec;
+        I.n_orb = n_orb;
+        I.words = z.W;
+        I.e0 = E0;
+        I.e_core = e_core;
+        I.p_double = p_double;
+        I.d53 = d53;
+        I.n_single_ref = hf[0];
+        I.n_double_ref = hf[1];
+        I.reference[0] = ref[0];
+        I.reference[1] = ref[1];
+        I.main_capacity = z.cap;
+        I.index_capacity = z.idx_cap;
+        I.spawn_capacity = z.mt_cap;
+        I.history_capacity = z.hist_cap;
+        I.workspace_bytes = L.total;
+        build_graph(h);
+    }
+#undef FQ_TRY
+    *out = h;
+    return FCIQMC_OK;
+fail:
+    delete h;
+    return rc;
+}
+
+int fciqmc_step(fciqmc_handle *h, int32_t n_iterations) {
+    if (!h || n_iterations < 0) return FCIQMC_ERR_INVALID_ARG;
+    for (int i = 0; i < n_iterations; ++i) {
+        if (h->graph_ready) FQ_CUDA(cudaGraphLaunch(h->graph, h->stream));
+        else enqueue(h, h->stream);
+    }
+    FQ_CUDA(cudaGetLastError());
+    return FCIQMC_OK;
+}
+
+int fciqmc_profile(fciqmc_handle *h, int32_t n_iterations, double *kernel_ms) {
+    if (!h || !kernel_ms || n_iterations < 0) return FCIQMC_ERR_INVALID_ARG;
+    cudaEvent_t ev[FCIQMC_N_KERNELS + 1];
+    for (int k = 0; k <= FCIQMC_N_KERNELS; ++k) FQ_CUDA(cudaEventCreate(&ev[k]));
+    const Params &P = h->P;
+    cudaStream_t s = h->stream;
+    for (int it = 0; it < n_iterations; ++it) {
+        cudaEventRecord(ev[0], s);
+        for (int k = 0; k < FCIQMC_N_KERNELS; ++k) {
+            if (h->z.W == 1) {
+                switch (k) {
+                    case 0: fq::k_compact_copy<1><<<h->small_grid, 256, 0, s>>>(P); break;
+                    case 1: fq::k_index_clear<<<h->small_grid, 256, 0, s>>>(P, 0); break;
+                    case 2: fq::k_index_fill<1><<<h->small_grid, 256, 0, s>>>(P, 0); break;
+                    case 3: fq::k_compact_finish<<<1, 32, 0, s>>>(P); break;
+                    case 4: fq::k_sweep<1><<<h->sweep_grid, fq::kTile, 0, s>>>(P); break;
+                    case 5: fq::k_heavy<1><<<h->heavy_grid, fq::kTile, 0, s>>>(P); break;
+                    case 6: fq::k_annihilate<1><<<h->ann_grid, 256, h->smem_w, s>>>(P); break;
+                    default: fq::k_finish<<<1, 32, 0, s>>>(P); break;
+                }
+            } else {
+                switch (k) {
+                    case 0: fq::k_compact_copy<2><<<h->small_grid, 256, 0, s>>>(P); break;
+                    case 1: fq::k_index_clear<<<h->small_grid, 256, 0, s>>>(P, 0); break;
+                    case 2: fq::k_index_fill<2><<<h->small_grid, 256, 0, s>>>(P, 0); break;
+                    case 3: fq::k_compact_finish<<<1, 32, 0, s>>>(P); break;
+                    case 4: fq::k_sweep<2><<<h->sweep_grid, fq::kTile, 0, s>>>(P); break;
+                    case 5: fq::k_heavy<2><<<h->heavy_grid, fq::kTile, 0, s>>>(P); break;
+                    case 6: fq::k_annihilate<2><<<h->ann_grid, 256, h->smem_w, s>>>(P); break;
+                    default: fq::k_finish<<<1, 32, 0, s>>>(P); break;
+                }
+            }
+            cudaEventRecord(ev[k + 1], s);
+        }
+        FQ_CUDA(cudaGetLastError());
+        FQ_CUDA(cudaEventSynchronize(ev[FCIQMC_N_KERNELS]));
+        for (int k = 0; k < FCIQMC_N_KERNELS; ++k) {
+            float ms = 0.f;
+            FQ_CUDA(cudaEventElapsedTime(&ms, ev[k], ev[k + 1]));
+            kernel_ms[k] += ms;
+        }
+    }
+    for (int k = 0; k <= FCIQMC_N_KERNELS; ++k) cudaEventDestroy(ev[k]);
+    return FCIQMC_OK;
+}
+
+int fciqmc_sync(fciqmc_handle *h) {
+    if (!h) return FCIQMC_ERR_INVALID_ARG;
+    int status = 0;
+    FQ_CUDA(cudaMemcpyAsync(&status, &h->P.st->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    FQ_CUDA(cudaStreamSynchronize(h->stream));
+    return status;
+}
+
+int fciqmc_estimators(fciqmc_handle *h, fciqmc_estimates *out) {
+    if (!h || !out) return FCIQMC_ERR_INVALID_ARG;
+    DevState *st = h->P.st;
+    FQ_CUDA(cudaMemsetAsync(&st->est_nw, 0, sizeof(unsigned long long) * 2 + sizeof(long long), h->stream));
+    const int blocks = std::min(h->small_grid, kMaxGrid);
+    if (h->z.W == 1) fq::k_estimate<1><<<blocks, 256, 0, h->stream>>>(h->P);
+    else fq::k_estimate<2><<<blocks, 256, 0, h->stream>>>(h->P);
+    fq::k_estimate_finish<<<1, 32, 0, h->stream>>>(h->P, blocks);
+    FQ_CUDA(cudaGetLastError());
+    DevState s;
+    int rc = read_state(h, s);
+    if (rc != FCIQMC_OK) return rc;
+    std::memset(out, 0, sizeof(*out));
+    out->iteration = s.iter;
+    out->shift = s.shift;
+    out->e_ref = h->P.E0 + h->e_core;
+    out->e_shift = out->e_ref + s.shift;
+    out->proj_num = s.est_num;
+    out->c0 = s.est_c0;
+    out->n_walkers = (int64_t)s.est_nw;
+    out->n_dets = (int64_t)s.est_nd;
+    out->e_proj = s.est_c0 != 0 ? out->e_ref + s.est_num / (double)s.est_c0 : NAN;
+    out->vary_shift = s.vary;
+    out->status = s.status;
+    out->list_slots = s.list_len;
+    out->compactions = s.compactions;
+    out->exact_spawns = (int64_t)s.exact_spawn;
+    out->exact_deaths = (int64_t)s.exact_death;
+    return s.status;
+}
+
+int fciqmc_history(fciqmc_handle *h, fciqmc_row *rows, int64_t max_rows, int64_t *n_rows) {
+    if (!h || !n_rows || max_rows < 0 || (max_rows > 0 && !rows)) return FCIQMC_ERR_INVALID_ARG;
+    DevState s;
+    int rc = read_state(h, s);
+    if (rc != FCIQMC_OK) return rc;
+    const long long avail = std::min<long long>(s.hist_n, h->z.hist_cap);
+    const long long n = std::min<long long>(avail, max_rows);
+    for (long long k = 0; k < n; ++k) {
+        long long idx = (s.hist_n - n + k) % h->z.hist_cap;
+        FQ_CUDA(cudaMemcpyAsync(rows + k, h->P.hist + idx, sizeof(fciqmc_row), cudaMemcpyDeviceToHost, h->stream));
+    }
+    FQ_CUDA(cudaStreamSynchronize(h->stream));
+    *n_rows = n;
+    return FCIQMC_OK;
+}
+
+int fciqmc_n_dets(fciqmc_handle *h, int64_t *n_dets) {
+    fciqmc_estimates e;
+    int rc = fciqmc_estimators(h, &e);
+    if (n_dets) *n_dets = e.n_dets;
+    return rc == e.status ? FCIQMC_OK : rc;
+}
+
+int fciqmc_get_walkers(fciqmc_handle *h, uint64_t *dets, int32_t *pops, double *hdiag, int64_t cap, int64_t *n) {
+    if (!h || !n || cap < 0 || (cap > 0 && (!dets || !pops))) return FCIQMC_ERR_INVALID_ARG;
+    DevState *st = h->P.st;
+    FQ_CUDA(cudaMemsetAsync(&st->new_len, 0, sizeof(unsigned long long), h->stream));
+    if (h->z.W == 1) fq::k_gather<1><<<h->small_grid, 256, 0, h->stream>>>(h->P);
+    else fq::k_gather<2><<<h->small_grid, 256, 0, h->stream>>>(h->P);
+    FQ_CUDA(cudaGetLastError());
+    DevState s;
+    int rc = read_state(h, s);
+    if (rc != FCIQMC_OK) return rc;
+    const long long cnt = (long long)s.new_len;
+    *n = cnt;
+    if (cnt > cap) {
+        FQ_CUDA(cudaMemsetAsync(&st->new_len, 0, sizeof(unsigned long long), h->stream));
+        FQ_CUDA(cudaStreamSynchronize(h->stream));
+        return FCIQMC_ERR_CAPACITY;
+    }
+    const int other = s.lb ^ 1;
+    if (cnt > 0) {
+        FQ_CUDA(cudaMemcpyAsync(dets, h->P.det[other], sizeof(uint64_t) * h->z.W * cnt, cudaMemcpyDeviceToHost, h->stream));
+        FQ_CUDA(cudaMemcpyAsync(pops, h->P.pop[other][s.pp], sizeof(int32_t) * cnt, cudaMemcpyDeviceToHost, h->stream));
+        if (hdiag) FQ_CUDA(cudaMemcpyAsync(hdiag, h->P.hd[other], sizeof(double) * cnt, cudaMemcpyDeviceToHost, h->stream));
+    }
+    FQ_CUDA(cudaMemsetAsync(&st->new_len, 0, sizeof(unsigned long long), h->stream));
+    FQ_CUDA(cudaStreamSynchronize(h->stream));
+    return FCIQMC_OK;
+}
+
+int fciqmc_set_walkers(fciqmc_handle *h, const uint64_t *dets, const int32_t *pops, const double *hdiag, int64_t n,
+                       const fciqmc_state *stin) {
+    if (!h || n < 0 || (n > 0 && (!dets || !pops))) return FCIQMC_ERR_INVALID_ARG;
+    if (n > h->z.cap) return FCIQMC_ERR_CAPACITY;
+    for (int64_t k = 0; k < n; ++k) {
+        if (pops[k] == 0 || pops[k] == INT32_MIN) return FCIQMC_ERR_INVALID_ARG;
+        if (!check_det(h, dets + k * h->z.W)) return FCIQMC_ERR_INVALID_ARG;
+    }
+    DevState cur;
+    int rc = read_state(h, cur);
+    if (rc != FCIQMC_OK) return rc;
+    DevState st0;
+    std::memset(&st0, 0, sizeof(st0));
+    if (stin) {
+        st0.iter = stin->iteration;
+        st0.shift = stin->shift;
+        st0.vary = stin->vary_shift;
+        st0.n_since = stin->shift_counter;
+        st0.nw_prev = stin->nw_last_update;
+    } else {
+        st0.iter = cur.iter;
+        st0.shift = cur.shift;
+        st0.vary = cur.vary;
+        st0.n_since = cur.n_since;
+        st0.nw_prev = cur.nw_prev;
+    }
+    st0.list_len = n;
+    st0.claim = (unsigned long long)n;
+    cudaStream_t s = h->stream;
+    FQ_CUDA(cudaMemcpyAsync(h->P.st, &st0, sizeof(st0), cudaMemcpyHostToDevice, s));
+    if (n > 0) {
+        FQ_CUDA(cudaMemcpyAsync(h->P.det[0], dets, sizeof(uint64_t) * h->z.W * n, cudaMemcpyHostToDevice, s));
+        FQ_CUDA(cudaMemcpyAsync(h->P.pop[0][0], pops, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+        if (hdiag) FQ_CUDA(cudaMemcpyAsync(h->P.hd[0], hdiag, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    }
+    if (h->z.W == 1) {
+        launch_prepare<1>(h, n, hdiag ? 0 : 1);
+        launch_index_rebuild<1>(h);
+    } else {
+        launch_prepare<2>(h, n, hdiag ? 0 : 1);
+        launch_index_rebuild<2>(h);
+    }
+    FQ_CUDA(cudaGetLastError());
+    // a failed step may have left claimed entries in the spawn table
+    fq::k_mt_clear<<<h->small_grid, 256, 0, s>>>(h->P, h->z.W);
+    FQ_CUDA(cudaGetLastError());
+    return fciqmc_sync(h);
+}
+
+int fciqmc_get_state(fciqmc_handle *h, fciqmc_state *out) {
+    if (!h || !out) return FCIQMC_ERR_INVALID_ARG;
+    DevState s;
+    int rc = read_state(h, s);
+    if (rc != FCIQMC_OK) return rc;
+    out->iteration = s.iter;
+    out->shift = s.shift;
+    out->vary_shift = s.vary;
+    out->shift_counter = s.n_since;
+    out->nw_last_update = s.nw_prev;
+    return FCIQMC_OK;
+}
+
+int fciqmc_get_info(const fciqmc_handle *h, fciqmc_info *info) {
+    if (!h || !info) return FCIQMC_ERR_INVALID_ARG;
+    *info = h->info;
+    return FCIQMC_OK;
+}
+
+void fciqmc_destroy(fciqmc_handle *h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    if (h->graph_ready) cudaGraphExecDestroy(h->graph);
+    delete h;
+}
+
+}  // extern "C"

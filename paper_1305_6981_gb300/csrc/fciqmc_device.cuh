@@ -1,0 +1,388 @@
+// Device building blocks of the FCIQMC walker cycle (sm_103a).
+//
+// Determinants are W uint64 words (W = 1 or 2); spin orbital k is bit k & 63
+// of word k >> 6, spatial orbital k >> 1, spin k & 1 (Sec. III bit strings).
+// Floating-point expressions that decide walker counts are written with
+// explicit round-to-nearest intrinsics (__dadd_rn, __dmul_rn, ...), which the
+// compiler never contracts into FMAs, so the values are the IEEE results of
+// the operation order stated next to each one.
+#pragma once
+
+#include <cstdint>
+#include <math_constants.h>
+
+#include "fciqmc.h"
+
+namespace fq {
+
+constexpr int MAXW = 2;
+constexpr int MAXN = 64;     // electrons
+constexpr int MAXSO = 128;   // spin orbitals
+constexpr int NCLASS = 16;   // 8 irreps x 2 spins
+constexpr int MAXPAIRS = MAXN * (MAXN - 1) / 2;
+constexpr unsigned long long EMPTY = ~0ull;
+constexpr int NCNT = 9;      // per-iteration counters, same order as fciqmc_row from `attempts`
+
+// ---------------------------------------------------------------------------
+// Shared state of one run, in device memory.
+struct DevState {
+    long long iter;            // iterations completed (keys the random numbers of the next one)
+    double shift;
+    int vary, n_since;
+    long long nw_prev;
+    int lb, pp;                // active list buffer, population parity
+    long long list_len;        // slots in use (live + vacated) in the active list
+    unsigned long long claim;  // slot claim counter during annihilation
+    int status;                // sticky error status (0 = OK)
+    int compact_pending;
+    unsigned long long n_merged, n_chunks;
+    unsigned long long nw_in, nd_in;
+    long long c0_in;
+    unsigned long long d_nw, d_nd;  // two's-complement signed changes
+    unsigned long long cnt[NCNT];
+    unsigned long long new_len;
+    unsigned long long exact_spawn, exact_death;  // exact-path evaluations (diagnostics)
+    long long hist_n;
+    long long compactions;
+    // last estimator sweep
+    unsigned long long est_nw, est_nd;
+    long long est_c0;
+    double est_num;
+};
+
+// Uniform parameters of a run, passed by value to every kernel.
+struct Params {
+    int n_elec, n_orb, n_so, npairs, n_irrep_used;
+    int init_thr;
+    unsigned seed;
+    unsigned long long d53;
+    double tau, cs, cd, E0, c_shift;
+    float tau_lo, tau_hi, cd_lo, cd_hi;   // float bounds: tau_lo <= tau <= tau_hi, cd_lo <= cd <= cd_hi
+    int period;
+    int sweep_grid;                        // blocks of k_sweep (number of partial sums)
+    int idx_stride;                        // 64-bit words per index entry
+    long long target;
+    // read-only tables
+    const double *h;        // n_orb x n_orb
+    const double *eri;      // packed 8-fold
+    const float *eri_f;     // same, rounded to float
+    const double *wpair;    // [2][n_orb][n_orb]: [0] opposite spin (pp|qq), [1] same spin (pp|qq) - (pq|qp)
+    const unsigned long long *map1;   // n_so, orbital map of Algorithm 1
+    const unsigned long long *cmask;  // [NCLASS][MAXW] spin orbitals of each (irrep, spin) class
+    const unsigned char *irrep;       // n_orb
+    const unsigned short *pairs;      // npairs: (i | j << 8), i < j electron indices
+    const double *recip;              // recip[L] = 1.0 / L, L < 2 * MAXSO + 2
+    unsigned long long ref[MAXW];
+    const unsigned char *ref_occ;     // n_elec ascending spin orbitals of the reference
+    // main list, two buffers for compaction, two population arrays per buffer
+    unsigned long long *det[2];
+    double *hd[2];
+    float *hdf[2];
+    int *pop[2][2];
+    long long cap;
+    // hash index: det -> slot
+    unsigned long long *idx;
+    long long idx_cap;
+    int idx_bits;
+    // spawn merge table
+    unsigned long long *mt;
+    long long mt_cap;
+    int mt_bits;
+    unsigned *merged;
+    uint4 *chunks;
+    long long chunk_cap;
+    double *partial;
+    fciqmc_row *hist;
+    long long hist_cap;
+    DevState *st;
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        unsigned lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        unsigned lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// Two 64-bit words keyed by (seed, iteration), counter (attempt, tag, fingerprint).
+__device__ __forceinline__ void draw2(unsigned a, unsigned tag, unsigned long long fp, unsigned seed, unsigned iter,
+                                      unsigned long long &w0, unsigned long long &w1) {
+    uint4 o = philox4x32_10(make_uint4(a, tag, (unsigned)fp, (unsigned)(fp >> 32)), make_uint2(seed, iter));
+    w0 = (unsigned long long)o.x | ((unsigned long long)o.y << 32);
+    w1 = (unsigned long long)o.z | ((unsigned long long)o.w << 32);
+}
+
+// floor(r * n / 2^64): uniform rank in [0, n)
+__device__ __forceinline__ unsigned rank_of(unsigned long long r, unsigned n) {
+    return (unsigned)__umul64hi(r, (unsigned long long)n);
+}
+
+// ---------------------------------------------------------------------------
+// bit-string helpers
+template <int W>
+__device__ __forceinline__ int bit_of(const unsigned long long (&d)[W], int k) {
+    return (int)((d[k >> 6] >> (k & 63)) & 1ull);
+}
+template <int W>
+__device__ __forceinline__ void flip(unsigned long long (&d)[W], int k) {
+    d[k >> 6] ^= 1ull << (k & 63);
+}
+// bits [0, n) of a 64-bit word, n in [0, 64]
+__device__ __forceinline__ unsigned long long low_bits(int n) {
+    return n >= 64 ? ~0ull : ((1ull << n) - 1ull);
+}
+// occupied spin orbitals strictly between k and l
+template <int W>
+__device__ __forceinline__ int count_between(const unsigned long long (&d)[W], int k, int l) {
+    int lo = min(k, l) + 1, hi = max(k, l);
+    int c = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        int a = max(lo - 64 * w, 0), b = min(hi - 64 * w, 64);
+        if (b > a) c += __popcll(d[w] & low_bits(b) & ~low_bits(a));
+    }
+    return c;
+}
+// position of the k-th (0-based) set bit of a 64-bit word (k < popc(x))
+__device__ __forceinline__ int select64(unsigned long long x, int k) {
+    int pos = 0, c;
+    c = __popc((unsigned)x);
+    if (k >= c) { k -= c; x >>= 32; pos += 32; }
+    c = __popc((unsigned)(x & 0xFFFFu));
+    if (k >= c) { k -= c; x >>= 16; pos += 16; }
+    c = __popc((unsigned)(x & 0xFFu));
+    if (k >= c) { k -= c; x >>= 8; pos += 8; }
+    c = __popc((unsigned)(x & 0xFu));
+    if (k >= c) { k -= c; x >>= 4; pos += 4; }
+    c = __popc((unsigned)(x & 0x3u));
+    if (k >= c) { k -= c; x >>= 2; pos += 2; }
+    c = (int)(x & 1u);
+    if (k >= c) { pos += 1; }
+    return pos;
+}
+template <int W>
+__device__ __forceinline__ int select_bit(const unsigned long long (&m)[W], int k) {
+    if (W == 1) return select64(m[0], k);
+    int c0 = __popcll(m[0]);
+    return k < c0 ? select64(m[0], k) : 64 + select64(m[W - 1], k - c0);
+}
+template <int W>
+__device__ __forceinline__ bool det_eq(const unsigned long long (&a)[W], const unsigned long long *b) {
+    bool e = true;
+#pragma unroll
+    for (int w = 0; w < W; ++w) e = e && (a[w] == b[w]);
+    return e;
+}
+
+// ---------------------------------------------------------------------------
+// integrals
+__device__ __forceinline__ int pidx(int p, int q) { return p >= q ? p * (p + 1) / 2 + q : q * (q + 1) / 2 + p; }
+__device__ __forceinline__ int eidx(int p, int q, int r, int s) {
+    int a = pidx(p, q), b = pidx(r, s);
+    return a >= b ? a * (a + 1) / 2 + b : b * (b + 1) / 2 + a;
+}
+__device__ __forceinline__ double eri_d(const Params &P, int p, int q, int r, int s) {
+    return __ldg(P.eri + eidx(p, q, r, s));
+}
+__device__ __forceinline__ float eri_f(const Params &P, int p, int q, int r, int s) {
+    return __ldg(P.eri_f + eidx(p, q, r, s));
+}
+
+// Algorithm 1 over the ascending occupied list: hash = p hash + map(orb_i) i (uint64 wraparound).
+__device__ __forceinline__ unsigned long long fingerprint(const unsigned char *occ, int n, const unsigned long long *map1) {
+    unsigned long long h = 0;
+    for (int i = 0; i < n; ++i) h = 1099511628211ull * h + map1[occ[i]] * (unsigned long long)(i + 1);
+    return h;
+}
+
+// Slater-Condon, single i -> a from source d (occupied list occ of d), exact FP64 in ascending order.
+template <int W>
+__device__ double hij_single(const Params &P, const unsigned long long (&d)[W], const unsigned char *occ, int i, int a) {
+    int I = i >> 1, A = a >> 1;
+    double v = __ldg(P.h + I * P.n_orb + A);
+    for (int x = 0; x < P.n_elec; ++x) {
+        int j = occ[x];
+        if (j == i) continue;
+        int J = j >> 1;
+        v = __dadd_rn(v, eri_d(P, I, A, J, J));
+        if ((j & 1) == (i & 1)) v = __dsub_rn(v, eri_d(P, I, J, J, A));
+    }
+    return (count_between<W>(d, i, a) & 1) ? -v : v;
+}
+
+// Parity of i -> a then j -> b (i < j, a < b) applied to d.
+template <int W>
+__device__ __forceinline__ int double_parity(const unsigned long long (&d)[W], int i, int j, int a, int b) {
+    unsigned long long t[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) t[w] = d[w];
+    int par = count_between<W>(t, i, a);
+    flip<W>(t, i);
+    flip<W>(t, a);
+    par += count_between<W>(t, j, b);
+    return par & 1;
+}
+
+// Slater-Condon, double (i<j) -> (a<b), exact FP64: 0 + (ia|jb) - (ib|ja) with spin deltas.
+template <int W>
+__device__ __forceinline__ double hij_double(const Params &P, const unsigned long long (&d)[W], int i, int j, int a, int b) {
+    double v = 0.0;
+    if ((i & 1) == (a & 1) && (j & 1) == (b & 1)) v = __dadd_rn(v, eri_d(P, i >> 1, a >> 1, j >> 1, b >> 1));
+    if ((i & 1) == (b & 1) && (j & 1) == (a & 1)) v = __dsub_rn(v, eri_d(P, i >> 1, b >> 1, j >> 1, a >> 1));
+    return double_parity<W>(d, i, j, a, b) ? -v : v;
+}
+
+// <D|H|D_0> from the reference side (projected-energy numerator, Eq. 2); 0 beyond doubles.
+template <int W>
+__device__ double h0i(const Params &P, const unsigned long long (&d)[W]) {
+    unsigned long long ref[W], holes[W], parts[W];
+    int nd = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        ref[w] = P.ref[w];
+        holes[w] = ref[w] & ~d[w];
+        parts[w] = d[w] & ~ref[w];
+        nd += __popcll(holes[w]) + __popcll(parts[w]);
+    }
+    if (nd == 2) {
+        int i = select_bit<W>(holes, 0), a = select_bit<W>(parts, 0);
+        return hij_single<W>(P, ref, P.ref_occ, i, a);
+    }
+    if (nd == 4) {
+        int i = select_bit<W>(holes, 0), j = select_bit<W>(holes, 1);
+        int a = select_bit<W>(parts, 0), b = select_bit<W>(parts, 1);
+        return hij_double<W>(P, ref, i, j, a, b);
+    }
+    return 0.0;
+}
+
+// Diagonal: sum_p h_pp (ascending) then, for p < q ascending, the pair term
+// (pp|qq) - delta_spin (pq|qp) added to the running sum. w: wpair table in shared memory.
+template <int W>
+__device__ double hdiag(const Params &P, const unsigned long long (&d)[W], const double *w, const double *hdiag_tab) {
+    const int M = P.n_orb;
+    double v = 0.0;
+#pragma unroll
+    for (int wa = 0; wa < W; ++wa) {
+        unsigned long long m = d[wa];
+        while (m) {
+            int k = 64 * wa + __ffsll((long long)m) - 1;
+            m &= m - 1;
+            v = __dadd_rn(v, hdiag_tab[k >> 1]);
+        }
+    }
+#pragma unroll
+    for (int wa = 0; wa < W; ++wa) {
+        unsigned long long m = d[wa];
+        while (m) {
+            int p = 64 * wa + __ffsll((long long)m) - 1;
+            m &= m - 1;
+            const double *row_same = w + M * M + (p >> 1) * M;
+            const double *row_diff = w + (p >> 1) * M;
+            // q > p: the rest of this word, then the following words
+            unsigned long long m2 = m;
+            int wb = wa;
+            while (true) {
+                while (m2) {
+                    int q = 64 * wb + __ffsll((long long)m2) - 1;
+                    m2 &= m2 - 1;
+                    double t = ((p & 1) == (q & 1)) ? row_same[q >> 1] : row_diff[q >> 1];
+                    v = __dadd_rn(v, t);
+                }
+                if (++wb >= W) break;
+                m2 = d[wb];
+            }
+        }
+    }
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// hash tables
+__device__ __forceinline__ unsigned long long mix64(unsigned long long x) {
+    x ^= x >> 31;
+    x *= 0x7FB5D329728EA185ull;
+    x ^= x >> 27;
+    x *= 0x81DADEF4BC2DD44Dull;
+    x ^= x >> 33;
+    return x;
+}
+template <int W>
+__device__ __forceinline__ unsigned long long table_hash(const unsigned long long (&d)[W], unsigned long long salt) {
+    unsigned long long x = mix64(d[0] ^ salt);
+    if (W == 2) x = mix64(x ^ (d[W - 1] * 0x9E3779B97F4A7C15ull));
+    return x;
+}
+
+__device__ __forceinline__ void cas128(unsigned long long *addr, unsigned long long c0, unsigned long long c1,
+                                       unsigned long long n0, unsigned long long n1, unsigned long long &o0,
+                                       unsigned long long &o1) {
+    asm volatile(
+        "{\n\t.reg .b128 c, n, o;\n\t"
+        "mov.b128 c, {%2, %3};\n\t"
+        "mov.b128 n, {%4, %5};\n\t"
+        "atom.global.cas.b128 o, [%6], c, n;\n\t"
+        "mov.b128 {%0, %1}, o;\n\t}"
+        : "=l"(o0), "=l"(o1)
+        : "l"(c0), "l"(c1), "l"(n0), "l"(n1), "l"(addr)
+        : "memory");
+}
+
+// Atomically claim an EMPTY key slot for `key` or report what is there: returns true if the slot now
+// holds `key` (claimed by us when *claimed is set).
+template <int W>
+__device__ __forceinline__ bool claim_key(unsigned long long *e, const unsigned long long (&key)[W], bool &claimed) {
+    claimed = false;
+    if (W == 1) {
+        unsigned long long old = atomicCAS(e, EMPTY, key[0]);
+        if (old == EMPTY) { claimed = true; return true; }
+        return old == key[0];
+    } else {
+        unsigned long long o0, o1;
+        cas128(e, EMPTY, EMPTY, key[0], key[W - 1], o0, o1);
+        if (o0 == EMPTY && o1 == EMPTY) { claimed = true; return true; }
+        return o0 == key[0] && o1 == key[W - 1];
+    }
+}
+
+// Volatile read of a key; `maybe_torn` is set when some word is still EMPTY (another thread may be
+// in the middle of writing it), in which case only an atomic CAS can tell what is there.
+template <int W>
+__device__ __forceinline__ int probe_key(const unsigned long long *e, const unsigned long long (&key)[W]) {
+    // 0: different key, 1: our key, 2: EMPTY or possibly being written
+    unsigned long long k0 = *(volatile const unsigned long long *)e;
+    if (W == 1) return k0 == key[0] ? 1 : (k0 == EMPTY ? 2 : 0);
+    unsigned long long k1 = *(volatile const unsigned long long *)(e + 1);
+    if (k0 == key[0] && k1 == key[W - 1]) return 1;
+    if (k0 == EMPTY || k1 == EMPTY) return 2;
+    return 0;
+}
+
+// Index/merge entry strides in 64-bit words (key words + one payload word, padded to a power of two)
+template <int W>
+struct Stride { static constexpr int v = (W == 1) ? 2 : 4; };
+
+// Warp-aggregated append: all 32 lanes must call it. Returns the position for lanes with want, else -1.
+__device__ __forceinline__ long long warp_append(unsigned long long *ctr, bool want) {
+    const unsigned full = 0xFFFFFFFFu;
+    unsigned m = __ballot_sync(full, want);
+    if (m == 0) return -1;
+    int lane = threadIdx.x & 31;
+    int leader = __ffs(m) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(ctr, (unsigned long long)__popc(m));
+    base = __shfl_sync(full, base, leader);
+    if (!want) return -1;
+    return (long long)(base + __popc(m & ((1u << lane) - 1u)));
+}
+
+__device__ __forceinline__ void set_status(DevState *st, int code) { atomicCAS(&st->status, 0, code); }
+
+}  // namespace fq

@@ -1,0 +1,953 @@
+// Kernels of one FCIQMC iteration (sm_103a).
+//
+// Per iteration, on the caller's stream (or as one CUDA graph):
+//   [compaction, only when flagged]  k_compact_copy -> k_index_clear -> k_index_fill -> k_compact_finish
+//   k_sweep        estimators of the incoming list, death/cloning (Eq. 4), and every spawning
+//                  attempt (Eq. 3, Sec. VI) of determinants with |C_i| <= kHeavy, merged on the fly
+//                  into the spawn table (sum of signed amounts, initiator flags counted)
+//   k_heavy        the attempts of determinants with |C_i| > kHeavy, split into chunks
+//   k_annihilate   the merged spawns against the post-death main list through the hash index, with
+//                  the initiator filter and H_ii on insertion (Sec. V B)
+//   k_finish       deterministic reduction of the projected-energy numerator, history row, shift
+//                  update, population parity flip
+#pragma once
+
+#include "fciqmc_device.cuh"
+
+namespace fq {
+
+constexpr int kTile = 256;          // determinants per sweep tile = threads per sweep block
+constexpr int kHeavy = 1024;        // |C_i| above this: attempts go to the chunked heavy path
+constexpr int kChunk = 2048;        // attempts per heavy chunk
+constexpr unsigned long long kSaltMerge = 0x5851F42D4C957F2Dull;
+constexpr unsigned long long kSaltIndex = 0x14057B7EF767814Full;
+constexpr unsigned long long kFlagUnit = 1ull << 40;  // merge payload: (#initiator spawns << 40) + amount
+
+enum { C_ATTEMPTS = 0, C_NULLS, C_EVENTS, C_SPAWNED, C_DEATH, C_CLONE, C_MERGED, C_ABORTED, C_INSERTED };
+
+// Per-determinant data used by every attempt from it, kept in shared memory.
+template <int W>
+struct DetView {
+    unsigned long long d[W];
+    unsigned long long fp;
+    int c;
+    unsigned char nok;      // electrons with at least one symmetry-allowed single (N - delta_s)
+    unsigned char flag;     // initiator
+    unsigned char cnt[NCLASS];
+    unsigned char occ[MAXN];
+};
+
+struct Tables {
+    unsigned long long map1[MAXSO];
+    unsigned long long mask[NCLASS * MAXW];
+    unsigned char irrep[MAXSO / 2];
+    unsigned short pairs[MAXPAIRS];
+};
+
+__device__ __forceinline__ void load_tables(const Params &P, Tables &T) {
+    for (int k = threadIdx.x; k < P.n_so; k += blockDim.x) T.map1[k] = P.map1[k];
+    for (int k = threadIdx.x; k < NCLASS * MAXW; k += blockDim.x) T.mask[k] = P.cmask[k];
+    for (int k = threadIdx.x; k < P.n_orb; k += blockDim.x) T.irrep[k] = P.irrep[k];
+    for (int k = threadIdx.x; k < P.npairs; k += blockDim.x) T.pairs[k] = P.pairs[k];
+}
+
+// ---------------------------------------------------------------------------- interval bounds
+// An interval [lo, hi] that contains a real number, propagated with directed rounding.
+struct Iv { float lo, hi; };
+// x rounded to nearest float as f: x lies within |f| 2^-24 (+ a subnormal guard) of f
+__device__ __forceinline__ Iv iv_rn(float f) {
+    float e = __fmaf_ru(fabsf(f), 0x1p-24f, 1e-30f);
+    return {__fsub_rd(f, e), __fadd_ru(f, e)};
+}
+__device__ __forceinline__ Iv iv_sub(Iv a, Iv b) { return {__fsub_rd(a.lo, b.hi), __fsub_ru(a.hi, b.lo)}; }
+__device__ __forceinline__ Iv iv_abs(Iv a) {
+    if (a.lo >= 0.f) return a;
+    if (a.hi <= 0.f) return {-a.hi, -a.lo};
+    return {0.f, fmaxf(-a.lo, a.hi)};
+}
+// product of nonnegative intervals
+__device__ __forceinline__ Iv iv_mul(Iv a, Iv b) { return {__fmul_rd(a.lo, b.lo), __fmul_ru(a.hi, b.hi)}; }
+// widen by the relative error of the FP64 evaluation (a few ulp of 2^-53)
+__device__ __forceinline__ Iv iv_slack(Iv a) { return {__fmul_rd(a.lo, 1.0f - 0x1p-20f), __fmul_ru(a.hi, 1.0f + 0x1p-20f)}; }
+
+// Decision n = floor(p) + [u < p - floor(p)] for p in the (nonnegative) interval pv and u = (r >> 11) 2^-53:
+// returns 0 or 1 when the bounds decide it, -1 when the exact FP64 evaluation is needed.
+__device__ __forceinline__ int bernoulli_decide(Iv pv, unsigned long long r) {
+    if (!(pv.hi < 1.0f)) return -1;
+    float u_lo = (float)(unsigned)(r >> 40) * 0x1p-24f;  // top 24 bits: u_lo <= u < u_lo + 2^-24
+    float u_hi = u_lo + 0x1p-24f;
+    if (u_lo > pv.hi) return 0;
+    if (pv.lo > 0.f && u_hi <= pv.lo) return 1;
+    return -1;
+}
+
+__device__ __forceinline__ double unit53(unsigned long long r) { return __dmul_rn(__ull2double_rn(r >> 11), 0x1p-53); }
+
+// ---------------------------------------------------------------------------- spawn merge table
+template <int W>
+__device__ __forceinline__ bool merge_insert(const Params &P, const unsigned long long (&key)[W], unsigned long long val,
+                                             unsigned &pos) {
+    constexpr int S = Stride<W>::v;
+    const unsigned long long mask = (unsigned long long)P.mt_cap - 1ull;
+    unsigned long long h = table_hash<W>(key, kSaltMerge) >> (64 - P.mt_bits);
+    for (long long probe = 0; probe < P.mt_cap; ++probe) {
+        unsigned long long *e = P.mt + h * S;
+        int r = probe_key<W>(e, key);
+        if (r == 1) {
+            atomicAdd(e + W, val);
+            return false;
+        }
+        if (r == 2) {
+            bool claimed;
+            if (claim_key<W>(e, key, claimed)) {
+                atomicAdd(e + W, val);
+                if (claimed) pos = (unsigned)h;
+                return claimed;
+            }
+        }
+        h = (h + 1ull) & mask;
+    }
+    set_status(P.st, FCIQMC_ERR_CAPACITY);
+    return false;
+}
+
+// ---------------------------------------------------------------------------- per-determinant preparation
+template <int W>
+__device__ __forceinline__ void prepare_det(const Params &P, const Tables &T, DetView<W> &v, int c) {
+    int n = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        unsigned long long m = v.d[w];
+        while (m) {
+            v.occ[n++] = (unsigned char)(64 * w + __ffsll((long long)m) - 1);
+            m &= m - 1;
+        }
+    }
+    const int ncls = 2 * P.n_irrep_used;
+    for (int cl = 0; cl < NCLASS; ++cl) {
+        int u = 0;
+        if (cl < ncls) {
+#pragma unroll
+            for (int w = 0; w < W; ++w) u += __popcll(~v.d[w] & T.mask[cl * MAXW + w]);
+        }
+        v.cnt[cl] = (unsigned char)u;
+    }
+    int nok = 0;
+    for (int x = 0; x < P.n_elec; ++x) {
+        int k = v.occ[x];
+        nok += v.cnt[T.irrep[k >> 1] * 2 + (k & 1)] > 0;
+    }
+    v.nok = (unsigned char)nok;
+    v.fp = fingerprint(v.occ, P.n_elec, T.map1);
+    v.c = c;
+    int ac = c < 0 ? -c : c;
+    bool is_ref = det_eq<W>(v.d, P.ref);
+    v.flag = (P.init_thr < 0 || ac > P.init_thr || is_ref) ? 1 : 0;
+}
+
+// ---------------------------------------------------------------------------- one spawning attempt
+struct AttemptOut {
+    bool claimed;
+    unsigned pos;
+};
+
+template <int W>
+__device__ __forceinline__ AttemptOut spawn_attempt(const Params &P, const Tables &T, const DetView<W> &v, unsigned a,
+                                                     unsigned iter, unsigned long long *cnt) {
+    AttemptOut out{false, 0u};
+    unsigned long long r0, r1, r2, r3, r4, r5;
+    draw2(a, 0u, v.fp, P.seed, iter, r0, r1);
+    draw2(a, 1u, v.fp, P.seed, iter, r2, r3);
+    const bool dbl = (r0 >> 11) < P.d53;
+    unsigned long long child[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) child[w] = v.d[w];
+    int n = 0, sgn_h = 0;
+    if (!dbl) {
+        // single excitation (Sec. VI A): i uniform over the N - delta_s electrons with M_allow > 0
+        if (v.nok == 0) { cnt[C_NULLS]++; return out; }
+        unsigned k1 = rank_of(r1, v.nok);
+        int i = -1;
+        for (int x = 0; x < P.n_elec; ++x) {
+            int k = v.occ[x];
+            if (v.cnt[T.irrep[k >> 1] * 2 + (k & 1)] > 0) {
+                if (k1 == 0) { i = k; break; }
+                --k1;
+            }
+        }
+        const int ci = T.irrep[i >> 1] * 2 + (i & 1);
+        const unsigned mallow = v.cnt[ci];
+        unsigned k2 = rank_of(r2, mallow);
+        unsigned long long um[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) um[w] = ~v.d[w] & T.mask[ci * MAXW + w];
+        const int ao = select_bit<W>(um, (int)k2);
+        flip<W>(child, i);
+        flip<W>(child, ao);
+        double hv = hij_single<W>(P, v.d, v.occ, i, ao);
+        if (hv == 0.0) return out;
+        // p = (|H| (tau / P_single)) (M_allow (N - delta_s))
+        double p = __dmul_rn(__dmul_rn(fabs(hv), P.cs), (double)((long long)mallow * (long long)v.nok));
+        draw2(a, 2u, v.fp, P.seed, iter, r4, r5);
+        double fl = floor(p);
+        if (fl >= 2147483647.0) { set_status(P.st, FCIQMC_ERR_NUMERIC); return out; }
+        n = (int)fl + (unit53(r4) < __dsub_rn(p, fl) ? 1 : 0);
+        sgn_h = hv > 0.0 ? 1 : -1;
+    } else {
+        // double excitation (Sec. VI B): pair by inverse triangular index, a among the "good" unoccupied
+        // orbitals of allowed spin, b from the class fixed by symmetry (Eq. sym1) and spin
+        if (P.npairs == 0) { cnt[C_NULLS]++; return out; }
+        unsigned k1 = rank_of(r1, (unsigned)P.npairs);
+        unsigned short pr = T.pairs[k1];
+        const int i = v.occ[pr & 0xFF], j = v.occ[pr >> 8];
+        const int si = i & 1, sj = j & 1;
+        const int gij = T.irrep[i >> 1] ^ T.irrep[j >> 1];
+        unsigned G = 0;
+        unsigned long long gm[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) gm[w] = 0ull;
+        for (int sa = 0; sa < 2; ++sa) {
+            if (si == sj && sa != si) continue;
+            const int sb = si + sj - sa;
+            for (int g = 0; g < P.n_irrep_used; ++g) {
+                const int ca = g * 2 + sa, cb = (gij ^ g) * 2 + sb;
+                const int avail = (int)v.cnt[cb] - (ca == cb ? 1 : 0);
+                if (avail >= 1 && v.cnt[ca] > 0) {
+                    G += v.cnt[ca];
+#pragma unroll
+                    for (int w = 0; w < W; ++w) gm[w] |= T.mask[ca * MAXW + w];
+                }
+            }
+        }
+        if (G == 0) { cnt[C_NULLS]++; return out; }
+#pragma unroll
+        for (int w = 0; w < W; ++w) gm[w] &= ~v.d[w];
+        const int ao = select_bit<W>(gm, (int)rank_of(r2, G));
+        const int ca = T.irrep[ao >> 1] * 2 + (ao & 1);
+        const int cb = (gij ^ T.irrep[ao >> 1]) * 2 + (si + sj - (ao & 1));
+        const unsigned m_ba = v.cnt[cb] - (ca == cb ? 1u : 0u);
+        const unsigned m_ab = v.cnt[ca] - (ca == cb ? 1u : 0u);
+        unsigned long long bm[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) bm[w] = ~v.d[w] & T.mask[cb * MAXW + w];
+        bm[ao >> 6] &= ~(1ull << (ao & 63));
+        const int bo = select_bit<W>(bm, (int)rank_of(r3, m_ba));
+        const int A = min(ao, bo), B = max(ao, bo);
+        // p = ((|H| (tau / P_double)) (npairs G M^(b|a) M^(a|b))) (1 / (M^(b|a) + M^(a|b)))
+        const long long K = (long long)P.npairs * (long long)G * (long long)m_ba * (long long)m_ab;
+        const unsigned L = m_ba + m_ab;
+        const bool t1 = ((i & 1) == (A & 1)) && ((j & 1) == (B & 1));
+        const bool t2 = ((i & 1) == (B & 1)) && ((j & 1) == (A & 1));
+        // bounds on |H| from the float copy of the integrals
+        Iv x = {0.f, 0.f}, y = {0.f, 0.f};
+        if (t1) x = iv_rn(eri_f(P, i >> 1, A >> 1, j >> 1, B >> 1));
+        if (t2) y = iv_rn(eri_f(P, i >> 1, B >> 1, j >> 1, A >> 1));
+        Iv hv = iv_sub(x, y);
+        const int par = double_parity<W>(v.d, i, j, A, B);
+        Iv ah = iv_abs(hv);
+        Iv pv = iv_mul(iv_mul(iv_mul(ah, Iv{P.cd_lo, P.cd_hi}),
+                              Iv{__ll2float_rd(K), __ll2float_ru(K)}),
+                       Iv{__frcp_rd((float)L), __frcp_ru((float)L)});
+        pv = iv_slack(pv);
+        draw2(a, 2u, v.fp, P.seed, iter, r4, r5);
+        const int dec = bernoulli_decide(pv, r4);
+        if (dec == 0) return out;
+        if (dec == 1 && (hv.lo > 0.f || hv.hi < 0.f)) {
+            n = 1;
+            sgn_h = (hv.lo > 0.f) ? 1 : -1;
+            if (par) sgn_h = -sgn_h;
+        } else {
+            atomicAdd(&P.st->exact_spawn, 1ull);
+            double hd = hij_double<W>(P, v.d, i, j, A, B);
+            if (hd == 0.0) return out;
+            double p = __dmul_rn(__dmul_rn(__dmul_rn(fabs(hd), P.cd), (double)K), P.recip[L]);
+            double fl = floor(p);
+            if (fl >= 2147483647.0) { set_status(P.st, FCIQMC_ERR_NUMERIC); return out; }
+            n = (int)fl + (unit53(r4) < __dsub_rn(p, fl) ? 1 : 0);
+            sgn_h = hd > 0.0 ? 1 : -1;
+        }
+        flip<W>(child, i);
+        flip<W>(child, j);
+        flip<W>(child, ao);
+        flip<W>(child, bo);
+    }
+    if (n == 0) return out;
+    cnt[C_EVENTS]++;
+    cnt[C_SPAWNED] += (unsigned long long)n;
+    const long long amt = -(long long)(v.c > 0 ? 1 : -1) * sgn_h * (long long)n;
+    const unsigned long long val = (v.flag ? kFlagUnit : 0ull) + (unsigned long long)amt;
+    out.claimed = merge_insert<W>(P, child, val, out.pos);
+    return out;
+}
+
+// ---------------------------------------------------------------------------- death / cloning (Eq. 4)
+// r = (tau ((H_ii - E0) - S)) |C|; n = floor(|r|) + [u < frac |r|]; C -= sign(C) n for r >= 0, += for r < 0.
+template <int W>
+__device__ __forceinline__ int death_step(const Params &P, const DetView<W> &v, float hdf, const double *hd_ptr,
+                                          double S, float S_lo, float S_hi, unsigned iter,
+                                          unsigned long long *cnt) {
+    const int c = v.c;
+    const unsigned ac = (unsigned)(c < 0 ? -c : c);
+    unsigned long long u, unused;
+    draw2(0u, 3u, v.fp, P.seed, iter, u, unused);
+    Iv hb = iv_rn(hdf);
+    Iv t = iv_sub(hb, Iv{S_lo, S_hi});
+    Iv at = iv_abs(t);
+    Iv ar = iv_slack(iv_mul(iv_mul(at, Iv{P.tau_lo, P.tau_hi}), Iv{__uint2float_rd(ac), __uint2float_ru(ac)}));
+    int dec = bernoulli_decide(ar, u);
+    int nd;
+    bool positive;
+    if (dec == 0) {
+        return c;
+    } else if (dec == 1 && (t.lo > 0.f || t.hi < 0.f)) {
+        nd = 1;
+        positive = t.lo > 0.f;
+    } else {
+        atomicAdd(&P.st->exact_death, 1ull);
+        double hd = *hd_ptr;
+        double r = __dmul_rn(__dmul_rn(P.tau, __dsub_rn(hd, S)), (double)ac);
+        double arr = fabs(r);
+        double fl = floor(arr);
+        if (fl >= 2147483647.0) { set_status(P.st, FCIQMC_ERR_NUMERIC); return c; }
+        nd = (int)fl + (unit53(u) < __dsub_rn(arr, fl) ? 1 : 0);
+        positive = r >= 0.0;
+    }
+    long long sc = c > 0 ? 1 : -1;
+    long long nc;
+    if (positive) { nc = (long long)c - sc * nd; cnt[C_DEATH] += (unsigned long long)nd; }
+    else { nc = (long long)c + sc * nd; cnt[C_CLONE] += (unsigned long long)nd; }
+    if (nc > 2147483647LL || nc < -2147483647LL) { set_status(P.st, FCIQMC_ERR_NUMERIC); return c; }
+    return (int)nc;
+}
+
+// ---------------------------------------------------------------------------- reductions
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x) {
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xFFFFFFFFu, x, o);
+    return x;
+}
+__device__ __forceinline__ double warp_sum_f64(double x) {
+    for (int o = 16; o > 0; o >>= 1) x = __dadd_rn(x, __shfl_down_sync(0xFFFFFFFFu, x, o));
+    return x;
+}
+// Block-wide sums, added once per block to global counters; the FP64 value is returned to thread 0
+// (fixed order: lane tree, then warps in order).
+template <int NT>
+__device__ __forceinline__ void flush_u64(unsigned long long *dst, unsigned long long v, unsigned long long *s_red) {
+    v = warp_sum_u64(v);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < NT / 32; ++w) t += s_red[w];
+        if (t) atomicAdd(dst, t);
+    }
+    __syncthreads();
+}
+template <int NT>
+__device__ __forceinline__ double block_sum_f64(double v, double *s_red) {
+    v = warp_sum_f64(v);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < NT / 32; ++w) t = __dadd_rn(t, s_red[w]);
+    __syncthreads();
+    return t;
+}
+
+// ---------------------------------------------------------------------------- kernels
+template <int W>
+__global__ void __launch_bounds__(kTile) k_sweep(Params P) {
+    DevState *st = P.st;
+    if (st->status) return;
+    __shared__ Tables T;
+    __shared__ DetView<W> s_dv[kTile];
+    __shared__ unsigned s_off[kTile + 1];
+    __shared__ unsigned s_wsum[kTile / 32];
+    __shared__ unsigned long long s_red[kTile / 32];
+    __shared__ double s_redf[kTile / 32];
+    load_tables(P, T);
+    const int lb = st->lb, pp = st->pp;
+    const long long len = st->list_len;
+    const unsigned iter = (unsigned)st->iter;
+    const double S = st->shift;
+    const float S_lo = __double2float_rd(S), S_hi = __double2float_ru(S);
+    const unsigned long long *det = P.det[lb];
+    const float *hdf = P.hdf[lb];
+    const double *hd = P.hd[lb];
+    const int *pop_in = P.pop[lb][pp];
+    int *pop_out = P.pop[lb][pp ^ 1];
+    __syncthreads();
+
+    unsigned long long cnt[NCNT];
+#pragma unroll
+    for (int k = 0; k < NCNT; ++k) cnt[k] = 0;
+    unsigned long long nw = 0, nd = 0, dnw = 0, dnd = 0;
+    double num = 0.0;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    for (long long tb = (long long)blockIdx.x * kTile; tb < len; tb += (long long)gridDim.x * kTile) {
+        const long long s = tb + tid;
+        unsigned att = 0;
+        if (s < len) {
+            const int c = __ldcs(pop_in + s);
+            if (c == 0) {
+                pop_out[s] = 0;
+            } else {
+                DetView<W> &v = s_dv[tid];
+                if (W == 2) {
+                    ulonglong2 dd = __ldcs(reinterpret_cast<const ulonglong2 *>(det) + s);
+                    v.d[0] = dd.x;
+                    v.d[W - 1] = dd.y;
+                } else {
+                    v.d[0] = __ldcs(det + s);
+                }
+                const float hf = __ldcs(hdf + s);
+                prepare_det<W>(P, T, v, c);
+                const unsigned ac = (unsigned)(c < 0 ? -c : c);
+                nw += ac;
+                nd += 1;
+                unsigned long long xd = 0;
+                int diff = 0;
+#pragma unroll
+                for (int w = 0; w < W; ++w) { xd |= v.d[w] ^ P.ref[w]; diff += __popcll(v.d[w] ^ P.ref[w]); }
+                if (xd == 0) st->c0_in = c;
+                else if (diff == 2 || diff == 4) num = __dadd_rn(num, __dmul_rn(h0i<W>(P, v.d), (double)c));
+                const int nc = death_step<W>(P, v, hf, hd + s, S, S_lo, S_hi, iter, cnt);
+                pop_out[s] = nc;
+                dnw += (unsigned long long)((long long)(nc < 0 ? -nc : nc) - (long long)ac);
+                if (nc == 0) dnd += (unsigned long long)(-1LL);
+                cnt[C_ATTEMPTS] += ac;
+                if (ac > (unsigned)kHeavy) {
+                    const unsigned nch = (ac + kChunk - 1) / kChunk;
+                    const unsigned long long base = atomicAdd(&st->n_chunks, (unsigned long long)nch);
+                    if (base + nch > (unsigned long long)P.chunk_cap) {
+                        set_status(st, FCIQMC_ERR_CAPACITY);
+                    } else {
+                        for (unsigned q = 0; q < nch; ++q)
+                            P.chunks[base + q] = make_uint4((unsigned)s, q * kChunk, min((q + 1) * kChunk, ac), 0u);
+                    }
+                } else {
+                    att = ac;
+                }
+            }
+        }
+        // exclusive scan of attempts over the tile
+        unsigned x = att;
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_wsum[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            unsigned ws = lane < kTile / 32 ? s_wsum[lane] : 0u;
+            unsigned wx = ws;
+            for (int o = 1; o < 32; o <<= 1) {
+                unsigned y = __shfl_up_sync(0xFFFFFFFFu, wx, o);
+                if (lane >= o) wx += y;
+            }
+            if (lane < kTile / 32) s_wsum[lane] = wx - ws;
+            if (lane == kTile / 32 - 1) s_off[kTile] = wx;
+        }
+        __syncthreads();
+        s_off[tid] = x - att + s_wsum[warp];
+        __syncthreads();
+        const unsigned total = s_off[kTile];
+        for (unsigned base = 0; base < total; base += kTile) {
+            const unsigned k = base + tid;
+            AttemptOut ao{false, 0u};
+            if (k < total) {
+                int lo = 0, hi = kTile - 1;  // last d with s_off[d] <= k
+                while (lo < hi) {
+                    int mid = (lo + hi + 1) >> 1;
+                    if (s_off[mid] <= k) lo = mid; else hi = mid - 1;
+                }
+                ao = spawn_attempt<W>(P, T, s_dv[lo], k - s_off[lo], iter, cnt);
+            }
+            long long slot = warp_append(&st->n_merged, ao.claimed);
+            if (ao.claimed && slot < P.mt_cap) P.merged[slot] = ao.pos;
+        }
+        __syncthreads();
+    }
+    // block reductions
+    for (int k = 0; k < NCNT; ++k) flush_u64<kTile>(&st->cnt[k], cnt[k], s_red);
+    flush_u64<kTile>(&st->nw_in, nw, s_red);
+    flush_u64<kTile>(&st->nd_in, nd, s_red);
+    flush_u64<kTile>(&st->d_nw, dnw, s_red);
+    flush_u64<kTile>(&st->d_nd, dnd, s_red);
+    double bs = block_sum_f64<kTile>(num, s_redf);
+    if (threadIdx.x == 0) P.partial[blockIdx.x] = bs;
+}
+
+template <int W>
+__global__ void __launch_bounds__(kTile) k_heavy(Params P) {
+    DevState *st = P.st;
+    if (st->status) return;
+    __shared__ Tables T;
+    __shared__ DetView<W> v;
+    __shared__ unsigned long long s_red[kTile / 32];
+    load_tables(P, T);
+    const unsigned long long nch = st->n_chunks;
+    const int lb = st->lb, pp = st->pp;
+    const unsigned iter = (unsigned)st->iter;
+    unsigned long long cnt[NCNT];
+#pragma unroll
+    for (int k = 0; k < NCNT; ++k) cnt[k] = 0;
+    __syncthreads();
+    for (unsigned long long q = blockIdx.x; q < nch && q < (unsigned long long)P.chunk_cap; q += gridDim.x) {
+        const uint4 ch = P.chunks[q];
+        if (threadIdx.x == 0) {
+            const long long s = ch.x;
+#pragma unroll
+            for (int w = 0; w < W; ++w) v.d[w] = P.det[lb][s * W + w];
+            prepare_det<W>(P, T, v, P.pop[lb][pp][s]);
+        }
+        __syncthreads();
+        const unsigned n = ch.z - ch.y;
+        for (unsigned base = 0; base < n; base += kTile) {
+            const unsigned k = base + threadIdx.x;
+            AttemptOut ao{false, 0u};
+            if (k < n) ao = spawn_attempt<W>(P, T, v, ch.y + k, iter, cnt);
+            long long slot = warp_append(&st->n_merged, ao.claimed);
+            if (ao.claimed && slot < P.mt_cap) P.merged[slot] = ao.pos;
+        }
+        __syncthreads();
+    }
+    for (int k = 1; k < NCNT; ++k) flush_u64<kTile>(&st->cnt[k], cnt[k], s_red);
+}
+
+template <int W>
+__global__ void __launch_bounds__(256) k_annihilate(Params P) {
+    extern __shared__ double s_w[];  // [2][M][M] pair terms, then M diagonal h_pp
+    __shared__ unsigned long long s_red[256 / 32];
+    DevState *st = P.st;
+    if (st->status) return;
+    constexpr int S = Stride<W>::v;
+    const unsigned long long nm = st->n_merged;
+    const long long len = st->list_len;
+    // every block sees the same values, so either all blocks proceed or none changes anything
+    if (nm > (unsigned long long)(P.mt_cap / 4 * 3) || (long long)nm + len > P.cap ||
+        (long long)nm + len > P.idx_cap / 4 * 3) {
+        set_status(st, FCIQMC_ERR_CAPACITY);
+        return;
+    }
+    const int M = P.n_orb;
+    for (int k = threadIdx.x; k < 2 * M * M; k += blockDim.x) s_w[k] = P.wpair[k];
+    for (int k = threadIdx.x; k < M; k += blockDim.x) s_w[2 * M * M + k] = P.h[k * M + k];
+    __syncthreads();
+    const int lb = st->lb, pp = st->pp;
+    int *pop_out = P.pop[lb][pp ^ 1];
+    unsigned long long *det = P.det[lb];
+    const unsigned long long imask = (unsigned long long)P.idx_cap - 1ull;
+    unsigned long long dnw = 0, dnd = 0, aborted = 0, inserted = 0;
+
+    for (unsigned long long i0 = (unsigned long long)blockIdx.x * blockDim.x; i0 < nm;
+         i0 += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long i = i0 + threadIdx.x;
+        bool want = false;
+        unsigned long long key[W];
+        long long amt = 0;
+        unsigned long long h = 0;
+        if (i < nm) {
+            const unsigned pos = P.merged[i];
+            unsigned long long *e = P.mt + (unsigned long long)pos * S;
+#pragma unroll
+            for (int w = 0; w < W; ++w) key[w] = e[w];
+            const unsigned long long val = e[W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) e[w] = EMPTY;
+            e[W] = 0ull;
+            // payload = (#initiator spawns << 40) + signed amount
+            unsigned long long low = val & (kFlagUnit - 1ull);
+            amt = (low & (1ull << 39)) ? (long long)low - (long long)kFlagUnit : (long long)low;
+            const bool flag = ((val - (unsigned long long)amt) >> 40) != 0ull;
+            if (amt != 0) {
+                h = table_hash<W>(key, kSaltIndex) >> (64 - P.idx_bits);
+                long long slot = -1;
+                for (long long probe = 0; probe < P.idx_cap; ++probe) {
+                    const unsigned long long *x = P.idx + h * S;
+                    bool match = true, empty = true;
+#pragma unroll
+                    for (int w = 0; w < W; ++w) {
+                        unsigned long long kw = __ldcg(x + w);
+                        match = match && (kw == key[w]);
+                        empty = empty && (kw == EMPTY);
+                    }
+                    if (match) { slot = (long long)__ldcg(x + W); break; }
+                    if (empty) break;
+                    h = (h + 1ull) & imask;
+                }
+                const bool allow = P.init_thr < 0 || flag;
+                const unsigned long long aa = (unsigned long long)(amt < 0 ? -amt : amt);
+                if (slot >= 0) {
+                    const int old = pop_out[slot];
+                    if (old != 0) {
+                        long long nv = (long long)old + amt;
+                        if (nv > 2147483647LL || nv < -2147483647LL) set_status(st, FCIQMC_ERR_NUMERIC);
+                        pop_out[slot] = (int)nv;
+                        dnw += (unsigned long long)((nv < 0 ? -nv : nv) - (long long)(old < 0 ? -old : old));
+                        if (nv == 0) dnd += (unsigned long long)(-1LL);
+                    } else if (allow) {
+                        if (amt > 2147483647LL || amt < -2147483647LL) set_status(st, FCIQMC_ERR_NUMERIC);
+                        pop_out[slot] = (int)amt;
+                        dnw += aa;
+                        dnd += 1;
+                        inserted += 1;
+                    } else {
+                        aborted += aa;
+                    }
+                } else if (allow) {
+                    want = true;
+                } else {
+                    aborted += aa;
+                }
+            }
+        }
+        const long long ns = warp_append(&st->claim, want);
+        if (want) {
+            if (amt > 2147483647LL || amt < -2147483647LL) set_status(st, FCIQMC_ERR_NUMERIC);
+            double v = hdiag<W>(P, key, s_w, s_w + 2 * M * M);
+            double hdv = __dsub_rn(v, P.E0);
+#pragma unroll
+            for (int w = 0; w < W; ++w) det[ns * W + w] = key[w];
+            P.hd[lb][ns] = hdv;
+            P.hdf[lb][ns] = __double2float_rn(hdv);
+            pop_out[ns] = (int)amt;
+            // publish in the index (distinct keys only: no other thread inserts this determinant)
+            for (long long probe = 0; probe < P.idx_cap; ++probe) {
+                unsigned long long *x = P.idx + h * S;
+                bool claimed;
+                if (claim_key<W>(x, key, claimed)) {
+                    x[W] = (unsigned long long)ns;
+                    break;
+                }
+                h = (h + 1ull) & imask;
+            }
+            dnw += (unsigned long long)(amt < 0 ? -amt : amt);
+            dnd += 1;
+            inserted += 1;
+        }
+    }
+    flush_u64<256>(&st->d_nw, dnw, s_red);
+    flush_u64<256>(&st->d_nd, dnd, s_red);
+    flush_u64<256>(&st->cnt[C_ABORTED], aborted, s_red);
+    flush_u64<256>(&st->cnt[C_INSERTED], inserted, s_red);
+}
+
+// Natural logarithm from the atanh series (shift update); same operation order as the oracle's.
+__device__ double own_log(double x) {
+    const double LN2_HI = 0x1.62e42fe800000p-1;
+    const double LN2_LO = 0x1.e8e7bcd5e4f1ep-31;
+    const double SQRT2 = 0x1.6a09e667f3bcdp+0;
+    if (!(x > 0.0)) return x == 0.0 ? -CUDART_INF : CUDART_NAN;
+    if (isinf(x)) return x;
+    int e = 0;
+    if (x < 0x1.0p-1022) { x = __dmul_rn(x, 0x1.0p54); e = -54; }
+    unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    e += (int)((bits >> 52) & 0x7FFull) - 1023;
+    bits = (bits & 0x000FFFFFFFFFFFFFull) | 0x3FF0000000000000ull;
+    double m = __longlong_as_double((long long)bits);
+    if (m > SQRT2) { m = __dmul_rn(m, 0.5); e += 1; }
+    double s = __ddiv_rn(__dsub_rn(m, 1.0), __dadd_rn(m, 1.0));
+    double z = __dmul_rn(s, s);
+    double poly = __ddiv_rn(1.0, 23.0);
+    for (int k = 10; k >= 0; --k) poly = __dadd_rn(__dmul_rn(poly, z), __ddiv_rn(1.0, (double)(2 * k + 1)));
+    double t = __dmul_rn(s, poly);
+    double lnm = __dadd_rn(t, t);
+    double de = (double)e;
+    double r = __dadd_rn(lnm, __dmul_rn(de, LN2_LO));
+    return __dadd_rn(__dmul_rn(de, LN2_HI), r);
+}
+
+__global__ void k_finish(Params P) {
+    DevState *st = P.st;
+    if (threadIdx.x != 0 || st->status) return;
+    double num = 0.0;
+    for (int b = 0; b < P.sweep_grid; ++b) num = __dadd_rn(num, P.partial[b]);
+    const long long nw_in = (long long)st->nw_in, nd_in = (long long)st->nd_in;
+    const long long nw_out = nw_in + (long long)st->d_nw, nd_out = nd_in + (long long)st->d_nd;
+    fciqmc_row row;
+    row.iteration = st->iter;
+    row.shift = st->shift;
+    row.nw_in = nw_in;
+    row.nd_in = nd_in;
+    row.c0_in = st->c0_in;
+    row.num_in = num;
+    row.nw_out = nw_out;
+    row.nd_out = nd_out;
+    row.attempts = (long long)st->cnt[C_ATTEMPTS];
+    row.nulls = (long long)st->cnt[C_NULLS];
+    row.spawn_events = (long long)st->cnt[C_EVENTS];
+    row.spawned_walkers = (long long)st->cnt[C_SPAWNED];
+    row.death_walkers = (long long)st->cnt[C_DEATH];
+    row.clone_walkers = (long long)st->cnt[C_CLONE];
+    row.merged_entries = (long long)st->n_merged;
+    row.aborted_walkers = (long long)st->cnt[C_ABORTED];
+    row.inserted_dets = (long long)st->cnt[C_INSERTED];
+    P.hist[st->hist_n % P.hist_cap] = row;
+    st->hist_n++;
+    // shift: S <- S - zeta/(A tau) ln(N_w(n) / N_w(n-A)) every A iterations once N_w reached the target
+    if (!st->vary) {
+        if (nw_out >= P.target) { st->vary = 1; st->nw_prev = nw_out; st->n_since = 0; }
+    } else {
+        st->n_since++;
+        if (st->n_since == P.period) {
+            double ratio = __ddiv_rn((double)nw_out, (double)st->nw_prev);
+            st->shift = __dsub_rn(st->shift, __dmul_rn(P.c_shift, own_log(ratio)));
+            st->nw_prev = nw_out;
+            st->n_since = 0;
+        }
+    }
+    const long long new_len = (long long)st->claim;
+    st->list_len = new_len;
+    st->pp ^= 1;
+    st->iter++;
+    const long long vacated = new_len - nd_out;
+    if ((vacated > 64 && vacated * 4 > new_len) || (vacated > 0 && new_len * 4 > P.cap * 3))
+        st->compact_pending = 1;
+    st->n_merged = 0;
+    st->n_chunks = 0;
+    st->nw_in = st->nd_in = 0;
+    st->c0_in = 0;
+    st->d_nw = st->d_nd = 0;
+    for (int k = 0; k < NCNT; ++k) st->cnt[k] = 0;
+}
+
+// ---------------------------------------------------------------------------- compaction and index
+template <int W>
+__global__ void k_compact_copy(Params P) {
+    DevState *st = P.st;
+    if (!st->compact_pending || st->status) return;
+    const int lb = st->lb, pp = st->pp;
+    const long long len = st->list_len;
+    for (long long s0 = (long long)blockIdx.x * blockDim.x; s0 < len; s0 += (long long)gridDim.x * blockDim.x) {
+        const long long s = s0 + threadIdx.x;
+        int c = s < len ? P.pop[lb][pp][s] : 0;
+        const long long ns = warp_append(&st->new_len, c != 0);
+        if (c != 0) {
+#pragma unroll
+            for (int w = 0; w < W; ++w) P.det[lb ^ 1][ns * W + w] = P.det[lb][s * W + w];
+            P.hd[lb ^ 1][ns] = P.hd[lb][s];
+            P.hdf[lb ^ 1][ns] = P.hdf[lb][s];
+            P.pop[lb ^ 1][pp][ns] = c;
+        }
+    }
+}
+
+__global__ void k_index_clear(Params P, int force) {
+    DevState *st = P.st;
+    if (st->status || (!force && !st->compact_pending)) return;
+    const long long nwords = P.idx_cap * (P.idx_stride);
+    ulonglong2 *p = reinterpret_cast<ulonglong2 *>(P.idx);
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < nwords / 2; k += (long long)gridDim.x * blockDim.x)
+        p[k] = make_ulonglong2(EMPTY, EMPTY);
+}
+
+// Inserts slots [0, n) of a list buffer into the (cleared) index. force: rebuild the active list
+// (after set_walkers); otherwise the compacted list in the other buffer.
+template <int W>
+__global__ void k_index_fill(Params P, int force) {
+    DevState *st = P.st;
+    if (st->status || (!force && !st->compact_pending)) return;
+    constexpr int S = Stride<W>::v;
+    const int buf = force ? st->lb : (st->lb ^ 1);
+    const long long n = force ? st->list_len : (long long)st->new_len;
+    const unsigned long long imask = (unsigned long long)P.idx_cap - 1ull;
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
+        unsigned long long key[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) key[w] = P.det[buf][s * W + w];
+        unsigned long long h = table_hash<W>(key, kSaltIndex) >> (64 - P.idx_bits);
+        bool done = false;
+        for (long long probe = 0; probe < P.idx_cap; ++probe) {
+            unsigned long long *x = P.idx + h * S;
+            bool claimed;
+            if (claim_key<W>(x, key, claimed)) {
+                if (!claimed) set_status(st, FCIQMC_ERR_INVALID_ARG);  // duplicate determinant
+                else x[W] = (unsigned long long)s;
+                done = true;
+                break;
+            }
+            h = (h + 1ull) & imask;
+        }
+        if (!done) set_status(st, FCIQMC_ERR_CAPACITY);
+    }
+}
+
+// Empties the spawn merge table (EMPTY keys, zero payloads).
+__global__ void k_mt_clear(Params P, int W) {
+    const int S = P.idx_stride;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < P.mt_cap; e += (long long)gridDim.x * blockDim.x) {
+        for (int w = 0; w < W; ++w) P.mt[e * S + w] = EMPTY;
+        P.mt[e * S + W] = 0ull;
+    }
+}
+
+__global__ void k_compact_finish(Params P) {
+    DevState *st = P.st;
+    if (threadIdx.x != 0 || !st->compact_pending || st->status) return;
+    st->lb ^= 1;
+    st->list_len = (long long)st->new_len;
+    st->claim = st->new_len;
+    st->new_len = 0;
+    st->compact_pending = 0;
+    st->compactions++;
+}
+
+// ---------------------------------------------------------------------------- estimators, gather, setup
+template <int W>
+__global__ void __launch_bounds__(256) k_estimate(Params P) {
+    __shared__ unsigned long long s_red[8];
+    __shared__ double s_redf[8];
+    DevState *st = P.st;
+    const int lb = st->lb, pp = st->pp;
+    const long long len = st->list_len;
+    unsigned long long nw = 0, nd = 0;
+    double num = 0.0;
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < len; s += (long long)gridDim.x * blockDim.x) {
+        const int c = P.pop[lb][pp][s];
+        if (c == 0) continue;
+        unsigned long long d[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) d[w] = P.det[lb][s * W + w];
+        nw += (unsigned)(c < 0 ? -c : c);
+        nd += 1;
+        unsigned long long xd = 0;
+        int diff = 0;
+#pragma unroll
+        for (int w = 0; w < W; ++w) { xd |= d[w] ^ P.ref[w]; diff += __popcll(d[w] ^ P.ref[w]); }
+        if (xd == 0) st->est_c0 = c;
+        else if (diff == 2 || diff == 4) num = __dadd_rn(num, __dmul_rn(h0i<W>(P, d), (double)c));
+    }
+    flush_u64<256>(&st->est_nw, nw, s_red);
+    flush_u64<256>(&st->est_nd, nd, s_red);
+    double bs = block_sum_f64<256>(num, s_redf);
+    if (threadIdx.x == 0) P.partial[blockIdx.x] = bs;
+}
+
+__global__ void k_estimate_finish(Params P, int nblocks) {
+    if (threadIdx.x != 0) return;
+    double num = 0.0;
+    for (int b = 0; b < nblocks; ++b) num = __dadd_rn(num, P.partial[b]);
+    P.st->est_num = num;
+}
+
+// Copies the occupied entries of the active list to the other buffer (for read-back), count in new_len.
+template <int W>
+__global__ void k_gather(Params P) {
+    DevState *st = P.st;
+    const int lb = st->lb, pp = st->pp;
+    const long long len = st->list_len;
+    for (long long s0 = (long long)blockIdx.x * blockDim.x; s0 < len; s0 += (long long)gridDim.x * blockDim.x) {
+        const long long s = s0 + threadIdx.x;
+        int c = s < len ? P.pop[lb][pp][s] : 0;
+        const long long ns = warp_append(&st->new_len, c != 0);
+        if (c != 0) {
+#pragma unroll
+            for (int w = 0; w < W; ++w) P.det[lb ^ 1][ns * W + w] = P.det[lb][s * W + w];
+            P.hd[lb ^ 1][ns] = P.hd[lb][s];
+            P.pop[lb ^ 1][pp][ns] = c;
+        }
+    }
+}
+
+// Diagonal elements of slots [0, n) of list buffer 0: computed (compute != 0) or taken as given; the
+// float copy is the nearest float.
+template <int W>
+__global__ void __launch_bounds__(256) k_prepare_list(Params P, long long n, int compute) {
+    extern __shared__ double s_w[];
+    const int M = P.n_orb;
+    for (int k = threadIdx.x; k < 2 * M * M; k += blockDim.x) s_w[k] = P.wpair[k];
+    for (int k = threadIdx.x; k < M; k += blockDim.x) s_w[2 * M * M + k] = P.h[k * M + k];
+    __syncthreads();
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
+        double v;
+        if (compute) {
+            unsigned long long d[W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) d[w] = P.det[0][s * W + w];
+            v = __dsub_rn(hdiag<W>(P, d, s_w, s_w + 2 * M * M), P.E0);
+            P.hd[0][s] = v;
+        } else {
+            v = P.hd[0][s];
+        }
+        P.hdf[0][s] = __double2float_rn(v);
+    }
+}
+
+// Setup tables and reference facts: float integrals, pair terms, orbital map (Philox, key
+// ("FCIQ", "MAP1"), counter (k, 0, 0, 0)), 1/L, E0 = H_00, and the reference's allowed single and
+// double excitation counts (for P_double, Sec. VI). One block.
+template <int W>
+__global__ void __launch_bounds__(256) k_setup(Params P, long long n_eri, unsigned long long *map1_out, double *wpair_out,
+                                               float *eri_f_out, double *recip_out, long long *facts, double *e0_out) {
+    const int M = P.n_orb;
+    for (long long k = threadIdx.x; k < n_eri; k += blockDim.x) eri_f_out[k] = __double2float_rn(P.eri[k]);
+    for (int k = threadIdx.x; k < P.n_so; k += blockDim.x) {
+        uint4 o = philox4x32_10(make_uint4((unsigned)k, 0u, 0u, 0u), make_uint2(0x46434951u, 0x4D415031u));
+        map1_out[k] = (unsigned long long)o.x | ((unsigned long long)o.y << 32);
+    }
+    for (int k = threadIdx.x; k < M * M; k += blockDim.x) {
+        int p = k / M, q = k % M;
+        double jpq = eri_d(P, p, p, q, q);
+        wpair_out[k] = jpq;
+        wpair_out[M * M + k] = __dsub_rn(jpq, eri_d(P, p, q, q, p));
+    }
+    for (int k = threadIdx.x; k < 2 * MAXSO + 2; k += blockDim.x) recip_out[k] = k == 0 ? 0.0 : __ddiv_rn(1.0, (double)k);
+    __syncthreads();
+    // reference excitation counts by enumeration
+    __shared__ unsigned long long s_ns, s_nd;
+    if (threadIdx.x == 0) { s_ns = 0; s_nd = 0; }
+    __syncthreads();
+    unsigned long long ref[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) ref[w] = P.ref[w];
+    const int N = P.n_elec, NS = P.n_so;
+    unsigned long long ns = 0, nd = 0;
+    for (int x = threadIdx.x; x < N; x += blockDim.x) {
+        int i = P.ref_occ[x];
+        for (int a = 0; a < NS; ++a)
+            if (!bit_of<W>(ref, a) && (a & 1) == (i & 1) && P.irrep[a >> 1] == P.irrep[i >> 1]) ns++;
+    }
+    for (int pq = threadIdx.x; pq < N * N; pq += blockDim.x) {
+        int x = pq / N, y = pq % N;
+        if (y <= x) continue;
+        int i = P.ref_occ[x], j = P.ref_occ[y];
+        int gij = P.irrep[i >> 1] ^ P.irrep[j >> 1];
+        for (int a = 0; a < NS; ++a) {
+            if (bit_of<W>(ref, a)) continue;
+            for (int b = a + 1; b < NS; ++b) {
+                if (bit_of<W>(ref, b)) continue;
+                if ((a & 1) + (b & 1) != (i & 1) + (j & 1)) continue;
+                if ((P.irrep[a >> 1] ^ P.irrep[b >> 1]) != gij) continue;
+                nd++;
+            }
+        }
+    }
+    atomicAdd(&s_ns, ns);
+    atomicAdd(&s_nd, nd);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        facts[0] = (long long)s_ns;
+        facts[1] = (long long)s_nd;
+    }
+}
+
+// E0 = H_00 of the reference (needs the pair table built by k_setup).
+template <int W>
+__global__ void k_reference_energy(Params P, double *e0_out) {
+    extern __shared__ double s_w[];
+    const int M = P.n_orb;
+    for (int k = threadIdx.x; k < 2 * M * M; k += blockDim.x) s_w[k] = P.wpair[k];
+    for (int k = threadIdx.x; k < M; k += blockDim.x) s_w[2 * M * M + k] = P.h[k * M + k];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long ref[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) ref[w] = P.ref[w];
+        *e0_out = hdiag<W>(P, ref, s_w, s_w + 2 * M * M);
+    }
+}
+
+}  // namespace fq

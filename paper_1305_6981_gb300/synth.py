@@ -176,3 +176,67 @@ def batch_systems(n_runs: int = 64, seed: int = 3) -> list[dict]:
         runs.append(dict(n_elec=n_elec, n_orb=n_orb, target=target, seed=1000 + r,
                          sys_seed=int(rng.integers(0, 2**31))))
     return runs
+
+
+def walker_snapshot(system: System, n_walkers: int, seed: int = 0, ref_fraction: float = 0.05,
+                    max_level: int = 4) -> tuple[np.ndarray, np.ndarray]:
+    """A synthetic walker list with the structure of an FCIQMC snapshot of a closed-shell system: the
+    aufbau reference holds `ref_fraction` of the walkers; the others sit on distinct determinants
+    reached from it by 1..max_level random same-spin substitutions (level L drawn with weight 2^-L)
+    that keep the reference's spatial symmetry, with random signs and geometric magnitudes (mean 3).
+    Returns (dets (n, W) uint64, pops (n,) int32)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    M, N = system.n_orb, system.n_elec
+    nh = N // 2
+    W = (2 * M + 63) // 64
+    irr = np.asarray(system.irrep if system.irrep is not None else np.zeros(M), dtype=np.int64)
+    levels = np.arange(1, max_level + 1)
+    wl = 0.5 ** levels
+    wl = wl / wl.sum()
+    n_ref = max(1, int(ref_fraction * n_walkers))
+    ref_bits = np.zeros(64 * W, dtype=bool)
+    ref_bits[:N] = True
+    seen = {np.packbits(ref_bits, bitorder="little").tobytes()}
+    rows, pops = [ref_bits], [n_ref]
+    total = n_ref
+    B = 4096
+    while total < n_walkers:
+        occ = [np.tile(np.arange(nh), (B, 1)) for _ in range(2)]
+        vir = [np.tile(np.arange(nh, M), (B, 1)) for _ in range(2)]
+        g = np.zeros(B, dtype=np.int64)
+        L = rng.choice(levels, size=B, p=wl)
+        r = np.arange(B)
+        for step in range(max_level):
+            act = L > step
+            spin = rng.integers(0, 2, size=B)
+            pi = rng.integers(0, nh, size=B)
+            pa = rng.integers(0, M - nh, size=B)
+            for sp in (0, 1):
+                sel = r[act & (spin == sp)]
+                i = occ[sp][sel, pi[sel]]
+                a = vir[sp][sel, pa[sel]]
+                occ[sp][sel, pi[sel]] = a
+                vir[sp][sel, pa[sel]] = i
+                g[sel] ^= irr[i] ^ irr[a]
+        keep = r[g == 0]
+        bits = np.zeros((len(keep), 64 * W), dtype=bool)
+        kk = np.repeat(np.arange(len(keep)), nh)
+        bits[kk, 2 * occ[0][keep].reshape(-1)] = True
+        bits[kk, 2 * occ[1][keep].reshape(-1) + 1] = True
+        packed = np.packbits(bits, axis=1, bitorder="little")
+        mags = rng.geometric(1.0 / 3.0, size=len(keep))
+        sgns = np.where(rng.random(len(keep)) < 0.5, 1, -1)
+        for k in range(len(keep)):
+            key = packed[k].tobytes()
+            if key in seen:
+                continue
+            seen.add(key)
+            rows.append(bits[k])
+            pops.append(int(mags[k] * sgns[k]))
+            total += int(mags[k])
+            if total >= n_walkers:
+                break
+        B = min(1 << 20, 2 * B)
+    bits = np.array(rows)
+    dets = np.packbits(bits, axis=1, bitorder="little").view("<u8").astype(np.uint64)
+    return dets.reshape(len(rows), W), np.array(pops, dtype=np.int32)

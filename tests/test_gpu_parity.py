@@ -1,0 +1,187 @@
+"""Parity of the CUDA walker cycle with the CPU oracle, through the C ABI (GPU only).
+
+Walker lists (determinant, population) must be identical after every iteration; every integer
+counter of every iteration must be identical; the shift is bit-identical; the projected-energy
+numerator agrees within 1e-11 relative (the GPU reduces it in a different order).
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import bruteforce as bf
+from oracle.oracle import Oracle
+from parity import canonical, compare_rows, same_lists
+from paper_1305_6981_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+
+
+def make_pair(system, tau, thr, **kw):
+    from paper_1305_6981_gb300 import Fciqmc
+    caps = {k: kw.pop(k) for k in ("main_capacity", "spawn_capacity") if k in kw}
+    g = Fciqmc(system, tau, thr, **kw, **caps)
+    q = Oracle(system, tau=tau, initiator_threshold=thr, **kw)
+    return g, q
+
+
+def run_lockstep(g, q, n_iter, every=1):
+    """Advance both; compare walker lists every `every` iterations; return (gpu rows, oracle rows)."""
+    rows_q = []
+    for k in range(n_iter):
+        g.step(1)
+        rows_q += q.iterate(1)
+        if (k + 1) % every == 0 or k + 1 == n_iter:
+            assert same_lists(g.walkers(), q.walkers()), f"walker lists differ after iteration {k + 1}"
+    return g.history(n_iter), rows_q
+
+
+def test_setup_facts_match_oracle():
+    for s in (synth.tiny_8e8o(), synth.init_12e24o(), synth.large_24e60o()):
+        g, q = make_pair(s, 0.01, 3, main_capacity=1 << 12)
+        gi, qi = g.info(), q.info()
+        assert gi["e0"] == qi["E0"]
+        assert gi["d53"] == qi["d53"] and gi["p_double"] == qi["p_double"]
+        assert gi["n_single_ref"] == qi["n_single_ref"] and gi["n_double_ref"] == qi["n_double_ref"]
+        assert np.array_equal(gi["reference"], qi["ref"])
+        g.close()
+
+
+def test_plain_8e8o_every_iteration():
+    """8e/8o, no initiator, tau 0.01, 2^14 target walkers: every iteration of a 1000-iteration run."""
+    s = synth.tiny_8e8o()
+    g, q = make_pair(s, 0.01, -1, target_walkers=1 << 14, initial_population=1000, initial_shift=0.5, seed=5,
+                     main_capacity=1 << 14)
+    rows_q = []
+    for k in range(1000):
+        g.step(1)
+        rows_q += q.iterate(1)
+        assert same_lists(g.walkers(), q.walkers()), f"iteration {k + 1}"
+    compare_rows(g.history(1000), rows_q)
+    e = g.estimates()
+    est = q.estimate()
+    assert e["n_walkers"] == est["nw"] and e["c0"] == est["c0"] and e["n_dets"] == est["nd"]
+    assert abs(e["proj_num"] - est["num"]) <= 1e-11 * abs(est["num"])
+    assert e["vary_shift"] == 1
+    g.close()
+
+
+def test_initiator_12e24o_every_iteration():
+    """12e/24o, 8 irreps, initiator threshold 3, tau 0.005."""
+    s = synth.init_12e24o()
+    g, q = make_pair(s, 0.005, 3, target_walkers=200000, initial_population=3000, initial_shift=1.0, seed=7,
+                     main_capacity=1 << 17)
+    rows, rows_q = run_lockstep(g, q, 150)
+    compare_rows(rows, rows_q)
+    assert sum(r["aborted_walkers"] for r in rows) > 0
+    g.close()
+
+
+def test_two_words_24e60o_heavy_reference():
+    """24e/60o (two words), initiator 3, tau 0.001; 5000 walkers on the reference exercise the chunked
+    heavy-determinant path."""
+    s = synth.large_24e60o()
+    g, q = make_pair(s, 0.001, 3, initial_population=5000, initial_shift=2.0, seed=3, main_capacity=1 << 16)
+    rows_q = []
+    for k in range(40):
+        g.step(1)
+        rows_q += q.iterate(1)
+        assert same_lists(g.walkers(), q.walkers()), f"iteration {k + 1}"
+    compare_rows(g.history(40), rows_q)
+    g.close()
+
+
+def test_heavy_path_one_word():
+    s = synth.tiny_8e8o()
+    g, q = make_pair(s, 0.01, 3, initial_population=20000, initial_shift=0.1, seed=9, main_capacity=1 << 13)
+    rows_q = []
+    for k in range(30):
+        g.step(1)
+        rows_q += q.iterate(1)
+        assert same_lists(g.walkers(), q.walkers()), f"iteration {k + 1}"
+    compare_rows(g.history(30), rows_q)
+    g.close()
+
+
+def test_snapshot_roundtrip_and_windows():
+    """set_walkers from an oracle snapshot, then both advance identically (C ABI read/write path)."""
+    s = synth.init_12e24o()
+    g, q = make_pair(s, 0.005, 3, initial_population=2000, initial_shift=0.8, seed=21, main_capacity=1 << 16)
+    q.iterate(60)
+    d, p, hd = q.walkers()
+    st = q.state()
+    g.set_walkers(d, p, iteration=st["iteration"], shift=st["shift"], vary=st["vary"], shift_counter=st["n_since"],
+                  nw_last_update=st["nw_prev"])
+    dg, pg, hg = g.walkers()
+    a = canonical(dg, pg, hg)
+    b = canonical(d, p, hd)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    assert np.array_equal(a[2], b[2])  # H_ii - E0 computed on the GPU, bit-identical
+    rows_q = q.iterate(20)
+    g.step(20)
+    compare_rows(g.history(20), rows_q)
+    assert same_lists(g.walkers(), q.walkers())
+    g.close()
+
+
+def test_duplicate_determinants_rejected():
+    from paper_1305_6981_gb300._native import FciqmcError
+    s = synth.tiny_8e8o()
+    g, _ = make_pair(s, 0.01, -1, main_capacity=1 << 12)
+    d = np.array([[0xFF], [0xFF]], dtype=np.uint64)
+    with pytest.raises(FciqmcError):
+        g.set_walkers(d, np.array([1, 2], dtype=np.int32))
+    g.close()
+
+
+def test_capacity_error_keeps_last_completed_state():
+    """A main list too small for the run stops with CAPACITY; the list read back is the oracle's state
+    at the last completed iteration."""
+    from paper_1305_6981_gb300._native import FciqmcError
+    s = synth.tiny_8e8o()
+    g, q = make_pair(s, 0.02, -1, initial_population=3000, initial_shift=1.0, seed=2, main_capacity=1024)
+    g.step(200)
+    with pytest.raises(FciqmcError) as ei:
+        g.sync()
+    assert ei.value.status == -2
+    done = g.state()["iteration"]
+    assert 0 < done < 200
+    q.iterate(done)
+    assert same_lists(g.walkers(), q.walkers())
+    g.close()
+
+
+def test_gpu_run_is_deterministic():
+    s = synth.init_12e24o()
+    out = []
+    for _ in range(2):
+        from paper_1305_6981_gb300 import Fciqmc
+        g = Fciqmc(s, 0.005, 3, initial_population=2000, initial_shift=1.0, seed=4, main_capacity=1 << 16)
+        g.step(100)
+        out.append(g.history(100))
+        g.close()
+    for a, b in zip(*out):
+        assert a == b
+
+
+def test_compaction_preserves_parity():
+    """A run with heavy determinant turnover triggers main-list compaction; parity holds across it."""
+    s = synth.tiny_8e8o()
+    g, q = make_pair(s, 0.05, 3, initial_population=3000, initial_shift=0.0, seed=13, main_capacity=1 << 13)
+    rows_q = []
+    for k in range(150):
+        g.step(1)
+        rows_q += q.iterate(1)
+    assert same_lists(g.walkers(), q.walkers())
+    compare_rows(g.history(150), rows_q)
+    assert g.estimates()["compactions"] > 0
+    g.close()
