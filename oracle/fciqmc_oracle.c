@@ -41,7 +41,9 @@
  *     instead of redraw loops (same distribution, fixed draw count);
  *   - single/double choice: double iff (r0 >> 11) < floor(P_double 2^53), and
  *     P_double itself is the double/single ratio of the reference rounded to a
- *     multiple of 2^-53 so that the draw realises it exactly;
+ *     multiple of 2^-53 so that the draw realises it exactly; the same word,
+ *     uniform within the chosen type's sub-range, realises the Bernoulli part
+ *     of the spawn (two Philox blocks per attempt);
  *   - initiator: |C_i| > threshold, or D_i is the reference;
  *   - shift: S <- S - zeta/(A tau) ln(N_w(n) / N_w(n-A)) every A iterations
  *     once N_w first reaches the target.
@@ -551,7 +553,7 @@ static void sbuf_push(sbuf_t *b, int W, const uint64_t *d, int64_t amt, int flag
 static int64_t attempt_one(const oq_t *q, const uint64_t *d, int32_t c, uint64_t fp, uint32_t a,
                            uint64_t *child, int *is_null, int *err)
 {
-    uint64_t r0, r1, r2, r3, r4, r5;
+    uint64_t r0, r1, r2, r3;
     *is_null = 0;
     draw2(a, 0u, fp, q->seed, q->iter, &r0, &r1);
     draw2(a, 1u, fp, q->seed, q->iter, &r2, &r3);
@@ -581,10 +583,16 @@ static int64_t attempt_one(const oq_t *q, const uint64_t *d, int32_t c, uint64_t
     double p;
     if (kind == 1) p = (fabs(hv) * q->cs) * (double)info[5];
     else p = ((fabs(hv) * q->cd) * (double)info[5]) * (1.0 / (double)info[4]);
-    draw2(a, 2u, fp, q->seed, q->iter, &r4, &r5);
+    /* floor(p) walkers, plus one with probability p - floor(p). The Bernoulli draw reuses the type
+     * word: given the type, t = r0 >> 11 is uniform on [0, d53) (double) or [d53, 2^53) (single), so
+     * with the offset s and the range n of that interval, [t - s < (p - floor p) n] has probability
+     * ceil((p - floor p) n) / n, within 1/n of p - floor p. */
     double fl = floor(p);
     if (fl >= 2147483647.0) { *err = 1; return 0; }
-    int64_t nsp = (int64_t)fl + (unit53(r4) < p - fl ? 1 : 0);
+    uint64_t t = r0 >> 11;
+    uint64_t off = kind == 2 ? 0 : q->d53;
+    uint64_t range = kind == 2 ? q->d53 : ((uint64_t)1 << 53) - q->d53;
+    int64_t nsp = (int64_t)fl + ((double)(t - off) < (p - fl) * (double)range ? 1 : 0);
     if (nsp == 0) return 0;
     int sgn_c = c > 0 ? 1 : -1, sgn_h = hv > 0.0 ? 1 : -1;
     return -(int64_t)sgn_c * sgn_h * nsp;

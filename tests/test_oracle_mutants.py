@@ -26,6 +26,9 @@ MUTANTS = [
     ("death_sign", "if (r >= 0.0) { nc = (int64_t)c - sc * nd;", "if (r >= 0.0) { nc = (int64_t)c + sc * nd;"),
     ("initiator_flag_and", "m.flag |= sp[y].flag;", "m.flag &= sp[y].flag;"),
     ("spin_rule_double", "if (si == sj && sa != si) continue;", "if (sa != si) continue;"),
+    ("accept_single_offset_dropped", "uint64_t off = kind == 2 ? 0 : q->d53;", "uint64_t off = 0;"),
+    ("accept_range_swapped", "uint64_t range = kind == 2 ? q->d53 : ((uint64_t)1 << 53) - q->d53;",
+     "uint64_t range = kind == 1 ? q->d53 : ((uint64_t)1 << 53) - q->d53;"),
 ]
 
 FAST_PINS = ("philox or own_log or second_quantisation or symmetry_and_spin or two_words and hamiltonian "
