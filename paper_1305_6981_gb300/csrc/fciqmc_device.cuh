@@ -35,7 +35,7 @@ struct DevState {
     unsigned long long claim;  // slot claim counter during annihilation
     int status;                // sticky error status (0 = OK)
     int compact_pending;
-    unsigned long long n_merged, n_chunks;
+    unsigned long long n_merged, n_chunks, n_heavy;
     unsigned long long nw_in, nd_in;
     long long c0_in;
     unsigned long long d_nw, d_nd;  // two's-complement signed changes
@@ -58,6 +58,9 @@ struct Params {
     unsigned long long d53;
     double tau, cs, cd, E0, c_shift;
     float tau_lo, tau_hi, cd_lo, cd_hi;   // float bounds: tau_lo <= tau <= tau_hi, cd_lo <= cd <= cd_hi
+    float cdn_lo, cdn_hi;                  // bounds of cd * npairs
+    float d53_lo, d53_hi;                  // bounds of (float)d53
+    double d53_d;                          // (double)d53, exact
     int period;
     int sweep_grid;                        // blocks of k_sweep (number of partial sums)
     int idx_stride;                        // 64-bit words per index entry
@@ -72,6 +75,7 @@ struct Params {
     const unsigned char *irrep;       // n_orb
     const unsigned short *pairs;      // npairs: (i | j << 8), i < j electron indices
     const double *recip;              // recip[L] = 1.0 / L, L < 2 * MAXSO + 2
+    const float2 *rcpb;               // float bounds (lo, hi) of 1 / L
     unsigned long long ref[MAXW];
     const unsigned char *ref_occ;     // n_elec ascending spin orbitals of the reference
     // main list, two buffers for compaction, two population arrays per buffer
@@ -91,6 +95,8 @@ struct Params {
     unsigned *merged;
     uint4 *chunks;
     long long chunk_cap;
+    void *heavy;                      // DetView records of determinants spawned from by chunks
+    long long heavy_cap;
     double *partial;
     fciqmc_row *hist;
     long long hist_cap;

@@ -18,7 +18,7 @@ namespace fq {
 
 constexpr int kTile = 256;          // determinants per sweep tile = threads per sweep block
 constexpr int kHeavy = 1024;        // |C_i| above this: attempts go to the chunked heavy path
-constexpr int kChunk = 2048;        // attempts per heavy chunk
+constexpr int kChunk = 1024;        // attempts per heavy chunk (one warp task)
 constexpr unsigned long long kSaltMerge = 0x5851F42D4C957F2Dull;
 constexpr unsigned long long kSaltIndex = 0x14057B7EF767814Full;
 constexpr unsigned long long kFlagUnit = 1ull << 40;  // merge payload: (#initiator spawns << 40) + amount
@@ -151,14 +151,57 @@ struct AttemptOut {
     unsigned pos;
 };
 
+// Exact float of a small nonnegative integer (x < 2^23) without a conversion instruction.
+__device__ __forceinline__ float small_f(unsigned x) { return __int_as_float(0x4B000000 | x) - 8388608.0f; }
+
+// Per-determinant table of the "good" first virtual orbitals a of a double excitation (Sec. VI B),
+// indexed by the spin case of the pair (0: alpha alpha, 1: beta beta, 2: mixed) times 8 plus the
+// irrep product of the pair: their number G = M^a - delta_d and their bit mask (unoccupied only).
 template <int W>
-__device__ __forceinline__ AttemptOut spawn_attempt(const Params &P, const Tables &T, const DetView<W> &v, unsigned a,
+struct GoodTable {
+    unsigned long long gm[24][W];
+    unsigned short G[24];
+};
+
+// Good a-orbitals for one (spin case, pair irrep): loop over the classes of allowed spin.
+template <int W>
+__device__ __forceinline__ unsigned good_set(const Params &P, const Tables &T, const DetView<W> &v, int si, int sj,
+                                             int gij, unsigned long long (&gm)[W]) {
+    unsigned G = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) gm[w] = 0ull;
+    for (int sa = 0; sa < 2; ++sa) {
+        if (si == sj && sa != si) continue;
+        const int sb = si + sj - sa;
+        for (int g = 0; g < P.n_irrep_used; ++g) {
+            const int ca = g * 2 + sa, cb = (gij ^ g) * 2 + sb;
+            const int avail = (int)v.cnt[cb] - (ca == cb ? 1 : 0);
+            if (avail >= 1 && v.cnt[ca] > 0) {
+                G += v.cnt[ca];
+#pragma unroll
+                for (int w = 0; w < W; ++w) gm[w] |= T.mask[ca * MAXW + w];
+            }
+        }
+    }
+#pragma unroll
+    for (int w = 0; w < W; ++w) gm[w] &= ~v.d[w];
+    return G;
+}
+
+// One spawning attempt a from determinant v (Eq. 3 with the generator of Sec. VI). Random numbers:
+// two Philox blocks keyed by (seed, iteration), counter (a, tag 0/1, fingerprint). The type word r0
+// also realises the Bernoulli part of the spawn: given the type, t = r0 >> 11 is uniform on
+// [0, d53) for a double and on [d53, 2^53) for a single.
+template <int W, bool TAB>
+__device__ __forceinline__ AttemptOut spawn_attempt(const Params &P, const Tables &T, const DetView<W> &v,
+                                                     const GoodTable<W> *tab, const float2 *rcpb, unsigned a,
                                                      unsigned iter, unsigned long long *cnt) {
     AttemptOut out{false, 0u};
-    unsigned long long r0, r1, r2, r3, r4, r5;
+    unsigned long long r0, r1, r2, r3;
     draw2(a, 0u, v.fp, P.seed, iter, r0, r1);
     draw2(a, 1u, v.fp, P.seed, iter, r2, r3);
-    const bool dbl = (r0 >> 11) < P.d53;
+    const unsigned long long t = r0 >> 11;
+    const bool dbl = t < P.d53;
     unsigned long long child[W];
 #pragma unroll
     for (int w = 0; w < W; ++w) child[w] = v.d[w];
@@ -188,10 +231,10 @@ __device__ __forceinline__ AttemptOut spawn_attempt(const Params &P, const Table
         if (hv == 0.0) return out;
         // p = (|H| (tau / P_single)) (M_allow (N - delta_s))
         double p = __dmul_rn(__dmul_rn(fabs(hv), P.cs), (double)((long long)mallow * (long long)v.nok));
-        draw2(a, 2u, v.fp, P.seed, iter, r4, r5);
         double fl = floor(p);
         if (fl >= 2147483647.0) { set_status(P.st, FCIQMC_ERR_NUMERIC); return out; }
-        n = (int)fl + (unit53(r4) < __dsub_rn(p, fl) ? 1 : 0);
+        const double range = __dsub_rn(9007199254740992.0, P.d53_d);
+        n = (int)fl + (__ull2double_rn(t - P.d53) < __dmul_rn(__dsub_rn(p, fl), range) ? 1 : 0);
         sgn_h = hv > 0.0 ? 1 : -1;
     } else {
         // double excitation (Sec. VI B): pair by inverse triangular index, a among the "good" unoccupied
@@ -202,26 +245,17 @@ __device__ __forceinline__ AttemptOut spawn_attempt(const Params &P, const Table
         const int i = v.occ[pr & 0xFF], j = v.occ[pr >> 8];
         const int si = i & 1, sj = j & 1;
         const int gij = T.irrep[i >> 1] ^ T.irrep[j >> 1];
-        unsigned G = 0;
+        unsigned G;
         unsigned long long gm[W];
+        if (TAB) {
+            const int e = (si == sj ? si : 2) * 8 + gij;
+            G = tab->G[e];
 #pragma unroll
-        for (int w = 0; w < W; ++w) gm[w] = 0ull;
-        for (int sa = 0; sa < 2; ++sa) {
-            if (si == sj && sa != si) continue;
-            const int sb = si + sj - sa;
-            for (int g = 0; g < P.n_irrep_used; ++g) {
-                const int ca = g * 2 + sa, cb = (gij ^ g) * 2 + sb;
-                const int avail = (int)v.cnt[cb] - (ca == cb ? 1 : 0);
-                if (avail >= 1 && v.cnt[ca] > 0) {
-                    G += v.cnt[ca];
-#pragma unroll
-                    for (int w = 0; w < W; ++w) gm[w] |= T.mask[ca * MAXW + w];
-                }
-            }
+            for (int w = 0; w < W; ++w) gm[w] = tab->gm[e][w];
+        } else {
+            G = good_set<W>(P, T, v, si, sj, gij, gm);
         }
         if (G == 0) { cnt[C_NULLS]++; return out; }
-#pragma unroll
-        for (int w = 0; w < W; ++w) gm[w] &= ~v.d[w];
         const int ao = select_bit<W>(gm, (int)rank_of(r2, G));
         const int ca = T.irrep[ao >> 1] * 2 + (ao & 1);
         const int cb = (gij ^ T.irrep[ao >> 1]) * 2 + (si + sj - (ao & 1));
@@ -233,37 +267,44 @@ __device__ __forceinline__ AttemptOut spawn_attempt(const Params &P, const Table
         bm[ao >> 6] &= ~(1ull << (ao & 63));
         const int bo = select_bit<W>(bm, (int)rank_of(r3, m_ba));
         const int A = min(ao, bo), B = max(ao, bo);
-        // p = ((|H| (tau / P_double)) (npairs G M^(b|a) M^(a|b))) (1 / (M^(b|a) + M^(a|b)))
-        const long long K = (long long)P.npairs * (long long)G * (long long)m_ba * (long long)m_ab;
         const unsigned L = m_ba + m_ab;
         const bool t1 = ((i & 1) == (A & 1)) && ((j & 1) == (B & 1));
         const bool t2 = ((i & 1) == (B & 1)) && ((j & 1) == (A & 1));
-        // bounds on |H| from the float copy of the integrals
+        // bounds of p = |H| tau / P_gen from the float copy of the integrals
         Iv x = {0.f, 0.f}, y = {0.f, 0.f};
         if (t1) x = iv_rn(eri_f(P, i >> 1, A >> 1, j >> 1, B >> 1));
         if (t2) y = iv_rn(eri_f(P, i >> 1, B >> 1, j >> 1, A >> 1));
-        Iv hv = iv_sub(x, y);
-        const int par = double_parity<W>(v.d, i, j, A, B);
-        Iv ah = iv_abs(hv);
-        Iv pv = iv_mul(iv_mul(iv_mul(ah, Iv{P.cd_lo, P.cd_hi}),
-                              Iv{__ll2float_rd(K), __ll2float_ru(K)}),
-                       Iv{__frcp_rd((float)L), __frcp_ru((float)L)});
+        const Iv hv = iv_sub(x, y);
+        const Iv ah = iv_abs(hv);
+        const float gf = small_f(G), baf = small_f(m_ba), abf = small_f(m_ab);
+        const float2 rl = rcpb[L];
+        Iv pv;
+        pv.lo = __fmul_rd(__fmul_rd(__fmul_rd(__fmul_rd(__fmul_rd(ah.lo, P.cdn_lo), gf), baf), abf), rl.x);
+        pv.hi = __fmul_ru(__fmul_ru(__fmul_ru(__fmul_ru(__fmul_ru(ah.hi, P.cdn_hi), gf), baf), abf), rl.y);
         pv = iv_slack(pv);
-        draw2(a, 2u, v.fp, P.seed, iter, r4, r5);
-        const int dec = bernoulli_decide(pv, r4);
+        int dec = -1;
+        if (pv.hi < 1.0f) {
+            // Bernoulli threshold t < p d53: bounds on both sides; t known to 2^30
+            const Iv th = iv_slack(Iv{__fmul_rd(pv.lo, P.d53_lo), __fmul_ru(pv.hi, P.d53_hi)});
+            const float q_lo = small_f((unsigned)(t >> 30)) * 0x1p30f;
+            if (q_lo >= th.hi) dec = 0;
+            else if (pv.lo > 0.f && q_lo + 0x1p30f <= th.lo) dec = 1;
+        }
         if (dec == 0) return out;
         if (dec == 1 && (hv.lo > 0.f || hv.hi < 0.f)) {
             n = 1;
             sgn_h = (hv.lo > 0.f) ? 1 : -1;
-            if (par) sgn_h = -sgn_h;
+            if (double_parity<W>(v.d, i, j, A, B)) sgn_h = -sgn_h;
         } else {
             atomicAdd(&P.st->exact_spawn, 1ull);
             double hd = hij_double<W>(P, v.d, i, j, A, B);
             if (hd == 0.0) return out;
+            // p = ((|H| (tau / P_double)) (npairs G M^(b|a) M^(a|b))) (1 / (M^(b|a) + M^(a|b)))
+            const long long K = (long long)P.npairs * (long long)G * (long long)m_ba * (long long)m_ab;
             double p = __dmul_rn(__dmul_rn(__dmul_rn(fabs(hd), P.cd), (double)K), P.recip[L]);
             double fl = floor(p);
             if (fl >= 2147483647.0) { set_status(P.st, FCIQMC_ERR_NUMERIC); return out; }
-            n = (int)fl + (unit53(r4) < __dsub_rn(p, fl) ? 1 : 0);
+            n = (int)fl + (__ull2double_rn(t) < __dmul_rn(__dsub_rn(p, fl), P.d53_d) ? 1 : 0);
             sgn_h = hd > 0.0 ? 1 : -1;
         }
         flip<W>(child, i);
@@ -329,20 +370,24 @@ __device__ __forceinline__ double warp_sum_f64(double x) {
     for (int o = 16; o > 0; o >>= 1) x = __dadd_rn(x, __shfl_down_sync(0xFFFFFFFFu, x, o));
     return x;
 }
-// Block-wide sums, added once per block to global counters; the FP64 value is returned to thread 0
-// (fixed order: lane tree, then warps in order).
-template <int NT>
-__device__ __forceinline__ void flush_u64(unsigned long long *dst, unsigned long long v, unsigned long long *s_red) {
-    v = warp_sum_u64(v);
-    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long t = 0;
-        for (int w = 0; w < NT / 32; ++w) t += s_red[w];
-        if (t) atomicAdd(dst, t);
+// Block-wide sums of NV per-thread counters with one barrier; thread k adds counter k to *dst[k].
+template <int NT, int NV>
+__device__ __forceinline__ void flush_counters(unsigned long long (&v)[NV], unsigned long long *const (&dst)[NV],
+                                               unsigned long long *s_red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        unsigned long long x = warp_sum_u64(v[k]);
+        if (lane == 0) s_red[warp * NV + k] = x;
     }
     __syncthreads();
+    if (threadIdx.x < NV) {
+        unsigned long long t = 0;
+        for (int w = 0; w < NT / 32; ++w) t += s_red[w * NV + threadIdx.x];
+        if (t) atomicAdd(dst[threadIdx.x], t);
+    }
 }
+// Deterministic block sum of an FP64 value (lane tree, then warps in order), returned to thread 0.
 template <int NT>
 __device__ __forceinline__ double block_sum_f64(double v, double *s_red) {
     v = warp_sum_f64(v);
@@ -351,11 +396,15 @@ __device__ __forceinline__ double block_sum_f64(double v, double *s_red) {
     double t = 0.0;
     if (threadIdx.x == 0)
         for (int w = 0; w < NT / 32; ++w) t = __dadd_rn(t, s_red[w]);
-    __syncthreads();
     return t;
 }
 
 // ---------------------------------------------------------------------------- kernels
+// Float bounds of 1/L for the spawn bound, copied to shared memory.
+__device__ __forceinline__ void load_rcpb(const Params &P, float2 *s_rcpb) {
+    for (int k = threadIdx.x; k < 2 * MAXSO + 2; k += blockDim.x) s_rcpb[k] = P.rcpb[k];
+}
+
 template <int W>
 __global__ void __launch_bounds__(kTile) k_sweep(Params P) {
     DevState *st = P.st;
@@ -364,9 +413,11 @@ __global__ void __launch_bounds__(kTile) k_sweep(Params P) {
     __shared__ DetView<W> s_dv[kTile];
     __shared__ unsigned s_off[kTile + 1];
     __shared__ unsigned s_wsum[kTile / 32];
-    __shared__ unsigned long long s_red[kTile / 32];
+    __shared__ float2 s_rcpb[2 * MAXSO + 2];
+    __shared__ unsigned long long s_red[(kTile / 32) * (NCNT + 4)];
     __shared__ double s_redf[kTile / 32];
     load_tables(P, T);
+    load_rcpb(P, s_rcpb);
     const int lb = st->lb, pp = st->pp;
     const long long len = st->list_len;
     const unsigned iter = (unsigned)st->iter;
@@ -377,12 +428,12 @@ __global__ void __launch_bounds__(kTile) k_sweep(Params P) {
     const double *hd = P.hd[lb];
     const int *pop_in = P.pop[lb][pp];
     int *pop_out = P.pop[lb][pp ^ 1];
+    DetView<W> *heavy = reinterpret_cast<DetView<W> *>(P.heavy);
     __syncthreads();
 
-    unsigned long long cnt[NCNT];
+    unsigned long long acc[NCNT + 4];  // counters, then nw, nd, d_nw, d_nd
 #pragma unroll
-    for (int k = 0; k < NCNT; ++k) cnt[k] = 0;
-    unsigned long long nw = 0, nd = 0, dnw = 0, dnd = 0;
+    for (int k = 0; k < NCNT + 4; ++k) acc[k] = 0;
     double num = 0.0;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
@@ -405,27 +456,30 @@ __global__ void __launch_bounds__(kTile) k_sweep(Params P) {
                 const float hf = __ldcs(hdf + s);
                 prepare_det<W>(P, T, v, c);
                 const unsigned ac = (unsigned)(c < 0 ? -c : c);
-                nw += ac;
-                nd += 1;
+                acc[NCNT] += ac;
+                acc[NCNT + 1] += 1;
                 unsigned long long xd = 0;
                 int diff = 0;
 #pragma unroll
                 for (int w = 0; w < W; ++w) { xd |= v.d[w] ^ P.ref[w]; diff += __popcll(v.d[w] ^ P.ref[w]); }
                 if (xd == 0) st->c0_in = c;
                 else if (diff == 2 || diff == 4) num = __dadd_rn(num, __dmul_rn(h0i<W>(P, v.d), (double)c));
-                const int nc = death_step<W>(P, v, hf, hd + s, S, S_lo, S_hi, iter, cnt);
+                const int nc = death_step<W>(P, v, hf, hd + s, S, S_lo, S_hi, iter, acc);
                 pop_out[s] = nc;
-                dnw += (unsigned long long)((long long)(nc < 0 ? -nc : nc) - (long long)ac);
-                if (nc == 0) dnd += (unsigned long long)(-1LL);
-                cnt[C_ATTEMPTS] += ac;
+                acc[NCNT + 2] += (unsigned long long)((long long)(nc < 0 ? -nc : nc) - (long long)ac);
+                if (nc == 0) acc[NCNT + 3] += (unsigned long long)(-1LL);
+                acc[C_ATTEMPTS] += ac;
                 if (ac > (unsigned)kHeavy) {
+                    // heavily populated determinant: its attempts go to warp-sized chunks of k_heavy
+                    const unsigned long long hidx = atomicAdd(&st->n_heavy, 1ull);
                     const unsigned nch = (ac + kChunk - 1) / kChunk;
                     const unsigned long long base = atomicAdd(&st->n_chunks, (unsigned long long)nch);
-                    if (base + nch > (unsigned long long)P.chunk_cap) {
+                    if (hidx >= (unsigned long long)P.heavy_cap || base + nch > (unsigned long long)P.chunk_cap) {
                         set_status(st, FCIQMC_ERR_CAPACITY);
                     } else {
+                        heavy[hidx] = v;
                         for (unsigned q = 0; q < nch; ++q)
-                            P.chunks[base + q] = make_uint4((unsigned)s, q * kChunk, min((q + 1) * kChunk, ac), 0u);
+                            P.chunks[base + q] = make_uint4((unsigned)hidx, q * kChunk, min((q + 1) * kChunk, ac), 0u);
                     }
                 } else {
                     att = ac;
@@ -463,64 +517,86 @@ __global__ void __launch_bounds__(kTile) k_sweep(Params P) {
                     int mid = (lo + hi + 1) >> 1;
                     if (s_off[mid] <= k) lo = mid; else hi = mid - 1;
                 }
-                ao = spawn_attempt<W>(P, T, s_dv[lo], k - s_off[lo], iter, cnt);
+                ao = spawn_attempt<W, false>(P, T, s_dv[lo], nullptr, s_rcpb, k - s_off[lo], iter, acc);
             }
             long long slot = warp_append(&st->n_merged, ao.claimed);
             if (ao.claimed && slot < P.mt_cap) P.merged[slot] = ao.pos;
         }
         __syncthreads();
     }
-    // block reductions
-    for (int k = 0; k < NCNT; ++k) flush_u64<kTile>(&st->cnt[k], cnt[k], s_red);
-    flush_u64<kTile>(&st->nw_in, nw, s_red);
-    flush_u64<kTile>(&st->nd_in, nd, s_red);
-    flush_u64<kTile>(&st->d_nw, dnw, s_red);
-    flush_u64<kTile>(&st->d_nd, dnd, s_red);
+    unsigned long long *const dst[NCNT + 4] = {&st->cnt[0], &st->cnt[1], &st->cnt[2], &st->cnt[3], &st->cnt[4],
+                                               &st->cnt[5], &st->cnt[6], &st->cnt[7], &st->cnt[8], &st->nw_in,
+                                               &st->nd_in, &st->d_nw, &st->d_nd};
+    flush_counters<kTile, NCNT + 4>(acc, dst, s_red);
     double bs = block_sum_f64<kTile>(num, s_redf);
     if (threadIdx.x == 0) P.partial[blockIdx.x] = bs;
 }
 
+// Attempts of heavily populated determinants: one warp per chunk of up to kChunk attempts of one
+// determinant; the warp builds that determinant's good-orbital table once per chunk.
 template <int W>
 __global__ void __launch_bounds__(kTile) k_heavy(Params P) {
     DevState *st = P.st;
     if (st->status) return;
+    constexpr int NW = kTile / 32;
     __shared__ Tables T;
-    __shared__ DetView<W> v;
-    __shared__ unsigned long long s_red[kTile / 32];
+    __shared__ DetView<W> s_v[NW];
+    __shared__ GoodTable<W> s_tab[NW];
+    __shared__ float2 s_rcpb[2 * MAXSO + 2];
+    __shared__ unsigned long long s_red[NW * NCNT];
     load_tables(P, T);
+    load_rcpb(P, s_rcpb);
     const unsigned long long nch = st->n_chunks;
-    const int lb = st->lb, pp = st->pp;
     const unsigned iter = (unsigned)st->iter;
+    const DetView<W> *heavy = reinterpret_cast<const DetView<W> *>(P.heavy);
     unsigned long long cnt[NCNT];
 #pragma unroll
     for (int k = 0; k < NCNT; ++k) cnt[k] = 0;
     __syncthreads();
-    for (unsigned long long q = blockIdx.x; q < nch && q < (unsigned long long)P.chunk_cap; q += gridDim.x) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned long long gw = (unsigned long long)blockIdx.x * NW + warp;
+    const unsigned long long nwarps = (unsigned long long)gridDim.x * NW;
+    unsigned cur = 0xFFFFFFFFu;
+    DetView<W> &v = s_v[warp];
+    GoodTable<W> &tab = s_tab[warp];
+    for (unsigned long long q = gw; q < nch && q < (unsigned long long)P.chunk_cap; q += nwarps) {
         const uint4 ch = P.chunks[q];
-        if (threadIdx.x == 0) {
-            const long long s = ch.x;
+        if (ch.x != cur) {
+            const unsigned long long *src = reinterpret_cast<const unsigned long long *>(heavy + ch.x);
+            unsigned long long *dstv = reinterpret_cast<unsigned long long *>(&v);
+            for (int k = lane; k < (int)(sizeof(DetView<W>) / 8); k += 32) dstv[k] = src[k];
+            __syncwarp();
+            if (lane < 24) {
+                const int sc = lane >> 3, gij = lane & 7;
+                const int si = sc == 1 ? 1 : 0, sj = sc == 0 ? 0 : 1;
+                unsigned long long gm[W];
+                unsigned G = good_set<W>(P, T, v, si, sj, gij, gm);
+                tab.G[lane] = (unsigned short)G;
 #pragma unroll
-            for (int w = 0; w < W; ++w) v.d[w] = P.det[lb][s * W + w];
-            prepare_det<W>(P, T, v, P.pop[lb][pp][s]);
+                for (int w = 0; w < W; ++w) tab.gm[lane][w] = gm[w];
+            }
+            __syncwarp();
+            cur = ch.x;
         }
-        __syncthreads();
-        const unsigned n = ch.z - ch.y;
-        for (unsigned base = 0; base < n; base += kTile) {
-            const unsigned k = base + threadIdx.x;
+        for (unsigned base = ch.y; base < ch.z; base += 32) {
+            const unsigned a = base + lane;
             AttemptOut ao{false, 0u};
-            if (k < n) ao = spawn_attempt<W>(P, T, v, ch.y + k, iter, cnt);
+            if (a < ch.z) ao = spawn_attempt<W, true>(P, T, v, &tab, s_rcpb, a, iter, cnt);
             long long slot = warp_append(&st->n_merged, ao.claimed);
             if (ao.claimed && slot < P.mt_cap) P.merged[slot] = ao.pos;
         }
-        __syncthreads();
+        __syncwarp();
     }
-    for (int k = 1; k < NCNT; ++k) flush_u64<kTile>(&st->cnt[k], cnt[k], s_red);
+    unsigned long long *const dst[NCNT] = {&st->cnt[0], &st->cnt[1], &st->cnt[2], &st->cnt[3], &st->cnt[4],
+                                           &st->cnt[5], &st->cnt[6], &st->cnt[7], &st->cnt[8]};
+    cnt[C_ATTEMPTS] = 0;  // attempts are counted by the sweep
+    flush_counters<kTile, NCNT>(cnt, dst, s_red);
 }
 
 template <int W>
 __global__ void __launch_bounds__(256) k_annihilate(Params P) {
     extern __shared__ double s_w[];  // [2][M][M] pair terms, then M diagonal h_pp
-    __shared__ unsigned long long s_red[256 / 32];
+    __shared__ unsigned long long s_red[(256 / 32) * 4];
     DevState *st = P.st;
     if (st->status) return;
     constexpr int S = Stride<W>::v;
@@ -629,10 +705,9 @@ __global__ void __launch_bounds__(256) k_annihilate(Params P) {
             inserted += 1;
         }
     }
-    flush_u64<256>(&st->d_nw, dnw, s_red);
-    flush_u64<256>(&st->d_nd, dnd, s_red);
-    flush_u64<256>(&st->cnt[C_ABORTED], aborted, s_red);
-    flush_u64<256>(&st->cnt[C_INSERTED], inserted, s_red);
+    unsigned long long accv[4] = {dnw, dnd, aborted, inserted};
+    unsigned long long *const dst[4] = {&st->d_nw, &st->d_nd, &st->cnt[C_ABORTED], &st->cnt[C_INSERTED]};
+    flush_counters<256, 4>(accv, dst, s_red);
 }
 
 // Natural logarithm from the atanh series (shift update); same operation order as the oracle's.
@@ -708,6 +783,7 @@ __global__ void k_finish(Params P) {
         st->compact_pending = 1;
     st->n_merged = 0;
     st->n_chunks = 0;
+    st->n_heavy = 0;
     st->nw_in = st->nd_in = 0;
     st->c0_in = 0;
     st->d_nw = st->d_nd = 0;
@@ -798,7 +874,7 @@ __global__ void k_compact_finish(Params P) {
 // ---------------------------------------------------------------------------- estimators, gather, setup
 template <int W>
 __global__ void __launch_bounds__(256) k_estimate(Params P) {
-    __shared__ unsigned long long s_red[8];
+    __shared__ unsigned long long s_red[16];
     __shared__ double s_redf[8];
     DevState *st = P.st;
     const int lb = st->lb, pp = st->pp;
@@ -820,8 +896,9 @@ __global__ void __launch_bounds__(256) k_estimate(Params P) {
         if (xd == 0) st->est_c0 = c;
         else if (diff == 2 || diff == 4) num = __dadd_rn(num, __dmul_rn(h0i<W>(P, d), (double)c));
     }
-    flush_u64<256>(&st->est_nw, nw, s_red);
-    flush_u64<256>(&st->est_nd, nd, s_red);
+    unsigned long long accv[2] = {nw, nd};
+    unsigned long long *const dst[2] = {&st->est_nw, &st->est_nd};
+    flush_counters<256, 2>(accv, dst, s_red);
     double bs = block_sum_f64<256>(num, s_redf);
     if (threadIdx.x == 0) P.partial[blockIdx.x] = bs;
 }
