@@ -44,7 +44,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc(), ARCH, *NVCC_FLAGS, "-I" + INCLUDE, "-o", tmp] + [os.path.join(CSRC, s) for s in SOURCES]
+    extra = os.environ.get("FCIQMC_NVCC_FLAGS", "").split()  # tuning defines, e.g. -DFQ_SWEEP_MIN_BLOCKS=3
+    cmd = [nvcc(), ARCH, *NVCC_FLAGS, *extra, "-I" + INCLUDE, "-o", tmp] + [os.path.join(CSRC, s) for s in SOURCES]
     if verbose:
         print(" ".join(cmd))
     subprocess.check_call(cmd)

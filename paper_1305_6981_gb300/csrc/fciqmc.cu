@@ -41,7 +41,7 @@ int log2_exact(long long x) {
 
 struct Sizes {
     int W, n_so, npairs;
-    long long n_eri, cap, idx_cap, mt_cap, chunk_cap, hist_cap, heavy_cap;
+    long long n_eri, cap, idx_cap, mt_cap, hist_cap, heavy_cap;
 };
 
 bool sizes_of(int n_elec, int n_orb, const fciqmc_options &o, Sizes &z) {
@@ -56,15 +56,14 @@ bool sizes_of(int n_elec, int n_orb, const fciqmc_options &o, Sizes &z) {
     z.idx_cap = next_pow2(std::max<long long>(2 * z.cap, 1 << 12));
     z.mt_cap = next_pow2(std::max<long long>(o.spawn_capacity > 0 ? o.spawn_capacity : z.cap / 2, 1 << 12));
     if (z.mt_cap > (1LL << 32)) return false;
-    z.chunk_cap = std::max<long long>(1 << 17, z.cap / 8);
     z.heavy_cap = std::max<long long>(1 << 14, std::min<long long>(z.cap, 1 << 20));
     z.hist_cap = std::max<long long>(o.history_capacity > 0 ? o.history_capacity : (1LL << 16), 16);
     return true;
 }
 
 struct Layout {
-    size_t state, h, eri, eri_f, wpair, map1, cmask, irrep, pairs, recip, rcpb, ref_occ, facts, e0;
-    size_t det[2], hd[2], hdf[2], pop[2][2], idx, mt, merged, chunks, heavy, partial, hist;
+    size_t state, h, eri, eri_f, wpair, map1, cmask, irrep, pairs, recip, rcpf, ref_occ, facts, e0;
+    size_t det[2], hd[2], hdf[2], pop[2][2], idx, mt, merged, heavy, heavy_base, heavy_att, partial, hist;
     size_t total;
 };
 
@@ -86,7 +85,7 @@ Layout layout_of(const Sizes &z, int n_orb) {
     L.irrep = take(fq::MAXSO);
     L.pairs = take(sizeof(unsigned short) * std::max(z.npairs, 1));
     L.recip = take(sizeof(double) * (2 * fq::MAXSO + 2));
-    L.rcpb = take(sizeof(float2) * (2 * fq::MAXSO + 2));
+    L.rcpf = take(sizeof(float) * (2 * fq::MAXSO + 2));
     L.ref_occ = take(fq::MAXN);
     L.facts = take(sizeof(long long) * 4);
     L.e0 = take(sizeof(double));
@@ -101,23 +100,13 @@ Layout layout_of(const Sizes &z, int n_orb) {
     L.idx = take(sizeof(unsigned long long) * stride * z.idx_cap);
     L.mt = take(sizeof(unsigned long long) * stride * z.mt_cap);
     L.merged = take(sizeof(unsigned) * z.mt_cap);
-    L.chunks = take(sizeof(uint4) * z.chunk_cap);
     L.heavy = take(sizeof(fq::DetView<2>) * z.heavy_cap);
+    L.heavy_base = take(sizeof(unsigned) * z.heavy_cap);
+    L.heavy_att = take(sizeof(unsigned) * z.heavy_cap);
     L.partial = take(sizeof(double) * kMaxGrid);
     L.hist = take(sizeof(fciqmc_row) * z.hist_cap);
     L.total = off;
     return L;
-}
-
-float f32_down(double x) {
-    float f = (float)x;
-    if ((double)f > x) f = std::nextafter(f, -INFINITY);
-    return f;
-}
-float f32_up(double x) {
-    float f = (float)x;
-    if ((double)f < x) f = std::nextafter(f, INFINITY);
-    return f;
 }
 
 }  // namespace
@@ -329,8 +318,7 @@ int fciqmc_create(const double *h1, const double *eri_s8, double e_core, int n_e
     P.period = o.shift_period;
     P.target = o.target_walkers;
     P.c_shift = o.shift_damping / ((double)o.shift_period * tau);
-    P.tau_lo = f32_down(tau);
-    P.tau_hi = f32_up(tau);
+    P.tau_f = (float)tau;
     P.h = at<double>(h, L.h);
     P.eri = at<double>(h, L.eri);
     P.eri_f = at<float>(h, L.eri_f);
@@ -359,11 +347,11 @@ int fciqmc_create(const double *h1, const double *eri_s8, double e_core, int n_e
     P.mt_cap = z.mt_cap;
     P.mt_bits = log2_exact(z.mt_cap);
     P.merged = at<unsigned>(h, L.merged);
-    P.chunks = at<uint4>(h, L.chunks);
-    P.chunk_cap = z.chunk_cap;
     P.heavy = h->ws + L.heavy;
+    P.heavy_base = at<unsigned>(h, L.heavy_base);
+    P.heavy_att = at<unsigned>(h, L.heavy_att);
     P.heavy_cap = z.heavy_cap;
-    P.rcpb = at<float2>(h, L.rcpb);
+    P.rcpf = at<float>(h, L.rcpf);
     P.partial = at<double>(h, L.partial);
     P.hist = at<fciqmc_row>(h, L.hist);
     P.hist_cap = z.hist_cap;
@@ -410,16 +398,10 @@ int fciqmc_create(const double *h1, const double *eri_s8, double e_core, int n_e
         FQ_TRY(cudaMemcpyAsync(const_cast<unsigned char *>(P.irrep), irr.data(), irr.size(), cudaMemcpyHostToDevice, s));
         FQ_TRY(cudaMemcpyAsync(const_cast<unsigned short *>(P.pairs), pairs.data(), sizeof(unsigned short) * pairs.size(), cudaMemcpyHostToDevice, s));
         FQ_TRY(cudaMemcpyAsync(const_cast<unsigned char *>(P.ref_occ), ref_occ.data(), ref_occ.size(), cudaMemcpyHostToDevice, s));
-        // float bounds lo <= 1/L <= hi (products with L are exact in double, so the checks are exact)
-        std::vector<float2> rcpb(2 * fq::MAXSO + 2);
-        rcpb[0] = make_float2(0.f, 0.f);
-        for (int L = 1; L < 2 * fq::MAXSO + 2; ++L) {
-            float lo = f32_down(1.0 / L), hi = f32_up(1.0 / L);
-            while ((double)lo * L > 1.0) lo = std::nextafter(lo, -INFINITY);
-            while ((double)hi * L < 1.0) hi = std::nextafter(hi, INFINITY);
-            rcpb[L] = make_float2(lo, hi);
-        }
-        FQ_TRY(cudaMemcpyAsync(const_cast<float2 *>(P.rcpb), rcpb.data(), sizeof(float2) * rcpb.size(), cudaMemcpyHostToDevice, s));
+        // nearest floats of 1/L
+        std::vector<float> rcpf(2 * fq::MAXSO + 2, 0.f);
+        for (int L = 1; L < 2 * fq::MAXSO + 2; ++L) rcpf[L] = (float)(1.0 / L);
+        FQ_TRY(cudaMemcpyAsync(const_cast<float *>(P.rcpf), rcpf.data(), sizeof(float) * rcpf.size(), cudaMemcpyHostToDevice, s));
         long long *facts = at<long long>(h, L.facts);
         double *e0 = at<double>(h, L.e0);
         if (z.W == 1) {
@@ -449,17 +431,9 @@ int fciqmc_create(const double *h1, const double *eri_s8, double e_core, int n_e
         P.E0 = E0;
         P.cs = tau / p_single;
         P.cd = tau / p_double;
-        P.cd_lo = f32_down(P.cd);
-        P.cd_hi = f32_up(P.cd);
-        // bounds of cd * npairs: the product of float bounds with directed rounding
-        {
-            double lo = (double)P.cd_lo * (double)z.npairs, hi = (double)P.cd_hi * (double)z.npairs;
-            P.cdn_lo = f32_down(lo);
-            P.cdn_hi = f32_up(hi);
-        }
+        P.cdn_f = (float)(P.cd * (double)z.npairs);
         P.d53_d = (double)d53;
-        P.d53_lo = f32_down((double)d53);
-        P.d53_hi = f32_up((double)d53);
+        P.d53_f = (float)d53;
         // initial state: the reference with the initial population
         DevState st0;
         std::memset(&st0, 0, sizeof(st0));

@@ -35,7 +35,8 @@ struct DevState {
     unsigned long long claim;  // slot claim counter during annihilation
     int status;                // sticky error status (0 = OK)
     int compact_pending;
-    unsigned long long n_merged, n_chunks, n_heavy;
+    unsigned long long n_merged;
+    unsigned long long heavy_packed;  // (heavy determinants << 40) | chunks, claimed together
     unsigned long long nw_in, nd_in;
     long long c0_in;
     unsigned long long d_nw, d_nd;  // two's-complement signed changes
@@ -57,9 +58,7 @@ struct Params {
     unsigned seed;
     unsigned long long d53;
     double tau, cs, cd, E0, c_shift;
-    float tau_lo, tau_hi, cd_lo, cd_hi;   // float bounds: tau_lo <= tau <= tau_hi, cd_lo <= cd <= cd_hi
-    float cdn_lo, cdn_hi;                  // bounds of cd * npairs
-    float d53_lo, d53_hi;                  // bounds of (float)d53
+    float tau_f, cdn_f, d53_f;             // nearest floats of tau, cd * npairs and d53
     double d53_d;                          // (double)d53, exact
     int period;
     int sweep_grid;                        // blocks of k_sweep (number of partial sums)
@@ -75,7 +74,7 @@ struct Params {
     const unsigned char *irrep;       // n_orb
     const unsigned short *pairs;      // npairs: (i | j << 8), i < j electron indices
     const double *recip;              // recip[L] = 1.0 / L, L < 2 * MAXSO + 2
-    const float2 *rcpb;               // float bounds (lo, hi) of 1 / L
+    const float *rcpf;                // nearest float of 1 / L
     unsigned long long ref[MAXW];
     const unsigned char *ref_occ;     // n_elec ascending spin orbitals of the reference
     // main list, two buffers for compaction, two population arrays per buffer
@@ -93,9 +92,9 @@ struct Params {
     long long mt_cap;
     int mt_bits;
     unsigned *merged;
-    uint4 *chunks;
-    long long chunk_cap;
-    void *heavy;                      // DetView records of determinants spawned from by chunks
+    void *heavy;                      // DetView records of heavily populated determinants
+    unsigned *heavy_base;             // first chunk of each (nondecreasing in the record index)
+    unsigned *heavy_att;              // attempts of each
     long long heavy_cap;
     double *partial;
     fciqmc_row *hist;
@@ -125,20 +124,33 @@ __device__ __forceinline__ void draw2(unsigned a, unsigned tag, unsigned long lo
     w1 = (unsigned long long)o.z | ((unsigned long long)o.w << 32);
 }
 
-// floor(r * n / 2^64): uniform rank in [0, n)
+// floor(r * n / 2^64): uniform rank in [0, n). With n < 2^32, r n = r_hi n 2^32 + r_lo n and the
+// low product only contributes floor(r_lo n / 2^32) to the carry, so two 32x32 products suffice.
 __device__ __forceinline__ unsigned rank_of(unsigned long long r, unsigned n) {
-    return (unsigned)__umul64hi(r, (unsigned long long)n);
+    const unsigned long long hi = (unsigned long long)(unsigned)(r >> 32) * n;
+    const unsigned long long lo = __umulhi((unsigned)r, n);
+    return (unsigned)((hi + lo) >> 32);
 }
 
 // ---------------------------------------------------------------------------
 // bit-string helpers
+// Word selection by comparison rather than by a computed index keeps W-word arrays in registers.
 template <int W>
 __device__ __forceinline__ int bit_of(const unsigned long long (&d)[W], int k) {
-    return (int)((d[k >> 6] >> (k & 63)) & 1ull);
+    const unsigned long long w = (W == 1 || k < 64) ? d[0] : d[W - 1];
+    return (int)((w >> (k & 63)) & 1ull);
 }
 template <int W>
 __device__ __forceinline__ void flip(unsigned long long (&d)[W], int k) {
-    d[k >> 6] ^= 1ull << (k & 63);
+    const unsigned long long b = 1ull << (k & 63);
+    if (W == 1 || k < 64) d[0] ^= b;
+    else d[W - 1] ^= b;
+}
+template <int W>
+__device__ __forceinline__ void clear_bit(unsigned long long (&d)[W], int k) {
+    const unsigned long long b = ~(1ull << (k & 63));
+    if (W == 1 || k < 64) d[0] &= b;
+    else d[W - 1] &= b;
 }
 // bits [0, n) of a 64-bit word, n in [0, 64]
 __device__ __forceinline__ unsigned long long low_bits(int n) {
@@ -197,8 +209,19 @@ __device__ __forceinline__ int eidx(int p, int q, int r, int s) {
 __device__ __forceinline__ double eri_d(const Params &P, int p, int q, int r, int s) {
     return __ldg(P.eri + eidx(p, q, r, s));
 }
-__device__ __forceinline__ float eri_f(const Params &P, int p, int q, int r, int s) {
-    return __ldg(P.eri_f + eidx(p, q, r, s));
+// L2 policy that keeps the integral tables resident while the walker list streams past them.
+__device__ __forceinline__ unsigned long long keep_policy() {
+    unsigned long long pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ float ld_keep(const float *p, unsigned long long pol) {
+    float v;
+    asm volatile("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ float eri_f(const Params &P, int p, int q, int r, int s, unsigned long long pol) {
+    return ld_keep(P.eri_f + eidx(p, q, r, s), pol);
 }
 
 // Algorithm 1 over the ascending occupied list: hash = p hash + map(orb_i) i (uint64 wraparound).

@@ -17,8 +17,11 @@
 namespace fq {
 
 constexpr int kTile = 256;          // determinants per sweep tile = threads per sweep block
+#ifndef FQ_SWEEP_MIN_BLOCKS
+#define FQ_SWEEP_MIN_BLOCKS 4          // resident sweep blocks per SM the register budget is sized for
+#endif
 constexpr int kHeavy = 1024;        // |C_i| above this: attempts go to the chunked heavy path
-constexpr int kChunk = 1024;        // attempts per heavy chunk (one warp task)
+constexpr int kChunk = 256;         // attempts per heavy chunk (one warp task)
 constexpr unsigned long long kSaltMerge = 0x5851F42D4C957F2Dull;
 constexpr unsigned long long kSaltIndex = 0x14057B7EF767814Full;
 constexpr unsigned long long kFlagUnit = 1ull << 40;  // merge payload: (#initiator spawns << 40) + amount
@@ -51,33 +54,21 @@ __device__ __forceinline__ void load_tables(const Params &P, Tables &T) {
     for (int k = threadIdx.x; k < P.npairs; k += blockDim.x) T.pairs[k] = P.pairs[k];
 }
 
-// ---------------------------------------------------------------------------- interval bounds
-// An interval [lo, hi] that contains a real number, propagated with directed rounding.
-struct Iv { float lo, hi; };
-// x rounded to nearest float as f: x lies within |f| 2^-24 (+ a subnormal guard) of f
-__device__ __forceinline__ Iv iv_rn(float f) {
-    float e = __fmaf_ru(fabsf(f), 0x1p-24f, 1e-30f);
-    return {__fsub_rd(f, e), __fadd_ru(f, e)};
-}
-__device__ __forceinline__ Iv iv_sub(Iv a, Iv b) { return {__fsub_rd(a.lo, b.hi), __fsub_ru(a.hi, b.lo)}; }
-__device__ __forceinline__ Iv iv_abs(Iv a) {
-    if (a.lo >= 0.f) return a;
-    if (a.hi <= 0.f) return {-a.hi, -a.lo};
-    return {0.f, fmaxf(-a.lo, a.hi)};
-}
-// product of nonnegative intervals
-__device__ __forceinline__ Iv iv_mul(Iv a, Iv b) { return {__fmul_rd(a.lo, b.lo), __fmul_ru(a.hi, b.hi)}; }
-// widen by the relative error of the FP64 evaluation (a few ulp of 2^-53)
-__device__ __forceinline__ Iv iv_slack(Iv a) { return {__fmul_rd(a.lo, 1.0f - 0x1p-20f), __fmul_ru(a.hi, 1.0f + 0x1p-20f)}; }
+// ---------------------------------------------------------------------------- float bounds
+// Decisions n = floor(p) + [u < p - floor(p)] are first tried with float bounds lo <= p_d <= hi of the
+// value p_d the exact FP64 expression would give; only undecided cases evaluate p_d. Bounds use
+// round-to-nearest float arithmetic with explicit margins: an input rounded to the nearest float f
+// lies within |f| 2^-24 of it, every float operation adds at most 2^-24 relative, and the final
+// factors (1 +- 2^-18) cover those roundings and the FP64 rounding of p_d with room to spare.
+constexpr float kUp = 1.0f + 0x1p-18f;
+constexpr float kDown = 1.0f - 0x1p-18f;
 
-// Decision n = floor(p) + [u < p - floor(p)] for p in the (nonnegative) interval pv and u = (r >> 11) 2^-53:
-// returns 0 or 1 when the bounds decide it, -1 when the exact FP64 evaluation is needed.
-__device__ __forceinline__ int bernoulli_decide(Iv pv, unsigned long long r) {
-    if (!(pv.hi < 1.0f)) return -1;
-    float u_lo = (float)(unsigned)(r >> 40) * 0x1p-24f;  // top 24 bits: u_lo <= u < u_lo + 2^-24
-    float u_hi = u_lo + 0x1p-24f;
-    if (u_lo > pv.hi) return 0;
-    if (pv.lo > 0.f && u_hi <= pv.lo) return 1;
+// Decision against u = (r >> 11) 2^-53 (death draw): 0 or 1 when decided, -1 otherwise.
+__device__ __forceinline__ int bernoulli_decide(float lo, float hi, unsigned long long r) {
+    if (!(hi < 1.0f)) return -1;
+    const float u_lo = (float)(unsigned)(r >> 40) * 0x1p-24f;  // exact: u_lo <= u < u_lo + 2^-24
+    if (u_lo > hi) return 0;
+    if (lo > 0.f && u_lo + 0x1p-24f <= lo) return 1;
     return -1;
 }
 
@@ -194,7 +185,7 @@ __device__ __forceinline__ unsigned good_set(const Params &P, const Tables &T, c
 // [0, d53) for a double and on [d53, 2^53) for a single.
 template <int W, bool TAB>
 __device__ __forceinline__ AttemptOut spawn_attempt(const Params &P, const Tables &T, const DetView<W> &v,
-                                                     const GoodTable<W> *tab, const float2 *rcpb, unsigned a,
+                                                     const GoodTable<W> *tab, const float *rcpf, unsigned a,
                                                      unsigned iter, unsigned long long *cnt) {
     AttemptOut out{false, 0u};
     unsigned long long r0, r1, r2, r3;
@@ -264,36 +255,34 @@ __device__ __forceinline__ AttemptOut spawn_attempt(const Params &P, const Table
         unsigned long long bm[W];
 #pragma unroll
         for (int w = 0; w < W; ++w) bm[w] = ~v.d[w] & T.mask[cb * MAXW + w];
-        bm[ao >> 6] &= ~(1ull << (ao & 63));
+        clear_bit<W>(bm, ao);
         const int bo = select_bit<W>(bm, (int)rank_of(r3, m_ba));
         const int A = min(ao, bo), B = max(ao, bo);
         const unsigned L = m_ba + m_ab;
         const bool t1 = ((i & 1) == (A & 1)) && ((j & 1) == (B & 1));
         const bool t2 = ((i & 1) == (B & 1)) && ((j & 1) == (A & 1));
         // bounds of p = |H| tau / P_gen from the float copy of the integrals
-        Iv x = {0.f, 0.f}, y = {0.f, 0.f};
-        if (t1) x = iv_rn(eri_f(P, i >> 1, A >> 1, j >> 1, B >> 1));
-        if (t2) y = iv_rn(eri_f(P, i >> 1, B >> 1, j >> 1, A >> 1));
-        const Iv hv = iv_sub(x, y);
-        const Iv ah = iv_abs(hv);
-        const float gf = small_f(G), baf = small_f(m_ba), abf = small_f(m_ab);
-        const float2 rl = rcpb[L];
-        Iv pv;
-        pv.lo = __fmul_rd(__fmul_rd(__fmul_rd(__fmul_rd(__fmul_rd(ah.lo, P.cdn_lo), gf), baf), abf), rl.x);
-        pv.hi = __fmul_ru(__fmul_ru(__fmul_ru(__fmul_ru(__fmul_ru(ah.hi, P.cdn_hi), gf), baf), abf), rl.y);
-        pv = iv_slack(pv);
+        const unsigned long long pol = keep_policy();
+        const float xf = t1 ? eri_f(P, i >> 1, A >> 1, j >> 1, B >> 1, pol) : 0.f;
+        const float yf = t2 ? eri_f(P, i >> 1, B >> 1, j >> 1, A >> 1, pol) : 0.f;
+        const float hf = xf - yf;
+        const float eh = fmaf(fabsf(xf) + fabsf(yf), 0x1p-22f, 1e-30f);  // >= |H - hf| with a factor 2
+        const float ah_lo = fabsf(hf) - eh, ah_hi = fabsf(hf) + eh;
+        const float F = P.cdn_f * small_f(G) * small_f(m_ba) * small_f(m_ab) * rcpf[L];
+        const float p_hi = ah_hi * F * kUp;
+        const float p_lo = ah_lo * F * kDown;
         int dec = -1;
-        if (pv.hi < 1.0f) {
-            // Bernoulli threshold t < p d53: bounds on both sides; t known to 2^30
-            const Iv th = iv_slack(Iv{__fmul_rd(pv.lo, P.d53_lo), __fmul_ru(pv.hi, P.d53_hi)});
+        if (p_hi < 1.0f) {
+            // threshold t < p d53 with t known to 2^30
+            const float th_hi = p_hi * P.d53_f * kUp, th_lo = p_lo * P.d53_f * kDown;
             const float q_lo = small_f((unsigned)(t >> 30)) * 0x1p30f;
-            if (q_lo >= th.hi) dec = 0;
-            else if (pv.lo > 0.f && q_lo + 0x1p30f <= th.lo) dec = 1;
+            if (q_lo >= th_hi) dec = 0;
+            else if (ah_lo > 0.f && q_lo + 0x1p30f <= th_lo) dec = 1;
         }
         if (dec == 0) return out;
-        if (dec == 1 && (hv.lo > 0.f || hv.hi < 0.f)) {
+        if (dec == 1) {
             n = 1;
-            sgn_h = (hv.lo > 0.f) ? 1 : -1;
+            sgn_h = hf > 0.f ? 1 : -1;  // |hf| > eh: same sign as H
             if (double_parity<W>(v.d, i, j, A, B)) sgn_h = -sgn_h;
         } else {
             atomicAdd(&P.st->exact_spawn, 1ull);
@@ -325,24 +314,24 @@ __device__ __forceinline__ AttemptOut spawn_attempt(const Params &P, const Table
 // r = (tau ((H_ii - E0) - S)) |C|; n = floor(|r|) + [u < frac |r|]; C -= sign(C) n for r >= 0, += for r < 0.
 template <int W>
 __device__ __forceinline__ int death_step(const Params &P, const DetView<W> &v, float hdf, const double *hd_ptr,
-                                          double S, float S_lo, float S_hi, unsigned iter,
-                                          unsigned long long *cnt) {
+                                          double S, float S_f, unsigned iter, unsigned long long *cnt) {
     const int c = v.c;
     const unsigned ac = (unsigned)(c < 0 ? -c : c);
     unsigned long long u, unused;
     draw2(0u, 3u, v.fp, P.seed, iter, u, unused);
-    Iv hb = iv_rn(hdf);
-    Iv t = iv_sub(hb, Iv{S_lo, S_hi});
-    Iv at = iv_abs(t);
-    Iv ar = iv_slack(iv_mul(iv_mul(at, Iv{P.tau_lo, P.tau_hi}), Iv{__uint2float_rd(ac), __uint2float_ru(ac)}));
-    int dec = bernoulli_decide(ar, u);
+    const float tf = hdf - S_f;
+    const float et = fmaf(fabsf(hdf) + fabsf(S_f), 0x1p-22f, 1e-30f);  // >= |(H_ii - E0 - S) - tf|
+    const float acf = __uint2float_rn(ac);
+    const float at_lo = fabsf(tf) - et, at_hi = fabsf(tf) + et;
+    const float r_hi = at_hi * P.tau_f * acf * kUp, r_lo = at_lo * P.tau_f * acf * kDown;
+    const int dec = bernoulli_decide(r_lo, r_hi, u);
     int nd;
     bool positive;
     if (dec == 0) {
         return c;
-    } else if (dec == 1 && (t.lo > 0.f || t.hi < 0.f)) {
+    } else if (dec == 1) {
         nd = 1;
-        positive = t.lo > 0.f;
+        positive = tf > 0.f;  // at_lo > 0: the sign of tf is the sign of r
     } else {
         atomicAdd(&P.st->exact_death, 1ull);
         double hd = *hd_ptr;
@@ -400,29 +389,29 @@ __device__ __forceinline__ double block_sum_f64(double v, double *s_red) {
 }
 
 // ---------------------------------------------------------------------------- kernels
-// Float bounds of 1/L for the spawn bound, copied to shared memory.
-__device__ __forceinline__ void load_rcpb(const Params &P, float2 *s_rcpb) {
-    for (int k = threadIdx.x; k < 2 * MAXSO + 2; k += blockDim.x) s_rcpb[k] = P.rcpb[k];
+// Nearest floats of 1/L for the spawn bound, copied to shared memory.
+__device__ __forceinline__ void load_rcpf(const Params &P, float *s_rcpf) {
+    for (int k = threadIdx.x; k < 2 * MAXSO + 2; k += blockDim.x) s_rcpf[k] = P.rcpf[k];
 }
 
 template <int W>
-__global__ void __launch_bounds__(kTile) k_sweep(Params P) {
+__global__ void __launch_bounds__(kTile, FQ_SWEEP_MIN_BLOCKS) k_sweep(Params P) {
     DevState *st = P.st;
     if (st->status) return;
     __shared__ Tables T;
     __shared__ DetView<W> s_dv[kTile];
     __shared__ unsigned s_off[kTile + 1];
     __shared__ unsigned s_wsum[kTile / 32];
-    __shared__ float2 s_rcpb[2 * MAXSO + 2];
+    __shared__ float s_rcpf[2 * MAXSO + 2];
     __shared__ unsigned long long s_red[(kTile / 32) * (NCNT + 4)];
     __shared__ double s_redf[kTile / 32];
     load_tables(P, T);
-    load_rcpb(P, s_rcpb);
+    load_rcpf(P, s_rcpf);
     const int lb = st->lb, pp = st->pp;
     const long long len = st->list_len;
     const unsigned iter = (unsigned)st->iter;
     const double S = st->shift;
-    const float S_lo = __double2float_rd(S), S_hi = __double2float_ru(S);
+    const float S_f = __double2float_rn(S);
     const unsigned long long *det = P.det[lb];
     const float *hdf = P.hdf[lb];
     const double *hd = P.hd[lb];
@@ -464,22 +453,24 @@ __global__ void __launch_bounds__(kTile) k_sweep(Params P) {
                 for (int w = 0; w < W; ++w) { xd |= v.d[w] ^ P.ref[w]; diff += __popcll(v.d[w] ^ P.ref[w]); }
                 if (xd == 0) st->c0_in = c;
                 else if (diff == 2 || diff == 4) num = __dadd_rn(num, __dmul_rn(h0i<W>(P, v.d), (double)c));
-                const int nc = death_step<W>(P, v, hf, hd + s, S, S_lo, S_hi, iter, acc);
+                const int nc = death_step<W>(P, v, hf, hd + s, S, S_f, iter, acc);
                 pop_out[s] = nc;
                 acc[NCNT + 2] += (unsigned long long)((long long)(nc < 0 ? -nc : nc) - (long long)ac);
                 if (nc == 0) acc[NCNT + 3] += (unsigned long long)(-1LL);
                 acc[C_ATTEMPTS] += ac;
                 if (ac > (unsigned)kHeavy) {
-                    // heavily populated determinant: its attempts go to warp-sized chunks of k_heavy
-                    const unsigned long long hidx = atomicAdd(&st->n_heavy, 1ull);
+                    // heavily populated determinant: a record for k_heavy, whose warps take chunks of kChunk
+                    // attempts; record index and first chunk are claimed by one atomic, so the first
+                    // chunks are nondecreasing in the record index
                     const unsigned nch = (ac + kChunk - 1) / kChunk;
-                    const unsigned long long base = atomicAdd(&st->n_chunks, (unsigned long long)nch);
-                    if (hidx >= (unsigned long long)P.heavy_cap || base + nch > (unsigned long long)P.chunk_cap) {
+                    const unsigned long long old = atomicAdd(&st->heavy_packed, (1ull << 40) | nch);
+                    const unsigned long long hidx = old >> 40;
+                    if (hidx >= (unsigned long long)P.heavy_cap) {
                         set_status(st, FCIQMC_ERR_CAPACITY);
                     } else {
                         heavy[hidx] = v;
-                        for (unsigned q = 0; q < nch; ++q)
-                            P.chunks[base + q] = make_uint4((unsigned)hidx, q * kChunk, min((q + 1) * kChunk, ac), 0u);
+                        P.heavy_base[hidx] = (unsigned)(old & ((1ull << 40) - 1ull));
+                        P.heavy_att[hidx] = ac;
                     }
                 } else {
                     att = ac;
@@ -517,7 +508,7 @@ __global__ void __launch_bounds__(kTile) k_sweep(Params P) {
                     int mid = (lo + hi + 1) >> 1;
                     if (s_off[mid] <= k) lo = mid; else hi = mid - 1;
                 }
-                ao = spawn_attempt<W, false>(P, T, s_dv[lo], nullptr, s_rcpb, k - s_off[lo], iter, acc);
+                ao = spawn_attempt<W, false>(P, T, s_dv[lo], nullptr, s_rcpf, k - s_off[lo], iter, acc);
             }
             long long slot = warp_append(&st->n_merged, ao.claimed);
             if (ao.claimed && slot < P.mt_cap) P.merged[slot] = ao.pos;
@@ -542,11 +533,13 @@ __global__ void __launch_bounds__(kTile) k_heavy(Params P) {
     __shared__ Tables T;
     __shared__ DetView<W> s_v[NW];
     __shared__ GoodTable<W> s_tab[NW];
-    __shared__ float2 s_rcpb[2 * MAXSO + 2];
+    __shared__ float s_rcpf[2 * MAXSO + 2];
     __shared__ unsigned long long s_red[NW * NCNT];
     load_tables(P, T);
-    load_rcpb(P, s_rcpb);
-    const unsigned long long nch = st->n_chunks;
+    load_rcpf(P, s_rcpf);
+    const unsigned long long packed = st->heavy_packed;
+    const long long nh = min((long long)(packed >> 40), P.heavy_cap);
+    const unsigned long long nch = packed & ((1ull << 40) - 1ull);
     const unsigned iter = (unsigned)st->iter;
     const DetView<W> *heavy = reinterpret_cast<const DetView<W> *>(P.heavy);
     unsigned long long cnt[NCNT];
@@ -556,13 +549,20 @@ __global__ void __launch_bounds__(kTile) k_heavy(Params P) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned long long gw = (unsigned long long)blockIdx.x * NW + warp;
     const unsigned long long nwarps = (unsigned long long)gridDim.x * NW;
-    unsigned cur = 0xFFFFFFFFu;
+    long long cur = -1;
     DetView<W> &v = s_v[warp];
     GoodTable<W> &tab = s_tab[warp];
-    for (unsigned long long q = gw; q < nch && q < (unsigned long long)P.chunk_cap; q += nwarps) {
-        const uint4 ch = P.chunks[q];
-        if (ch.x != cur) {
-            const unsigned long long *src = reinterpret_cast<const unsigned long long *>(heavy + ch.x);
+    for (unsigned long long q = gw; q < nch && nh > 0; q += nwarps) {
+        // record holding chunk q: last record whose first chunk is <= q
+        long long lo = 0, hi = nh - 1;
+        while (lo < hi) {
+            const long long mid = (lo + hi + 1) >> 1;
+            if ((unsigned long long)P.heavy_base[mid] <= q) lo = mid; else hi = mid - 1;
+        }
+        const unsigned a0 = (unsigned)(q - P.heavy_base[lo]) * kChunk;
+        const unsigned a1 = min(a0 + (unsigned)kChunk, P.heavy_att[lo]);
+        if (lo != cur) {
+            const unsigned long long *src = reinterpret_cast<const unsigned long long *>(heavy + lo);
             unsigned long long *dstv = reinterpret_cast<unsigned long long *>(&v);
             for (int k = lane; k < (int)(sizeof(DetView<W>) / 8); k += 32) dstv[k] = src[k];
             __syncwarp();
@@ -570,18 +570,18 @@ __global__ void __launch_bounds__(kTile) k_heavy(Params P) {
                 const int sc = lane >> 3, gij = lane & 7;
                 const int si = sc == 1 ? 1 : 0, sj = sc == 0 ? 0 : 1;
                 unsigned long long gm[W];
-                unsigned G = good_set<W>(P, T, v, si, sj, gij, gm);
+                const unsigned G = good_set<W>(P, T, v, si, sj, gij, gm);
                 tab.G[lane] = (unsigned short)G;
 #pragma unroll
                 for (int w = 0; w < W; ++w) tab.gm[lane][w] = gm[w];
             }
             __syncwarp();
-            cur = ch.x;
+            cur = lo;
         }
-        for (unsigned base = ch.y; base < ch.z; base += 32) {
+        for (unsigned base = a0; base < a1; base += 32) {
             const unsigned a = base + lane;
             AttemptOut ao{false, 0u};
-            if (a < ch.z) ao = spawn_attempt<W, true>(P, T, v, &tab, s_rcpb, a, iter, cnt);
+            if (a < a1) ao = spawn_attempt<W, true>(P, T, v, &tab, s_rcpf, a, iter, cnt);
             long long slot = warp_append(&st->n_merged, ao.claimed);
             if (ao.claimed && slot < P.mt_cap) P.merged[slot] = ao.pos;
         }
@@ -782,8 +782,7 @@ __global__ void k_finish(Params P) {
     if ((vacated > 64 && vacated * 4 > new_len) || (vacated > 0 && new_len * 4 > P.cap * 3))
         st->compact_pending = 1;
     st->n_merged = 0;
-    st->n_chunks = 0;
-    st->n_heavy = 0;
+    st->heavy_packed = 0;
     st->nw_in = st->nd_in = 0;
     st->c0_in = 0;
     st->d_nw = st->d_nd = 0;
