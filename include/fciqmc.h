@@ -225,6 +225,47 @@ int fciqmc_get_info(const fciqmc_handle *h, fciqmc_info *info);
  * into kernel_ms[FCIQMC_N_KERNELS] (host array, not cleared). */
 int fciqmc_profile(fciqmc_handle *h, int32_t n_iterations, double *kernel_ms);
 
+/* Largest walker list fciqmc_estimate_list_static accepts. Its scratch is one
+ * static device array per device: FCIQMC_STATIC_MAX_DETS / 256 doubles (256 KiB)
+ * and three 64-bit counters. */
+#define FCIQMC_STATIC_MAX_DETS (1LL << 23)
+
+/* The paper has no counterpart to this entry point: it is an allocation-free
+ * form of fciqmc_estimators for callers that hold a walker list on the device
+ * but cannot allocate device memory when they need its estimators. Examples
+ * are a process that commits all device memory to a fixed pool up front, code
+ * for which cudaMalloc's implicit device synchronisation is not acceptable,
+ * and tools that only see device views of another program's list. It needs no
+ * handle and no workspace.
+ *
+ * Computes, for the list (dets, pops) of n_dets entries (zero populations are
+ * skipped): out[0] = sum |C_i|, out[1] = number of nonzero entries, out[2] =
+ * C_0 (population of `reference`, 0 if absent), out[3] = sum_{i != 0}
+ * <D_i|H|D_0> C_i (the Eq. 2 numerator; each term as in fciqmc_estimators,
+ * summed per 256-entry tile and then over tiles in order, so the value agrees
+ * with fciqmc_estimators to rounding).
+ *   h_dev, eri_dev  device arrays in the layout of fciqmc_create (n_orb^2 and
+ *                   the 8-fold packed ERIs), read only.
+ *   reference       host array of W words with n_elec bits set.
+ *   dets_dev        device, n_dets x W words; pops_dev device, n_dets int32.
+ *   out_dev         device, 4 doubles, written by the last kernel.
+ *   cuda_stream     stream the three kernels are enqueued on (asynchronous).
+ * Returns FCIQMC_ERR_CAPACITY, before launching anything, if n_dets >
+ * FCIQMC_STATIC_MAX_DETS; FCIQMC_ERR_UNSUPPORTED for sizes beyond the
+ * library's limits; FCIQMC_ERR_INVALID_ARG for null pointers or a reference
+ * with the wrong electron count.
+ * Scratch: the first call on each device looks up the device address of the
+ * static array (cudaGetSymbolAddress, with that device current) and caches
+ * it, so that first call should come before any stream capture. The array
+ * stays resident on every device that loaded the library until the process
+ * exits, is shared by all calls on that device and keeps the last call's
+ * contents; each call clears its counters before use. Calls whose kernels
+ * overlap on the GPU (different streams, no ordering) race on the array.
+ * Allocates no memory: no cudaMalloc, no cudaFree, no allocating library call. */
+int fciqmc_estimate_list_static(const double *h_dev, const double *eri_dev, int n_elec, int n_orb,
+                                const uint64_t *reference, const uint64_t *dets_dev, const int32_t *pops_dev,
+                                int64_t n_dets, double *out_dev, void *cuda_stream);
+
 /* Releases host-side resources (graphs, events). Synchronising. The
  * workspace stays the caller's. Accepts NULL. */
 void fciqmc_destroy(fciqmc_handle *h);

@@ -16,8 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfciqmc.so")
-SOURCES = ["fciqmc.cu"]
-DEPS = ["fciqmc.cu", "fciqmc_kernels.cuh", "fciqmc_device.cuh"]
+SOURCES = ["fciqmc.cu", "fciqmc_static.cu"]
+DEPS = ["fciqmc.cu", "fciqmc_static.cu", "fciqmc_kernels.cuh", "fciqmc_device.cuh"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
               "-Xcompiler", "-ffp-contract=off", "-fmad=false"]
@@ -96,7 +96,9 @@ class Info(ctypes.Structure):
 # every symbol declared in include/fciqmc.h
 SYMBOLS = ["fciqmc_default_options", "fciqmc_workspace_bytes", "fciqmc_create", "fciqmc_step", "fciqmc_sync",
            "fciqmc_estimators", "fciqmc_history", "fciqmc_n_dets", "fciqmc_get_walkers", "fciqmc_set_walkers",
-           "fciqmc_get_state", "fciqmc_get_info", "fciqmc_profile", "fciqmc_destroy", "fciqmc_strerror"]
+           "fciqmc_get_state", "fciqmc_get_info", "fciqmc_profile", "fciqmc_estimate_list_static", "fciqmc_destroy",
+           "fciqmc_strerror"]
+STATIC_MAX_DETS = 1 << 23
 N_KERNELS = 8
 KERNEL_NAMES = ["compact_copy", "index_clear", "index_fill", "compact_finish", "sweep", "heavy", "annihilate",
                 "finish"]
@@ -125,6 +127,8 @@ def _declare(L):
     L.fciqmc_get_state.argtypes = [vp, P(State)]
     L.fciqmc_get_info.argtypes = [vp, P(Info)]
     L.fciqmc_profile.argtypes = [vp, i32, f64p]
+    L.fciqmc_estimate_list_static.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, u64p, vp, vp, i64, vp, vp]
+    L.fciqmc_estimate_list_static.restype = ctypes.c_int
     L.fciqmc_destroy.argtypes = [vp]
     L.fciqmc_destroy.restype = None
     L.fciqmc_strerror.argtypes = [ctypes.c_int]

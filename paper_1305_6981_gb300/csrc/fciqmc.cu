@@ -400,7 +400,7 @@ int fciqmc_create(const double *h1, const double *eri_s8, double e_core, int n_e
         FQ_TRY(cudaMemcpyAsync(const_cast<unsigned char *>(P.ref_occ), ref_occ.data(), ref_occ.size(), cudaMemcpyHostToDevice, s));
         // nearest floats of 1/L
         std::vector<float> rcpf(2 * fq::MAXSO + 2, 0.f);
-        for (int L = 1; L < 2 * fq::MAXSO + 2; ++L) rcpf[L] = (float)(1.0 / L);
+        for (int l = 1; l < 2 * fq::MAXSO + 2; ++l) rcpf[l] = (float)(1.0 / l);
         FQ_TRY(cudaMemcpyAsync(const_cast<float *>(P.rcpf), rcpf.data(), sizeof(float) * rcpf.size(), cudaMemcpyHostToDevice, s));
         long long *facts = at<long long>(h, L.facts);
         double *e0 = at<double>(h, L.e0);
