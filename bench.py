@@ -38,6 +38,16 @@ from paper_1305_6981_gb300 import synth  # noqa: E402
 
 METRIC = "spawn attempts/s at 1e8 walkers (24e/60o, initiator, tau 0.001)"
 
+# Instruction-issue roofline of the spawning kernels (they are bound by their instruction stream, not
+# by HBM). Per-unit figures are warp instructions per attempt from ncu (smsp__inst_executed.sum of one
+# launch divided by the attempts that launch made), taken with the --ncu-case command recorded in the
+# summary under profiles/; they must be re-measured whenever those kernels change.
+WARP_INST_PER_ATTEMPT = {"heavy": 22.5, "sweep": 56.8}
+# DRAM bytes (read + write) per launch of each kernel at the full workload, from the same summary.
+DRAM_BYTES_PER_LAUNCH = {"heavy": 18_496_896, "sweep": 124_689_024, "annihilate": 51_637_248}
+ISSUE_PER_CLK_PER_SM = 4  # warp instructions: 4 schedulers per SM, one issue each per clock
+N_SMS = 152
+
 WORKLOADS = {
     "24e60o": dict(system=synth.large_24e60o, tau=0.001, thr=3, target=100_000_000, main_capacity=200_000_000,
                    spawn_capacity=1 << 27, initial_population=20_000, initial_shift=3.0, max_growth=40_000,
@@ -64,6 +74,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle baseline")
     ap.add_argument("--growth-log", default="")
+    ap.add_argument("--ncu-case", action="store_true",
+                    help="grow to --target walkers, run one iteration inside the NVTX range 'prof' and exit "
+                         "(the case the ncu summaries are taken on)")
     return ap.parse_args()
 
 
@@ -191,21 +204,16 @@ def algorithmic_bytes(W, nd, slots, merged, inserted):
     return sweep, annih
 
 
-def run_gpu(args, wl, rank, world, local_rank):
-    import torch
-    import torch.distributed as dist
-
+def grow(args, wl, rank):
+    """Create the run and grow the population on the GPU until the shift starts varying (untimed)."""
     from paper_1305_6981_gb300 import Fciqmc
 
-    torch.cuda.set_device(local_rank)
     system = wl["system"]()
     target = args.target or wl["target"]
-    cap = wl["main_capacity"] if not args.target else max(4 * args.target, 1 << 16)
-    scap = wl["spawn_capacity"] if not args.target else max(1 << 14, 1 << int(np.ceil(np.log2(2 * args.target))))
+    cap = wl["main_capacity"] if not args.target else max(2 * args.target, 1 << 16)
+    scap = wl["spawn_capacity"] if not args.target else max(1 << 14, 1 << int(np.ceil(np.log2(args.target))))
     g = Fciqmc(system, wl["tau"], wl["thr"], target_walkers=target, initial_population=wl["initial_population"],
                initial_shift=wl["initial_shift"], seed=1 + rank, main_capacity=cap, spawn_capacity=scap)
-    info = g.info()
-    # growth (untimed)
     t_grow = time.perf_counter()
     grown, chunk = 0, 50
     log = []
@@ -220,7 +228,32 @@ def run_gpu(args, wl, rank, world, local_rank):
             break
     g.step(wl["equilibrate"])
     grown += wl["equilibrate"]
-    t_grow = time.perf_counter() - t_grow
+    return g, grown, time.perf_counter() - t_grow, log
+
+
+def run_ncu_case(args, wl):
+    import torch
+    torch.cuda.set_device(0)
+    g, grown, _, _ = grow(args, wl, 0)
+    g.sync()
+    torch.cuda.nvtx.range_push("prof")
+    g.step(1)
+    torch.cuda.nvtx.range_pop()
+    st = g.sync()
+    row = g.history(1)[0]
+    info = g.info()
+    print(json.dumps({"ncu_case": args.workload, "target": args.target or wl["target"], "grown": grown, "status": st,
+                      "workspace_gb": info["workspace_bytes"] / 1e9, "row": row}), flush=True)
+    g.close()
+
+
+def run_gpu(args, wl, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    torch.cuda.set_device(local_rank)
+    g, grown, t_grow, log = grow(args, wl, rank)
+    info = g.info()
     if args.growth_log and rank == 0:
         with open(args.growth_log, "w") as f:
             json.dump(log, f)
@@ -265,6 +298,7 @@ def run_gpu(args, wl, rank, world, local_rank):
     exact = {"spawn_per_iter": (est["exact_spawns"] - e_before["exact_spawns"]) / args.steps,
              "death_per_iter": (est["exact_deaths"] - e_before["exact_deaths"]) / args.steps}
     prof = g.profile(5)
+    prow = g.history(5)
     slots = est["list_slots"]
     sweep_b, annih_b = algorithmic_bytes(info["words"], nd_mean, slots, merged_mean, inserted_mean)
     peaks = {}
@@ -274,10 +308,16 @@ def run_gpu(args, wl, rank, world, local_rank):
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    dom = max(("sweep", "heavy", "annihilate"), key=lambda k: prof[k])
+    # dominant kernel and its instruction-issue roofline
+    heavy_att = float(np.mean([r["heavy_attempts"] for r in prow]))
+    light_att = float(np.mean([r["attempts"] - r["heavy_attempts"] for r in prow]))
+    units = {"heavy": heavy_att, "sweep": light_att}
+    dom = max(("sweep", "heavy"), key=lambda k: prof[k])
     dom_ms = prof[dom] / 5.0
-    dom_bytes = {"sweep": sweep_b, "annihilate": annih_b, "heavy": merged_mean * (8 * info["words"] + 12)}[dom]
-    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
+    sm_mhz = clk.get("sm_mhz") or float(peaks.get("sm_max_mhz", 2070.0))
+    issue_peak = ISSUE_PER_CLK_PER_SM * N_SMS * sm_mhz * 1e6 / 1e9  # Gwarp-inst/s
+    achieved = WARP_INST_PER_ATTEMPT[dom] * units[dom] / (dom_ms * 1e-3) / 1e9
+    cycle_gbs = (sweep_b + annih_b) / (ms_max / args.steps * 1e-3) / 1e9
     out = None
     if rank == 0:
         out = {
@@ -290,11 +330,15 @@ def run_gpu(args, wl, rank, world, local_rank):
                        "inserted_per_iter": inserted_mean, "growth_iterations": grown,
                        "growth_seconds": round(t_grow, 1), "l2": "inputs larger than L2 (main list ~GBs)",
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
-            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": achieved / hbm_peak, "traffic": None, "peak_source": peak_src,
-                         "algorithmic_bytes_per_launch": dom_bytes, "launch_ms": dom_ms},
+            "roofline": {"bound": "alu", "kernel": f"k_{dom}", "achieved": achieved, "peak": issue_peak,
+                         "unit": "Gwarp-inst/s", "frac": achieved / issue_peak,
+                         "traffic": DRAM_BYTES_PER_LAUNCH.get(dom),
+                         "per_unit": f"{WARP_INST_PER_ATTEMPT[dom]} warp instructions per attempt (ncu)",
+                         "units_per_launch": units[dom], "launch_ms": dom_ms,
+                         "peak_derivation": f"{ISSUE_PER_CLK_PER_SM} warp-inst/clk/SM x {N_SMS} SMs x {sm_mhz:.0f} MHz"},
+            "hbm": {"cycle_algorithmic_gbs": cycle_gbs, "peak": hbm_peak, "frac": cycle_gbs / hbm_peak,
+                    "peak_source": peak_src, "bytes_per_iter": sweep_b + annih_b},
             "kernel_ms_per_iter": {k: v / 5.0 for k, v in prof.items()},
-            "cycle_hbm_gbs": (sweep_b + annih_b) / (ms_max / args.steps * 1e-3) / 1e9,
             "clocks": clk,
             "status": st,
             "exact_path": exact,
@@ -343,6 +387,9 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
     if args.impl == "reference":
         run_reference(args, wl, rank, world)
+        return
+    if args.ncu_case:
+        run_ncu_case(args, wl)
         return
     import torch.distributed as dist
     if world > 1:

@@ -878,3 +878,130 @@ int64_t oq_attempt(const oq_t *q, const uint64_t *d, int32_t c, uint32_t a, uint
     memcpy(child, d, sizeof(uint64_t) * q->W);
     return attempt_one(q, d, c, fp, a, child, is_null, &err);
 }
+
+/* ------------------------------------------------------------------------- */
+/* Energy functional E(h, V; c) = c^T H c / c^T c over an explicit determinant list and its gradient
+ * with respect to h (full matrix, symmetric convention: dE = sum_pq grad_h[p][q] dh[p][q] for
+ * symmetric dh) and to the packed ERIs (total derivative with respect to each stored element).
+ * E uses the Slater-Condon elements above (over all ordered pairs, I and J ascending); the gradient
+ * uses the density matrices obtained by applying the operators themselves:
+ *   gamma_PQ   = sum_{I,J} c_J c_I <J| a+_{P s} a_{Q s} |I>                         (spin summed)
+ *   Gamma_PQRS = sum_{I,J} c_J c_I <J| a+_{P s} a+_{R t} a_{S t} a_{Q s} |I>         (spin summed)
+ * so that E = (sum h_PQ gamma_PQ + 1/2 sum (PQ|RS) Gamma_PQRS) / c^T c, grad_h = gamma / c^T c and
+ * grad_eri[k] = 1/2 sum_{PQRS stored at k} Gamma_PQRS / c^T c. O(n^2) pairs: small lists only. */
+static int occ_below(const uint64_t *d, int W, int k)
+{
+    int c = 0;
+    for (int w = 0; w < W; ++w) {
+        int lo = 64 * w;
+        if (k <= lo) break;
+        int nb = k - lo >= 64 ? 64 : k - lo;
+        uint64_t m = nb >= 64 ? ~0ull : ((1ull << nb) - 1ull);
+        c += __builtin_popcountll(d[w] & m);
+    }
+    return c;
+}
+/* apply a_k (annihilate) or a+_k (create) in place; returns the sign, 0 if the result vanishes */
+static int apply_op(uint64_t *d, int W, int k, int create)
+{
+    int occ = (int)((d[k >> 6] >> (k & 63)) & 1u);
+    if (create == occ) return 0;
+    int s = (occ_below(d, W, k) & 1) ? -1 : 1;
+    d[k >> 6] ^= (uint64_t)1 << (k & 63);
+    return s;
+}
+
+int oq_rdm(const oq_t *q, const uint64_t *dets, const double *c, int64_t n, double *E_out, double *grad_h,
+           double *grad_eri)
+{
+    const int W = q->W, M = q->n_orb, NS = q->n_so;
+    double norm = 0.0;
+    for (int64_t x = 0; x < n; ++x) norm = norm + c[x] * c[x];
+    int64_t neri = q->npair_sp * (q->npair_sp + 1) / 2;
+    int nthreads = 1;
+#ifdef _OPENMP
+    nthreads = omp_get_max_threads();
+#endif
+    /* per-thread accumulators (rows I split statically), combined in thread order */
+    double *t_num = calloc((size_t)nthreads, sizeof(double));
+    double *t_h = calloc((size_t)nthreads * M * M, sizeof(double));
+    double *t_e = calloc((size_t)nthreads * neri, sizeof(double));
+    if (!t_num || !t_h || !t_e) { free(t_num); free(t_h); free(t_e); return -1; }
+#pragma omp parallel for schedule(static)
+    for (int64_t I = 0; I < n; ++I) {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        double *gh = t_h + (size_t)tid * M * M, *ge = t_e + (size_t)tid * neri;
+        const uint64_t *dI = dets + I * W;
+        for (int64_t J = 0; J < n; ++J) {
+            const uint64_t *dJ = dets + J * W;
+            int nd = 0;
+            for (int w = 0; w < W; ++w) nd += __builtin_popcountll(dI[w] ^ dJ[w]);
+            if (nd > 4) continue;
+            const double cc = c[J] * c[I];
+            t_num[tid] = t_num[tid] + oq_hij(q, dI, dJ) * cc;
+            /* one-body: a+_p a_qq |I> = |J> */
+            for (int qq = 0; qq < NS; ++qq) {
+                uint64_t K[OQ_MAXW];
+                memcpy(K, dI, sizeof(uint64_t) * W);
+                int s1 = apply_op(K, W, qq, 0);
+                if (!s1) continue;
+                for (int p = 0; p < NS; ++p) {
+                    if ((p & 1) != (qq & 1)) continue;
+                    uint64_t K2[OQ_MAXW];
+                    memcpy(K2, K, sizeof(uint64_t) * W);
+                    int s2 = apply_op(K2, W, p, 1);
+                    if (!s2 || !det_eq(q, K2, dJ)) continue;
+                    gh[(p >> 1) * M + (qq >> 1)] += cc * (double)(s1 * s2);
+                }
+            }
+            /* two-body: a+_p a+_r a_s a_qq |I> = |J> */
+            for (int qq = 0; qq < NS; ++qq) {
+                uint64_t K1[OQ_MAXW];
+                memcpy(K1, dI, sizeof(uint64_t) * W);
+                int s1 = apply_op(K1, W, qq, 0);
+                if (!s1) continue;
+                for (int s = 0; s < NS; ++s) {
+                    uint64_t K2[OQ_MAXW];
+                    memcpy(K2, K1, sizeof(uint64_t) * W);
+                    int s2 = apply_op(K2, W, s, 0);
+                    if (!s2) continue;
+                    /* the two created orbitals are J minus K2 */
+                    int cre[2], nc = 0, bad = 0;
+                    for (int k = 0; k < NS; ++k) {
+                        int inJ = det_bit(q, dJ, k), inK = det_bit(q, K2, k);
+                        if (inK && !inJ) bad = 1;
+                        if (inJ && !inK) { if (nc < 2) cre[nc] = k; nc++; }
+                    }
+                    if (bad || nc != 2) continue;
+                    for (int o = 0; o < 2; ++o) {
+                        int r = cre[o], p = cre[1 - o];
+                        if ((p & 1) != (qq & 1) || (r & 1) != (s & 1)) continue;
+                        uint64_t K3[OQ_MAXW];
+                        memcpy(K3, K2, sizeof(uint64_t) * W);
+                        int s3 = apply_op(K3, W, r, 1);
+                        int s4 = apply_op(K3, W, p, 1);
+                        if (!s3 || !s4) continue;
+                        ge[pair_index(pair_index(p >> 1, qq >> 1), pair_index(r >> 1, s >> 1))] +=
+                            0.5 * cc * (double)(s1 * s2 * s3 * s4);
+                    }
+                }
+            }
+        }
+    }
+    double num = 0.0;
+    memset(grad_h, 0, sizeof(double) * M * M);
+    memset(grad_eri, 0, sizeof(double) * neri);
+    for (int t = 0; t < nthreads; ++t) {
+        num = num + t_num[t];
+        for (int k = 0; k < M * M; ++k) grad_h[k] += t_h[(size_t)t * M * M + k];
+        for (int64_t k = 0; k < neri; ++k) grad_eri[k] += t_e[(size_t)t * neri + k];
+    }
+    free(t_num); free(t_h); free(t_e);
+    for (int k = 0; k < M * M; ++k) grad_h[k] = grad_h[k] / norm;
+    for (int64_t k = 0; k < neri; ++k) grad_eri[k] = grad_eri[k] / norm;
+    *E_out = num / norm;
+    return 0;
+}

@@ -78,6 +78,8 @@ def lib():
         L.oq_map1.argtypes = [ctypes.c_void_p, u64p]
         L.oq_hmatrix.argtypes = [ctypes.c_void_p, u64p, ctypes.c_int64, f64p]
         L.oq_estimate.argtypes = [ctypes.c_void_p, i64p, i64p, i64p, f64p]
+        L.oq_rdm.restype = ctypes.c_int
+        L.oq_rdm.argtypes = [ctypes.c_void_p, u64p, f64p, ctypes.c_int64, f64p, f64p, f64p]
         L.oq_attempt.restype = ctypes.c_int64
         L.oq_attempt.argtypes = [ctypes.c_void_p, u64p, ctypes.c_int32, ctypes.c_uint32, u64p,
                                  P(ctypes.c_int)]
@@ -183,6 +185,19 @@ class Oracle:
         amt = lib().oq_attempt(self.h, _p(self._det(d), ctypes.c_uint64), c, a, _p(child, ctypes.c_uint64),
                                ctypes.byref(is_null))
         return int(amt), child[:self.W].copy(), bool(is_null.value)
+
+    def rdm_energy(self, dets, c):
+        """E = c^T H c / c^T c over the list and its gradients (grad_h (M, M), grad_eri packed)."""
+        dets = np.ascontiguousarray(np.asarray(dets, dtype=np.uint64).reshape(-1, self.W))
+        c = np.ascontiguousarray(c, dtype=np.float64)
+        M = self.n_orb
+        npair = M * (M + 1) // 2
+        gh = np.zeros((M, M))
+        ge = np.zeros(npair * (npair + 1) // 2)
+        E = ctypes.c_double()
+        lib().oq_rdm(self.h, _p(dets, ctypes.c_uint64), _p(c, ctypes.c_double), len(c), ctypes.byref(E),
+                     _p(gh, ctypes.c_double), _p(ge, ctypes.c_double))
+        return E.value, gh, ge
 
     # -- dynamics
     def iterate(self, n: int = 1) -> list[dict]:

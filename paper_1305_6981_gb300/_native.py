@@ -63,7 +63,7 @@ class Options(ctypes.Structure):
 
 ROW_FIELDS = ["iteration", "shift", "nw_in", "nd_in", "c0_in", "num_in", "nw_out", "nd_out", "attempts", "nulls",
               "spawn_events", "spawned_walkers", "death_walkers", "clone_walkers", "merged_entries",
-              "aborted_walkers", "inserted_dets"]
+              "aborted_walkers", "inserted_dets", "heavy_attempts"]
 
 
 class Row(ctypes.Structure):

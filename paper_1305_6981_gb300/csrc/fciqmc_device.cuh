@@ -21,7 +21,7 @@ constexpr int MAXSO = 128;   // spin orbitals
 constexpr int NCLASS = 16;   // 8 irreps x 2 spins
 constexpr int MAXPAIRS = MAXN * (MAXN - 1) / 2;
 constexpr unsigned long long EMPTY = ~0ull;
-constexpr int NCNT = 9;      // per-iteration counters, same order as fciqmc_row from `attempts`
+constexpr int NCNT = 10;     // per-iteration counters, same order as fciqmc_row from `attempts`
 
 // ---------------------------------------------------------------------------
 // Shared state of one run, in device memory.

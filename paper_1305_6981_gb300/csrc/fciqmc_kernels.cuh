@@ -26,7 +26,7 @@ constexpr unsigned long long kSaltMerge = 0x5851F42D4C957F2Dull;
 constexpr unsigned long long kSaltIndex = 0x14057B7EF767814Full;
 constexpr unsigned long long kFlagUnit = 1ull << 40;  // merge payload: (#initiator spawns << 40) + amount
 
-enum { C_ATTEMPTS = 0, C_NULLS, C_EVENTS, C_SPAWNED, C_DEATH, C_CLONE, C_MERGED, C_ABORTED, C_INSERTED };
+enum { C_ATTEMPTS = 0, C_NULLS, C_EVENTS, C_SPAWNED, C_DEATH, C_CLONE, C_MERGED, C_ABORTED, C_INSERTED, C_HEAVY };
 
 // Per-determinant data used by every attempt from it, kept in shared memory.
 template <int W>
@@ -462,6 +462,7 @@ __global__ void __launch_bounds__(kTile, FQ_SWEEP_MIN_BLOCKS) k_sweep(Params P) 
                     // heavily populated determinant: a record for k_heavy, whose warps take chunks of kChunk
                     // attempts; record index and first chunk are claimed by one atomic, so the first
                     // chunks are nondecreasing in the record index
+                    acc[C_HEAVY] += ac;
                     const unsigned nch = (ac + kChunk - 1) / kChunk;
                     const unsigned long long old = atomicAdd(&st->heavy_packed, (1ull << 40) | nch);
                     const unsigned long long hidx = old >> 40;
@@ -516,8 +517,8 @@ __global__ void __launch_bounds__(kTile, FQ_SWEEP_MIN_BLOCKS) k_sweep(Params P) 
         __syncthreads();
     }
     unsigned long long *const dst[NCNT + 4] = {&st->cnt[0], &st->cnt[1], &st->cnt[2], &st->cnt[3], &st->cnt[4],
-                                               &st->cnt[5], &st->cnt[6], &st->cnt[7], &st->cnt[8], &st->nw_in,
-                                               &st->nd_in, &st->d_nw, &st->d_nd};
+                                               &st->cnt[5], &st->cnt[6], &st->cnt[7], &st->cnt[8], &st->cnt[9],
+                                               &st->nw_in, &st->nd_in, &st->d_nw, &st->d_nd};
     flush_counters<kTile, NCNT + 4>(acc, dst, s_red);
     double bs = block_sum_f64<kTile>(num, s_redf);
     if (threadIdx.x == 0) P.partial[blockIdx.x] = bs;
@@ -588,7 +589,7 @@ __global__ void __launch_bounds__(kTile) k_heavy(Params P) {
         __syncwarp();
     }
     unsigned long long *const dst[NCNT] = {&st->cnt[0], &st->cnt[1], &st->cnt[2], &st->cnt[3], &st->cnt[4],
-                                           &st->cnt[5], &st->cnt[6], &st->cnt[7], &st->cnt[8]};
+                                           &st->cnt[5], &st->cnt[6], &st->cnt[7], &st->cnt[8], &st->cnt[9]};
     cnt[C_ATTEMPTS] = 0;  // attempts are counted by the sweep
     flush_counters<kTile, NCNT>(cnt, dst, s_red);
 }
@@ -760,6 +761,7 @@ __global__ void k_finish(Params P) {
     row.merged_entries = (long long)st->n_merged;
     row.aborted_walkers = (long long)st->cnt[C_ABORTED];
     row.inserted_dets = (long long)st->cnt[C_INSERTED];
+    row.heavy_attempts = (long long)st->cnt[C_HEAVY];
     P.hist[st->hist_n % P.hist_cap] = row;
     st->hist_n++;
     // shift: S <- S - zeta/(A tau) ln(N_w(n) / N_w(n-A)) every A iterations once N_w reached the target

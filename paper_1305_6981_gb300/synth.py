@@ -240,3 +240,56 @@ def walker_snapshot(system: System, n_walkers: int, seed: int = 0, ref_fraction:
     bits = np.array(rows)
     dets = np.packbits(bits, axis=1, bitorder="little").view("<u8").astype(np.uint64)
     return dets.reshape(len(rows), W), np.array(pops, dtype=np.int32)
+
+
+def sampled_vector(system: System, n_dets: int, seed: int = 5, max_level: int = 6) -> tuple[np.ndarray, np.ndarray]:
+    """A fixed amplitude vector with the structure of a time-averaged FCIQMC wavefunction: the aufbau
+    reference (amplitude 1) plus distinct S_z-conserving excitations of it whose level L (electrons
+    moved) is uniform on 1..max_level, amplitude exp(-L) with a random sign. Returns
+    (dets (n, W) uint64, c (n,) float64), the reference first."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    M, N = system.n_orb, system.n_elec
+    na, nb = (N + 1) // 2, N // 2
+    W = (2 * M + 63) // 64
+    nv = (M - na, M - nb)
+    ref = np.zeros(64 * W, dtype=bool)
+    ref[:N] = True
+    seen = {np.packbits(ref, bitorder="little").tobytes()}
+    rows, amps = [ref], [1.0]
+    while len(rows) < n_dets:
+        B = min(1 << 18, 2 * (n_dets - len(rows)) + 1024)
+        L = rng.integers(1, max_level + 1, size=B)
+        lo = np.maximum(0, L - min(nb, nv[1]))
+        hi = np.minimum(L, min(na, nv[0]))
+        ok = lo <= hi
+        La = lo + (rng.random(B) * (hi - lo + 1)).astype(np.int64)
+        La = np.minimum(La, hi)
+        Lb = L - La
+        bits = np.zeros((B, 64 * W), dtype=bool)
+        for spin, nocc, cnt in ((0, na, La), (1, nb, Lb)):
+            occ_rank = np.argsort(rng.random((B, nocc)), axis=1).argsort(axis=1)
+            vir_rank = np.argsort(rng.random((B, M - nocc)), axis=1).argsort(axis=1)
+            keep_occ = occ_rank >= cnt[:, None]           # occupied orbitals that stay
+            take_vir = vir_rank < cnt[:, None]            # virtual orbitals that get an electron
+            occ_orbs = 2 * np.arange(nocc) + spin
+            vir_orbs = 2 * np.arange(nocc, M) + spin
+            r_o, c_o = np.nonzero(keep_occ)
+            bits[r_o, occ_orbs[c_o]] = True
+            r_v, c_v = np.nonzero(take_vir)
+            bits[r_v, vir_orbs[c_v]] = True
+        bits = bits[ok]
+        Lk = L[ok]
+        packed = np.packbits(bits, axis=1, bitorder="little")
+        sg = np.where(rng.random(len(Lk)) < 0.5, 1.0, -1.0)
+        for k in range(len(Lk)):
+            key = packed[k].tobytes()
+            if key in seen:
+                continue
+            seen.add(key)
+            rows.append(bits[k])
+            amps.append(float(np.exp(-Lk[k])) * sg[k])
+            if len(rows) >= n_dets:
+                break
+    bits = np.array(rows)
+    dets = np.packbits(bits, axis=1, bitorder="little").view("<u8").astype(np.uint64)
+    return dets.reshape(len(rows), W), np.array(amps)

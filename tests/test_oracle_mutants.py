@@ -29,10 +29,13 @@ MUTANTS = [
     ("accept_single_offset_dropped", "uint64_t off = kind == 2 ? 0 : q->d53;", "uint64_t off = 0;"),
     ("accept_range_swapped", "uint64_t range = kind == 2 ? q->d53 : ((uint64_t)1 << 53) - q->d53;",
      "uint64_t range = kind == 1 ? q->d53 : ((uint64_t)1 << 53) - q->d53;"),
+    ("rdm_half_dropped", "0.5 * cc * (double)(s1 * s2 * s3 * s4);", "cc * (double)(s1 * s2 * s3 * s4);"),
+    ("rdm_spin_rule", "if ((p & 1) != (qq & 1) || (r & 1) != (s & 1)) continue;",
+     "if ((p & 1) != (s & 1) || (r & 1) != (qq & 1)) continue;"),
 ]
 
 FAST_PINS = ("philox or own_log or second_quantisation or symmetry_and_spin or two_words and hamiltonian "
-             "or pdouble or normalised or eq1 or initiator_rule")
+             "or pdouble or normalised or eq1 or initiator_rule or on_a_subset or functional_two_words")
 
 
 @pytest.mark.slow
@@ -50,7 +53,8 @@ def test_every_planted_mistake_is_caught():
                                "-o", path_so, path_c, "-lm"])
         env = dict(os.environ, FCIQMC_ORACLE_LIB=path_so, OMP_NUM_THREADS="1")
         procs[name] = subprocess.Popen(
-            [sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_pins.py"), "-x", "-q",
+            [sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_pins.py"),
+             os.path.join(ROOT, "tests", "test_oracle_rdm.py"), "-x", "-q",
              "-p", "no:cacheprovider", "-k", FAST_PINS],
             env=env, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, cwd=ROOT)
     survivors = []
