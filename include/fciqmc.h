@@ -227,6 +227,48 @@ int fciqmc_get_info(const fciqmc_handle *h, fciqmc_info *info);
  * into kernel_ms[FCIQMC_N_KERNELS] (host array, not cleared). */
 int fciqmc_profile(fciqmc_handle *h, int32_t n_iterations, double *kernel_ms);
 
+/* ---------------------------------------------------------------------------
+ * Energy functional of a fixed amplitude vector and its density-matrix gradient.
+ *
+ * For n distinct determinants D_I (W words each) with real amplitudes c_I, and integrals h, (pq|rs)
+ * in the layout of fciqmc_create,
+ *   E(h, V) = sum_{I,J} c_I c_J <D_I|H|D_J> / sum_I c_I^2,
+ * the variational energy of the vector (the Eq. 1 Hamiltonian restricted to it; a time-averaged
+ * FCIQMC vector is the usual input). E is linear in h and V for fixed c; its gradient is the spin-
+ * summed one-body density matrix gamma_PQ / c^T c with respect to h (symmetric convention: for a
+ * symmetric change dh, dE = sum_PQ grad_h[P][Q] dh[P][Q]) and, with respect to each stored element
+ * of the 8-fold packed ERIs, 1/2 the sum of the two-body density matrix Gamma_PQRS / c^T c over the
+ * index orders stored there. The pairs that H connects are found once at creation (determinants
+ * sharing a key D minus two electrons); the density matrices are computed at the first gradient
+ * call and kept. All device memory comes from the caller's workspace. */
+typedef struct fciqmc_rdm fciqmc_rdm;
+
+/* Device bytes fciqmc_rdm_create needs (0 for unsupported sizes: n_orb <= 64, 2 <= n_elec <= 64,
+ * n_elec < 2 n_orb, n_dets * n_elec (n_elec - 1) / 2 < 2^31). */
+size_t fciqmc_rdm_workspace_bytes(int n_elec, int n_orb, int64_t n_dets);
+
+/* Copies the determinants (device, n_dets x W, distinct, n_elec bits each) and amplitudes (device,
+ * n_dets doubles) into the workspace and finds the connected pairs. Synchronising. */
+int fciqmc_rdm_create(int n_elec, int n_orb, const uint64_t *dets_dev, const double *c_dev, int64_t n_dets,
+                      void *workspace, size_t workspace_bytes, void *cuda_stream, fciqmc_rdm **out);
+
+/* Enqueues E(h, V) for device integrals h_dev (n_orb^2) and eri_dev (packed) into e_dev (device,
+ * one double). Asynchronous; the reduction order is fixed, so repeated calls give identical values. */
+int fciqmc_rdm_energy(fciqmc_rdm *r, const double *h_dev, const double *eri_dev, double *e_dev);
+
+/* Enqueues grad_h_dev (n_orb^2) = s dE/dh and grad_eri_dev (packed) = s dE/dV, with the scalar s
+ * read from scale_dev (device, one double, e.g. the incoming gradient of a loss). Overwrites the
+ * outputs. Asynchronous. */
+int fciqmc_rdm_gradient(fciqmc_rdm *r, const double *scale_dev, double *grad_h_dev, double *grad_eri_dev);
+
+/* Synchronising: counts[0..4] = key buckets, members of buckets with two or more determinants,
+ * candidate pairs, connected single-excitation pairs and double-excitation pairs (the last two once
+ * the gradient has been computed). Returns the construction status. */
+int fciqmc_rdm_info(fciqmc_rdm *r, int64_t *counts);
+
+/* Releases the host-side object (synchronising); the workspace stays the caller's. Accepts NULL. */
+void fciqmc_rdm_destroy(fciqmc_rdm *r);
+
 /* Largest walker list fciqmc_estimate_list_static accepts. Its scratch is one
  * static device array per device: FCIQMC_STATIC_MAX_DETS / 256 doubles (256 KiB)
  * and three 64-bit counters. */

@@ -16,8 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfciqmc.so")
-SOURCES = ["fciqmc.cu", "fciqmc_static.cu"]
-DEPS = ["fciqmc.cu", "fciqmc_static.cu", "fciqmc_kernels.cuh", "fciqmc_device.cuh"]
+SOURCES = ["fciqmc.cu", "fciqmc_static.cu", "fciqmc_rdm.cu"]
+DEPS = ["fciqmc.cu", "fciqmc_static.cu", "fciqmc_rdm.cu", "fciqmc_kernels.cuh", "fciqmc_device.cuh"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
               "-Xcompiler", "-ffp-contract=off", "-fmad=false"]
@@ -97,7 +97,8 @@ class Info(ctypes.Structure):
 SYMBOLS = ["fciqmc_default_options", "fciqmc_workspace_bytes", "fciqmc_create", "fciqmc_step", "fciqmc_sync",
            "fciqmc_estimators", "fciqmc_history", "fciqmc_n_dets", "fciqmc_get_walkers", "fciqmc_set_walkers",
            "fciqmc_get_state", "fciqmc_get_info", "fciqmc_profile", "fciqmc_estimate_list_static", "fciqmc_destroy",
-           "fciqmc_strerror"]
+           "fciqmc_strerror", "fciqmc_rdm_workspace_bytes", "fciqmc_rdm_create", "fciqmc_rdm_energy",
+           "fciqmc_rdm_gradient", "fciqmc_rdm_info", "fciqmc_rdm_destroy"]
 STATIC_MAX_DETS = 1 << 23
 N_KERNELS = 8
 KERNEL_NAMES = ["compact_copy", "index_clear", "index_fill", "compact_finish", "sweep", "heavy", "annihilate",
@@ -129,6 +130,16 @@ def _declare(L):
     L.fciqmc_profile.argtypes = [vp, i32, f64p]
     L.fciqmc_estimate_list_static.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, u64p, vp, vp, i64, vp, vp]
     L.fciqmc_estimate_list_static.restype = ctypes.c_int
+    L.fciqmc_rdm_workspace_bytes.argtypes = [ctypes.c_int, ctypes.c_int, i64]
+    L.fciqmc_rdm_workspace_bytes.restype = ctypes.c_size_t
+    L.fciqmc_rdm_create.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, i64, vp, ctypes.c_size_t, vp, P(vp)]
+    L.fciqmc_rdm_energy.argtypes = [vp, vp, vp, vp]
+    L.fciqmc_rdm_gradient.argtypes = [vp, vp, vp, vp]
+    L.fciqmc_rdm_info.argtypes = [vp, P(i64)]
+    L.fciqmc_rdm_destroy.argtypes = [vp]
+    L.fciqmc_rdm_destroy.restype = None
+    for name in ("fciqmc_rdm_create", "fciqmc_rdm_energy", "fciqmc_rdm_gradient", "fciqmc_rdm_info"):
+        getattr(L, name).restype = ctypes.c_int
     L.fciqmc_destroy.argtypes = [vp]
     L.fciqmc_destroy.restype = None
     L.fciqmc_strerror.argtypes = [ctypes.c_int]

@@ -1,0 +1,806 @@
+// Energy functional E(h, V; c) = c^T H c / c^T c over a fixed determinant list, and its gradient with
+// respect to the one- and two-electron integrals (the 1- and 2-RDMs of c divided by c^T c).
+//
+// Pairs of determinants that H connects (differing in at most two spin orbitals) are found without a
+// sort: every determinant I emits, for each pair {x, y} of its occupied spin orbitals, the key
+// I - {x, y}. Two distinct determinants share a key exactly when they differ by a double excitation
+// (one shared key, their hole sets removed) or a single excitation (one shared key per common
+// electron; the pair is kept only in the bucket of the lowest common electron). Keys are grouped in
+// an open-addressing table (128-bit compare-and-swap for two-word determinants), buckets with two or
+// more members get contiguous member segments (sorted by determinant index, so sums are
+// deterministic), and each thread then evaluates one candidate pair.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+
+#include "fciqmc.h"
+#include "fciqmc_device.cuh"
+
+namespace {
+
+using fq::Params;
+
+constexpr int kThreads = 256;
+constexpr int kMaxGrid = 4096;
+constexpr unsigned long long kSaltKey = 0x2545F4914F6CDD1Dull;
+
+struct RdmLayout {
+    size_t dets, c, keys, counts, cursor, moff, poff, members, bsum, partial, state, gh, ge, npair_tab, wpair, scan_tmp;
+    size_t total;
+};
+
+struct RdmState {
+    unsigned long long n_buckets;
+    unsigned long long n_members;  // members of buckets with two or more entries
+    unsigned long long n_pairs;    // candidate pairs
+    unsigned long long n_single, n_double;
+    double norm;
+    int status;
+    int pad;
+};
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+long long next_pow2(long long x) {
+    long long p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+int log2i(long long x) {
+    int b = 0;
+    while ((1LL << b) < x) ++b;
+    return b;
+}
+
+struct Dims {
+    int n_elec, n_orb, W, npairs;
+    long long n, n_keys, kcap, n_eri;
+};
+
+bool dims_of(int n_elec, int n_orb, long long n, Dims &d) {
+    if (n_orb < 1 || n_orb > 64 || n_elec < 2 || n_elec > fq::MAXN || n_elec >= 2 * n_orb || n < 1 || n > (1LL << 30))
+        return false;
+    d.n_elec = n_elec;
+    d.n_orb = n_orb;
+    d.W = (2 * n_orb + 63) / 64;
+    d.npairs = n_elec * (n_elec - 1) / 2;
+    d.n = n;
+    d.n_keys = n * d.npairs;
+    d.kcap = next_pow2(std::max<long long>(2 * d.n_keys, 1 << 12));
+    long long np = (long long)n_orb * (n_orb + 1) / 2;
+    d.n_eri = np * (np + 1) / 2;
+    return d.n_keys < (1LL << 31);
+}
+
+RdmLayout layout_of(const Dims &d) {
+    RdmLayout L{};
+    size_t off = 0;
+    auto take = [&](size_t b) {
+        size_t o = off;
+        off = align256(off + b);
+        return o;
+    };
+    const int stride = d.W == 1 ? 2 : 4;
+    L.dets = take(sizeof(unsigned long long) * d.W * d.n);
+    L.c = take(sizeof(double) * d.n);
+    L.keys = take(sizeof(unsigned long long) * stride * d.kcap);
+    L.counts = take(sizeof(unsigned) * d.n_keys);
+    L.cursor = take(sizeof(unsigned) * d.n_keys);
+    L.moff = take(sizeof(unsigned long long) * (d.n_keys + 1));
+    L.poff = take(sizeof(unsigned long long) * (d.n_keys + 1));
+    L.members = take(sizeof(unsigned long long) * d.n_keys);
+    L.bsum = take(sizeof(unsigned long long) * 2 * (kMaxGrid + 1));
+    L.partial = take(sizeof(double) * kMaxGrid);
+    L.state = take(sizeof(RdmState));
+    L.gh = take(sizeof(double) * d.n_orb * d.n_orb);
+    L.ge = take(sizeof(double) * d.n_eri);
+    L.npair_tab = take(sizeof(double) * 2 * fq::MAXSO * fq::MAXSO);
+    L.wpair = take(sizeof(double) * 2 * d.n_orb * d.n_orb);
+    L.scan_tmp = take(sizeof(unsigned long long) * 4);
+    L.total = off;
+    return L;
+}
+
+// ------------------------------------------------------------------------------------ device helpers
+template <int W>
+__device__ __forceinline__ void load_det(const unsigned long long *dets, long long i, unsigned long long (&d)[W]) {
+#pragma unroll
+    for (int w = 0; w < W; ++w) d[w] = dets[i * W + w];
+}
+
+// x-th occupied spin orbital (ascending) of d
+template <int W>
+__device__ __forceinline__ int nth_occ(const unsigned long long (&d)[W], int x) {
+    return fq::select_bit<W>(d, x);
+}
+
+// member word: determinant index (bits 0..31), removed orbitals x (32..39) and y (40..47)
+__device__ __forceinline__ unsigned long long pack_member(unsigned I, int x, int y) {
+    return (unsigned long long)I | ((unsigned long long)x << 32) | ((unsigned long long)y << 40);
+}
+
+template <int W>
+__device__ __forceinline__ long long key_lookup(const unsigned long long *tab, long long kcap, int kbits,
+                                                const unsigned long long (&key)[W]) {
+    constexpr int S = fq::Stride<W>::v;
+    unsigned long long h = fq::table_hash<W>(key, kSaltKey) >> (64 - kbits);
+    for (long long probe = 0; probe < kcap; ++probe) {
+        const unsigned long long *e = tab + h * S;
+        bool match = true, empty = true;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            match = match && (e[w] == key[w]);
+            empty = empty && (e[w] == fq::EMPTY);
+        }
+        if (match) return (long long)h;
+        if (empty) return -1;
+        h = (h + 1ull) & ((unsigned long long)kcap - 1ull);
+    }
+    return -1;
+}
+
+// ------------------------------------------------------------------------------------ construction kernels
+// Empty key table: EMPTY key words, zero payloads.
+__global__ void k_key_init(unsigned long long *tab, long long kcap, int W) {
+    const int S = W == 1 ? 2 : 4;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < kcap; e += (long long)gridDim.x * blockDim.x) {
+        for (int w = 0; w < W; ++w) tab[e * S + w] = fq::EMPTY;
+        tab[e * S + W] = 0ull;
+    }
+}
+
+// Key table entries: key words, then (bucket id << 32) + number of determinants with that key.
+template <int W>
+__global__ void k_keys(const unsigned long long *dets, long long n, int n_elec, unsigned long long *tab, long long kcap,
+                       int kbits, RdmState *st) {
+    constexpr int S = fq::Stride<W>::v;
+    const int npairs = n_elec * (n_elec - 1) / 2;
+    const long long total = n * npairs;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+        const long long I = t / npairs;
+        int k = (int)(t - I * npairs);
+        int y = 1;
+        while ((y + 1) * y / 2 <= k) ++y;
+        const int x = k - y * (y - 1) / 2;
+        unsigned long long d[W];
+        load_det<W>(dets, I, d);
+        unsigned long long key[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) key[w] = d[w];
+        fq::flip<W>(key, nth_occ<W>(d, x));
+        fq::flip<W>(key, nth_occ<W>(d, y));
+        unsigned long long h = fq::table_hash<W>(key, kSaltKey) >> (64 - kbits);
+        bool done = false;
+        for (long long probe = 0; probe < kcap && !done; ++probe) {
+            unsigned long long *e = tab + h * S;
+            int r = fq::probe_key<W>(e, key);
+            if (r == 1) {
+                atomicAdd(e + W, 1ull);
+                done = true;
+            } else if (r == 2) {
+                bool claimed;
+                if (fq::claim_key<W>(e, key, claimed)) {
+                    unsigned long long add = 1ull;
+                    if (claimed) add += atomicAdd(&st->n_buckets, 1ull) << 32;
+                    atomicAdd(e + W, add);
+                    done = true;
+                }
+            }
+            if (!done) h = (h + 1ull) & ((unsigned long long)kcap - 1ull);
+        }
+        if (!done) atomicCAS(&st->status, 0, FCIQMC_ERR_CAPACITY);
+    }
+}
+
+template <int W>
+__global__ void k_counts(const unsigned long long *tab, long long kcap, unsigned *counts) {
+    constexpr int S = fq::Stride<W>::v;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < kcap; e += (long long)gridDim.x * blockDim.x) {
+        bool empty = true;
+#pragma unroll
+        for (int w = 0; w < W; ++w) empty = empty && (tab[e * S + w] == fq::EMPTY);
+        if (empty) continue;
+        const unsigned long long v = tab[e * S + W];
+        counts[v >> 32] = (unsigned)(v & 0xFFFFFFFFull);
+    }
+}
+
+// Exclusive scans over buckets b < nb of m_b = count if count >= 2 else 0 (member offsets) and of
+// p_b = C(m_b, 2) (pair offsets), in three passes: per-block sums, a scan of the block sums, then
+// per-element offsets. Both outputs have nb + 1 entries.
+__global__ void k_scan_blocks(const unsigned *counts, long long nb, long long per_block, unsigned long long *bsum) {
+    __shared__ unsigned long long s_m[kThreads], s_p[kThreads];
+    const long long lo = (long long)blockIdx.x * per_block, hi = min(lo + per_block, nb);
+    unsigned long long m = 0, p = 0;
+    for (long long b = lo + threadIdx.x; b < hi; b += blockDim.x) {
+        const unsigned long long c = counts[b] >= 2 ? counts[b] : 0;
+        m += c;
+        p += c * (c - 1) / 2;
+    }
+    s_m[threadIdx.x] = m;
+    s_p[threadIdx.x] = p;
+    __syncthreads();
+    for (int o = kThreads / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            s_m[threadIdx.x] += s_m[threadIdx.x + o];
+            s_p[threadIdx.x] += s_p[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        bsum[2 * blockIdx.x] = s_m[0];
+        bsum[2 * blockIdx.x + 1] = s_p[0];
+    }
+}
+
+__global__ void k_scan_top(unsigned long long *bsum, int nblocks, RdmState *st) {
+    if (threadIdx.x != 0) return;
+    unsigned long long m = 0, p = 0;
+    for (int b = 0; b < nblocks; ++b) {
+        const unsigned long long bm = bsum[2 * b], bp = bsum[2 * b + 1];
+        bsum[2 * b] = m;
+        bsum[2 * b + 1] = p;
+        m += bm;
+        p += bp;
+    }
+    st->n_members = m;
+    st->n_pairs = p;
+}
+
+__global__ void k_scan_out(const unsigned *counts, long long nb, long long per_block, const unsigned long long *bsum,
+                           unsigned long long *moff, unsigned long long *poff, const RdmState *st) {
+    if (threadIdx.x != 0) return;  // one thread per block walks its range in order
+    const long long lo = (long long)blockIdx.x * per_block, hi = min(lo + per_block, nb);
+    unsigned long long m = bsum[2 * blockIdx.x], p = bsum[2 * blockIdx.x + 1];
+    for (long long b = lo; b < hi; ++b) {
+        moff[b] = m;
+        poff[b] = p;
+        const unsigned long long c = counts[b] >= 2 ? counts[b] : 0;
+        m += c;
+        p += c * (c - 1) / 2;
+    }
+    if (hi == nb && lo < hi) {
+        moff[nb] = st->n_members;
+        poff[nb] = st->n_pairs;
+    }
+}
+
+template <int W>
+__global__ void k_members(const unsigned long long *dets, long long n, int n_elec, const unsigned long long *tab,
+                          long long kcap, int kbits, const unsigned *counts, unsigned *cursor,
+                          const unsigned long long *moff, unsigned long long *members) {
+    constexpr int S = fq::Stride<W>::v;
+    const int npairs = n_elec * (n_elec - 1) / 2;
+    const long long total = n * npairs;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+        const long long I = t / npairs;
+        int k = (int)(t - I * npairs);
+        int y = 1;
+        while ((y + 1) * y / 2 <= k) ++y;
+        const int x = k - y * (y - 1) / 2;
+        unsigned long long d[W];
+        load_det<W>(dets, I, d);
+        unsigned long long key[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) key[w] = d[w];
+        const int ox = nth_occ<W>(d, x), oy = nth_occ<W>(d, y);
+        fq::flip<W>(key, ox);
+        fq::flip<W>(key, oy);
+        const long long e = key_lookup<W>(tab, kcap, kbits, key);
+        if (e < 0) continue;
+        const unsigned long long b = tab[e * S + W] >> 32;
+        if (counts[b] < 2) continue;
+        const unsigned pos = atomicAdd(&cursor[b], 1u);
+        members[moff[b] + pos] = pack_member((unsigned)I, ox, oy);
+    }
+}
+
+// Sorts each bucket's members by determinant index (insertion sort; buckets are small).
+__global__ void k_sort_members(long long nb, const unsigned *counts, const unsigned long long *moff,
+                               unsigned long long *members) {
+    for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += (long long)gridDim.x * blockDim.x) {
+        const unsigned c = counts[b];
+        if (c < 2) continue;
+        unsigned long long *m = members + moff[b];
+        for (unsigned i = 1; i < c; ++i) {
+            const unsigned long long v = m[i];
+            unsigned j = i;
+            while (j > 0 && (m[j - 1] & 0xFFFFFFFFull) > (v & 0xFFFFFFFFull)) {
+                m[j] = m[j - 1];
+                --j;
+            }
+            m[j] = v;
+        }
+    }
+}
+
+__global__ void k_norm(const double *c, long long n, double *partial) {
+    __shared__ double s[kThreads];
+    double v = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        v = __dadd_rn(v, __dmul_rn(c[i], c[i]));
+    s[threadIdx.x] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < kThreads; ++k) t = __dadd_rn(t, s[k]);
+        partial[blockIdx.x] = t;
+    }
+}
+
+__global__ void k_sum_partials(const double *partial, int n, double *out) {
+    if (threadIdx.x != 0) return;
+    double t = 0.0;
+    for (int b = 0; b < n; ++b) t = __dadd_rn(t, partial[b]);
+    *out = t;
+}
+
+// ------------------------------------------------------------------------------------ pairs
+struct PairInfo {
+    long long I, J;
+    int kind;            // 0: skip, 1: single i -> a (from I), 2: double (i<j) -> (a<b) (from I)
+    int i, j, a, b;
+};
+
+// Candidate pair t: bucket by binary search over pair offsets, (u < v) by inverse triangular index.
+template <int W>
+__device__ __forceinline__ PairInfo pair_of(unsigned long long t, long long nb, const unsigned long long *poff,
+                                            const unsigned long long *moff, const unsigned long long *members,
+                                            const unsigned long long *dets, unsigned long long (&dI)[W],
+                                            unsigned long long (&dJ)[W]) {
+    PairInfo P{};
+    long long lo = 0, hi = nb - 1;  // last bucket with poff <= t
+    while (lo < hi) {
+        const long long mid = (lo + hi + 1) >> 1;
+        if (poff[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    const unsigned long long l = t - poff[lo];
+    unsigned long long v = (unsigned long long)((1.0 + sqrt(1.0 + 8.0 * (double)l)) * 0.5);
+    while (v * (v - 1) / 2 > l) --v;
+    while ((v + 1) * v / 2 <= l) ++v;
+    const unsigned long long u = l - v * (v - 1) / 2;
+    const unsigned long long mu = members[moff[lo] + u], mv = members[moff[lo] + v];
+    P.I = (long long)(mu & 0xFFFFFFFFull);
+    P.J = (long long)(mv & 0xFFFFFFFFull);
+    load_det<W>(dets, P.I, dI);
+    load_det<W>(dets, P.J, dJ);
+    int nd = 0;
+    unsigned long long holes[W], parts[W], common[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        holes[w] = dI[w] & ~dJ[w];
+        parts[w] = dJ[w] & ~dI[w];
+        common[w] = dI[w] & dJ[w];
+        nd += __popcll(holes[w]);
+    }
+    if (nd == 2) {
+        P.kind = 2;
+        P.i = fq::select_bit<W>(holes, 0);
+        P.j = fq::select_bit<W>(holes, 1);
+        P.a = fq::select_bit<W>(parts, 0);
+        P.b = fq::select_bit<W>(parts, 1);
+    } else if (nd == 1) {
+        // single: kept only in the bucket whose shared removed orbital is the lowest common electron
+        const int xu = (int)((mu >> 32) & 0xFF), yu = (int)((mu >> 40) & 0xFF);
+        const int hole = fq::select_bit<W>(holes, 0);
+        const int shared = xu == hole ? yu : xu;
+        if (shared == fq::select_bit<W>(common, 0)) {
+            P.kind = 1;
+            P.i = hole;
+            P.a = fq::select_bit<W>(parts, 0);
+        }
+    }
+    return P;
+}
+
+template <int W>
+__device__ __forceinline__ double single_h(const Params &P, const unsigned long long (&d)[W], int i, int a) {
+    const int I = i >> 1, A = a >> 1;
+    double v = P.h[I * P.n_orb + A];
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        unsigned long long m = d[w];
+        while (m) {
+            const int j = 64 * w + __ffsll((long long)m) - 1;
+            m &= m - 1;
+            if (j == i) continue;
+            const int J = j >> 1;
+            v = __dadd_rn(v, fq::eri_d(P, I, A, J, J));
+            if ((j & 1) == (i & 1)) v = __dsub_rn(v, fq::eri_d(P, I, J, J, A));
+        }
+    }
+    return (fq::count_between<W>(d, i, a) & 1) ? -v : v;
+}
+
+// 2 c_I c_J H_IJ summed over candidate pairs, per block in a fixed order.
+template <int W>
+__global__ void __launch_bounds__(kThreads) k_pair_energy(Params P, const unsigned long long *dets, const double *c,
+                                                          long long nb, const unsigned long long *poff,
+                                                          const unsigned long long *moff,
+                                                          const unsigned long long *members, const RdmState *st,
+                                                          double *partial) {
+    __shared__ double s[kThreads];
+    const unsigned long long np = st->n_pairs;
+    double acc = 0.0;
+    for (unsigned long long t = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; t < np;
+         t += (unsigned long long)gridDim.x * blockDim.x) {
+        unsigned long long dI[W], dJ[W];
+        const PairInfo q = pair_of<W>(t, nb, poff, moff, members, dets, dI, dJ);
+        if (q.kind == 0) continue;
+        const double hv = q.kind == 1 ? single_h<W>(P, dI, q.i, q.a) : fq::hij_double<W>(P, dI, q.i, q.j, q.a, q.b);
+        acc = __dadd_rn(acc, __dmul_rn(__dmul_rn(2.0, __dmul_rn(c[q.I], c[q.J])), hv));
+    }
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tsum = 0.0;
+        for (int k = 0; k < kThreads; ++k) tsum = __dadd_rn(tsum, s[k]);
+        partial[blockIdx.x] = tsum;
+    }
+}
+
+// c_I^2 H_II per block (pair-term table in shared memory).
+template <int W>
+__global__ void __launch_bounds__(kThreads) k_diag_energy(Params P, const unsigned long long *dets, const double *c,
+                                                          long long n, double *partial) {
+    extern __shared__ double s_w[];
+    __shared__ double s[kThreads];
+    const int M = P.n_orb;
+    for (int k = threadIdx.x; k < 2 * M * M; k += blockDim.x) s_w[k] = P.wpair[k];
+    for (int k = threadIdx.x; k < M; k += blockDim.x) s_w[2 * M * M + k] = P.h[k * M + k];
+    __syncthreads();
+    double acc = 0.0;
+    for (long long I = (long long)blockIdx.x * blockDim.x + threadIdx.x; I < n; I += (long long)gridDim.x * blockDim.x) {
+        unsigned long long d[W];
+        load_det<W>(dets, I, d);
+        acc = __dadd_rn(acc, __dmul_rn(__dmul_rn(c[I], c[I]), fq::hdiag<W>(P, d, s_w, s_w + 2 * M * M)));
+    }
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tsum = 0.0;
+        for (int k = 0; k < kThreads; ++k) tsum = __dadd_rn(tsum, s[k]);
+        partial[blockIdx.x] = tsum;
+    }
+}
+
+__global__ void k_energy_finish(const double *pp, int npp, const double *pd, int npd, const RdmState *st, double *e) {
+    if (threadIdx.x != 0) return;
+    double t = 0.0;
+    for (int b = 0; b < npd; ++b) t = __dadd_rn(t, pd[b]);
+    for (int b = 0; b < npp; ++b) t = __dadd_rn(t, pp[b]);
+    *e = __ddiv_rn(t, st->norm);
+}
+
+__global__ void k_pair_wpair(Params P, double *wpair) {
+    const int M = P.n_orb;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < M * M; k += gridDim.x * blockDim.x) {
+        const int p = k / M, q = k % M;
+        const double j = fq::eri_d(P, p, p, q, q);
+        wpair[k] = j;
+        wpair[M * M + k] = __dsub_rn(j, fq::eri_d(P, p, q, q, p));
+    }
+}
+
+// Gradient contributions of the connected pairs (atomics into the unscaled RDM arrays).
+template <int W>
+__global__ void __launch_bounds__(kThreads) k_pair_grad(int n_orb, const unsigned long long *dets, const double *c,
+                                                        long long nb, const unsigned long long *poff,
+                                                        const unsigned long long *moff, const unsigned long long *members,
+                                                        RdmState *st, double *gh, double *ge) {
+    const unsigned long long np = st->n_pairs;
+    unsigned long long ns = 0, ndb = 0;
+    for (unsigned long long t = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; t < np;
+         t += (unsigned long long)gridDim.x * blockDim.x) {
+        unsigned long long dI[W], dJ[W];
+        const PairInfo q = pair_of<W>(t, nb, poff, moff, members, dets, dI, dJ);
+        if (q.kind == 0) continue;
+        const double cc = c[q.I] * c[q.J];
+        if (q.kind == 1) {
+            ++ns;
+            const double sg = (fq::count_between<W>(dI, q.i, q.a) & 1) ? -cc : cc;
+            const int I = q.i >> 1, A = q.a >> 1;
+            atomicAdd(&gh[I * n_orb + A], sg);
+            atomicAdd(&gh[A * n_orb + I], sg);
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                unsigned long long m = dI[w];
+                while (m) {
+                    const int j = 64 * w + __ffsll((long long)m) - 1;
+                    m &= m - 1;
+                    if (j == q.i) continue;
+                    const int J = j >> 1;
+                    atomicAdd(&ge[fq::eidx(I, A, J, J)], 2.0 * sg);
+                    if ((j & 1) == (q.i & 1)) atomicAdd(&ge[fq::eidx(I, J, J, A)], -2.0 * sg);
+                }
+            }
+        } else {
+            ++ndb;
+            const double sg = fq::double_parity<W>(dI, q.i, q.j, q.a, q.b) ? -cc : cc;
+            if ((q.i & 1) == (q.a & 1) && (q.j & 1) == (q.b & 1))
+                atomicAdd(&ge[fq::eidx(q.i >> 1, q.a >> 1, q.j >> 1, q.b >> 1)], 2.0 * sg);
+            if ((q.i & 1) == (q.b & 1) && (q.j & 1) == (q.a & 1))
+                atomicAdd(&ge[fq::eidx(q.i >> 1, q.b >> 1, q.j >> 1, q.a >> 1)], -2.0 * sg);
+        }
+    }
+    if (ns) atomicAdd(&st->n_single, ns);
+    if (ndb) atomicAdd(&st->n_double, ndb);
+}
+
+// Diagonal contributions: occupation-pair sums O_pq = sum_I c_I^2 n_p n_q over spin orbitals p <= q
+// (p == q gives sum_I c_I^2 n_p), each thread accumulating a fixed strided set of (p, q) in registers
+// over tiles of determinants staged in shared memory, flushed once per block. O is stored at p * n_so + q.
+template <int W>
+__global__ void __launch_bounds__(kThreads) k_diag_grad(int n_so, const unsigned long long *dets, const double *c,
+                                                        long long n, double *occ_pair) {
+    __shared__ unsigned long long s_d[kThreads][W];
+    __shared__ double s_c2[kThreads];
+    constexpr int PER = 33;  // 33 * 256 >= 128 * 129 / 2 triangular entries
+    const int nent = n_so * (n_so + 1) / 2;
+    double acc[PER];
+    int ep[PER], eq[PER];
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+        acc[r] = 0.0;
+        const int e = threadIdx.x + r * kThreads;
+        int q = 0;
+        while ((q + 1) * (q + 2) / 2 <= e) ++q;  // e = q (q + 1) / 2 + p with p <= q
+        eq[r] = e < nent ? q : -1;
+        ep[r] = e < nent ? e - q * (q + 1) / 2 : -1;
+    }
+    for (long long base = (long long)blockIdx.x * kThreads; base < n; base += (long long)gridDim.x * kThreads) {
+        const long long I = base + threadIdx.x;
+#pragma unroll
+        for (int w = 0; w < W; ++w) s_d[threadIdx.x][w] = I < n ? dets[I * W + w] : 0ull;
+        s_c2[threadIdx.x] = I < n ? c[I] * c[I] : 0.0;
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < PER; ++r) {
+            const int p = ep[r], q = eq[r];
+            if (q < 0) continue;
+            double a = acc[r];
+            for (int k = 0; k < kThreads; ++k) {
+                const unsigned long long wp = (W == 1 || p < 64) ? s_d[k][0] : s_d[k][W - 1];
+                const unsigned long long wq = (W == 1 || q < 64) ? s_d[k][0] : s_d[k][W - 1];
+                if (((wp >> (p & 63)) & (wq >> (q & 63)) & 1ull) != 0ull) a += s_c2[k];
+            }
+            acc[r] = a;
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int r = 0; r < PER; ++r)
+        if (eq[r] >= 0 && acc[r] != 0.0) atomicAdd(&occ_pair[ep[r] * n_so + eq[r]], acc[r]);
+}
+
+// Maps the occupation-pair sums onto h and the packed ERIs and scales the whole RDM by 1 / c^T c.
+__global__ void k_diag_finish(int n_orb, const double *occ_pair, double *gh, double *ge, const RdmState *st) {
+    if (blockIdx.x != 0) return;
+    const int n_so = 2 * n_orb;
+    for (int e = threadIdx.x; e < n_so * n_so; e += blockDim.x) {
+        const int p = e / n_so, q = e % n_so;
+        if (q < p) continue;
+        const double v = occ_pair[e];
+        if (v == 0.0) continue;
+        const int P = p >> 1, Q = q >> 1;
+        if (p == q) {
+            atomicAdd(&gh[P * n_orb + P], v);
+        } else {
+            atomicAdd(&ge[fq::eidx(P, P, Q, Q)], v);
+            if ((p & 1) == (q & 1)) atomicAdd(&ge[fq::eidx(P, Q, Q, P)], -v);
+        }
+    }
+}
+
+__global__ void k_scale_out(const double *gh, const double *ge, long long n_h, long long n_e, const double *scale,
+                            const RdmState *st, double *out_h, double *out_e) {
+    const double f = __ddiv_rn(*scale, st->norm);
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n_h + n_e; k += (long long)gridDim.x * blockDim.x) {
+        if (k < n_h) out_h[k] = __dmul_rn(gh[k], f);
+        else out_e[k - n_h] = __dmul_rn(ge[k - n_h], f);
+    }
+}
+
+}  // namespace
+
+struct fciqmc_rdm {
+    Dims d;
+    RdmLayout L;
+    char *ws;
+    cudaStream_t s;
+    int grid;
+    int sms;
+    long long nb;  // buckets (host copy after construction)
+    RdmState host;
+    bool rdm_ready;  // unscaled density matrices computed
+};
+
+namespace {
+template <typename T>
+T *ptr(fciqmc_rdm *r, size_t off) {
+    return reinterpret_cast<T *>(r->ws + off);
+}
+Params params_for(fciqmc_rdm *r, const double *h, const double *eri) {
+    Params P{};
+    P.n_elec = r->d.n_elec;
+    P.n_orb = r->d.n_orb;
+    P.n_so = 2 * r->d.n_orb;
+    P.h = h;
+    P.eri = eri;
+    P.wpair = ptr<double>(r, r->L.wpair);
+    return P;
+}
+
+template <int W>
+int construct(fciqmc_rdm *r) {
+    const Dims &d = r->d;
+    cudaStream_t s = r->s;
+    const int stride = W == 1 ? 2 : 4;
+    const int g = r->grid;
+    RdmState *st = ptr<RdmState>(r, r->L.state);
+    unsigned long long *tab = ptr<unsigned long long>(r, r->L.keys);
+    (void)stride;
+    k_key_init<<<g, kThreads, 0, s>>>(tab, d.kcap, W);
+    cudaMemsetAsync(st, 0, sizeof(RdmState), s);
+    k_keys<W><<<g, kThreads, 0, s>>>(ptr<unsigned long long>(r, r->L.dets), d.n, d.n_elec, tab, d.kcap, log2i(d.kcap), st);
+    if (cudaMemcpyAsync(&r->host, st, sizeof(RdmState), cudaMemcpyDeviceToHost, s) != cudaSuccess) return FCIQMC_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return FCIQMC_ERR_CUDA;
+    if (r->host.status) return r->host.status;
+    const long long nb = (long long)r->host.n_buckets;
+    r->nb = nb;
+    unsigned *counts = ptr<unsigned>(r, r->L.counts);
+    k_counts<W><<<g, kThreads, 0, s>>>(tab, d.kcap, counts);
+    const int nblk = (int)std::min<long long>(kMaxGrid, std::max<long long>(1, (nb + 4095) / 4096));
+    const long long per_block = (nb + nblk - 1) / nblk;
+    unsigned long long *bsum = ptr<unsigned long long>(r, r->L.bsum);
+    unsigned long long *moff = ptr<unsigned long long>(r, r->L.moff), *poff = ptr<unsigned long long>(r, r->L.poff);
+    k_scan_blocks<<<nblk, kThreads, 0, s>>>(counts, nb, per_block, bsum);
+    k_scan_top<<<1, 32, 0, s>>>(bsum, nblk, st);
+    k_scan_out<<<nblk, 32, 0, s>>>(counts, nb, per_block, bsum, moff, poff, st);
+    unsigned *cursor = ptr<unsigned>(r, r->L.cursor);
+    cudaMemsetAsync(cursor, 0, sizeof(unsigned) * nb, s);
+    unsigned long long *members = ptr<unsigned long long>(r, r->L.members);
+    k_members<W><<<g, kThreads, 0, s>>>(ptr<unsigned long long>(r, r->L.dets), d.n, d.n_elec, tab, d.kcap, log2i(d.kcap),
+                                        counts, cursor, moff, members);
+    k_sort_members<<<g, kThreads, 0, s>>>(nb, counts, moff, members);
+    double *partial = ptr<double>(r, r->L.partial);
+    k_norm<<<g, kThreads, 0, s>>>(ptr<double>(r, r->L.c), d.n, partial);
+    k_sum_partials<<<1, 32, 0, s>>>(partial, g, &st->norm);
+    if (cudaGetLastError() != cudaSuccess) return FCIQMC_ERR_CUDA;
+    if (cudaMemcpyAsync(&r->host, st, sizeof(RdmState), cudaMemcpyDeviceToHost, s) != cudaSuccess) return FCIQMC_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return FCIQMC_ERR_CUDA;
+    return r->host.status;
+}
+
+template <int W>
+void launch_energy(fciqmc_rdm *r, const Params &P, double *e) {
+    const Dims &d = r->d;
+    cudaStream_t s = r->s;
+    const int g = r->grid;
+    RdmState *st = ptr<RdmState>(r, r->L.state);
+    double *partial = ptr<double>(r, r->L.partial);
+    const int gd = std::min(g, kMaxGrid / 2);
+    const size_t smem = sizeof(double) * (2 * d.n_orb * d.n_orb + d.n_orb);
+    k_pair_wpair<<<8, kThreads, 0, s>>>(P, const_cast<double *>(P.wpair));
+    k_diag_energy<W><<<gd, kThreads, smem, s>>>(P, ptr<unsigned long long>(r, r->L.dets), ptr<double>(r, r->L.c), d.n,
+                                                partial);
+    k_pair_energy<W><<<gd, kThreads, 0, s>>>(P, ptr<unsigned long long>(r, r->L.dets), ptr<double>(r, r->L.c), r->nb,
+                                             ptr<unsigned long long>(r, r->L.poff), ptr<unsigned long long>(r, r->L.moff),
+                                             ptr<unsigned long long>(r, r->L.members), st, partial + gd);
+    k_energy_finish<<<1, 32, 0, s>>>(partial + gd, gd, partial, gd, st, e);
+}
+
+template <int W>
+void launch_rdm(fciqmc_rdm *r) {
+    const Dims &d = r->d;
+    cudaStream_t s = r->s;
+    const int g = r->grid;
+    RdmState *st = ptr<RdmState>(r, r->L.state);
+    double *gh = ptr<double>(r, r->L.gh), *ge = ptr<double>(r, r->L.ge);
+    double *occ_pair = ptr<double>(r, r->L.npair_tab);
+    cudaMemsetAsync(gh, 0, sizeof(double) * d.n_orb * d.n_orb, s);
+    cudaMemsetAsync(ge, 0, sizeof(double) * d.n_eri, s);
+    cudaMemsetAsync(occ_pair, 0, sizeof(double) * 4 * d.n_orb * d.n_orb, s);
+    k_pair_grad<W><<<g, kThreads, 0, s>>>(d.n_orb, ptr<unsigned long long>(r, r->L.dets), ptr<double>(r, r->L.c), r->nb,
+                                          ptr<unsigned long long>(r, r->L.poff), ptr<unsigned long long>(r, r->L.moff),
+                                          ptr<unsigned long long>(r, r->L.members), st, gh, ge);
+    k_diag_grad<W><<<std::min<long long>(g, (d.n + kThreads - 1) / kThreads), kThreads, 0, s>>>(
+        2 * d.n_orb, ptr<unsigned long long>(r, r->L.dets), ptr<double>(r, r->L.c), d.n, occ_pair);
+    k_diag_finish<<<1, kThreads, 0, s>>>(d.n_orb, occ_pair, gh, ge, st);
+}
+}  // namespace
+
+extern "C" {
+
+size_t fciqmc_rdm_workspace_bytes(int n_elec, int n_orb, int64_t n_dets) {
+    Dims d;
+    if (!dims_of(n_elec, n_orb, n_dets, d)) return 0;
+    return layout_of(d).total;
+}
+
+int fciqmc_rdm_create(int n_elec, int n_orb, const uint64_t *dets_dev, const double *c_dev, int64_t n_dets,
+                      void *workspace, size_t workspace_bytes, void *cuda_stream, fciqmc_rdm **out) {
+    if (!out) return FCIQMC_ERR_INVALID_ARG;
+    *out = nullptr;
+    Dims d;
+    if (!dims_of(n_elec, n_orb, n_dets, d)) return FCIQMC_ERR_UNSUPPORTED;
+    if (!dets_dev || !c_dev) return FCIQMC_ERR_INVALID_ARG;
+    RdmLayout L = layout_of(d);
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) % 256) != 0 || workspace_bytes < L.total)
+        return FCIQMC_ERR_WORKSPACE;
+    fciqmc_rdm *r = new (std::nothrow) fciqmc_rdm();
+    if (!r) return FCIQMC_ERR_INVALID_ARG;
+    r->d = d;
+    r->L = L;
+    r->ws = static_cast<char *>(workspace);
+    r->s = static_cast<cudaStream_t>(cuda_stream);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&r->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        delete r;
+        return FCIQMC_ERR_CUDA;
+    }
+    r->grid = std::min(kMaxGrid, r->sms * 8);
+    const size_t smem = sizeof(double) * (2 * d.n_orb * d.n_orb + d.n_orb);
+    if (cudaFuncSetAttribute(k_diag_energy<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaFuncSetAttribute(k_diag_energy<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        delete r;
+        return FCIQMC_ERR_CUDA;
+    }
+    if (cudaMemcpyAsync(ptr<unsigned long long>(r, L.dets), dets_dev, sizeof(uint64_t) * d.W * d.n, cudaMemcpyDeviceToDevice, r->s) != cudaSuccess ||
+        cudaMemcpyAsync(ptr<double>(r, L.c), c_dev, sizeof(double) * d.n, cudaMemcpyDeviceToDevice, r->s) != cudaSuccess) {
+        delete r;
+        return FCIQMC_ERR_CUDA;
+    }
+    const int rc = d.W == 1 ? construct<1>(r) : construct<2>(r);
+    if (rc != FCIQMC_OK) {
+        delete r;
+        return rc;
+    }
+    *out = r;
+    return FCIQMC_OK;
+}
+
+int fciqmc_rdm_energy(fciqmc_rdm *r, const double *h_dev, const double *eri_dev, double *e_dev) {
+    if (!r || !h_dev || !eri_dev || !e_dev) return FCIQMC_ERR_INVALID_ARG;
+    Params P = params_for(r, h_dev, eri_dev);
+    if (r->d.W == 1) launch_energy<1>(r, P, e_dev);
+    else launch_energy<2>(r, P, e_dev);
+    return cudaGetLastError() == cudaSuccess ? FCIQMC_OK : FCIQMC_ERR_CUDA;
+}
+
+int fciqmc_rdm_gradient(fciqmc_rdm *r, const double *scale_dev, double *grad_h_dev, double *grad_eri_dev) {
+    if (!r || !scale_dev || !grad_h_dev || !grad_eri_dev) return FCIQMC_ERR_INVALID_ARG;
+    RdmState *st = ptr<RdmState>(r, r->L.state);
+    if (!r->rdm_ready) {
+        if (r->d.W == 1) launch_rdm<1>(r);
+        else launch_rdm<2>(r);
+        r->rdm_ready = true;
+    }
+    const long long nh = (long long)r->d.n_orb * r->d.n_orb;
+    k_scale_out<<<std::min(r->grid, 1024), kThreads, 0, r->s>>>(ptr<double>(r, r->L.gh), ptr<double>(r, r->L.ge), nh,
+                                                                r->d.n_eri, scale_dev, st, grad_h_dev, grad_eri_dev);
+    return cudaGetLastError() == cudaSuccess ? FCIQMC_OK : FCIQMC_ERR_CUDA;
+}
+
+int fciqmc_rdm_info(fciqmc_rdm *r, int64_t *counts) {
+    if (!r || !counts) return FCIQMC_ERR_INVALID_ARG;
+    RdmState h;
+    if (cudaMemcpyAsync(&h, ptr<RdmState>(r, r->L.state), sizeof(RdmState), cudaMemcpyDeviceToHost, r->s) != cudaSuccess ||
+        cudaStreamSynchronize(r->s) != cudaSuccess)
+        return FCIQMC_ERR_CUDA;
+    counts[0] = (int64_t)h.n_buckets;
+    counts[1] = (int64_t)h.n_members;
+    counts[2] = (int64_t)h.n_pairs;
+    counts[3] = (int64_t)h.n_single;
+    counts[4] = (int64_t)h.n_double;
+    return h.status;
+}
+
+void fciqmc_rdm_destroy(fciqmc_rdm *r) {
+    if (!r) return;
+    cudaStreamSynchronize(r->s);
+    delete r;
+}
+
+}  // extern "C"
