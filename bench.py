@@ -56,6 +56,10 @@ WORKLOADS = {
     "12e24o": dict(system=synth.init_12e24o, tau=0.005, thr=3, target=1_000_000, main_capacity=4_000_000,
                    spawn_capacity=1 << 22, initial_population=2_000, initial_shift=1.0, max_growth=20_000,
                    equilibrate=50, desc="12e/24o (W=1), 8 irreps, initiator 3, tau 0.005, 1e6 target walkers"),
+    "batch64": dict(system=None, tau=0.005, thr=3, target=0, main_capacity=0, spawn_capacity=0, initial_population=0,
+                    initial_shift=1.0, max_growth=6000, equilibrate=20,
+                    desc="64 independent runs, 8e/16o..16e/40o (seeded), targets log-uniform 1e4..2e6, tau 0.005, "
+                         "initiator 3, one CUDA graph per launch vs the same runs advanced one at a time"),
     "8e8o": dict(system=synth.tiny_8e8o, tau=0.01, thr=-1, target=1 << 14, main_capacity=1 << 14,
                  spawn_capacity=1 << 14, initial_population=1_000, initial_shift=0.5, max_growth=5_000,
                  equilibrate=50, desc="8e/8o (W=1), no symmetry, plain FCIQMC, tau 0.01, 2^14 target walkers"),
@@ -347,6 +351,93 @@ def run_gpu(args, wl, rank, world, local_rank):
     return g, out, info
 
 
+def run_batch(args, wl):
+    """Aggregate spawn attempts/s of 64 uneven runs advanced by one graph per launch, against the same
+    runs advanced one at a time (each with its own graph launches on its own stream, in sequence)."""
+    import torch
+
+    from paper_1305_6981_gb300 import Batch, Fciqmc
+    from paper_1305_6981_gb300.autotune import tune
+
+    torch.cuda.set_device(0)
+    specs = synth.batch_systems(64, seed=3)
+    systems = [synth.make_system(sp["n_orb"], sp["n_elec"], seed=sp["sys_seed"] % 100000, n_chol=sp["n_orb"] // 2,
+                                 name=f"run{k}") for k, sp in enumerate(specs)]
+    targets = np.array([sp["target"] for sp in specs])
+    # autotune three representative runs (smallest, median and largest target); each run takes the options of
+    # the representative nearest in log(target)
+    reps = [int(np.argmin(targets)), int(np.argsort(targets)[len(targets) // 2]), int(np.argmax(targets))]
+    tuned = {}
+    t_tune = time.perf_counter()
+    for r in reps:
+        tuned[r] = tune(systems[r], wl["tau"], wl["thr"], int(targets[r]), trial_iterations=10,
+                        candidates={"grid_blocks": [0, 38, 152], "index_load": [0.5], "spawn_factor": [0.5]})
+    t_tune = time.perf_counter() - t_tune
+
+    def opts_for(k):
+        r = min(reps, key=lambda q: abs(np.log(targets[q]) - np.log(targets[k])))
+        return dict(tuned[r]["best"])
+
+    def make(k):
+        o = opts_for(k)
+        o["main_capacity"] = max(4 * int(targets[k]), 1 << 14)
+        o["spawn_capacity"] = max(1 << 12, int(targets[k]) // 2)
+        return Fciqmc(systems[k], wl["tau"], wl["thr"], target_walkers=int(targets[k]),
+                      initial_population=max(100, int(targets[k]) // 100), initial_shift=wl["initial_shift"],
+                      seed=specs[k]["seed"], **o)
+
+    runs = [make(k) for k in range(64)]
+    L = 10
+    batch = Batch(runs, iterations_per_launch=L)
+    t_grow = time.perf_counter()
+    grown = 0
+    while grown < wl["max_growth"]:
+        batch.step(5)
+        grown += 5 * L
+        if all(r.estimates()["vary_shift"] for r in runs):
+            break
+    batch.step(max(1, wl["equilibrate"] // L))
+    t_grow = time.perf_counter() - t_grow
+    torch.cuda.synchronize()
+    K = max(1, args.steps)
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    batch.step(max(1, args.warmup))
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    batch.step(K)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms_batch = ev0.elapsed_time(ev1)
+    att_batch = sum(sum(r2["attempts"] for r2 in r.history(K * L)) for r in runs)
+    # the same runs, one at a time
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for r in runs:
+        r.step(K * L)
+        r.sync()
+    ms_seq = (time.perf_counter() - t0) * 1e3
+    att_seq = sum(sum(r2["attempts"] for r2 in r.history(K * L)) for r in runs)
+    status = max(abs(r.sync()) for r in runs)
+    out = {
+        "metric": "aggregate spawn attempts/s, 64 uneven independent runs (one graph per launch)",
+        "value": att_batch / (ms_batch * 1e-3), "unit": "attempts/s", "n_gpus": 1, "steps": K, "warmup": args.warmup,
+        "ms_per_step": ms_batch / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "batch64", "system": wl["desc"], "iterations_per_launch": L,
+                   "walkers_total": int(sum(r.estimates()["n_walkers"] for r in runs)),
+                   "growth_iterations": grown, "growth_seconds": round(t_grow, 1), "tune_seconds": round(t_tune, 1),
+                   "tuned": {str(k): tuned[k]["best"] for k in reps}},
+        "sequential": {"value": att_seq / (ms_seq * 1e-3), "unit": "attempts/s", "ms_total": ms_seq},
+        "speedup_vs_sequential": (att_batch / ms_batch) / (att_seq / ms_seq),
+        "status": status,
+    }
+    print(json.dumps(out), flush=True)
+    batch.close()
+    for r in runs:
+        r.close()
+
+
 def e2e_rate(g, args, info, world):
     """Same metric through the C ABI with host buffers: per step the walker list (determinants,
     populations, diagonal elements) goes host->device from pinned memory, one iteration runs, and the
@@ -390,6 +481,9 @@ def main():
         return
     if args.ncu_case:
         run_ncu_case(args, wl)
+        return
+    if args.workload == "batch64":
+        run_batch(args, wl)
         return
     import torch.distributed as dist
     if world > 1:

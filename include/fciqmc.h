@@ -81,6 +81,11 @@ typedef struct {
                                     default main_capacity / 2 */
     int64_t history_capacity;    /* per-iteration estimator rows kept (ring), default 1 << 16 */
     const uint64_t *reference;   /* W words, NULL: aufbau (lowest orbitals of each spin filled) */
+    int32_t grid_blocks;         /* blocks of the spawning and annihilation kernels; 0: enough to fill
+                                    every SM at the kernels' occupancy. Never changes results. */
+    double index_load;           /* largest load factor of the determinant hash index (its capacity is
+                                    the next power of two >= main_capacity / index_load); 0: 0.5.
+                                    Never changes results. */
 } fciqmc_options;
 
 /* Per-iteration record. The estimators (nw_in .. num_in) describe the list at
@@ -206,6 +211,26 @@ int fciqmc_get_walkers(fciqmc_handle *h, uint64_t *dets, int32_t *pops, double *
  * count. Clears the history and the device status. */
 int fciqmc_set_walkers(fciqmc_handle *h, const uint64_t *dets, const int32_t *pops, const double *hdiag,
                        int64_t n, const fciqmc_state *st);
+
+/* ---------------------------------------------------------------------------
+ * Batched runs: several independent runs (any sizes, each with its own handle, workspace and seed)
+ * advanced together by one CUDA graph whose independent branches are the runs' iteration sequences,
+ * so their kernels execute concurrently. Results are those of advancing each run alone (the random
+ * numbers are keyed per run and iteration). */
+typedef struct fciqmc_batch fciqmc_batch;
+
+/* Builds the graph for runs[0..n_runs) (same device; each run at most once), each advancing
+ * iterations_per_launch iterations per launch. The batch does not own the runs; they must outlive
+ * it. Synchronising. */
+int fciqmc_batch_create(fciqmc_handle *const *runs, int n_runs, int32_t iterations_per_launch, fciqmc_batch **out);
+
+/* Enqueues n_launches launches of the batch graph on cuda_stream, ordered after all work previously
+ * enqueued on the runs' own streams; the runs' streams are made to wait for the batch, so later
+ * calls on a run see its result. Asynchronous. */
+int fciqmc_batch_step(fciqmc_batch *b, int32_t n_launches, void *cuda_stream);
+
+/* Releases the graph and events (synchronising on the last batch stream). Accepts NULL. */
+void fciqmc_batch_destroy(fciqmc_batch *b);
 
 /* Synchronising: dynamic state of the run. */
 int fciqmc_get_state(fciqmc_handle *h, fciqmc_state *st);

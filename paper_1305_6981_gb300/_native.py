@@ -58,7 +58,8 @@ class Options(ctypes.Structure):
                 ("initial_population", ctypes.c_int32), ("initial_shift", ctypes.c_double),
                 ("target_walkers", ctypes.c_int64), ("seed", ctypes.c_uint64), ("p_double", ctypes.c_double),
                 ("main_capacity", ctypes.c_int64), ("spawn_capacity", ctypes.c_int64),
-                ("history_capacity", ctypes.c_int64), ("reference", ctypes.POINTER(ctypes.c_uint64))]
+                ("history_capacity", ctypes.c_int64), ("reference", ctypes.POINTER(ctypes.c_uint64)),
+                ("grid_blocks", ctypes.c_int32), ("index_load", ctypes.c_double)]
 
 
 ROW_FIELDS = ["iteration", "shift", "nw_in", "nd_in", "c0_in", "num_in", "nw_out", "nd_out", "attempts", "nulls",
@@ -98,7 +99,8 @@ SYMBOLS = ["fciqmc_default_options", "fciqmc_workspace_bytes", "fciqmc_create", 
            "fciqmc_estimators", "fciqmc_history", "fciqmc_n_dets", "fciqmc_get_walkers", "fciqmc_set_walkers",
            "fciqmc_get_state", "fciqmc_get_info", "fciqmc_profile", "fciqmc_estimate_list_static", "fciqmc_destroy",
            "fciqmc_strerror", "fciqmc_rdm_workspace_bytes", "fciqmc_rdm_create", "fciqmc_rdm_energy",
-           "fciqmc_rdm_gradient", "fciqmc_rdm_info", "fciqmc_rdm_destroy"]
+           "fciqmc_rdm_gradient", "fciqmc_rdm_info", "fciqmc_rdm_destroy", "fciqmc_batch_create",
+           "fciqmc_batch_step", "fciqmc_batch_destroy"]
 STATIC_MAX_DETS = 1 << 23
 N_KERNELS = 8
 KERNEL_NAMES = ["compact_copy", "index_clear", "index_fill", "compact_finish", "sweep", "heavy", "annihilate",
@@ -140,6 +142,12 @@ def _declare(L):
     L.fciqmc_rdm_destroy.restype = None
     for name in ("fciqmc_rdm_create", "fciqmc_rdm_energy", "fciqmc_rdm_gradient", "fciqmc_rdm_info"):
         getattr(L, name).restype = ctypes.c_int
+    L.fciqmc_batch_create.argtypes = [P(vp), ctypes.c_int, i32, P(vp)]
+    L.fciqmc_batch_create.restype = ctypes.c_int
+    L.fciqmc_batch_step.argtypes = [vp, i32, vp]
+    L.fciqmc_batch_step.restype = ctypes.c_int
+    L.fciqmc_batch_destroy.argtypes = [vp]
+    L.fciqmc_batch_destroy.restype = None
     L.fciqmc_destroy.argtypes = [vp]
     L.fciqmc_destroy.restype = None
     L.fciqmc_strerror.argtypes = [ctypes.c_int]

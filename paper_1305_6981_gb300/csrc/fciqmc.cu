@@ -53,7 +53,8 @@ bool sizes_of(int n_elec, int n_orb, const fciqmc_options &o, Sizes &z) {
     z.n_eri = npair * (npair + 1) / 2;
     z.cap = std::max<long long>(o.main_capacity > 0 ? o.main_capacity : (1LL << 20), 1024);
     if (z.cap > (1LL << 31) - 2) return false;
-    z.idx_cap = next_pow2(std::max<long long>(2 * z.cap, 1 << 12));
+    const double load = (o.index_load > 0.0 && o.index_load < 1.0) ? o.index_load : 0.5;
+    z.idx_cap = next_pow2(std::max<long long>((long long)std::ceil((double)z.cap / load), 1 << 12));
     z.mt_cap = next_pow2(std::max<long long>(o.spawn_capacity > 0 ? o.spawn_capacity : z.cap / 2, 1 << 12));
     if (z.mt_cap > (1LL << 32)) return false;
     z.heavy_cap = std::max<long long>(1 << 14, std::min<long long>(z.cap, 1 << 20));
@@ -121,8 +122,10 @@ struct fciqmc_handle {
     int sweep_grid, heavy_grid, ann_grid, small_grid;
     size_t smem_w;
     double e_core;
+    cudaGraph_t graph_tmpl;  // one iteration, kept for composing batch graphs
     cudaGraphExec_t graph;
     bool graph_ready;
+    int grid_request;
 };
 
 namespace {
@@ -145,6 +148,12 @@ int configure_kernels(fciqmc_handle *h) {
     FQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fq::k_annihilate<W>, 256, h->smem_w));
     h->ann_grid = std::min(kMaxGrid, std::max(1, sms * std::max(per_sm, 1)));
     h->heavy_grid = std::min(kMaxGrid, sms * 4);
+    if (h->grid_request > 0) {
+        const int g = std::min(kMaxGrid, h->grid_request);
+        h->sweep_grid = std::min(h->sweep_grid, g);
+        h->ann_grid = std::min(h->ann_grid, g);
+        h->heavy_grid = std::min(h->heavy_grid, g);
+    }
     h->small_grid = std::min(kMaxGrid, sms * 8);
     h->info.num_sms = sms;
     h->info.grid_blocks = h->sweep_grid;
@@ -180,7 +189,8 @@ int build_graph(fciqmc_handle *h) {
         e = cudaStreamEndCapture(cs, &g);
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&h->graph, g, 0);
-    if (g) cudaGraphDestroy(g);
+    if (e == cudaSuccess) h->graph_tmpl = g;
+    else if (g) cudaGraphDestroy(g);
     cudaStreamDestroy(cs);
     h->graph_ready = (e == cudaSuccess);
     cudaGetLastError();
@@ -303,6 +313,8 @@ int fciqmc_create(const double *h1, const double *eri_s8, double e_core, int n_e
     h->stream = static_cast<cudaStream_t>(cuda_stream);
     h->e_core = e_core;
     h->graph_ready = false;
+    h->graph_tmpl = nullptr;
+    h->grid_request = o.grid_blocks;
     h->smem_w = sizeof(double) * (2 * n_orb * n_orb + n_orb);
 
     Params &P = h->P;
@@ -705,7 +717,92 @@ void fciqmc_destroy(fciqmc_handle *h) {
     if (!h) return;
     cudaStreamSynchronize(h->stream);
     if (h->graph_ready) cudaGraphExecDestroy(h->graph);
+    if (h->graph_tmpl) cudaGraphDestroy(h->graph_tmpl);
     delete h;
+}
+
+}  // extern "C"
+
+struct fciqmc_batch {
+    std::vector<fciqmc_handle *> runs;
+    std::vector<cudaEvent_t> run_events;
+    cudaEvent_t done;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    cudaStream_t last_stream;
+};
+
+extern "C" {
+
+int fciqmc_batch_create(fciqmc_handle *const *runs, int n_runs, int32_t iterations_per_launch, fciqmc_batch **out) {
+    if (!out || !runs || n_runs < 1 || iterations_per_launch < 1) return FCIQMC_ERR_INVALID_ARG;
+    *out = nullptr;
+    for (int r = 0; r < n_runs; ++r) {
+        if (!runs[r] || !runs[r]->graph_ready || !runs[r]->graph_tmpl) return FCIQMC_ERR_INVALID_ARG;
+        for (int q = 0; q < r; ++q)
+            if (runs[q] == runs[r]) return FCIQMC_ERR_INVALID_ARG;
+    }
+    fciqmc_batch *b = new (std::nothrow) fciqmc_batch();
+    if (!b) return FCIQMC_ERR_INVALID_ARG;
+    b->runs.assign(runs, runs + n_runs);
+    b->last_stream = nullptr;
+    b->graph = nullptr;
+    b->exec = nullptr;
+    int rc = FCIQMC_OK;
+    if (cudaGraphCreate(&b->graph, 0) != cudaSuccess) rc = FCIQMC_ERR_CUDA;
+    for (int r = 0; r < n_runs && rc == FCIQMC_OK; ++r) {
+        // each run: a chain of iterations_per_launch copies of its one-iteration graph
+        cudaGraphNode_t prev = nullptr;
+        for (int it = 0; it < iterations_per_launch; ++it) {
+            cudaGraphNode_t node;
+            if (cudaGraphAddChildGraphNode(&node, b->graph, prev ? &prev : nullptr, prev ? 1 : 0,
+                                           runs[r]->graph_tmpl) != cudaSuccess) {
+                rc = FCIQMC_ERR_CUDA;
+                break;
+            }
+            prev = node;
+        }
+    }
+    if (rc == FCIQMC_OK && cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess) rc = FCIQMC_ERR_CUDA;
+    if (rc == FCIQMC_OK) {
+        b->run_events.resize(n_runs);
+        for (int r = 0; r < n_runs && rc == FCIQMC_OK; ++r)
+            if (cudaEventCreateWithFlags(&b->run_events[r], cudaEventDisableTiming) != cudaSuccess) rc = FCIQMC_ERR_CUDA;
+        if (rc == FCIQMC_OK && cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) != cudaSuccess) rc = FCIQMC_ERR_CUDA;
+    }
+    if (rc != FCIQMC_OK) {
+        cudaGetLastError();
+        if (b->exec) cudaGraphExecDestroy(b->exec);
+        if (b->graph) cudaGraphDestroy(b->graph);
+        delete b;
+        return rc;
+    }
+    *out = b;
+    return FCIQMC_OK;
+}
+
+int fciqmc_batch_step(fciqmc_batch *b, int32_t n_launches, void *cuda_stream) {
+    if (!b || n_launches < 0) return FCIQMC_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    for (size_t r = 0; r < b->runs.size(); ++r) {
+        FQ_CUDA(cudaEventRecord(b->run_events[r], b->runs[r]->stream));
+        FQ_CUDA(cudaStreamWaitEvent(s, b->run_events[r], 0));
+    }
+    for (int k = 0; k < n_launches; ++k) FQ_CUDA(cudaGraphLaunch(b->exec, s));
+    FQ_CUDA(cudaEventRecord(b->done, s));
+    for (size_t r = 0; r < b->runs.size(); ++r) FQ_CUDA(cudaStreamWaitEvent(b->runs[r]->stream, b->done, 0));
+    b->last_stream = s;
+    return FCIQMC_OK;
+}
+
+void fciqmc_batch_destroy(fciqmc_batch *b) {
+    if (!b) return;
+    if (b->last_stream) cudaStreamSynchronize(b->last_stream);
+    for (cudaEvent_t e : b->run_events) cudaEventDestroy(e);
+    if (!b->run_events.empty()) cudaEventDestroy(b->done);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    delete b;
 }
 
 }  // extern "C"

@@ -91,7 +91,7 @@ RdmLayout layout_of(const Dims &d) {
     L.poff = take(sizeof(unsigned long long) * (d.n_keys + 1));
     L.members = take(sizeof(unsigned long long) * d.n_keys);
     L.bsum = take(sizeof(unsigned long long) * 2 * (kMaxGrid + 1));
-    L.partial = take(sizeof(double) * kMaxGrid);
+    L.partial = take(sizeof(double) * 4 * kMaxGrid);
     L.state = take(sizeof(RdmState));
     L.gh = take(sizeof(double) * d.n_orb * d.n_orb);
     L.ge = take(sizeof(double) * d.n_eri);
@@ -336,6 +336,25 @@ __global__ void k_sum_partials(const double *partial, int n, double *out) {
     *out = t;
 }
 
+// ------------------------------------------------------------------------------------ compensated sums
+// Sum and running error of a sequence of FP64 additions (Knuth's TwoSum per addition, Neumaier's
+// compensated summation): the result is the rounded exact sum up to a few ulp whatever the number of
+// terms, so finite differences of E are not swamped by accumulated rounding.
+struct CSum {
+    double s, c;
+};
+__device__ __forceinline__ void csum_add(CSum &a, double x) {
+    const double t = __dadd_rn(a.s, x);
+    const double bb = __dsub_rn(t, a.s);
+    const double err = __dadd_rn(__dsub_rn(a.s, __dsub_rn(t, bb)), __dsub_rn(x, bb));
+    a.s = t;
+    a.c = __dadd_rn(a.c, err);
+}
+__device__ __forceinline__ void csum_merge(CSum &a, const CSum &b) {
+    csum_add(a, b.s);
+    a.c = __dadd_rn(a.c, b.c);
+}
+
 // ------------------------------------------------------------------------------------ pairs
 struct PairInfo {
     long long I, J;
@@ -413,64 +432,66 @@ __device__ __forceinline__ double single_h(const Params &P, const unsigned long 
     return (fq::count_between<W>(d, i, a) & 1) ? -v : v;
 }
 
-// 2 c_I c_J H_IJ summed over candidate pairs, per block in a fixed order.
+// 2 c_I c_J H_IJ summed over candidate pairs, per block in a fixed order (compensated).
 template <int W>
 __global__ void __launch_bounds__(kThreads) k_pair_energy(Params P, const unsigned long long *dets, const double *c,
                                                           long long nb, const unsigned long long *poff,
                                                           const unsigned long long *moff,
                                                           const unsigned long long *members, const RdmState *st,
                                                           double *partial) {
-    __shared__ double s[kThreads];
+    __shared__ CSum s[kThreads];
     const unsigned long long np = st->n_pairs;
-    double acc = 0.0;
+    CSum acc{0.0, 0.0};
     for (unsigned long long t = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; t < np;
          t += (unsigned long long)gridDim.x * blockDim.x) {
         unsigned long long dI[W], dJ[W];
         const PairInfo q = pair_of<W>(t, nb, poff, moff, members, dets, dI, dJ);
         if (q.kind == 0) continue;
         const double hv = q.kind == 1 ? single_h<W>(P, dI, q.i, q.a) : fq::hij_double<W>(P, dI, q.i, q.j, q.a, q.b);
-        acc = __dadd_rn(acc, __dmul_rn(__dmul_rn(2.0, __dmul_rn(c[q.I], c[q.J])), hv));
+        csum_add(acc, __dmul_rn(__dmul_rn(2.0, __dmul_rn(c[q.I], c[q.J])), hv));
     }
     s[threadIdx.x] = acc;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double tsum = 0.0;
-        for (int k = 0; k < kThreads; ++k) tsum = __dadd_rn(tsum, s[k]);
-        partial[blockIdx.x] = tsum;
+        CSum tot{0.0, 0.0};
+        for (int k = 0; k < kThreads; ++k) csum_merge(tot, s[k]);
+        partial[2 * blockIdx.x] = tot.s;
+        partial[2 * blockIdx.x + 1] = tot.c;
     }
 }
 
-// c_I^2 H_II per block (pair-term table in shared memory).
+// c_I^2 H_II per block (pair-term table in shared memory, compensated).
 template <int W>
 __global__ void __launch_bounds__(kThreads) k_diag_energy(Params P, const unsigned long long *dets, const double *c,
                                                           long long n, double *partial) {
     extern __shared__ double s_w[];
-    __shared__ double s[kThreads];
+    __shared__ CSum s[kThreads];
     const int M = P.n_orb;
     for (int k = threadIdx.x; k < 2 * M * M; k += blockDim.x) s_w[k] = P.wpair[k];
     for (int k = threadIdx.x; k < M; k += blockDim.x) s_w[2 * M * M + k] = P.h[k * M + k];
     __syncthreads();
-    double acc = 0.0;
+    CSum acc{0.0, 0.0};
     for (long long I = (long long)blockIdx.x * blockDim.x + threadIdx.x; I < n; I += (long long)gridDim.x * blockDim.x) {
         unsigned long long d[W];
         load_det<W>(dets, I, d);
-        acc = __dadd_rn(acc, __dmul_rn(__dmul_rn(c[I], c[I]), fq::hdiag<W>(P, d, s_w, s_w + 2 * M * M)));
+        csum_add(acc, __dmul_rn(__dmul_rn(c[I], c[I]), fq::hdiag<W>(P, d, s_w, s_w + 2 * M * M)));
     }
     s[threadIdx.x] = acc;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double tsum = 0.0;
-        for (int k = 0; k < kThreads; ++k) tsum = __dadd_rn(tsum, s[k]);
-        partial[blockIdx.x] = tsum;
+        CSum tot{0.0, 0.0};
+        for (int k = 0; k < kThreads; ++k) csum_merge(tot, s[k]);
+        partial[2 * blockIdx.x] = tot.s;
+        partial[2 * blockIdx.x + 1] = tot.c;
     }
 }
 
 __global__ void k_energy_finish(const double *pp, int npp, const double *pd, int npd, const RdmState *st, double *e) {
     if (threadIdx.x != 0) return;
-    double t = 0.0;
-    for (int b = 0; b < npd; ++b) t = __dadd_rn(t, pd[b]);
-    for (int b = 0; b < npp; ++b) t = __dadd_rn(t, pp[b]);
-    *e = __ddiv_rn(t, st->norm);
+    CSum tot{0.0, 0.0};
+    for (int b = 0; b < npd; ++b) csum_merge(tot, CSum{pd[2 * b], pd[2 * b + 1]});
+    for (int b = 0; b < npp; ++b) csum_merge(tot, CSum{pp[2 * b], pp[2 * b + 1]});
+    *e = __ddiv_rn(__dadd_rn(tot.s, tot.c), st->norm);
 }
 
 __global__ void k_pair_wpair(Params P, double *wpair) {
@@ -687,8 +708,8 @@ void launch_energy(fciqmc_rdm *r, const Params &P, double *e) {
                                                 partial);
     k_pair_energy<W><<<gd, kThreads, 0, s>>>(P, ptr<unsigned long long>(r, r->L.dets), ptr<double>(r, r->L.c), r->nb,
                                              ptr<unsigned long long>(r, r->L.poff), ptr<unsigned long long>(r, r->L.moff),
-                                             ptr<unsigned long long>(r, r->L.members), st, partial + gd);
-    k_energy_finish<<<1, 32, 0, s>>>(partial + gd, gd, partial, gd, st, e);
+                                             ptr<unsigned long long>(r, r->L.members), st, partial + 2 * gd);
+    k_energy_finish<<<1, 32, 0, s>>>(partial + 2 * gd, gd, partial, gd, st, e);
 }
 
 template <int W>

@@ -169,3 +169,36 @@ class Fciqmc:
 
 def _native_capacity() -> int:
     return -2  # FCIQMC_ERR_CAPACITY
+
+
+class Batch:
+    """Several independent runs advanced together by one CUDA graph (fciqmc_batch_*): each launch advances
+    every run by `iterations_per_launch` iterations, the runs' kernels executing concurrently."""
+
+    def __init__(self, runs: list, iterations_per_launch: int = 10, stream=None):
+        import torch
+
+        self._L = L = _native.load()
+        self.runs = list(runs)
+        self.iterations_per_launch = int(iterations_per_launch)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.runs[0].device)
+        arr = (ctypes.c_void_p * len(self.runs))(*[r.handle.value for r in self.runs])
+        h = ctypes.c_void_p()
+        check(L.fciqmc_batch_create(arr, len(self.runs), self.iterations_per_launch, ctypes.byref(h)),
+              "fciqmc_batch_create")
+        self.handle = h
+
+    def step(self, n_launches: int = 1):
+        check(self._L.fciqmc_batch_step(self.handle, int(n_launches), ctypes.c_void_p(self.stream.cuda_stream)),
+              "fciqmc_batch_step")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._L.fciqmc_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
