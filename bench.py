@@ -69,7 +69,7 @@ WORKLOADS = {
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="24e60o", choices=sorted(WORKLOADS))
@@ -78,6 +78,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle baseline")
     ap.add_argument("--growth-log", default="")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched-runs and energy-functional measurements appended to the default line")
     ap.add_argument("--ncu-case", action="store_true",
                     help="grow to --target walkers, run one iteration inside the NVTX range 'prof' and exit "
                          "(the case the ncu summaries are taken on)")
@@ -432,10 +434,44 @@ def run_batch(args, wl):
         "speedup_vs_sequential": (att_batch / ms_batch) / (att_seq / ms_seq),
         "status": status,
     }
-    print(json.dumps(out), flush=True)
     batch.close()
     for r in runs:
         r.close()
+    return out
+
+
+def energy_functional_timing(n_dets: int = 1_000_000):
+    """Forward and backward of E(h, V; c) on the 16e/40o sampled vector: pair construction, one forward,
+    the first backward (density matrices), one more forward."""
+    import torch
+
+    from paper_1305_6981_gb300 import EnergyFunctional
+
+    s = synth.rdm_16e40o()
+    dets, c = synth.sampled_vector(s, n_dets, seed=5)
+    h = torch.as_tensor(s.h).cuda()
+    v = torch.as_tensor(s.eri_s8).cuda()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    f = EnergyFunctional(s.n_elec, s.n_orb, dets, c)
+    torch.cuda.synchronize()
+    t_create = time.perf_counter() - t0
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record()
+    E = f.energy(h, v)
+    ev[1].record()
+    gh, ge = f.gradient(torch.ones((), dtype=torch.float64, device="cuda"))
+    ev[2].record()
+    f.energy(h, v)
+    ev[3].record()
+    torch.cuda.synchronize()
+    info = f.info()
+    out = {"n_dets": n_dets, "system": "16e/40o (W=2), amplitudes exp(-level), levels 1..6",
+           "energy": float(E), "create_ms": 1e3 * t_create, "forward_ms": ev[0].elapsed_time(ev[1]),
+           "backward_first_ms": ev[1].elapsed_time(ev[2]), "forward_again_ms": ev[2].elapsed_time(ev[3]),
+           **info}
+    f.close()
+    return out
 
 
 def e2e_rate(g, args, info, world):
@@ -483,7 +519,7 @@ def main():
         run_ncu_case(args, wl)
         return
     if args.workload == "batch64":
-        run_batch(args, wl)
+        print(json.dumps(run_batch(args, wl)), flush=True)
         return
     import torch.distributed as dist
     if world > 1:
@@ -504,8 +540,18 @@ def main():
                                    "sample": f"{its} oracle iterations on {len(sp)} determinants / "
                                              f"{int(np.abs(sp).sum())} walkers sampled uniformly from the "
                                              f"GPU list ({att} attempts)"}
+        if not args.no_extras and world == 1 and args.workload == "24e60o":
+            g.close()
+            bargs = argparse.Namespace(**vars(args))
+            bargs.steps, bargs.warmup = 5, 1
+            b = run_batch(bargs, WORKLOADS["batch64"])
+            out["batched_64_runs"] = {k: b[k] for k in ("value", "unit", "sequential", "speedup_vs_sequential",
+                                                         "ms_per_step", "status")}
+            out["batched_64_runs"]["walkers_total"] = b["config"]["walkers_total"]
+            out["energy_functional"] = energy_functional_timing()
         print(json.dumps(out), flush=True)
-    g.close()
+    if getattr(g, "handle", None):
+        g.close()
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
