@@ -63,7 +63,7 @@ bool sizes_of(int n_elec, int n_orb, const fciqmc_options &o, Sizes &z) {
 }
 
 struct Layout {
-    size_t state, h, eri, eri_f, wpair, map1, cmask, irrep, pairs, recip, rcpf, ref_occ, facts, e0;
+    size_t state, h, h_f, eri, eri_f, wpair, map1, cmask, irrep, pairs, recip, rcpf, ref_occ, facts, e0;
     size_t det[2], hd[2], hdf[2], pop[2][2], idx, mt, merged, heavy, heavy_base, heavy_att, partial, hist;
     size_t total;
 };
@@ -78,6 +78,7 @@ Layout layout_of(const Sizes &z, int n_orb) {
     };
     L.state = take(sizeof(DevState));
     L.h = take(sizeof(double) * n_orb * n_orb);
+    L.h_f = take(sizeof(float) * n_orb * n_orb);
     L.eri = take(sizeof(double) * z.n_eri);
     L.eri_f = take(sizeof(float) * z.n_eri);
     L.wpair = take(sizeof(double) * 2 * n_orb * n_orb);
@@ -334,6 +335,7 @@ int fciqmc_create(const double *h1, const double *eri_s8, double e_core, int n_e
     P.h = at<double>(h, L.h);
     P.eri = at<double>(h, L.eri);
     P.eri_f = at<float>(h, L.eri_f);
+    P.h_f = at<float>(h, L.h_f);
     P.wpair = at<double>(h, L.wpair);
     P.map1 = at<unsigned long long>(h, L.map1);
     P.cmask = at<unsigned long long>(h, L.cmask);
@@ -410,7 +412,10 @@ int fciqmc_create(const double *h1, const double *eri_s8, double e_core, int n_e
         FQ_TRY(cudaMemcpyAsync(const_cast<unsigned char *>(P.irrep), irr.data(), irr.size(), cudaMemcpyHostToDevice, s));
         FQ_TRY(cudaMemcpyAsync(const_cast<unsigned short *>(P.pairs), pairs.data(), sizeof(unsigned short) * pairs.size(), cudaMemcpyHostToDevice, s));
         FQ_TRY(cudaMemcpyAsync(const_cast<unsigned char *>(P.ref_occ), ref_occ.data(), ref_occ.size(), cudaMemcpyHostToDevice, s));
-        // nearest floats of 1/L
+        // nearest floats of h and of 1/L
+        std::vector<float> hf32((size_t)n_orb * n_orb);
+        for (size_t k = 0; k < hf32.size(); ++k) hf32[k] = (float)h1[k];
+        FQ_TRY(cudaMemcpyAsync(const_cast<float *>(P.h_f), hf32.data(), sizeof(float) * hf32.size(), cudaMemcpyHostToDevice, s));
         std::vector<float> rcpf(2 * fq::MAXSO + 2, 0.f);
         for (int l = 1; l < 2 * fq::MAXSO + 2; ++l) rcpf[l] = (float)(1.0 / l);
         FQ_TRY(cudaMemcpyAsync(const_cast<float *>(P.rcpf), rcpf.data(), sizeof(float) * rcpf.size(), cudaMemcpyHostToDevice, s));
@@ -446,6 +451,11 @@ int fciqmc_create(const double *h1, const double *eri_s8, double e_core, int n_e
         P.cdn_f = (float)(P.cd * (double)z.npairs);
         P.d53_d = (double)d53;
         P.d53_f = (float)d53;
+        P.cs_f = (float)P.cs;
+        P.srange_f = (float)(0x1.0p53 - (double)d53);
+        // the float single-excitation element sums at most 2N - 1 terms, each rounded to float once
+        // (relative 2^-24), with at most 2N - 2 float additions; the FP64 sum adds far less
+        P.serr_f = (float)((2.0 * n_elec + 2.0) * 0x1.0p-24 * (1.0 + 0x1.0p-6));
         // initial state: the reference with the initial population
         DevState st0;
         std::memset(&st0, 0, sizeof(st0));

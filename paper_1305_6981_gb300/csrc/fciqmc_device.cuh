@@ -59,6 +59,8 @@ struct Params {
     unsigned long long d53;
     double tau, cs, cd, E0, c_shift;
     float tau_f, cdn_f, d53_f;             // nearest floats of tau, cd * npairs and d53
+    float cs_f, srange_f;                  // nearest floats of cs and 2^53 - d53
+    float serr_f;                          // relative error bound of the float single-excitation element
     double d53_d;                          // (double)d53, exact
     int period;
     int sweep_grid;                        // blocks of k_sweep (number of partial sums)
@@ -68,6 +70,7 @@ struct Params {
     const double *h;        // n_orb x n_orb
     const double *eri;      // packed 8-fold
     const float *eri_f;     // same, rounded to float
+    const float *h_f;       // h rounded to float
     const double *wpair;    // [2][n_orb][n_orb]: [0] opposite spin (pp|qq), [1] same spin (pp|qq) - (pq|qp)
     const unsigned long long *map1;   // n_so, orbital map of Algorithm 1
     const unsigned long long *cmask;  // [NCLASS][MAXW] spin orbitals of each (irrep, spin) class
@@ -168,28 +171,32 @@ __device__ __forceinline__ int count_between(const unsigned long long (&d)[W], i
     }
     return c;
 }
-// position of the k-th (0-based) set bit of a 64-bit word (k < popc(x))
-__device__ __forceinline__ int select64(unsigned long long x, int k) {
+// position of the k-th (0-based) set bit of a word (k < popc(x)): the half holding it is chosen by a
+// population count, down to single bits; one word is searched, on 32-bit operations
+__device__ __forceinline__ int select32(unsigned x, int k) {
     int pos = 0, c;
-    c = __popc((unsigned)x);
-    if (k >= c) { k -= c; x >>= 32; pos += 32; }
-    c = __popc((unsigned)(x & 0xFFFFu));
+    c = __popc(x & 0xFFFFu);
     if (k >= c) { k -= c; x >>= 16; pos += 16; }
-    c = __popc((unsigned)(x & 0xFFu));
+    c = __popc(x & 0xFFu);
     if (k >= c) { k -= c; x >>= 8; pos += 8; }
-    c = __popc((unsigned)(x & 0xFu));
+    c = __popc(x & 0xFu);
     if (k >= c) { k -= c; x >>= 4; pos += 4; }
-    c = __popc((unsigned)(x & 0x3u));
+    c = __popc(x & 0x3u);
     if (k >= c) { k -= c; x >>= 2; pos += 2; }
-    c = (int)(x & 1u);
-    if (k >= c) { pos += 1; }
-    return pos;
+    return pos + (k >= (int)(x & 1u) ? 1 : 0);
+}
+__device__ __forceinline__ int select64(unsigned long long x, int k) {
+    const unsigned lo = (unsigned)x, hi = (unsigned)(x >> 32);
+    const int c = __popc(lo);
+    const bool up = k >= c;
+    return (up ? 32 : 0) + select32(up ? hi : lo, up ? k - c : k);
 }
 template <int W>
 __device__ __forceinline__ int select_bit(const unsigned long long (&m)[W], int k) {
     if (W == 1) return select64(m[0], k);
-    int c0 = __popcll(m[0]);
-    return k < c0 ? select64(m[0], k) : 64 + select64(m[W - 1], k - c0);
+    const int c0 = __popcll(m[0]);
+    const bool up = k >= c0;
+    return (up ? 64 : 0) + select64(up ? m[W - 1] : m[0], up ? k - c0 : k);
 }
 template <int W>
 __device__ __forceinline__ bool det_eq(const unsigned long long (&a)[W], const unsigned long long *b) {
@@ -212,12 +219,12 @@ __device__ __forceinline__ double eri_d(const Params &P, int p, int q, int r, in
 // L2 policy that keeps the integral tables resident while the walker list streams past them.
 __device__ __forceinline__ unsigned long long keep_policy() {
     unsigned long long pol;
-    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
     return pol;
 }
 __device__ __forceinline__ float ld_keep(const float *p, unsigned long long pol) {
     float v;
-    asm volatile("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+    asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
     return v;
 }
 __device__ __forceinline__ float eri_f(const Params &P, int p, int q, int r, int s, unsigned long long pol) {

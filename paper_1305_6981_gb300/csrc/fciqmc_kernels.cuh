@@ -33,6 +33,7 @@ template <int W>
 struct DetView {
     unsigned long long d[W];
     unsigned long long fp;
+    unsigned long long okm; // bit x: electron x has at least one symmetry-allowed single
     int c;
     unsigned char nok;      // electrons with at least one symmetry-allowed single (N - delta_s)
     unsigned char flag;     // initiator
@@ -123,12 +124,13 @@ __device__ __forceinline__ void prepare_det(const Params &P, const Tables &T, De
         }
         v.cnt[cl] = (unsigned char)u;
     }
-    int nok = 0;
+    unsigned long long okm = 0;
     for (int x = 0; x < P.n_elec; ++x) {
         int k = v.occ[x];
-        nok += v.cnt[T.irrep[k >> 1] * 2 + (k & 1)] > 0;
+        if (v.cnt[T.irrep[k >> 1] * 2 + (k & 1)] > 0) okm |= 1ull << x;
     }
-    v.nok = (unsigned char)nok;
+    v.okm = okm;
+    v.nok = (unsigned char)__popcll(okm);
     v.fp = fingerprint(v.occ, P.n_elec, T.map1);
     v.c = c;
     int ac = c < 0 ? -c : c;
@@ -145,12 +147,15 @@ struct AttemptOut {
 // Exact float of a small nonnegative integer (x < 2^23) without a conversion instruction.
 __device__ __forceinline__ float small_f(unsigned x) { return __int_as_float(0x4B000000 | x) - 8388608.0f; }
 
-// Per-determinant table of the "good" first virtual orbitals a of a double excitation (Sec. VI B),
-// indexed by the spin case of the pair (0: alpha alpha, 1: beta beta, 2: mixed) times 8 plus the
-// irrep product of the pair: their number G = M^a - delta_d and their bit mask (unoccupied only).
-template <int W>
-struct GoodTable {
-    unsigned long long gm[24][W];
+// Tables of one heavily populated determinant, built by the warp that takes it up and used for all of
+// that warp's attempts from it: for each double-excitation entry (spin case of the pair: 0 alpha alpha,
+// 1 beta beta, 2 mixed; times 8, plus the irrep product of the pair) the "good" first virtuals a of
+// Sec. VI B in ascending order and their number G; for each (irrep, spin) class its unoccupied spin
+// orbitals in ascending order, and the position of each unoccupied spin orbital in its class list.
+struct HeavyTab {
+    unsigned char glist[24][MAXSO];
+    unsigned char ulist[NCLASS][MAXSO / 2];
+    unsigned char urank[MAXSO];
     unsigned short G[24];
 };
 
@@ -179,134 +184,285 @@ __device__ __forceinline__ unsigned good_set(const Params &P, const Tables &T, c
     return G;
 }
 
-// One spawning attempt a from determinant v (Eq. 3 with the generator of Sec. VI). Random numbers:
-// two Philox blocks keyed by (seed, iteration), counter (a, tag 0/1, fingerprint). The type word r0
-// also realises the Bernoulli part of the spawn: given the type, t = r0 >> 11 is uniform on
-// [0, d53) for a double and on [d53, 2^53) for a single.
-template <int W, bool TAB>
-__device__ __forceinline__ AttemptOut spawn_attempt(const Params &P, const Tables &T, const DetView<W> &v,
-                                                     const GoodTable<W> *tab, const float *rcpf, unsigned a,
-                                                     unsigned iter, unsigned long long *cnt) {
-    AttemptOut out{false, 0u};
-    unsigned long long r0, r1, r2, r3;
-    draw2(a, 0u, v.fp, P.seed, iter, r0, r1);
-    draw2(a, 1u, v.fp, P.seed, iter, r2, r3);
-    const unsigned long long t = r0 >> 11;
-    const bool dbl = t < P.d53;
-    unsigned long long child[W];
+// Builds tab for determinant v; called by all 32 lanes of a warp. Lanes 0..23 take one entry each,
+// lanes 24..31 two classes each.
+template <int W>
+__device__ __forceinline__ void build_heavy_tab(const Params &P, const Tables &T, const DetView<W> &v, HeavyTab &tab,
+                                                int lane) {
+    if (lane < 24) {
+        const int sc = lane >> 3, gij = lane & 7;
+        const int si = sc == 1 ? 1 : 0, sj = sc == 0 ? 0 : 1;
+        unsigned long long gm[W];
+        tab.G[lane] = (unsigned short)good_set<W>(P, T, v, si, sj, gij, gm);
+        int n = 0;
 #pragma unroll
-    for (int w = 0; w < W; ++w) child[w] = v.d[w];
-    int n = 0, sgn_h = 0;
-    if (!dbl) {
-        // single excitation (Sec. VI A): i uniform over the N - delta_s electrons with M_allow > 0
-        if (v.nok == 0) { cnt[C_NULLS]++; return out; }
-        unsigned k1 = rank_of(r1, v.nok);
-        int i = -1;
-        for (int x = 0; x < P.n_elec; ++x) {
-            int k = v.occ[x];
-            if (v.cnt[T.irrep[k >> 1] * 2 + (k & 1)] > 0) {
-                if (k1 == 0) { i = k; break; }
-                --k1;
+        for (int w = 0; w < W; ++w) {
+            unsigned long long m = gm[w];
+            while (m) {
+                tab.glist[lane][n++] = (unsigned char)(64 * w + __ffsll((long long)m) - 1);
+                m &= m - 1;
             }
         }
-        const int ci = T.irrep[i >> 1] * 2 + (i & 1);
-        const unsigned mallow = v.cnt[ci];
-        unsigned k2 = rank_of(r2, mallow);
-        unsigned long long um[W];
-#pragma unroll
-        for (int w = 0; w < W; ++w) um[w] = ~v.d[w] & T.mask[ci * MAXW + w];
-        const int ao = select_bit<W>(um, (int)k2);
-        flip<W>(child, i);
-        flip<W>(child, ao);
-        double hv = hij_single<W>(P, v.d, v.occ, i, ao);
-        if (hv == 0.0) return out;
-        // p = (|H| (tau / P_single)) (M_allow (N - delta_s))
-        double p = __dmul_rn(__dmul_rn(fabs(hv), P.cs), (double)((long long)mallow * (long long)v.nok));
-        double fl = floor(p);
-        if (fl >= 2147483647.0) { set_status(P.st, FCIQMC_ERR_NUMERIC); return out; }
-        const double range = __dsub_rn(9007199254740992.0, P.d53_d);
-        n = (int)fl + (__ull2double_rn(t - P.d53) < __dmul_rn(__dsub_rn(p, fl), range) ? 1 : 0);
-        sgn_h = hv > 0.0 ? 1 : -1;
     } else {
-        // double excitation (Sec. VI B): pair by inverse triangular index, a among the "good" unoccupied
-        // orbitals of allowed spin, b from the class fixed by symmetry (Eq. sym1) and spin
-        if (P.npairs == 0) { cnt[C_NULLS]++; return out; }
-        unsigned k1 = rank_of(r1, (unsigned)P.npairs);
-        unsigned short pr = T.pairs[k1];
-        const int i = v.occ[pr & 0xFF], j = v.occ[pr >> 8];
-        const int si = i & 1, sj = j & 1;
-        const int gij = T.irrep[i >> 1] ^ T.irrep[j >> 1];
-        unsigned G;
-        unsigned long long gm[W];
-        if (TAB) {
-            const int e = (si == sj ? si : 2) * 8 + gij;
-            G = tab->G[e];
+        for (int c = lane - 24; c < NCLASS; c += 8) {
+            int n = 0;
 #pragma unroll
-            for (int w = 0; w < W; ++w) gm[w] = tab->gm[e][w];
-        } else {
-            G = good_set<W>(P, T, v, si, sj, gij, gm);
+            for (int w = 0; w < W; ++w) {
+                unsigned long long m = ~v.d[w] & T.mask[c * MAXW + w];
+                while (m) {
+                    const int so = 64 * w + __ffsll((long long)m) - 1;
+                    tab.ulist[c][n] = (unsigned char)so;
+                    tab.urank[so] = (unsigned char)n;
+                    ++n;
+                    m &= m - 1;
+                }
+            }
         }
-        if (G == 0) { cnt[C_NULLS]++; return out; }
-        const int ao = select_bit<W>(gm, (int)rank_of(r2, G));
-        const int ca = T.irrep[ao >> 1] * 2 + (ao & 1);
-        const int cb = (gij ^ T.irrep[ao >> 1]) * 2 + (si + sj - (ao & 1));
-        const unsigned m_ba = v.cnt[cb] - (ca == cb ? 1u : 0u);
-        const unsigned m_ab = v.cnt[ca] - (ca == cb ? 1u : 0u);
-        unsigned long long bm[W];
-#pragma unroll
-        for (int w = 0; w < W; ++w) bm[w] = ~v.d[w] & T.mask[cb * MAXW + w];
-        clear_bit<W>(bm, ao);
-        const int bo = select_bit<W>(bm, (int)rank_of(r3, m_ba));
-        const int A = min(ao, bo), B = max(ao, bo);
-        const unsigned L = m_ba + m_ab;
-        const bool t1 = ((i & 1) == (A & 1)) && ((j & 1) == (B & 1));
-        const bool t2 = ((i & 1) == (B & 1)) && ((j & 1) == (A & 1));
-        // bounds of p = |H| tau / P_gen from the float copy of the integrals
-        const unsigned long long pol = keep_policy();
-        const float xf = t1 ? eri_f(P, i >> 1, A >> 1, j >> 1, B >> 1, pol) : 0.f;
-        const float yf = t2 ? eri_f(P, i >> 1, B >> 1, j >> 1, A >> 1, pol) : 0.f;
-        const float hf = xf - yf;
-        const float eh = fmaf(fabsf(xf) + fabsf(yf), 0x1p-22f, 1e-30f);  // >= |H - hf| with a factor 2
-        const float ah_lo = fabsf(hf) - eh, ah_hi = fabsf(hf) + eh;
-        const float F = P.cdn_f * small_f(G) * small_f(m_ba) * small_f(m_ab) * rcpf[L];
-        const float p_hi = ah_hi * F * kUp;
-        const float p_lo = ah_lo * F * kDown;
-        int dec = -1;
-        if (p_hi < 1.0f) {
-            // threshold t < p d53 with t known to 2^30
-            const float th_hi = p_hi * P.d53_f * kUp, th_lo = p_lo * P.d53_f * kDown;
-            const float q_lo = small_f((unsigned)(t >> 30)) * 0x1p30f;
-            if (q_lo >= th_hi) dec = 0;
-            else if (ah_lo > 0.f && q_lo + 0x1p30f <= th_lo) dec = 1;
-        }
-        if (dec == 0) return out;
-        if (dec == 1) {
-            n = 1;
-            sgn_h = hf > 0.f ? 1 : -1;  // |hf| > eh: same sign as H
-            if (double_parity<W>(v.d, i, j, A, B)) sgn_h = -sgn_h;
-        } else {
-            atomicAdd(&P.st->exact_spawn, 1ull);
-            double hd = hij_double<W>(P, v.d, i, j, A, B);
-            if (hd == 0.0) return out;
-            // p = ((|H| (tau / P_double)) (npairs G M^(b|a) M^(a|b))) (1 / (M^(b|a) + M^(a|b)))
-            const long long K = (long long)P.npairs * (long long)G * (long long)m_ba * (long long)m_ab;
-            double p = __dmul_rn(__dmul_rn(__dmul_rn(fabs(hd), P.cd), (double)K), P.recip[L]);
-            double fl = floor(p);
-            if (fl >= 2147483647.0) { set_status(P.st, FCIQMC_ERR_NUMERIC); return out; }
-            n = (int)fl + (__ull2double_rn(t) < __dmul_rn(__dsub_rn(p, fl), P.d53_d) ? 1 : 0);
-            sgn_h = hd > 0.0 ? 1 : -1;
-        }
-        flip<W>(child, i);
-        flip<W>(child, j);
-        flip<W>(child, ao);
-        flip<W>(child, bo);
     }
-    if (n == 0) return out;
+    __syncwarp();
+}
+
+// n = floor(p) + [q < (p - floor(p)) R] for an FP64 value p known only to lie in [p_lo, p_hi], an integer
+// q < 2^53 and R given as its nearest float rf: n, or -1 when the bounds do not decide it. p - m and
+// max(p_lo, 0) - m are exact (Sterbenz); the products round to nearest within the kUp/kDown margins.
+__device__ __forceinline__ int decide_spawn(float p_lo, float p_hi, unsigned long long q, float rf) {
+    if (!(p_hi < 0x1p22f)) return -1;
+    const float pl = fmaxf(p_lo, 0.f);
+    const float m = floorf(pl);
+    if (floorf(p_hi) != m) return -1;
+    const float th_hi = (p_hi - m) * rf * kUp, th_lo = (pl - m) * rf * kDown;
+    const float q_lo = small_f((unsigned)(q >> 30)) * 0x1p30f;  // q_lo <= q < q_lo + 2^30, exact
+    if (q_lo >= th_hi) return (int)m;
+    if (q_lo + 0x1p30f <= th_lo) return (int)m + 1;
+    return -1;
+}
+
+// Counters and merge-table entry of an attempt that spawns n > 0 walkers onto child.
+template <int W>
+__device__ __forceinline__ void emit_spawn(const Params &P, const DetView<W> &v, const unsigned long long (&child)[W],
+                                           int n, int sgn_h, unsigned long long *cnt, AttemptOut &out) {
     cnt[C_EVENTS]++;
     cnt[C_SPAWNED] += (unsigned long long)n;
     const long long amt = -(long long)(v.c > 0 ? 1 : -1) * sgn_h * (long long)n;
     const unsigned long long val = (v.flag ? kFlagUnit : 0ull) + (unsigned long long)amt;
     out.claimed = merge_insert<W>(P, child, val, out.pos);
+}
+
+// First part of attempt a from determinant v (Eq. 3 with the generator of Sec. VI). Random numbers:
+// two Philox blocks keyed by (seed, iteration), counter (a, tag 0/1, fingerprint). The type word r0
+// also realises the Bernoulli part of the spawn: given the type, t = r0 >> 11 is uniform on
+// [0, d53) for a double and on [d53, 2^53) for a single. A double is completed here; a single is
+// selected (electron i, virtual ao) and returned pending (true) for the warp to evaluate its element.
+template <int W, bool TAB>
+__device__ __forceinline__ bool attempt_begin(const Params &P, const Tables &T, const DetView<W> &v,
+                                              const HeavyTab *tab, const float *rcpf, unsigned a, unsigned iter,
+                                              unsigned long long pol, unsigned long long *cnt, AttemptOut &out,
+                                              int &i_out, int &a_out, unsigned &mallow_out, unsigned long long &q_out) {
+    unsigned long long r0, r1, r2, r3;
+    draw2(a, 0u, v.fp, P.seed, iter, r0, r1);
+    draw2(a, 1u, v.fp, P.seed, iter, r2, r3);
+    const unsigned long long t = r0 >> 11;
+    if (t >= P.d53) {
+        // single excitation (Sec. VI A): i uniform over the N - delta_s electrons with M_allow > 0, a
+        // uniform over the unoccupied spin orbitals of i's class
+        if (v.nok == 0) { cnt[C_NULLS]++; return false; }
+        const int i = v.occ[select64(v.okm, (int)rank_of(r1, v.nok))];
+        const int ci = T.irrep[i >> 1] * 2 + (i & 1);
+        const unsigned mallow = v.cnt[ci];
+        const int k2 = (int)rank_of(r2, mallow);
+        int ao;
+        if (TAB) {
+            ao = tab->ulist[ci][k2];
+        } else {
+            unsigned long long um[W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) um[w] = ~v.d[w] & T.mask[ci * MAXW + w];
+            ao = select_bit<W>(um, k2);
+        }
+        i_out = i;
+        a_out = ao;
+        mallow_out = mallow;
+        q_out = t - P.d53;
+        return true;
+    }
+    // double excitation (Sec. VI B): pair by inverse triangular index, a among the "good" unoccupied
+    // orbitals of allowed spin, b from the class fixed by symmetry (Eq. sym1) and spin
+    if (P.npairs == 0) { cnt[C_NULLS]++; return false; }
+    const unsigned short pr = T.pairs[rank_of(r1, (unsigned)P.npairs)];
+    const int i = v.occ[pr & 0xFF], j = v.occ[pr >> 8];
+    const int si = i & 1, sj = j & 1;
+    const int gij = T.irrep[i >> 1] ^ T.irrep[j >> 1];
+    unsigned G;
+    int ao;
+    if (TAB) {
+        const int e = (si == sj ? si : 2) * 8 + gij;
+        G = tab->G[e];
+        if (G == 0) { cnt[C_NULLS]++; return false; }
+        ao = tab->glist[e][rank_of(r2, G)];
+    } else {
+        unsigned long long gm[W];
+        G = good_set<W>(P, T, v, si, sj, gij, gm);
+        if (G == 0) { cnt[C_NULLS]++; return false; }
+        ao = select_bit<W>(gm, (int)rank_of(r2, G));
+    }
+    const int ga = T.irrep[ao >> 1];
+    const int ca = ga * 2 + (ao & 1);
+    const int cb = (gij ^ ga) * 2 + (si + sj - (ao & 1));
+    const unsigned same = ca == cb ? 1u : 0u;
+    const unsigned m_ba = v.cnt[cb] - same;
+    const unsigned m_ab = v.cnt[ca] - same;
+    int k3 = (int)rank_of(r3, m_ba);
+    int bo;
+    if (TAB) {
+        if (same && k3 >= tab->urank[ao]) ++k3;  // the list of class cb still holds a
+        bo = tab->ulist[cb][k3];
+    } else {
+        unsigned long long bm[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) bm[w] = ~v.d[w] & T.mask[cb * MAXW + w];
+        clear_bit<W>(bm, ao);
+        bo = select_bit<W>(bm, k3);
+    }
+    const int A = min(ao, bo), B = max(ao, bo);
+    const unsigned L = m_ba + m_ab;
+    const bool t1 = ((i & 1) == (A & 1)) && ((j & 1) == (B & 1));
+    const bool t2 = ((i & 1) == (B & 1)) && ((j & 1) == (A & 1));
+    // bounds of p = |H| tau / P_gen from the float copy of the integrals
+    const float xf = t1 ? eri_f(P, i >> 1, A >> 1, j >> 1, B >> 1, pol) : 0.f;
+    const float yf = t2 ? eri_f(P, i >> 1, B >> 1, j >> 1, A >> 1, pol) : 0.f;
+    const float hf = xf - yf;
+    const float eh = fmaf(fabsf(xf) + fabsf(yf), 0x1p-22f, 1e-30f);  // >= |H - hf| with a factor 2
+    const float ah_lo = fabsf(hf) - eh, ah_hi = fabsf(hf) + eh;
+    const float F = P.cdn_f * small_f(G) * small_f(m_ba) * small_f(m_ab) * rcpf[L];
+    int n = decide_spawn(ah_lo * F * kDown, ah_hi * F * kUp, t, P.d53_f);
+    int sgn_h;
+    if (n >= 0) {
+        if (n == 0) return false;
+        sgn_h = hf > 0.f ? 1 : -1;  // |hf| > eh: same sign as H
+        if (double_parity<W>(v.d, i, j, A, B)) sgn_h = -sgn_h;
+    } else {
+        atomicAdd(&P.st->exact_spawn, 1ull);
+        const double hd = hij_double<W>(P, v.d, i, j, A, B);
+        if (hd == 0.0) return false;
+        // p = ((|H| (tau / P_double)) (npairs G M^(b|a) M^(a|b))) (1 / (M^(b|a) + M^(a|b)))
+        const long long K = (long long)P.npairs * (long long)G * (long long)m_ba * (long long)m_ab;
+        const double p = __dmul_rn(__dmul_rn(__dmul_rn(fabs(hd), P.cd), (double)K), P.recip[L]);
+        const double fl = floor(p);
+        if (fl >= 2147483647.0) { set_status(P.st, FCIQMC_ERR_NUMERIC); return false; }
+        n = (int)fl + (__ull2double_rn(t) < __dmul_rn(__dsub_rn(p, fl), P.d53_d) ? 1 : 0);
+        sgn_h = hd > 0.0 ? 1 : -1;
+        if (n == 0) return false;
+    }
+    unsigned long long child[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) child[w] = v.d[w];
+    flip<W>(child, i);
+    flip<W>(child, j);
+    flip<W>(child, ao);
+    flip<W>(child, bo);
+    emit_spawn<W>(P, v, child, n, sgn_h, cnt, out);
+    return false;
+}
+
+// Float value and sum of absolute terms of the single-excitation element h_ia + sum_j [(ia|jj) -
+// delta_spin (ij|ja)] (without the parity sign) for every lane with a pending single, each evaluated by
+// the whole warp: lane x takes electrons x, x + 32. Called by all 32 lanes.
+template <int W>
+__device__ __forceinline__ void single_elements_warp(const Params &P, const DetView<W> *vp, bool pend, int i, int a,
+                                                     unsigned long long pol, float &hs, float &hab) {
+    unsigned need = __ballot_sync(0xFFFFFFFFu, pend);
+    const int lane = threadIdx.x & 31;
+    while (need) {
+        const int src = __ffs(need) - 1;
+        need &= need - 1;
+        const DetView<W> *sv = reinterpret_cast<const DetView<W> *>(
+            __shfl_sync(0xFFFFFFFFu, reinterpret_cast<unsigned long long>(vp), src));
+        const int ii = __shfl_sync(0xFFFFFFFFu, i, src), aa = __shfl_sync(0xFFFFFFFFu, a, src);
+        const int I = ii >> 1, A = aa >> 1;
+        float s = 0.f, b = 0.f;
+        for (int x = lane; x < P.n_elec; x += 32) {
+            const int j = sv->occ[x];
+            if (j != ii) {
+                const int J = j >> 1;
+                const float u = eri_f(P, I, A, J, J, pol);
+                s += u;
+                b += fabsf(u);
+                if ((j & 1) == (ii & 1)) {
+                    const float w = eri_f(P, I, J, J, A, pol);
+                    s -= w;
+                    b += fabsf(w);
+                }
+            }
+        }
+        if (lane == 0) {
+            const float hh = __ldg(P.h_f + I * P.n_orb + A);
+            s += hh;
+            b += fabsf(hh);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            s += __shfl_down_sync(0xFFFFFFFFu, s, o);
+            b += __shfl_down_sync(0xFFFFFFFFu, b, o);
+        }
+        s = __shfl_sync(0xFFFFFFFFu, s, 0);
+        b = __shfl_sync(0xFFFFFFFFu, b, 0);
+        if (lane == src) {
+            hs = s;
+            hab = b;
+        }
+    }
+}
+
+// Completes a pending single i -> ao: |H - hs| <= hab serr (float sum of at most 2N - 1 rounded terms,
+// and the FP64 sum), so most decisions need no FP64; the rest evaluate H in FP64.
+template <int W>
+__device__ __forceinline__ void attempt_single_end(const Params &P, const DetView<W> &v, int i, int ao, unsigned mallow,
+                                                   unsigned long long q, float hs, float hab, unsigned long long *cnt,
+                                                   AttemptOut &out) {
+    const float eh = fmaf(hab, P.serr_f, 1e-30f);
+    const float ah_lo = fabsf(hs) - eh, ah_hi = fabsf(hs) + eh;
+    const float F = P.cs_f * small_f(mallow * v.nok);
+    int n = decide_spawn(ah_lo * F * kDown, ah_hi * F * kUp, q, P.srange_f);
+    int sgn_h;
+    if (n >= 0) {
+        if (n == 0) return;
+        sgn_h = hs > 0.f ? 1 : -1;
+        if (count_between<W>(v.d, i, ao) & 1) sgn_h = -sgn_h;
+    } else {
+        atomicAdd(&P.st->exact_spawn, 1ull);
+        const double hv = hij_single<W>(P, v.d, v.occ, i, ao);
+        if (hv == 0.0) return;
+        // p = (|H| (tau / P_single)) (M_allow (N - delta_s))
+        const double p = __dmul_rn(__dmul_rn(fabs(hv), P.cs), (double)((long long)mallow * (long long)v.nok));
+        const double fl = floor(p);
+        if (fl >= 2147483647.0) { set_status(P.st, FCIQMC_ERR_NUMERIC); return; }
+        const double range = __dsub_rn(9007199254740992.0, P.d53_d);
+        n = (int)fl + (__ull2double_rn(q) < __dmul_rn(__dsub_rn(p, fl), range) ? 1 : 0);
+        sgn_h = hv > 0.0 ? 1 : -1;
+        if (n == 0) return;
+    }
+    unsigned long long child[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) child[w] = v.d[w];
+    flip<W>(child, i);
+    flip<W>(child, ao);
+    emit_spawn<W>(P, v, child, n, sgn_h, cnt, out);
+}
+
+// One spawning attempt per lane (active lanes only); called by all 32 lanes of a warp.
+template <int W, bool TAB>
+__device__ __forceinline__ AttemptOut spawn_attempt(const Params &P, const Tables &T, const DetView<W> &v,
+                                                     const HeavyTab *tab, const float *rcpf, bool active, unsigned a,
+                                                     unsigned iter, unsigned long long *cnt) {
+    AttemptOut out{false, 0u};
+    const unsigned long long pol = keep_policy();
+    int i = 0, ao = 0;
+    unsigned mallow = 0;
+    unsigned long long q = 0;
+    bool pend = false;
+    if (active) pend = attempt_begin<W, TAB>(P, T, v, tab, rcpf, a, iter, pol, cnt, out, i, ao, mallow, q);
+    float hs = 0.f, hab = 0.f;
+    single_elements_warp<W>(P, &v, pend, i, ao, pol, hs, hab);
+    if (pend) attempt_single_end<W>(P, v, i, ao, mallow, q, hs, hab, cnt, out);
     return out;
 }
 
@@ -502,15 +658,16 @@ __global__ void __launch_bounds__(kTile, FQ_SWEEP_MIN_BLOCKS) k_sweep(Params P) 
         const unsigned total = s_off[kTile];
         for (unsigned base = 0; base < total; base += kTile) {
             const unsigned k = base + tid;
-            AttemptOut ao{false, 0u};
-            if (k < total) {
-                int lo = 0, hi = kTile - 1;  // last d with s_off[d] <= k
+            const bool act = k < total;
+            int lo = 0;
+            if (act) {
+                int hi = kTile - 1;  // last d with s_off[d] <= k
                 while (lo < hi) {
                     int mid = (lo + hi + 1) >> 1;
                     if (s_off[mid] <= k) lo = mid; else hi = mid - 1;
                 }
-                ao = spawn_attempt<W, false>(P, T, s_dv[lo], nullptr, s_rcpf, k - s_off[lo], iter, acc);
             }
+            const AttemptOut ao = spawn_attempt<W, false>(P, T, s_dv[lo], nullptr, s_rcpf, act, k - s_off[lo], iter, acc);
             long long slot = warp_append(&st->n_merged, ao.claimed);
             if (ao.claimed && slot < P.mt_cap) P.merged[slot] = ao.pos;
         }
@@ -524,8 +681,9 @@ __global__ void __launch_bounds__(kTile, FQ_SWEEP_MIN_BLOCKS) k_sweep(Params P) 
     if (threadIdx.x == 0) P.partial[blockIdx.x] = bs;
 }
 
-// Attempts of heavily populated determinants: one warp per chunk of up to kChunk attempts of one
-// determinant; the warp builds that determinant's good-orbital table once per chunk.
+// Attempts of heavily populated determinants, split into chunks of kChunk attempts: each warp takes a
+// contiguous range of chunks (so it meets few determinants) and builds a determinant's tables once
+// when it reaches it.
 template <int W>
 __global__ void __launch_bounds__(kTile) k_heavy(Params P) {
     DevState *st = P.st;
@@ -533,14 +691,14 @@ __global__ void __launch_bounds__(kTile) k_heavy(Params P) {
     constexpr int NW = kTile / 32;
     __shared__ Tables T;
     __shared__ DetView<W> s_v[NW];
-    __shared__ GoodTable<W> s_tab[NW];
+    __shared__ HeavyTab s_tab[NW];
     __shared__ float s_rcpf[2 * MAXSO + 2];
     __shared__ unsigned long long s_red[NW * NCNT];
     load_tables(P, T);
     load_rcpf(P, s_rcpf);
     const unsigned long long packed = st->heavy_packed;
     const long long nh = min((long long)(packed >> 40), P.heavy_cap);
-    const unsigned long long nch = packed & ((1ull << 40) - 1ull);
+    const unsigned long long nch = nh > 0 ? (packed & ((1ull << 40) - 1ull)) : 0ull;
     const unsigned iter = (unsigned)st->iter;
     const DetView<W> *heavy = reinterpret_cast<const DetView<W> *>(P.heavy);
     unsigned long long cnt[NCNT];
@@ -550,39 +708,37 @@ __global__ void __launch_bounds__(kTile) k_heavy(Params P) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned long long gw = (unsigned long long)blockIdx.x * NW + warp;
     const unsigned long long nwarps = (unsigned long long)gridDim.x * NW;
+    const unsigned long long q0 = nch * gw / nwarps, q1 = nch * (gw + 1) / nwarps;
     long long cur = -1;
     DetView<W> &v = s_v[warp];
-    GoodTable<W> &tab = s_tab[warp];
-    for (unsigned long long q = gw; q < nch && nh > 0; q += nwarps) {
+    HeavyTab &tab = s_tab[warp];
+    for (unsigned long long q = q0; q < q1; ++q) {
         // record holding chunk q: last record whose first chunk is <= q
-        long long lo = 0, hi = nh - 1;
-        while (lo < hi) {
-            const long long mid = (lo + hi + 1) >> 1;
-            if ((unsigned long long)P.heavy_base[mid] <= q) lo = mid; else hi = mid - 1;
+        long long r;
+        if (cur < 0) {
+            long long lo = 0, hi = nh - 1;
+            while (lo < hi) {
+                const long long mid = (lo + hi + 1) >> 1;
+                if ((unsigned long long)P.heavy_base[mid] <= q) lo = mid; else hi = mid - 1;
+            }
+            r = lo;
+        } else {
+            r = cur;
+            while (r + 1 < nh && (unsigned long long)P.heavy_base[r + 1] <= q) ++r;
         }
-        const unsigned a0 = (unsigned)(q - P.heavy_base[lo]) * kChunk;
-        const unsigned a1 = min(a0 + (unsigned)kChunk, P.heavy_att[lo]);
-        if (lo != cur) {
-            const unsigned long long *src = reinterpret_cast<const unsigned long long *>(heavy + lo);
+        if (r != cur) {
+            const unsigned long long *src = reinterpret_cast<const unsigned long long *>(heavy + r);
             unsigned long long *dstv = reinterpret_cast<unsigned long long *>(&v);
             for (int k = lane; k < (int)(sizeof(DetView<W>) / 8); k += 32) dstv[k] = src[k];
             __syncwarp();
-            if (lane < 24) {
-                const int sc = lane >> 3, gij = lane & 7;
-                const int si = sc == 1 ? 1 : 0, sj = sc == 0 ? 0 : 1;
-                unsigned long long gm[W];
-                const unsigned G = good_set<W>(P, T, v, si, sj, gij, gm);
-                tab.G[lane] = (unsigned short)G;
-#pragma unroll
-                for (int w = 0; w < W; ++w) tab.gm[lane][w] = gm[w];
-            }
-            __syncwarp();
-            cur = lo;
+            build_heavy_tab<W>(P, T, v, tab, lane);
+            cur = r;
         }
+        const unsigned a0 = (unsigned)(q - P.heavy_base[r]) * kChunk;
+        const unsigned a1 = min(a0 + (unsigned)kChunk, P.heavy_att[r]);
         for (unsigned base = a0; base < a1; base += 32) {
             const unsigned a = base + lane;
-            AttemptOut ao{false, 0u};
-            if (a < a1) ao = spawn_attempt<W, true>(P, T, v, &tab, s_rcpf, a, iter, cnt);
+            const AttemptOut ao = spawn_attempt<W, true>(P, T, v, &tab, s_rcpf, a < a1, a, iter, cnt);
             long long slot = warp_append(&st->n_merged, ao.claimed);
             if (ao.claimed && slot < P.mt_cap) P.merged[slot] = ao.pos;
         }
