@@ -63,7 +63,7 @@ bool sizes_of(int n_elec, int n_orb, const fciqmc_options &o, Sizes &z) {
 }
 
 struct Layout {
-    size_t state, h, h_f, eri, eri_f, wpair, map1, cmask, irrep, pairs, recip, rcpf, ref_occ, facts, e0;
+    size_t state, h, h_f, eri, eri_f, wpair, map1, cmask, unionm, irrep, pairs, recip, rcpf, ref_occ, facts, e0;
     size_t det[2], hd[2], hdf[2], pop[2][2], idx, mt, merged, heavy, heavy_base, heavy_att, partial, hist;
     size_t total;
 };
@@ -84,6 +84,7 @@ Layout layout_of(const Sizes &z, int n_orb) {
     L.wpair = take(sizeof(double) * 2 * n_orb * n_orb);
     L.map1 = take(sizeof(unsigned long long) * fq::MAXSO);
     L.cmask = take(sizeof(unsigned long long) * fq::NCLASS * fq::MAXW);
+    L.unionm = take(sizeof(unsigned long long) * 2 * 256 * fq::MAXW);
     L.irrep = take(fq::MAXSO);
     L.pairs = take(sizeof(unsigned short) * std::max(z.npairs, 1));
     L.recip = take(sizeof(double) * (2 * fq::MAXSO + 2));
@@ -339,6 +340,7 @@ int fciqmc_create(const double *h1, const double *eri_s8, double e_core, int n_e
     P.wpair = at<double>(h, L.wpair);
     P.map1 = at<unsigned long long>(h, L.map1);
     P.cmask = at<unsigned long long>(h, L.cmask);
+    P.unionm = at<unsigned long long>(h, L.unionm);
     P.irrep = at<unsigned char>(h, L.irrep);
     P.pairs = at<unsigned short>(h, L.pairs);
     P.recip = at<double>(h, L.recip);
@@ -382,6 +384,13 @@ int fciqmc_create(const double *h1, const double *eri_s8, double e_core, int n_e
         cmask[cl * fq::MAXW + (k >> 6)] |= 1ull << (k & 63);
     }
     for (int p = 0; p < n_orb; ++p) irr[p] = orb_irrep ? (unsigned char)orb_irrep[p] : 0;
+    std::vector<unsigned long long> unionm(2 * 256 * fq::MAXW, 0ull);
+    for (int sp = 0; sp < 2; ++sp)
+        for (int set = 0; set < 256; ++set)
+            for (int g = 0; g < 8; ++g)
+                if ((set >> g) & 1)
+                    for (int w = 0; w < fq::MAXW; ++w)
+                        unionm[(sp * 256 + set) * fq::MAXW + w] |= cmask[(g * 2 + sp) * fq::MAXW + w];
     std::vector<unsigned short> pairs(std::max(z.npairs, 1), 0);
     for (int j = 1, k = 0; j < n_elec; ++j)
         for (int i = 0; i < j; ++i) pairs[k++] = (unsigned short)(i | (j << 8));
@@ -409,6 +418,7 @@ int fciqmc_create(const double *h1, const double *eri_s8, double e_core, int n_e
         FQ_TRY(cudaMemcpyAsync(const_cast<double *>(P.h), h1, sizeof(double) * n_orb * n_orb, cudaMemcpyHostToDevice, s));
         FQ_TRY(cudaMemcpyAsync(const_cast<double *>(P.eri), eri_s8, sizeof(double) * z.n_eri, cudaMemcpyHostToDevice, s));
         FQ_TRY(cudaMemcpyAsync(const_cast<unsigned long long *>(P.cmask), cmask.data(), sizeof(unsigned long long) * cmask.size(), cudaMemcpyHostToDevice, s));
+        FQ_TRY(cudaMemcpyAsync(const_cast<unsigned long long *>(P.unionm), unionm.data(), sizeof(unsigned long long) * unionm.size(), cudaMemcpyHostToDevice, s));
         FQ_TRY(cudaMemcpyAsync(const_cast<unsigned char *>(P.irrep), irr.data(), irr.size(), cudaMemcpyHostToDevice, s));
         FQ_TRY(cudaMemcpyAsync(const_cast<unsigned short *>(P.pairs), pairs.data(), sizeof(unsigned short) * pairs.size(), cudaMemcpyHostToDevice, s));
         FQ_TRY(cudaMemcpyAsync(const_cast<unsigned char *>(P.ref_occ), ref_occ.data(), ref_occ.size(), cudaMemcpyHostToDevice, s));

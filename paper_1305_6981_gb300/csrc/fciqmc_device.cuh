@@ -74,6 +74,7 @@ struct Params {
     const double *wpair;    // [2][n_orb][n_orb]: [0] opposite spin (pp|qq), [1] same spin (pp|qq) - (pq|qp)
     const unsigned long long *map1;   // n_so, orbital map of Algorithm 1
     const unsigned long long *cmask;  // [NCLASS][MAXW] spin orbitals of each (irrep, spin) class
+    const unsigned long long *unionm; // [2][256][MAXW] spin orbitals of spin s in the irreps of an 8-bit set
     const unsigned char *irrep;       // n_orb
     const unsigned short *pairs;      // npairs: (i | j << 8), i < j electron indices
     const double *recip;              // recip[L] = 1.0 / L, L < 2 * MAXSO + 2

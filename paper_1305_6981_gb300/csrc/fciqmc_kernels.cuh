@@ -34,6 +34,7 @@ struct DetView {
     unsigned long long d[W];
     unsigned long long fp;
     unsigned long long okm; // bit x: electron x has at least one symmetry-allowed single
+    unsigned long long cb8[2];  // byte g of cb8[s]: unoccupied spin orbitals of class (irrep g, spin s)
     int c;
     unsigned char nok;      // electrons with at least one symmetry-allowed single (N - delta_s)
     unsigned char flag;     // initiator
@@ -124,6 +125,13 @@ __device__ __forceinline__ void prepare_det(const Params &P, const Tables &T, De
         }
         v.cnt[cl] = (unsigned char)u;
     }
+    unsigned long long c0 = 0, c1 = 0;
+    for (int g = 0; g < NCLASS / 2; ++g) {
+        c0 |= (unsigned long long)v.cnt[2 * g] << (8 * g);
+        c1 |= (unsigned long long)v.cnt[2 * g + 1] << (8 * g);
+    }
+    v.cb8[0] = c0;
+    v.cb8[1] = c1;
     unsigned long long okm = 0;
     for (int x = 0; x < P.n_elec; ++x) {
         int k = v.occ[x];
@@ -159,25 +167,33 @@ struct HeavyTab {
     unsigned short G[24];
 };
 
-// Good a-orbitals for one (spin case, pair irrep): loop over the classes of allowed spin.
+// Good a-orbitals for one (spin case, pair irrep): a of spin sa in irrep g is good when its class has
+// an unoccupied orbital and the class of b (irrep g ^ gij, spin sb = si + sj - sa) has one left besides
+// a. All eight irreps of a spin are tested at once on the byte-packed class counts (counts <= 64, so no
+// byte carries); the union of the good classes' orbitals comes from a table indexed by the irrep set.
 template <int W>
-__device__ __forceinline__ unsigned good_set(const Params &P, const Tables &T, const DetView<W> &v, int si, int sj,
-                                             int gij, unsigned long long (&gm)[W]) {
+__device__ __forceinline__ unsigned good_set(const Params &P, const DetView<W> &v, int si, int sj, int gij,
+                                             unsigned long long (&gm)[W]) {
+    constexpr unsigned long long kOnes = 0x0101010101010101ull, kHigh = 0x8080808080808080ull;
     unsigned G = 0;
 #pragma unroll
     for (int w = 0; w < W; ++w) gm[w] = 0ull;
+#pragma unroll
     for (int sa = 0; sa < 2; ++sa) {
         if (si == sj && sa != si) continue;
         const int sb = si + sj - sa;
-        for (int g = 0; g < P.n_irrep_used; ++g) {
-            const int ca = g * 2 + sa, cb = (gij ^ g) * 2 + sb;
-            const int avail = (int)v.cnt[cb] - (ca == cb ? 1 : 0);
-            if (avail >= 1 && v.cnt[ca] > 0) {
-                G += v.cnt[ca];
+        const unsigned long long A = v.cb8[sa];
+        unsigned long long B = v.cb8[sb];
+        if (gij & 4) B = (B >> 32) | (B << 32);
+        const unsigned sel = 0x3210u ^ (0x1111u * (unsigned)(gij & 3));  // byte g <- byte g ^ (gij & 3)
+        B = ((unsigned long long)__byte_perm((unsigned)(B >> 32), 0u, sel) << 32) | __byte_perm((unsigned)B, 0u, sel);
+        const unsigned long long need = (sa == sb && gij == 0) ? 2ull : 1ull;  // a and b from one class
+        const unsigned long long cond = (A + 0x7F * kOnes) & (B + (0x80 - need) * kOnes) & kHigh;
+        const unsigned long long bits = cond >> 7;
+        G += (unsigned)(((A & (bits * 0xFFull)) * kOnes) >> 56);
+        const unsigned set = (unsigned)((bits * 0x0102040810204080ull) >> 56);
 #pragma unroll
-                for (int w = 0; w < W; ++w) gm[w] |= T.mask[ca * MAXW + w];
-            }
-        }
+        for (int w = 0; w < W; ++w) gm[w] |= __ldg(P.unionm + ((sa * 256 + set) * MAXW + w));
     }
 #pragma unroll
     for (int w = 0; w < W; ++w) gm[w] &= ~v.d[w];
@@ -193,7 +209,7 @@ __device__ __forceinline__ void build_heavy_tab(const Params &P, const Tables &T
         const int sc = lane >> 3, gij = lane & 7;
         const int si = sc == 1 ? 1 : 0, sj = sc == 0 ? 0 : 1;
         unsigned long long gm[W];
-        tab.G[lane] = (unsigned short)good_set<W>(P, T, v, si, sj, gij, gm);
+        tab.G[lane] = (unsigned short)good_set<W>(P, v, si, sj, gij, gm);
         int n = 0;
 #pragma unroll
         for (int w = 0; w < W; ++w) {
@@ -301,7 +317,7 @@ __device__ __forceinline__ bool attempt_begin(const Params &P, const Tables &T, 
         ao = tab->glist[e][rank_of(r2, G)];
     } else {
         unsigned long long gm[W];
-        G = good_set<W>(P, T, v, si, sj, gij, gm);
+        G = good_set<W>(P, v, si, sj, gij, gm);
         if (G == 0) { cnt[C_NULLS]++; return false; }
         ao = select_bit<W>(gm, (int)rank_of(r2, G));
     }
