@@ -39,12 +39,13 @@ from paper_1305_6981_gb300 import synth  # noqa: E402
 METRIC = "spawn attempts/s at 1e8 walkers (24e/60o, initiator, tau 0.001)"
 
 # Instruction-issue roofline of the spawning kernels (they are bound by their instruction stream, not
-# by HBM). Per-unit figures are warp instructions per attempt from ncu (smsp__inst_executed.sum of one
-# launch divided by the attempts that launch made), taken with the --ncu-case command recorded in the
-# summary under profiles/; they must be re-measured whenever those kernels change.
-WARP_INST_PER_ATTEMPT = {"heavy": 22.5, "sweep": 56.8}
+# by HBM). Per-unit figures are warp instructions per attempt from ncu (smsp__inst_executed.sum of a
+# full-size launch in the timed region divided by the attempts that launch made), taken with the
+# one-pass command recorded in profiles/counters_24e60o_1e8.txt; they must be re-measured whenever
+# those kernels change.
+WARP_INST_PER_ATTEMPT = {"heavy": 12.09, "sweep": 37.9}
 # DRAM bytes (read + write) per launch of each kernel at the full workload, from the same summary.
-DRAM_BYTES_PER_LAUNCH = {"heavy": 18_496_896, "sweep": 124_689_024, "annihilate": 51_637_248}
+DRAM_BYTES_PER_LAUNCH = {"heavy": 18_028_672, "sweep": 125_580_800, "annihilate": 51_655_552}
 ISSUE_PER_CLK_PER_SM = 4  # warp instructions: 4 schedulers per SM, one issue each per clock
 N_SMS = 152
 
@@ -339,7 +340,7 @@ def run_gpu(args, wl, rank, world, local_rank):
             "roofline": {"bound": "alu", "kernel": f"k_{dom}", "achieved": achieved, "peak": issue_peak,
                          "unit": "Gwarp-inst/s", "frac": achieved / issue_peak,
                          "traffic": DRAM_BYTES_PER_LAUNCH.get(dom),
-                         "per_unit": f"{WARP_INST_PER_ATTEMPT[dom]} warp instructions per attempt (ncu)",
+                         "per_unit": f"{WARP_INST_PER_ATTEMPT[dom]} warp instructions per attempt (ncu, full-size launch)",
                          "units_per_launch": units[dom], "launch_ms": dom_ms,
                          "peak_derivation": f"{ISSUE_PER_CLK_PER_SM} warp-inst/clk/SM x {N_SMS} SMs x {sm_mhz:.0f} MHz"},
             "hbm": {"cycle_algorithmic_gbs": cycle_gbs, "peak": hbm_peak, "frac": cycle_gbs / hbm_peak,
