@@ -232,13 +232,6 @@ __device__ __forceinline__ float eri_f(const Params &P, int p, int q, int r, int
     return ld_keep(P.eri_f + eidx(p, q, r, s), pol);
 }
 
-// Algorithm 1 over the ascending occupied list: hash = p hash + map(orb_i) i (uint64 wraparound).
-__device__ __forceinline__ unsigned long long fingerprint(const unsigned char *occ, int n, const unsigned long long *map1) {
-    unsigned long long h = 0;
-    for (int i = 0; i < n; ++i) h = 1099511628211ull * h + map1[occ[i]] * (unsigned long long)(i + 1);
-    return h;
-}
-
 // Slater-Condon, single i -> a from source d (occupied list occ of d), exact FP64 in ascending order.
 template <int W>
 __device__ double hij_single(const Params &P, const unsigned long long (&d)[W], const unsigned char *occ, int i, int a) {

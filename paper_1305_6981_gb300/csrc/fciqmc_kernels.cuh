@@ -33,12 +33,12 @@ template <int W>
 struct DetView {
     unsigned long long d[W];
     unsigned long long fp;
-    unsigned long long okm; // bit x: electron x has at least one symmetry-allowed single
+    unsigned long long okm;     // bit x: electron x has at least one symmetry-allowed single
     unsigned long long cb8[2];  // byte g of cb8[s]: unoccupied spin orbitals of class (irrep g, spin s)
+    unsigned char cnt[NCLASS];  // the same counts by class index 2 g + s
     int c;
-    unsigned char nok;      // electrons with at least one symmetry-allowed single (N - delta_s)
-    unsigned char flag;     // initiator
-    unsigned char cnt[NCLASS];
+    unsigned char nok;          // electrons with at least one symmetry-allowed single (N - delta_s)
+    unsigned char flag;         // initiator
     unsigned char occ[MAXN];
 };
 
@@ -105,41 +105,57 @@ __device__ __forceinline__ bool merge_insert(const Params &P, const unsigned lon
 }
 
 // ---------------------------------------------------------------------------- per-determinant preparation
+// Nonzero bytes of a byte-packed count word as an 8-bit set.
+__device__ __forceinline__ unsigned nonzero_bytes(unsigned long long x) {
+    const unsigned long long bits = ((x + 0x7F7F7F7F7F7F7F7Full) & 0x8080808080808080ull) >> 7;
+    return (unsigned)((bits * 0x0102040810204080ull) >> 56);
+}
+
+// Class counts first (population counts against the class masks); then one pass over the occupied
+// spin orbitals in ascending order gives the occupied list, the electrons with an allowed single (an
+// electron's class keeps an unoccupied orbital) and the fingerprint of Algorithm 1.
 template <int W>
 __device__ __forceinline__ void prepare_det(const Params &P, const Tables &T, DetView<W> &v, int c) {
+    unsigned long long cb0 = 0, cb1 = 0;
+    for (int g = 0; g < P.n_irrep_used; ++g) {
+        int u0 = 0, u1 = 0;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            u0 += __popcll(~v.d[w] & T.mask[(2 * g) * MAXW + w]);
+            u1 += __popcll(~v.d[w] & T.mask[(2 * g + 1) * MAXW + w]);
+        }
+        cb0 |= (unsigned long long)u0 << (8 * g);
+        cb1 |= (unsigned long long)u1 << (8 * g);
+    }
+    v.cb8[0] = cb0;
+    v.cb8[1] = cb1;
+    unsigned *cw = reinterpret_cast<unsigned *>(v.cnt);
+#pragma unroll
+    for (int j = 0; j < NCLASS / 4; ++j)  // class 2g + s: bytes (g = 2j, s = 0), (2j, 1), (2j + 1, 0), (2j + 1, 1)
+        cw[j] = __byte_perm((unsigned)(cb0 >> (16 * j)), (unsigned)(cb1 >> (16 * j)), 0x5140u);
+    const unsigned set0 = nonzero_bytes(cb0), set1 = nonzero_bytes(cb1);
+    unsigned long long ok[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w)
+        ok[w] = __ldg(P.unionm + (set0 * MAXW + w)) | __ldg(P.unionm + ((256 + set1) * MAXW + w));
     int n = 0;
+    unsigned long long okm = 0, h = 0;
 #pragma unroll
     for (int w = 0; w < W; ++w) {
         unsigned long long m = v.d[w];
         while (m) {
-            v.occ[n++] = (unsigned char)(64 * w + __ffsll((long long)m) - 1);
+            const int b = __ffsll((long long)m) - 1;
+            const int k = 64 * w + b;
+            v.occ[n] = (unsigned char)k;
+            okm |= ((ok[w] >> b) & 1ull) << n;
+            h = 1099511628211ull * h + T.map1[k] * (unsigned long long)(n + 1);
+            ++n;
             m &= m - 1;
         }
     }
-    const int ncls = 2 * P.n_irrep_used;
-    for (int cl = 0; cl < NCLASS; ++cl) {
-        int u = 0;
-        if (cl < ncls) {
-#pragma unroll
-            for (int w = 0; w < W; ++w) u += __popcll(~v.d[w] & T.mask[cl * MAXW + w]);
-        }
-        v.cnt[cl] = (unsigned char)u;
-    }
-    unsigned long long c0 = 0, c1 = 0;
-    for (int g = 0; g < NCLASS / 2; ++g) {
-        c0 |= (unsigned long long)v.cnt[2 * g] << (8 * g);
-        c1 |= (unsigned long long)v.cnt[2 * g + 1] << (8 * g);
-    }
-    v.cb8[0] = c0;
-    v.cb8[1] = c1;
-    unsigned long long okm = 0;
-    for (int x = 0; x < P.n_elec; ++x) {
-        int k = v.occ[x];
-        if (v.cnt[T.irrep[k >> 1] * 2 + (k & 1)] > 0) okm |= 1ull << x;
-    }
     v.okm = okm;
     v.nok = (unsigned char)__popcll(okm);
-    v.fp = fingerprint(v.occ, P.n_elec, T.map1);
+    v.fp = h;
     v.c = c;
     int ac = c < 0 ? -c : c;
     bool is_ref = det_eq<W>(v.d, P.ref);
