@@ -505,9 +505,9 @@ def e2e_rate(g, args, info, world):
                       vary=st["vary_shift"], shift_counter=st["shift_counter"], nw_last_update=st["nw_last_update"])
         h2d += n * (8 * W + 4 + 8)
         g.step(1)
+        att += g.history(1)[0]["attempts"]
         n = g.walkers_into(dets, pops, hd)
         d2h += n * (8 * W + 4 + 8)
-        att += int(np.abs(pops[:n]).sum())
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     return {"value": att / dt, "unit": "attempts/s", "h2d_bytes_per_step": h2d // K, "d2h_bytes_per_step": d2h // K,

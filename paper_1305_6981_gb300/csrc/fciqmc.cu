@@ -206,27 +206,57 @@ void launch_index_rebuild(fciqmc_handle *h) {
 }
 
 template <int W>
-void launch_prepare(fciqmc_handle *h, long long n, int compute) {
+void launch_prepare(fciqmc_handle *h, int b, long long n, int compute) {
     long long blocks = std::min<long long>((n + 255) / 256, h->small_grid);
     if (blocks < 1) blocks = 1;
-    fq::k_prepare_list<W><<<(unsigned)blocks, 256, h->smem_w, h->stream>>>(h->P, n, compute);
+    fq::k_prepare_list<W><<<(unsigned)blocks, 256, h->smem_w, h->stream>>>(h->P, b, n, compute);
+}
+
+// Loads a list into buffer b (validated on the device); on success makes it the active list with the
+// state st0: the old list's index entries are emptied (located first, or the whole index after a
+// failed step or for a dense index), the new keys inserted.
+template <int W>
+int load_list(fciqmc_handle *h, const DevState &cur, DevState &st0, const uint64_t *dets, const int32_t *pops,
+              const double *hdiag, long long n) {
+    cudaStream_t s = h->stream;
+    const Params &P = h->P;
+    const int b = cur.lb ^ 1;
+    const unsigned blocks = (unsigned)std::max<long long>(1, std::min<long long>((n + 255) / 256, h->small_grid));
+    if (n > 0) {
+        FQ_CUDA(cudaMemcpyAsync(P.det[b], dets, sizeof(uint64_t) * W * n, cudaMemcpyHostToDevice, s));
+        FQ_CUDA(cudaMemcpyAsync(P.pop[b][0], pops, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+        if (hdiag) FQ_CUDA(cudaMemcpyAsync(P.hd[b], hdiag, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    }
+    FQ_CUDA(cudaMemsetAsync(&P.st->check_bad, 0, sizeof(int), s));
+    fq::k_check_list<W><<<blocks, 256, 0, s>>>(P, b, n);
+    int bad = 0;
+    FQ_CUDA(cudaMemcpyAsync(&bad, &P.st->check_bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FQ_CUDA(cudaStreamSynchronize(s));
+    if (bad) return FCIQMC_ERR_INVALID_ARG;  // the active list and the index are untouched
+    st0.lb = b;
+    st0.pp = 0;
+    FQ_CUDA(cudaMemcpyAsync(P.st, &st0, sizeof(st0), cudaMemcpyHostToDevice, s));
+    const bool sparse = cur.status == 0 && cur.list_len >= 0 && cur.list_len * 16 <= h->z.idx_cap;
+    if (sparse && cur.list_len > 0) {
+        const unsigned ob = (unsigned)std::max<long long>(1, std::min<long long>((cur.list_len + 255) / 256, h->small_grid));
+        int *pos = P.pop[cur.lb][cur.pp ^ 1];  // the old list's idle population buffer
+        fq::k_index_locate<W><<<ob, 256, 0, s>>>(P, cur.lb, cur.list_len, pos);
+        fq::k_index_clear_at<<<ob, 256, 0, s>>>(P, pos, cur.list_len);
+    } else if (!sparse) {
+        fq::k_index_clear<<<h->small_grid, 256, 0, s>>>(P, 1);
+    }
+    launch_prepare<W>(h, b, n, hdiag ? 0 : 1);
+    fq::k_index_fill<W><<<h->small_grid, 256, 0, s>>>(P, 1);
+    // a failed step may have left claimed entries in the spawn table
+    if (cur.status != 0) fq::k_mt_clear<<<h->small_grid, 256, 0, s>>>(P, W);
+    FQ_CUDA(cudaGetLastError());
+    return FCIQMC_OK;
 }
 
 int read_state(fciqmc_handle *h, DevState &st) {
     FQ_CUDA(cudaMemcpyAsync(&st, h->P.st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
     FQ_CUDA(cudaStreamSynchronize(h->stream));
     return FCIQMC_OK;
-}
-
-int check_det(const fciqmc_handle *h, const uint64_t *d) {
-    int n = 0;
-    for (int w = 0; w < h->z.W; ++w) {
-        uint64_t x = d[w];
-        int hi_bits = h->z.n_so - 64 * w;
-        if (hi_bits < 64 && (x >> hi_bits) != 0) return 0;
-        n += __builtin_popcountll(x);
-    }
-    return n == h->P.n_elec;
 }
 
 }  // namespace
@@ -478,10 +508,10 @@ int fciqmc_create(const double *h1, const double *eri_s8, double e_core, int n_e
         int p0 = o.initial_population;
         FQ_TRY(cudaMemcpyAsync(P.pop[0][0], &p0, sizeof(int), cudaMemcpyHostToDevice, s));
         if (z.W == 1) {
-            launch_prepare<1>(h, 1, 1);
+            launch_prepare<1>(h, 0, 1, 1);
             launch_index_rebuild<1>(h);
         } else {
-            launch_prepare<2>(h, 1, 1);
+            launch_prepare<2>(h, 0, 1, 1);
             launch_index_rebuild<2>(h);
         }
         FQ_TRY(cudaGetLastError());
@@ -669,10 +699,6 @@ int fciqmc_set_walkers(fciqmc_handle *h, const uint64_t *dets, const int32_t *po
                        const fciqmc_state *stin) {
     if (!h || n < 0 || (n > 0 && (!dets || !pops))) return FCIQMC_ERR_INVALID_ARG;
     if (n > h->z.cap) return FCIQMC_ERR_CAPACITY;
-    for (int64_t k = 0; k < n; ++k) {
-        if (pops[k] == 0 || pops[k] == INT32_MIN) return FCIQMC_ERR_INVALID_ARG;
-        if (!check_det(h, dets + k * h->z.W)) return FCIQMC_ERR_INVALID_ARG;
-    }
     DevState cur;
     int rc = read_state(h, cur);
     if (rc != FCIQMC_OK) return rc;
@@ -693,24 +719,8 @@ int fciqmc_set_walkers(fciqmc_handle *h, const uint64_t *dets, const int32_t *po
     }
     st0.list_len = n;
     st0.claim = (unsigned long long)n;
-    cudaStream_t s = h->stream;
-    FQ_CUDA(cudaMemcpyAsync(h->P.st, &st0, sizeof(st0), cudaMemcpyHostToDevice, s));
-    if (n > 0) {
-        FQ_CUDA(cudaMemcpyAsync(h->P.det[0], dets, sizeof(uint64_t) * h->z.W * n, cudaMemcpyHostToDevice, s));
-        FQ_CUDA(cudaMemcpyAsync(h->P.pop[0][0], pops, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
-        if (hdiag) FQ_CUDA(cudaMemcpyAsync(h->P.hd[0], hdiag, sizeof(double) * n, cudaMemcpyHostToDevice, s));
-    }
-    if (h->z.W == 1) {
-        launch_prepare<1>(h, n, hdiag ? 0 : 1);
-        launch_index_rebuild<1>(h);
-    } else {
-        launch_prepare<2>(h, n, hdiag ? 0 : 1);
-        launch_index_rebuild<2>(h);
-    }
-    FQ_CUDA(cudaGetLastError());
-    // a failed step may have left claimed entries in the spawn table
-    fq::k_mt_clear<<<h->small_grid, 256, 0, s>>>(h->P, h->z.W);
-    FQ_CUDA(cudaGetLastError());
+    rc = h->z.W == 1 ? load_list<1>(h, cur, st0, dets, pops, hdiag, n) : load_list<2>(h, cur, st0, dets, pops, hdiag, n);
+    if (rc != FCIQMC_OK) return rc;
     return fciqmc_sync(h);
 }
 

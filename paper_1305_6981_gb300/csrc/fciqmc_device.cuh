@@ -49,6 +49,7 @@ struct DevState {
     unsigned long long est_nw, est_nd;
     long long est_c0;
     double est_num;
+    int check_bad;             // set by the check of a list being loaded
 };
 
 // Uniform parameters of a run, passed by value to every kernel.

@@ -1118,10 +1118,66 @@ __global__ void k_gather(Params P) {
     }
 }
 
-// Diagonal elements of slots [0, n) of list buffer 0: computed (compute != 0) or taken as given; the
+// Checks slots [0, n) of list buffer b as loaded: n_elec occupied spin orbitals, none at or above n_so,
+// population neither 0 nor INT32_MIN. A failure sets st->check_bad.
+template <int W>
+__global__ void k_check_list(Params P, int b, long long n) {
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
+        int cnt = 0;
+        bool ok = true;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            const unsigned long long x = P.det[b][s * W + w];
+            const int hi = P.n_so - 64 * w;
+            if (hi < 64 && (hi <= 0 ? x != 0ull : (x >> hi) != 0ull)) ok = false;
+            cnt += __popcll(x);
+        }
+        const int c = P.pop[b][0][s];
+        if (!ok || cnt != P.n_elec || c == 0 || c == (-2147483647 - 1)) atomicExch(&P.st->check_bad, 1);
+    }
+}
+
+// Index positions of the keys of slots [0, n) of list buffer b, into pos (-1 if absent). Lookups only:
+// entries are emptied afterwards by k_index_clear_at, so no probe chain is cut before every key is found.
+template <int W>
+__global__ void k_index_locate(Params P, int b, long long n, int *pos) {
+    constexpr int S = Stride<W>::v;
+    const unsigned long long imask = (unsigned long long)P.idx_cap - 1ull;
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
+        unsigned long long key[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) key[w] = P.det[b][s * W + w];
+        unsigned long long h = table_hash<W>(key, kSaltIndex) >> (64 - P.idx_bits);
+        int found = -1;
+        for (long long probe = 0; probe < P.idx_cap; ++probe) {
+            const unsigned long long *x = P.idx + h * S;
+            bool match = true, empty = true;
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                match = match && (x[w] == key[w]);
+                empty = empty && (x[w] == EMPTY);
+            }
+            if (match) { found = (int)h; break; }
+            if (empty) break;
+            h = (h + 1ull) & imask;
+        }
+        pos[s] = found;
+    }
+}
+
+// Empties the index entries at pos[0, n).
+__global__ void k_index_clear_at(Params P, const int *pos, long long n) {
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
+        const int h = pos[s];
+        if (h < 0) continue;
+        for (int w = 0; w < P.idx_stride; ++w) P.idx[(long long)h * P.idx_stride + w] = EMPTY;
+    }
+}
+
+// Diagonal elements of slots [0, n) of list buffer b: computed (compute != 0) or taken as given; the
 // float copy is the nearest float.
 template <int W>
-__global__ void __launch_bounds__(256) k_prepare_list(Params P, long long n, int compute) {
+__global__ void __launch_bounds__(256) k_prepare_list(Params P, int b, long long n, int compute) {
     extern __shared__ double s_w[];
     const int M = P.n_orb;
     for (int k = threadIdx.x; k < 2 * M * M; k += blockDim.x) s_w[k] = P.wpair[k];
@@ -1132,13 +1188,13 @@ __global__ void __launch_bounds__(256) k_prepare_list(Params P, long long n, int
         if (compute) {
             unsigned long long d[W];
 #pragma unroll
-            for (int w = 0; w < W; ++w) d[w] = P.det[0][s * W + w];
+            for (int w = 0; w < W; ++w) d[w] = P.det[b][s * W + w];
             v = __dsub_rn(hdiag<W>(P, d, s_w, s_w + 2 * M * M), P.E0);
-            P.hd[0][s] = v;
+            P.hd[b][s] = v;
         } else {
-            v = P.hd[0][s];
+            v = P.hd[b][s];
         }
-        P.hdf[0][s] = __double2float_rn(v);
+        P.hdf[b][s] = __double2float_rn(v);
     }
 }
 

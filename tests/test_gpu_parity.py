@@ -133,6 +133,40 @@ def test_snapshot_roundtrip_and_windows():
     g.close()
 
 
+def test_reloads_and_invalid_lists():
+    """Repeated set_walkers (the old list's index entries are located and emptied before the new keys go in):
+    after loading list A, running, and loading a different list B, both sides advance identically from B.
+    Invalid lists (wrong electron count, a bit beyond the basis, a zero population) are rejected on the
+    device and leave the current list untouched."""
+    from paper_1305_6981_gb300._native import FciqmcError
+    s = synth.init_12e24o()
+    g, q = make_pair(s, 0.005, 3, initial_population=2000, initial_shift=0.8, seed=23, main_capacity=1 << 16)
+    q.iterate(40)
+    dA, pA, _ = q.walkers()
+    g.set_walkers(dA, pA)
+    g.step(5)
+    q.iterate(40)
+    dB, pB, hB = q.walkers()
+    st = q.state()
+    g.set_walkers(dB, pB, hB, iteration=st["iteration"], shift=st["shift"], vary=st["vary"],
+                  shift_counter=st["n_since"], nw_last_update=st["nw_prev"])
+    before = g.walkers()
+    assert len(pB) > 8 and 2 * s.n_orb < 64
+    wrong_count, beyond_basis, zero_pop = dB.copy(), dB.copy(), pB.copy()
+    wrong_count[3, 0] ^= np.uint64(1 << 40)  # one electron more or fewer
+    beyond_basis[5, 0] |= np.uint64(1 << 63)  # spin orbital 63 of a 48-spin-orbital basis
+    zero_pop[7] = 0
+    for dd, pp in ((wrong_count, pB), (beyond_basis, pB), (dB, zero_pop)):
+        with pytest.raises(FciqmcError):
+            g.set_walkers(dd, pp)
+    assert same_lists(g.walkers(), before)
+    rows_q = q.iterate(25)
+    g.step(25)
+    compare_rows(g.history(25), rows_q)
+    assert same_lists(g.walkers(), q.walkers())
+    g.close()
+
+
 def test_duplicate_determinants_rejected():
     from paper_1305_6981_gb300._native import FciqmcError
     s = synth.tiny_8e8o()
