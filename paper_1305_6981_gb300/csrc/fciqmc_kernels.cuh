@@ -65,12 +65,17 @@ __device__ __forceinline__ void load_tables(const Params &P, Tables &T) {
 constexpr float kUp = 1.0f + 0x1p-18f;
 constexpr float kDown = 1.0f - 0x1p-18f;
 
-// Decision against u = (r >> 11) 2^-53 (death draw): 0 or 1 when decided, -1 otherwise.
-__device__ __forceinline__ int bernoulli_decide(float lo, float hi, unsigned long long r) {
-    if (!(hi < 1.0f)) return -1;
-    const float u_lo = (float)(unsigned)(r >> 40) * 0x1p-24f;  // exact: u_lo <= u < u_lo + 2^-24
-    if (u_lo > hi) return 0;
-    if (lo > 0.f && u_lo + 0x1p-24f <= lo) return 1;
+// n = floor(x) + [u < x - floor(x)] for u = (r >> 11) 2^-53 (death draw) and an FP64 value x >= 0 known
+// only to lie in [lo, hi]: n, or -1 when the bounds do not decide it. hi - m and max(lo, 0) - m are
+// exact (Sterbenz), and u_lo <= u < u_lo + 2^-24 exactly.
+__device__ __forceinline__ int decide_death(float lo, float hi, unsigned long long r) {
+    if (!(hi < 0x1p22f)) return -1;
+    const float l = fmaxf(lo, 0.f);
+    const float m = floorf(l);
+    if (floorf(hi) != m) return -1;
+    const float u_lo = (float)(unsigned)(r >> 40) * 0x1p-24f;
+    if (u_lo >= hi - m) return (int)m;
+    if (u_lo + 0x1p-24f <= l - m) return (int)m + 1;
     return -1;
 }
 
@@ -512,14 +517,14 @@ __device__ __forceinline__ int death_step(const Params &P, const DetView<W> &v, 
     const float acf = __uint2float_rn(ac);
     const float at_lo = fabsf(tf) - et, at_hi = fabsf(tf) + et;
     const float r_hi = at_hi * P.tau_f * acf * kUp, r_lo = at_lo * P.tau_f * acf * kDown;
-    const int dec = bernoulli_decide(r_lo, r_hi, u);
+    const int dec = decide_death(r_lo, r_hi, u);
     int nd;
     bool positive;
     if (dec == 0) {
         return c;
-    } else if (dec == 1) {
-        nd = 1;
-        positive = tf > 0.f;  // at_lo > 0: the sign of tf is the sign of r
+    } else if (dec > 0) {
+        nd = dec;
+        positive = tf > 0.f;  // r_lo > 0, so at_lo > 0: the sign of tf is the sign of r
     } else {
         atomicAdd(&P.st->exact_death, 1ull);
         double hd = *hd_ptr;
