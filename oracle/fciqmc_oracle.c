@@ -187,6 +187,10 @@ typedef struct {
     int64_t nw_prev;
     int n_since;
     int error;                 /* 0 ok, nonzero: numeric overflow */
+    /* permitted space (Sec. VI: excitations outside it are returned as null excitations) */
+    int space_flags;           /* bit 0: excitation level limit, bit 1: seniority limit */
+    int max_exc, max_sen;
+    uint64_t froz_occ[OQ_MAXW], froz_emp[OQ_MAXW];  /* spin orbitals that stay occupied / empty */
 } oq_t;
 
 /* ---------------- bit-string helpers ---------------- */
@@ -523,6 +527,54 @@ oq_t *oq_create(const double *h, const double *eri_s8, double e_core, int n_elec
     return q;
 }
 
+/* ---------------- permitted space (Sec. VI) ---------------- */
+/* A determinant lies in the permitted space when: at most max_exc of the reference's spin orbitals are
+ * empty in it (excitation level, flag bit 0); at most max_sen spatial orbitals are singly occupied
+ * (seniority, flag bit 1); every spin orbital of froz_occ is occupied and none of froz_emp is (an
+ * active space: frozen core and deleted virtuals). */
+static int in_space(const oq_t *q, const uint64_t *d)
+{
+    if (q->space_flags & 1) {
+        int exc = 0;
+        for (int k = 0; k < q->n_so; ++k)
+            if (det_bit(q, q->ref, k) && !det_bit(q, d, k)) exc++;
+        if (exc > q->max_exc) return 0;
+    }
+    if (q->space_flags & 2) {
+        int sen = 0;
+        for (int p = 0; p < q->n_orb; ++p)
+            if (det_bit(q, d, 2 * p) != det_bit(q, d, 2 * p + 1)) sen++;
+        if (sen > q->max_sen) return 0;
+    }
+    for (int k = 0; k < q->n_so; ++k) {
+        if (det_bit(q, q->froz_occ, k) && !det_bit(q, d, k)) return 0;
+        if (det_bit(q, q->froz_emp, k) && det_bit(q, d, k)) return 0;
+    }
+    return 1;
+}
+
+int oq_in_space(const oq_t *q, const uint64_t *d) { return in_space(q, d); }
+
+/* Sets the permitted space (froz_occ / froz_emp: W words or NULL). Returns -1, leaving the space
+ * unrestricted, when the reference lies outside it. */
+int oq_set_space(oq_t *q, int flags, int max_exc, int max_sen, const uint64_t *froz_occ, const uint64_t *froz_emp)
+{
+    q->space_flags = flags & 3;
+    q->max_exc = max_exc;
+    q->max_sen = max_sen;
+    memset(q->froz_occ, 0, sizeof(q->froz_occ));
+    memset(q->froz_emp, 0, sizeof(q->froz_emp));
+    if (froz_occ) memcpy(q->froz_occ, froz_occ, sizeof(uint64_t) * q->W);
+    if (froz_emp) memcpy(q->froz_emp, froz_emp, sizeof(uint64_t) * q->W);
+    if (!in_space(q, q->ref)) {
+        q->space_flags = 0;
+        memset(q->froz_occ, 0, sizeof(q->froz_occ));
+        memset(q->froz_emp, 0, sizeof(q->froz_emp));
+        return -1;
+    }
+    return 0;
+}
+
 /* ---------------- one spawning attempt and death (Eqs. 3, 4) ---------------- */
 typedef struct {
     spawn_t *s;
@@ -574,6 +626,7 @@ static int64_t attempt_one(const oq_t *q, const uint64_t *d, int32_t c, uint64_t
     }
     int kind = oq_excite_ranks(q, d, type, k1, k2, k3, child, info);
     if (kind == 0) { *is_null = 1; return 0; }
+    if (!in_space(q, child)) { *is_null = 1; return 0; }
     double hv = kind == 1 ? hij_single(q, d, (int)info[6], (int)info[8])
                           : hij_double(q, d, (int)info[6], (int)info[7], (int)info[8], (int)info[9]);
     if (hv == 0.0) return 0;
@@ -824,6 +877,8 @@ static int cmp_index(const void *x, const void *y)
 int oq_set_walkers(oq_t *q, const uint64_t *dets, const int32_t *pops, int64_t n, uint32_t iter,
                    double shift, int vary, int64_t nw_prev, int n_since)
 {
+    for (int64_t x = 0; x < n; ++x)
+        if (pops[x] != 0 && !in_space(q, dets + x * q->W)) return -3;
     int64_t *idx = malloc(sizeof(int64_t) * (n ? n : 1));
     for (int64_t x = 0; x < n; ++x) idx[x] = x;
     g_sort_base = dets; g_sort_w = q->W;

@@ -83,6 +83,10 @@ def lib():
         L.oq_attempt.restype = ctypes.c_int64
         L.oq_attempt.argtypes = [ctypes.c_void_p, u64p, ctypes.c_int32, ctypes.c_uint32, u64p,
                                  P(ctypes.c_int)]
+        L.oq_set_space.restype = ctypes.c_int
+        L.oq_set_space.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, u64p, u64p]
+        L.oq_in_space.restype = ctypes.c_int
+        L.oq_in_space.argtypes = [ctypes.c_void_p, u64p]
         _lib = L
     return _lib
 
@@ -108,7 +112,8 @@ class Oracle:
 
     def __init__(self, system, *, tau, initiator_threshold=-1, target_walkers=1 << 62,
                  shift_damping=0.05, shift_period=10, initial_shift=0.0, initial_population=10,
-                 seed=1, p_double=0.0, ms2=0, reference=None):
+                 seed=1, p_double=0.0, ms2=0, reference=None, max_excitation=None, max_seniority=None,
+                 frozen_occupied=None, frozen_empty=None):
         L = lib()
         self.system = system
         self.n_orb, self.n_elec = system.n_orb, system.n_elec
@@ -129,6 +134,14 @@ class Oracle:
                              initial_population, seed, p_double, ref)
         if not self.h:
             raise ValueError("oracle: invalid system or options")
+        if max_excitation is not None or max_seniority is not None or frozen_occupied is not None \
+                or frozen_empty is not None:
+            flags = (1 if max_excitation is not None else 0) | (2 if max_seniority is not None else 0)
+            self._fo = self._det(frozen_occupied if frozen_occupied is not None else [0, 0])
+            self._fe = self._det(frozen_empty if frozen_empty is not None else [0, 0])
+            if L.oq_set_space(self.h, flags, int(max_excitation or 0), int(max_seniority or 0),
+                              _p(self._fo, ctypes.c_uint64), _p(self._fe, ctypes.c_uint64)) != 0:
+                raise ValueError("oracle: the reference lies outside the permitted space")
 
     def __del__(self):
         if getattr(self, "h", None):
@@ -158,6 +171,9 @@ class Oracle:
 
     def fingerprint(self, d) -> int:
         return int(lib().oq_fingerprint(self.h, _p(self._det(d), ctypes.c_uint64)))
+
+    def in_space(self, d) -> bool:
+        return bool(lib().oq_in_space(self.h, _p(self._det(d), ctypes.c_uint64)))
 
     def hdiag(self, d) -> float:
         return lib().oq_hdiag(self.h, _p(self._det(d), ctypes.c_uint64))
@@ -220,6 +236,8 @@ class Oracle:
         pops = np.ascontiguousarray(pops, dtype=np.int32)
         rc = lib().oq_set_walkers(self.h, _p(dets, ctypes.c_uint64), _p(pops, ctypes.c_int32), len(pops),
                                   iteration, shift, int(vary), nw_prev, n_since)
+        if rc == -3:
+            raise ValueError("oracle: a determinant outside the permitted space in set_walkers")
         if rc != 0:
             raise ValueError("oracle: duplicate determinants in set_walkers")
 

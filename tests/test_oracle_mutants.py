@@ -32,10 +32,17 @@ MUTANTS = [
     ("rdm_half_dropped", "0.5 * cc * (double)(s1 * s2 * s3 * s4);", "cc * (double)(s1 * s2 * s3 * s4);"),
     ("rdm_spin_rule", "if ((p & 1) != (qq & 1) || (r & 1) != (s & 1)) continue;",
      "if ((p & 1) != (s & 1) || (r & 1) != (qq & 1)) continue;"),
+    ("space_excitation_off_by_one", "if (exc > q->max_exc) return 0;", "if (exc >= q->max_exc) return 0;"),
+    ("space_seniority_pairing", "if (det_bit(q, d, 2 * p) != det_bit(q, d, 2 * p + 1)) sen++;",
+     "if (det_bit(q, d, p) != det_bit(q, d, p + q->n_orb)) sen++;"),
+    ("space_frozen_inverted", "if (det_bit(q, q->froz_occ, k) && !det_bit(q, d, k)) return 0;",
+     "if (det_bit(q, q->froz_occ, k) && det_bit(q, d, k)) return 0;"),
+    ("space_check_skipped", "if (!in_space(q, child)) { *is_null = 1; return 0; }", ""),
 ]
 
 FAST_PINS = ("philox or own_log or second_quantisation or symmetry_and_spin or two_words and hamiltonian "
-             "or pdouble or normalised or eq1 or initiator_rule or on_a_subset or functional_two_words")
+             "or pdouble or normalised or eq1 or initiator_rule or on_a_subset or functional_two_words "
+             "or membership or outside_the_space or expectation_in_the_space")
 
 
 @pytest.mark.slow
@@ -54,7 +61,8 @@ def test_every_planted_mistake_is_caught():
         env = dict(os.environ, FCIQMC_ORACLE_LIB=path_so, OMP_NUM_THREADS="1")
         procs[name] = subprocess.Popen(
             [sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_pins.py"),
-             os.path.join(ROOT, "tests", "test_oracle_rdm.py"), "-x", "-q",
+             os.path.join(ROOT, "tests", "test_oracle_rdm.py"), os.path.join(ROOT, "tests", "test_oracle_space.py"),
+             "-x", "-q",
              "-p", "no:cacheprovider", "-k", FAST_PINS],
             env=env, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, cwd=ROOT)
     survivors = []
