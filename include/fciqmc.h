@@ -66,6 +66,12 @@ enum {
 
 typedef struct fciqmc_handle fciqmc_handle;
 
+/* Limits of the permitted space (fciqmc_options.space_flags). */
+enum {
+    FCIQMC_SPACE_EXCITATION = 1,   /* at most max_excitation reference spin orbitals empty */
+    FCIQMC_SPACE_SENIORITY = 2     /* at most max_seniority singly occupied spatial orbitals */
+};
+
 /* Run options. Zero-initialise and set what you need; fciqmc_default_options
  * fills the documented defaults. */
 typedef struct {
@@ -86,6 +92,15 @@ typedef struct {
     double index_load;           /* largest load factor of the determinant hash index (its capacity is
                                     the next power of two >= main_capacity / index_load); 0: 0.5.
                                     Never changes results. */
+    /* Permitted space (Sec. VI): an excitation generated outside it is a null excitation (no spawn;
+     * the generation probabilities of the others are unchanged), so truncated CI, seniority-limited
+     * and active-space calculations run unchanged otherwise. The reference and every loaded
+     * determinant must lie in the space (else FCIQMC_ERR_INVALID_ARG). Default: unrestricted. */
+    uint32_t space_flags;        /* FCIQMC_SPACE_* bits */
+    int32_t max_excitation;      /* with FCIQMC_SPACE_EXCITATION */
+    int32_t max_seniority;       /* with FCIQMC_SPACE_SENIORITY */
+    const uint64_t *frozen_occupied;  /* W words or NULL: spin orbitals every determinant keeps occupied */
+    const uint64_t *frozen_empty;     /* W words or NULL: spin orbitals no determinant occupies */
 } fciqmc_options;
 
 /* Per-iteration record. The estimators (nw_in .. num_in) describe the list at

@@ -59,7 +59,10 @@ class Options(ctypes.Structure):
                 ("target_walkers", ctypes.c_int64), ("seed", ctypes.c_uint64), ("p_double", ctypes.c_double),
                 ("main_capacity", ctypes.c_int64), ("spawn_capacity", ctypes.c_int64),
                 ("history_capacity", ctypes.c_int64), ("reference", ctypes.POINTER(ctypes.c_uint64)),
-                ("grid_blocks", ctypes.c_int32), ("index_load", ctypes.c_double)]
+                ("grid_blocks", ctypes.c_int32), ("index_load", ctypes.c_double),
+                ("space_flags", ctypes.c_uint32), ("max_excitation", ctypes.c_int32),
+                ("max_seniority", ctypes.c_int32), ("frozen_occupied", ctypes.POINTER(ctypes.c_uint64)),
+                ("frozen_empty", ctypes.POINTER(ctypes.c_uint64))]
 
 
 ROW_FIELDS = ["iteration", "shift", "nw_in", "nd_in", "c0_in", "num_in", "nw_out", "nd_out", "attempts", "nulls",

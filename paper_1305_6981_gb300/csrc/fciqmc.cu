@@ -145,7 +145,7 @@ int configure_kernels(fciqmc_handle *h) {
     int dev = 0, sms = 0, per_sm = 0;
     FQ_CUDA(cudaGetDevice(&dev));
     FQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    FQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fq::k_sweep<W>, fq::kTile, 0));
+    FQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fq::k_sweep<W, false>, fq::kTile, 0));
     h->sweep_grid = std::min(kMaxGrid, std::max(1, sms * std::max(per_sm, 1)));
     FQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fq::k_annihilate<W>, 256, h->smem_w));
     h->ann_grid = std::min(kMaxGrid, std::max(1, sms * std::max(per_sm, 1)));
@@ -163,6 +163,23 @@ int configure_kernels(fciqmc_handle *h) {
     return FCIQMC_OK;
 }
 
+// The spawning kernels, instantiated with the permitted-space test only for runs that have one.
+template <int W>
+void launch_sweep(fciqmc_handle *h, cudaStream_t s) {
+    if (h->P.space) fq::k_sweep<W, true><<<h->sweep_grid, fq::kTile, 0, s>>>(h->P);
+    else fq::k_sweep<W, false><<<h->sweep_grid, fq::kTile, 0, s>>>(h->P);
+}
+template <int W>
+void launch_heavy(fciqmc_handle *h, cudaStream_t s) {
+    if (h->P.space) fq::k_heavy<W, true><<<h->heavy_grid, fq::kTile, 0, s>>>(h->P);
+    else fq::k_heavy<W, false><<<h->heavy_grid, fq::kTile, 0, s>>>(h->P);
+}
+template <int W>
+void launch_spawning(fciqmc_handle *h, cudaStream_t s) {
+    launch_sweep<W>(h, s);
+    launch_heavy<W>(h, s);
+}
+
 template <int W>
 void enqueue_iteration(fciqmc_handle *h, cudaStream_t s) {
     const Params &P = h->P;
@@ -170,8 +187,7 @@ void enqueue_iteration(fciqmc_handle *h, cudaStream_t s) {
     fq::k_index_clear<<<h->small_grid, 256, 0, s>>>(P, 0);
     fq::k_index_fill<W><<<h->small_grid, 256, 0, s>>>(P, 0);
     fq::k_compact_finish<<<1, 32, 0, s>>>(P);
-    fq::k_sweep<W><<<h->sweep_grid, fq::kTile, 0, s>>>(P);
-    fq::k_heavy<W><<<h->heavy_grid, fq::kTile, 0, s>>>(P);
+    launch_spawning<W>(h, s);
     fq::k_annihilate<W><<<h->ann_grid, 256, h->smem_w, s>>>(P);
     fq::k_finish<<<1, 32, 0, s>>>(P);
 }
@@ -435,6 +451,21 @@ int fciqmc_create(const double *h1, const double *eri_s8, double e_core, int n_e
         if (n != n_elec) { delete h; return FCIQMC_ERR_INVALID_ARG; }
     }
     if (z.W == 1 && ref[1] != 0) { delete h; return FCIQMC_ERR_INVALID_ARG; }
+    // permitted space; the reference must lie in it
+    P.space = (int)(o.space_flags & 3u) | (o.frozen_occupied || o.frozen_empty ? 4 : 0);
+    P.max_exc = o.max_excitation;
+    P.max_sen = o.max_seniority;
+    for (int w = 0; w < z.W; ++w) {
+        P.froz_occ[w] = o.frozen_occupied ? o.frozen_occupied[w] : 0ull;
+        P.froz_emp[w] = o.frozen_empty ? o.frozen_empty[w] : 0ull;
+        if (((ref[w] & P.froz_emp[w]) | (~ref[w] & P.froz_occ[w])) != 0ull) { delete h; return FCIQMC_ERR_INVALID_ARG; }
+    }
+    if (((P.space & 1) && P.max_exc < 0) || ((P.space & 2) && P.max_sen < 0)) { delete h; return FCIQMC_ERR_INVALID_ARG; }
+    if (P.space & 2) {
+        int sen = 0;
+        for (int w = 0; w < z.W; ++w) sen += __builtin_popcountll((ref[w] ^ (ref[w] >> 1)) & 0x5555555555555555ull);
+        if (sen > P.max_sen) { delete h; return FCIQMC_ERR_INVALID_ARG; }
+    }
 
 #define FQ_TRY(call)                               \
     do {                                           \
@@ -574,8 +605,8 @@ int fciqmc_profile(fciqmc_handle *h, int32_t n_iterations, double *kernel_ms) {
                     case 1: fq::k_index_clear<<<h->small_grid, 256, 0, s>>>(P, 0); break;
                     case 2: fq::k_index_fill<1><<<h->small_grid, 256, 0, s>>>(P, 0); break;
                     case 3: fq::k_compact_finish<<<1, 32, 0, s>>>(P); break;
-                    case 4: fq::k_sweep<1><<<h->sweep_grid, fq::kTile, 0, s>>>(P); break;
-                    case 5: fq::k_heavy<1><<<h->heavy_grid, fq::kTile, 0, s>>>(P); break;
+                    case 4: launch_sweep<1>(h, s); break;
+                    case 5: launch_heavy<1>(h, s); break;
                     case 6: fq::k_annihilate<1><<<h->ann_grid, 256, h->smem_w, s>>>(P); break;
                     default: fq::k_finish<<<1, 32, 0, s>>>(P); break;
                 }
@@ -585,8 +616,8 @@ int fciqmc_profile(fciqmc_handle *h, int32_t n_iterations, double *kernel_ms) {
                     case 1: fq::k_index_clear<<<h->small_grid, 256, 0, s>>>(P, 0); break;
                     case 2: fq::k_index_fill<2><<<h->small_grid, 256, 0, s>>>(P, 0); break;
                     case 3: fq::k_compact_finish<<<1, 32, 0, s>>>(P); break;
-                    case 4: fq::k_sweep<2><<<h->sweep_grid, fq::kTile, 0, s>>>(P); break;
-                    case 5: fq::k_heavy<2><<<h->heavy_grid, fq::kTile, 0, s>>>(P); break;
+                    case 4: launch_sweep<2>(h, s); break;
+                    case 5: launch_heavy<2>(h, s); break;
                     case 6: fq::k_annihilate<2><<<h->ann_grid, 256, h->smem_w, s>>>(P); break;
                     default: fq::k_finish<<<1, 32, 0, s>>>(P); break;
                 }

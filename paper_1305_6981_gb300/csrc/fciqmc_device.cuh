@@ -82,6 +82,9 @@ struct Params {
     const float *rcpf;                // nearest float of 1 / L
     unsigned long long ref[MAXW];
     const unsigned char *ref_occ;     // n_elec ascending spin orbitals of the reference
+    // permitted space: bit 0 excitation limit, bit 1 seniority limit, bit 2 frozen spin orbitals
+    int space, max_exc, max_sen;
+    unsigned long long froz_occ[MAXW], froz_emp[MAXW];
     // main list, two buffers for compaction, two population arrays per buffer
     unsigned long long *det[2];
     double *hd[2];
@@ -206,6 +209,23 @@ __device__ __forceinline__ bool det_eq(const unsigned long long (&a)[W], const u
 #pragma unroll
     for (int w = 0; w < W; ++w) e = e && (a[w] == b[w]);
     return e;
+}
+
+// Permitted space (Sec. VI): at most max_exc reference spin orbitals empty, at most max_sen spatial
+// orbitals singly occupied (spin orbitals 2p and 2p + 1 share a word), frozen spin orbitals kept.
+template <int W>
+__device__ __forceinline__ bool in_space(const Params &P, const unsigned long long (&d)[W]) {
+    int exc = 0, sen = 0;
+    bool ok = true;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        exc += __popcll(P.ref[w] & ~d[w]);
+        sen += __popcll((d[w] ^ (d[w] >> 1)) & 0x5555555555555555ull);
+        ok = ok && (d[w] & P.froz_emp[w]) == 0ull && (~d[w] & P.froz_occ[w]) == 0ull;
+    }
+    if (P.space & 1) ok = ok && exc <= P.max_exc;
+    if (P.space & 2) ok = ok && sen <= P.max_sen;
+    return ok;
 }
 
 // ---------------------------------------------------------------------------

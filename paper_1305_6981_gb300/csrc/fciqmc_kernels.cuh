@@ -290,7 +290,7 @@ __device__ __forceinline__ void emit_spawn(const Params &P, const DetView<W> &v,
 // also realises the Bernoulli part of the spawn: given the type, t = r0 >> 11 is uniform on
 // [0, d53) for a double and on [d53, 2^53) for a single. A double is completed here; a single is
 // selected (electron i, virtual ao) and returned pending (true) for the warp to evaluate its element.
-template <int W, bool TAB>
+template <int W, bool TAB, bool SP>
 __device__ __forceinline__ bool attempt_begin(const Params &P, const Tables &T, const DetView<W> &v,
                                               const HeavyTab *tab, const float *rcpf, unsigned a, unsigned iter,
                                               unsigned long long pol, unsigned long long *cnt, AttemptOut &out,
@@ -315,6 +315,14 @@ __device__ __forceinline__ bool attempt_begin(const Params &P, const Tables &T, 
 #pragma unroll
             for (int w = 0; w < W; ++w) um[w] = ~v.d[w] & T.mask[ci * MAXW + w];
             ao = select_bit<W>(um, k2);
+        }
+        if (SP) {  // outside the permitted space: a null excitation (Sec. VI)
+            unsigned long long ch[W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) ch[w] = v.d[w];
+            flip<W>(ch, i);
+            flip<W>(ch, ao);
+            if (!in_space<W>(P, ch)) { cnt[C_NULLS]++; return false; }
         }
         i_out = i;
         a_out = ao;
@@ -359,6 +367,16 @@ __device__ __forceinline__ bool attempt_begin(const Params &P, const Tables &T, 
         for (int w = 0; w < W; ++w) bm[w] = ~v.d[w] & T.mask[cb * MAXW + w];
         clear_bit<W>(bm, ao);
         bo = select_bit<W>(bm, k3);
+    }
+    if (SP) {  // outside the permitted space: a null excitation (Sec. VI)
+        unsigned long long ch[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) ch[w] = v.d[w];
+        flip<W>(ch, i);
+        flip<W>(ch, j);
+        flip<W>(ch, ao);
+        flip<W>(ch, bo);
+        if (!in_space<W>(P, ch)) { cnt[C_NULLS]++; return false; }
     }
     const int A = min(ao, bo), B = max(ao, bo);
     const unsigned L = m_ba + m_ab;
@@ -486,7 +504,7 @@ __device__ __forceinline__ void attempt_single_end(const Params &P, const DetVie
 }
 
 // One spawning attempt per lane (active lanes only); called by all 32 lanes of a warp.
-template <int W, bool TAB>
+template <int W, bool TAB, bool SP>
 __device__ __forceinline__ AttemptOut spawn_attempt(const Params &P, const Tables &T, const DetView<W> &v,
                                                      const HeavyTab *tab, const float *rcpf, bool active, unsigned a,
                                                      unsigned iter, unsigned long long *cnt) {
@@ -496,7 +514,7 @@ __device__ __forceinline__ AttemptOut spawn_attempt(const Params &P, const Table
     unsigned mallow = 0;
     unsigned long long q = 0;
     bool pend = false;
-    if (active) pend = attempt_begin<W, TAB>(P, T, v, tab, rcpf, a, iter, pol, cnt, out, i, ao, mallow, q);
+    if (active) pend = attempt_begin<W, TAB, SP>(P, T, v, tab, rcpf, a, iter, pol, cnt, out, i, ao, mallow, q);
     float hs = 0.f, hab = 0.f;
     single_elements_warp<W>(P, &v, pend, i, ao, pol, hs, hab);
     if (pend) attempt_single_end<W>(P, v, i, ao, mallow, q, hs, hab, cnt, out);
@@ -587,7 +605,8 @@ __device__ __forceinline__ void load_rcpf(const Params &P, float *s_rcpf) {
     for (int k = threadIdx.x; k < 2 * MAXSO + 2; k += blockDim.x) s_rcpf[k] = P.rcpf[k];
 }
 
-template <int W>
+// SP: the run has a permitted space (its membership test is compiled in only then).
+template <int W, bool SP>
 __global__ void __launch_bounds__(kTile, FQ_SWEEP_MIN_BLOCKS) k_sweep(Params P) {
     DevState *st = P.st;
     if (st->status) return;
@@ -704,7 +723,7 @@ __global__ void __launch_bounds__(kTile, FQ_SWEEP_MIN_BLOCKS) k_sweep(Params P) 
                     if (s_off[mid] <= k) lo = mid; else hi = mid - 1;
                 }
             }
-            const AttemptOut ao = spawn_attempt<W, false>(P, T, s_dv[lo], nullptr, s_rcpf, act, k - s_off[lo], iter, acc);
+            const AttemptOut ao = spawn_attempt<W, false, SP>(P, T, s_dv[lo], nullptr, s_rcpf, act, k - s_off[lo], iter, acc);
             long long slot = warp_append(&st->n_merged, ao.claimed);
             if (ao.claimed && slot < P.mt_cap) P.merged[slot] = ao.pos;
         }
@@ -721,7 +740,7 @@ __global__ void __launch_bounds__(kTile, FQ_SWEEP_MIN_BLOCKS) k_sweep(Params P) 
 // Attempts of heavily populated determinants, split into chunks of kChunk attempts: each warp takes a
 // contiguous range of chunks (so it meets few determinants) and builds a determinant's tables once
 // when it reaches it.
-template <int W>
+template <int W, bool SP>
 __global__ void __launch_bounds__(kTile) k_heavy(Params P) {
     DevState *st = P.st;
     if (st->status) return;
@@ -775,7 +794,7 @@ __global__ void __launch_bounds__(kTile) k_heavy(Params P) {
         const unsigned a1 = min(a0 + (unsigned)kChunk, P.heavy_att[r]);
         for (unsigned base = a0; base < a1; base += 32) {
             const unsigned a = base + lane;
-            const AttemptOut ao = spawn_attempt<W, true>(P, T, v, &tab, s_rcpf, a < a1, a, iter, cnt);
+            const AttemptOut ao = spawn_attempt<W, true, SP>(P, T, v, &tab, s_rcpf, a < a1, a, iter, cnt);
             long long slot = warp_append(&st->n_merged, ao.claimed);
             if (ao.claimed && slot < P.mt_cap) P.merged[slot] = ao.pos;
         }
@@ -1124,15 +1143,19 @@ __global__ void k_gather(Params P) {
 }
 
 // Checks slots [0, n) of list buffer b as loaded: n_elec occupied spin orbitals, none at or above n_so,
-// population neither 0 nor INT32_MIN. A failure sets st->check_bad.
+// inside the permitted space, population neither 0 nor INT32_MIN. A failure sets st->check_bad.
 template <int W>
 __global__ void k_check_list(Params P, int b, long long n) {
     for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
         int cnt = 0;
         bool ok = true;
+        unsigned long long d[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) d[w] = P.det[b][s * W + w];
+        if (P.space && !in_space<W>(P, d)) ok = false;
 #pragma unroll
         for (int w = 0; w < W; ++w) {
-            const unsigned long long x = P.det[b][s * W + w];
+            const unsigned long long x = d[w];
             const int hi = P.n_so - 64 * w;
             if (hi < 64 && (hi <= 0 ? x != 0ull : (x >> hi) != 0ull)) ok = false;
             cnt += __popcll(x);

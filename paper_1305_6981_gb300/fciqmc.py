@@ -27,11 +27,14 @@ class Fciqmc:
 
     system: object with n_orb, n_elec, h (n_orb x n_orb), eri_s8 (packed), irrep (or None), e_core.
     Options are the fields of fciqmc_options (shift_damping, shift_period, initial_population,
-    initial_shift, target_walkers, seed, p_double, main_capacity, spawn_capacity, history_capacity).
+    initial_shift, target_walkers, seed, p_double, main_capacity, spawn_capacity, history_capacity,
+    grid_blocks, index_load). The permitted space (Sec. VI) is given by max_excitation, max_seniority
+    (None: no limit), frozen_occupied and frozen_empty (W words or None).
     """
 
     def __init__(self, system, tau: float, initiator_threshold: int = -1, *, ms2: int = 0, reference=None,
-                 device=None, stream=None, **options):
+                 device=None, stream=None, max_excitation=None, max_seniority=None, frozen_occupied=None,
+                 frozen_empty=None, **options):
         import torch
 
         self._L = L = _native.load()
@@ -40,9 +43,23 @@ class Fciqmc:
         o = Options()
         L.fciqmc_default_options(ctypes.byref(o))
         for k, v in options.items():
-            if not hasattr(o, k) or k == "reference":
+            if not hasattr(o, k) or k in ("reference", "space_flags", "max_excitation", "max_seniority",
+                                          "frozen_occupied", "frozen_empty"):
                 raise TypeError(f"unknown option {k}")
             setattr(o, k, v)
+        if max_excitation is not None:
+            o.space_flags |= 1
+            o.max_excitation = int(max_excitation)
+        if max_seniority is not None:
+            o.space_flags |= 2
+            o.max_seniority = int(max_seniority)
+        self._frozen = []
+        for name, mask in (("frozen_occupied", frozen_occupied), ("frozen_empty", frozen_empty)):
+            if mask is not None:
+                m = np.zeros(2, dtype=np.uint64)
+                m[:self.W] = np.asarray(mask, dtype=np.uint64).reshape(-1)[:self.W]
+                self._frozen.append(m)
+                setattr(o, name, _ptr(m, ctypes.c_uint64))
         self._ref = None
         if reference is not None:
             self._ref = np.zeros(2, dtype=np.uint64)
