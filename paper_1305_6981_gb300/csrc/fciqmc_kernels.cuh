@@ -741,7 +741,7 @@ __global__ void __launch_bounds__(kTile, FQ_SWEEP_MIN_BLOCKS) k_sweep(Params P) 
 // contiguous range of chunks (so it meets few determinants) and builds a determinant's tables once
 // when it reaches it.
 template <int W, bool SP>
-__global__ void __launch_bounds__(kTile) k_heavy(Params P) {
+__global__ void __launch_bounds__(kTile, 4) k_heavy(Params P) {
     DevState *st = P.st;
     if (st->status) return;
     constexpr int NW = kTile / 32;
