@@ -191,6 +191,7 @@ typedef struct {
     int space_flags;           /* bit 0: excitation level limit, bit 1: seniority limit */
     int max_exc, max_sen;
     uint64_t froz_occ[OQ_MAXW], froz_emp[OQ_MAXW];  /* spin orbitals that stay occupied / empty */
+    int hphf;                  /* walkers live on spin-coupled functions (Sec. VI C) */
 } oq_t;
 
 /* ---------------- bit-string helpers ---------------- */
@@ -527,6 +528,125 @@ oq_t *oq_create(const double *h, const double *eri_s8, double e_core, int n_elec
     return q;
 }
 
+/* ---------------- generation probability of a given target (Sec. VI A, B) ---------------- */
+/* Probability that one attempt from d generates the determinant x: the closed forms the generator
+ * realises, 0 when x is not a single or double excitation it can produce.
+ *   single i -> a (same class): P_single / (M_allow (N - delta_s))
+ *   double {i,j} -> {a,b}: P_double (M^(b|a) + M^(a|b)) / (npairs G M^(b|a) M^(a|b)), the two orders
+ *   of choosing a and b, G the number of good first virtuals of the pair. */
+double oq_gen_prob(const oq_t *q, const uint64_t *d, const uint64_t *x)
+{
+    int holes[2], parts[2], nh = 0, np = 0;
+    for (int k = 0; k < q->n_so; ++k) {
+        int s = det_bit(q, d, k), t = det_bit(q, x, k);
+        if (s && !t) { if (nh == 2) return 0.0; holes[nh++] = k; }
+        if (!s && t) { if (np == 2) return 0.0; parts[np++] = k; }
+    }
+    if (nh != np || nh == 0) return 0.0;
+    int occ[OQ_MAXSO], cnt[16];
+    int n = decode(q, d, occ);
+    unocc_counts(q, d, cnt);
+    if (nh == 1) {
+        if (class_of(q, holes[0]) != class_of(q, parts[0])) return 0.0;
+        int nok = 0;
+        for (int y = 0; y < n; ++y) if (cnt[class_of(q, occ[y])] > 0) nok++;
+        int mallow = cnt[class_of(q, holes[0])];
+        return q->p_single / (double)((int64_t)mallow * nok);
+    }
+    int i = holes[0], j = holes[1], a = parts[0], b = parts[1];
+    int si = spin_of(i), sj = spin_of(j);
+    if (spin_of(a) + spin_of(b) != si + sj) return 0.0;
+    int gij = q->irrep[spat_of(i)] ^ q->irrep[spat_of(j)];
+    if ((q->irrep[spat_of(a)] ^ q->irrep[spat_of(b)]) != gij) return 0.0;
+    if (si == sj && (spin_of(a) != si || spin_of(b) != si)) return 0.0;
+    int ngood = 0;   /* good first virtuals of the pair, as the generator counts them */
+    for (int k = 0; k < q->n_so; ++k) {
+        if (det_bit(q, d, k) || (si == sj && spin_of(k) != si)) continue;
+        int cb = class_make(gij ^ q->irrep[spat_of(k)], si + sj - spin_of(k));
+        if (cnt[cb] - (cb == class_of(q, k) ? 1 : 0) >= 1) ngood++;
+    }
+    int ca = class_of(q, a), cb = class_of(q, b);
+    int64_t m_ba = cnt[cb] - (ca == cb ? 1 : 0);
+    int64_t m_ab = cnt[ca] - (ca == cb ? 1 : 0);
+    int64_t npairs = (int64_t)n * (n - 1) / 2;
+    return (q->p_double * (double)(m_ba + m_ab)) / (double)(npairs * (int64_t)ngood * m_ba * m_ab);
+}
+
+/* ---------------- spin-coupled functions (Sec. VI C) ---------------- */
+/* For M_s = 0 the spin flip F (alpha <-> beta for every electron) maps |D> to pi(D) |Dbar>: Dbar has
+ * spin orbitals 2p and 2p + 1 exchanged, and pi(D) = (-1)^(doubly occupied spatial orbitals), since
+ * the two creation operators of a doubly occupied orbital trade places while a lone electron keeps its
+ * place among the others. F commutes with H. The functions are |D> for closed shells (Dbar = D) and
+ * (|D> + sigma pi(D) |Dbar>) / sqrt(2) for open shells, sigma = pi(reference) = (-1)^(N/2) (the sector
+ * of the closed-shell reference), stored on the smaller determinant of the pair. sigma pi(D) =
+ * (-1)^(n_open / 2) with n_open singly occupied spatial orbitals. */
+static const double SQRT2 = 0x1.6a09e667f3bcdp+0;   /* sqrt(2) rounded to nearest */
+
+static void flip_spins(const oq_t *q, const uint64_t *d, uint64_t *out)
+{
+    memset(out, 0, sizeof(uint64_t) * OQ_MAXW);
+    for (int k = 0; k < q->n_so; ++k) if (det_bit(q, d, k)) det_flip(out, k ^ 1);
+}
+static int n_open(const oq_t *q, const uint64_t *d)
+{
+    int c = 0;
+    for (int p = 0; p < q->n_orb; ++p) c += det_bit(q, d, 2 * p) != det_bit(q, d, 2 * p + 1);
+    return c;
+}
+static double pair_sign(const oq_t *q, const uint64_t *d) { return (n_open(q, d) / 2) % 2 ? -1.0 : 1.0; }
+
+/* <Phi_a|H|Phi_b> for the functions stored on a != b. With <abar|H|bbar> = pi_a pi_b <a|H|b> and
+ * <abar|H|b> = pi_a pi_b <a|H|bbar> the four determinant couplings fold into:
+ *   both open: <a|H|b> + sigma pi_b <a|H|bbar>; one closed: sqrt(2) <a|H|b>; both closed: <a|H|b>. */
+double oq_hphf_hij(const oq_t *q, const uint64_t *a, const uint64_t *b)
+{
+    uint64_t ab[OQ_MAXW], bb[OQ_MAXW];
+    flip_spins(q, a, ab);
+    flip_spins(q, b, bb);
+    int a_open = !det_eq(q, a, ab), b_open = !det_eq(q, b, bb);
+    double hab = oq_hij(q, a, b);
+    if (a_open && b_open) return hab + pair_sign(q, b) * oq_hij(q, a, bb);
+    if (a_open || b_open) return hab * SQRT2;
+    return hab;
+}
+
+/* <Phi_a|H|Phi_a> = <a|H|a> + sigma pi_a <a|H|abar> (the second term only for two open shells). */
+double oq_hphf_hdiag(const oq_t *q, const uint64_t *a)
+{
+    uint64_t ab[OQ_MAXW];
+    flip_spins(q, a, ab);
+    double v = oq_hdiag(q, a);
+    if (!det_eq(q, a, ab)) v = v + pair_sign(q, a) * oq_hij(q, a, ab);
+    return v;
+}
+
+/* H_ii (without e_core) of a stored walker: of the determinant, or of its spin-coupled function */
+static double hdiag_of(const oq_t *q, const uint64_t *d) { return q->hphf ? oq_hphf_hdiag(q, d) : oq_hdiag(q, d); }
+
+/* a determinant is stored as itself, or (spin-coupled functions) when it is the smaller of its pair */
+static int stored_form(const oq_t *q, const uint64_t *d)
+{
+    if (!q->hphf) return 1;
+    uint64_t db[OQ_MAXW];
+    flip_spins(q, d, db);
+    int na = 0;
+    for (int p = 0; p < q->n_orb; ++p) na += det_bit(q, d, 2 * p);
+    return na == q->n_alpha && det_cmp(q->W, d, db) <= 0;
+}
+
+/* Switches to spin-coupled functions; needs M_s = 0 and a closed-shell reference. */
+int oq_set_hphf(oq_t *q, int on)
+{
+    if (on) {
+        uint64_t rb[OQ_MAXW];
+        flip_spins(q, q->ref, rb);
+        if (q->n_alpha != q->n_beta || !det_eq(q, q->ref, rb)) return -1;
+    }
+    q->hphf = on ? 1 : 0;
+    for (int64_t x = 0; x < q->n; ++x) q->hd[x] = hdiag_of(q, q->det + x * q->W) - q->E0;
+    return 0;
+}
+
 /* ---------------- permitted space (Sec. VI) ---------------- */
 /* A determinant lies in the permitted space when: at most max_exc of the reference's spin orbitals are
  * empty in it (excitation level, flag bit 0); at most max_sen spatial orbitals are singly occupied
@@ -626,16 +746,31 @@ static int64_t attempt_one(const oq_t *q, const uint64_t *d, int32_t c, uint64_t
     }
     int kind = oq_excite_ranks(q, d, type, k1, k2, k3, child, info);
     if (kind == 0) { *is_null = 1; return 0; }
-    if (!in_space(q, child)) { *is_null = 1; return 0; }
-    double hv = kind == 1 ? hij_single(q, d, (int)info[6], (int)info[8])
-                          : hij_double(q, d, (int)info[6], (int)info[7], (int)info[8], (int)info[9]);
-    if (hv == 0.0) return 0;
-    /* p = tau |H| / P_gen (Eq. 3), evaluated in the fixed order
-     *   single: (|H| * (tau/P_single)) * (M_allow (N - delta_s))
-     *   double: ((|H| * (tau/P_double)) * (npairs G M^(b|a) M^(a|b))) * (1 / (M^(b|a) + M^(a|b))) */
-    double p;
-    if (kind == 1) p = (fabs(hv) * q->cs) * (double)info[5];
-    else p = ((fabs(hv) * q->cd) * (double)info[5]) * (1.0 / (double)info[4]);
+    double hv, p;
+    if (q->hphf) {
+        /* Sec. VI C: from the stored determinant only; the target function holds child and its flip,
+         * and its generation probability sums both: p = tau |H_AB| / (P(child) + P(flip)) */
+        uint64_t xb[OQ_MAXW], b[OQ_MAXW];
+        flip_spins(q, child, xb);
+        memcpy(b, det_cmp(q->W, child, xb) <= 0 ? child : xb, sizeof(uint64_t) * OQ_MAXW);
+        if (det_eq(q, b, d) || !in_space(q, b)) { *is_null = 1; return 0; }
+        hv = oq_hphf_hij(q, d, b);
+        if (hv == 0.0) return 0;
+        double g = oq_gen_prob(q, d, child);
+        if (!det_eq(q, xb, child)) g = g + oq_gen_prob(q, d, xb);
+        p = (q->tau * fabs(hv)) / g;
+        memcpy(child, b, sizeof(uint64_t) * q->W);
+    } else {
+        if (!in_space(q, child)) { *is_null = 1; return 0; }
+        hv = kind == 1 ? hij_single(q, d, (int)info[6], (int)info[8])
+                       : hij_double(q, d, (int)info[6], (int)info[7], (int)info[8], (int)info[9]);
+        if (hv == 0.0) return 0;
+        /* p = tau |H| / P_gen (Eq. 3), evaluated in the fixed order
+         *   single: (|H| * (tau/P_single)) * (M_allow (N - delta_s))
+         *   double: ((|H| * (tau/P_double)) * (npairs G M^(b|a) M^(a|b))) * (1 / (M^(b|a) + M^(a|b))) */
+        if (kind == 1) p = (fabs(hv) * q->cs) * (double)info[5];
+        else p = ((fabs(hv) * q->cd) * (double)info[5]) * (1.0 / (double)info[4]);
+    }
     /* floor(p) walkers, plus one with probability p - floor(p). The Bernoulli draw reuses the type
      * word: given the type, t = r0 >> 11 is uniform on [0, d53) (double) or [d53, 2^53) (single), so
      * with the offset s and the range n of that interval, [t - s < (p - floor p) n] has probability
@@ -691,7 +826,11 @@ void oq_estimate(const oq_t *q, int64_t *nw, int64_t *nd, int64_t *c0, double *n
         if (det_eq(q, d, q->ref)) { cz = c; continue; }
         int nx = 0;
         for (int k = 0; k < q->W; ++k) nx += __builtin_popcountll(d[k] ^ q->ref[k]);
-        if (nx == 2 || nx == 4) s = s + oq_hij(q, q->ref, d) * (double)c;
+        if (nx == 2 || nx == 4) {
+            double h0 = oq_hij(q, q->ref, d);
+            if (q->hphf && n_open(q, d) > 0) h0 = h0 * SQRT2;  /* closed reference, open function */
+            s = s + h0 * (double)c;
+        }
     }
     *nw = w; *nd = dd; *c0 = cz; *num = s;
 }
@@ -816,7 +955,7 @@ int oq_iterate(oq_t *q, int n_iter, oq_row *rows)
                         if (m->amt > 2147483647LL || m->amt < -2147483647LL) numeric = 1;
                         memcpy(nd_det + out * W, m->d, sizeof(uint64_t) * W);
                         nd_pop[out] = (int32_t)m->amt;
-                        nd_hd[out] = oq_hdiag(q, m->d) - q->E0;
+                        nd_hd[out] = hdiag_of(q, m->d) - q->E0;
                         out++;
                         row->inserted_dets++;
                     } else {
@@ -877,8 +1016,10 @@ static int cmp_index(const void *x, const void *y)
 int oq_set_walkers(oq_t *q, const uint64_t *dets, const int32_t *pops, int64_t n, uint32_t iter,
                    double shift, int vary, int64_t nw_prev, int n_since)
 {
-    for (int64_t x = 0; x < n; ++x)
+    for (int64_t x = 0; x < n; ++x) {
         if (pops[x] != 0 && !in_space(q, dets + x * q->W)) return -3;
+        if (pops[x] != 0 && !stored_form(q, dets + x * q->W)) return -4;
+    }
     int64_t *idx = malloc(sizeof(int64_t) * (n ? n : 1));
     for (int64_t x = 0; x < n; ++x) idx[x] = x;
     g_sort_base = dets; g_sort_w = q->W;
@@ -893,7 +1034,7 @@ int oq_set_walkers(oq_t *q, const uint64_t *dets, const int32_t *pops, int64_t n
         if (m > 0 && det_cmp(q->W, q->det + (m - 1) * q->W, d) == 0) { free(idx); return -1; }
         memcpy(q->det + m * q->W, d, sizeof(uint64_t) * q->W);
         q->pop[m] = pops[idx[x]];
-        q->hd[m] = oq_hdiag(q, d) - q->E0;
+        q->hd[m] = hdiag_of(q, d) - q->E0;
         m++;
     }
     free(idx);

@@ -87,6 +87,14 @@ def lib():
         L.oq_set_space.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, u64p, u64p]
         L.oq_in_space.restype = ctypes.c_int
         L.oq_in_space.argtypes = [ctypes.c_void_p, u64p]
+        L.oq_set_hphf.restype = ctypes.c_int
+        L.oq_set_hphf.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.oq_gen_prob.restype = ctypes.c_double
+        L.oq_gen_prob.argtypes = [ctypes.c_void_p, u64p, u64p]
+        L.oq_hphf_hij.restype = ctypes.c_double
+        L.oq_hphf_hij.argtypes = [ctypes.c_void_p, u64p, u64p]
+        L.oq_hphf_hdiag.restype = ctypes.c_double
+        L.oq_hphf_hdiag.argtypes = [ctypes.c_void_p, u64p]
         _lib = L
     return _lib
 
@@ -113,7 +121,7 @@ class Oracle:
     def __init__(self, system, *, tau, initiator_threshold=-1, target_walkers=1 << 62,
                  shift_damping=0.05, shift_period=10, initial_shift=0.0, initial_population=10,
                  seed=1, p_double=0.0, ms2=0, reference=None, max_excitation=None, max_seniority=None,
-                 frozen_occupied=None, frozen_empty=None):
+                 frozen_occupied=None, frozen_empty=None, hphf=False):
         L = lib()
         self.system = system
         self.n_orb, self.n_elec = system.n_orb, system.n_elec
@@ -142,6 +150,8 @@ class Oracle:
             if L.oq_set_space(self.h, flags, int(max_excitation or 0), int(max_seniority or 0),
                               _p(self._fo, ctypes.c_uint64), _p(self._fe, ctypes.c_uint64)) != 0:
                 raise ValueError("oracle: the reference lies outside the permitted space")
+        if hphf and L.oq_set_hphf(self.h, 1) != 0:
+            raise ValueError("oracle: spin-coupled functions need M_s = 0 and a closed-shell reference")
 
     def __del__(self):
         if getattr(self, "h", None):
@@ -171,6 +181,16 @@ class Oracle:
 
     def fingerprint(self, d) -> int:
         return int(lib().oq_fingerprint(self.h, _p(self._det(d), ctypes.c_uint64)))
+
+    def gen_prob(self, src, dst) -> float:
+        """Probability that one attempt from src generates the determinant dst."""
+        return lib().oq_gen_prob(self.h, _p(self._det(src), ctypes.c_uint64), _p(self._det(dst), ctypes.c_uint64))
+
+    def hphf_hij(self, a, b) -> float:
+        return lib().oq_hphf_hij(self.h, _p(self._det(a), ctypes.c_uint64), _p(self._det(b), ctypes.c_uint64))
+
+    def hphf_hdiag(self, a) -> float:
+        return lib().oq_hphf_hdiag(self.h, _p(self._det(a), ctypes.c_uint64))
 
     def in_space(self, d) -> bool:
         return bool(lib().oq_in_space(self.h, _p(self._det(d), ctypes.c_uint64)))
@@ -238,6 +258,8 @@ class Oracle:
                                   iteration, shift, int(vary), nw_prev, n_since)
         if rc == -3:
             raise ValueError("oracle: a determinant outside the permitted space in set_walkers")
+        if rc == -4:
+            raise ValueError("oracle: a determinant that is not the stored one of its spin-coupled pair")
         if rc != 0:
             raise ValueError("oracle: duplicate determinants in set_walkers")
 

@@ -38,11 +38,18 @@ MUTANTS = [
     ("space_frozen_inverted", "if (det_bit(q, q->froz_occ, k) && !det_bit(q, d, k)) return 0;",
      "if (det_bit(q, q->froz_occ, k) && det_bit(q, d, k)) return 0;"),
     ("space_check_skipped", "if (!in_space(q, child)) { *is_null = 1; return 0; }", ""),
+    ("hphf_second_primitive_dropped", "if (!det_eq(q, xb, child)) g = g + oq_gen_prob(q, d, xb);", ""),
+    ("hphf_pair_sign", "return (n_open(q, d) / 2) % 2 ? -1.0 : 1.0;", "return (n_open(q, d) / 2) % 2 ? 1.0 : -1.0;"),
+    ("hphf_sqrt2_dropped", "if (a_open || b_open) return hab * SQRT2;", "if (a_open || b_open) return hab;"),
+    ("hphf_diag_coupling_dropped", "if (!det_eq(q, a, ab)) v = v + pair_sign(q, a) * oq_hij(q, a, ab);", ""),
+    ("hphf_projected_sqrt2", "if (q->hphf && n_open(q, d) > 0) h0 = h0 * SQRT2;", ""),
+    ("gen_prob_double_orders", "return (q->p_double * (double)(m_ba + m_ab)) /", "return (q->p_double * (double)(m_ba + m_ba)) /"),
 ]
 
 FAST_PINS = ("philox or own_log or second_quantisation or symmetry_and_spin or two_words and hamiltonian "
              "or pdouble or normalised or eq1 or initiator_rule or on_a_subset or functional_two_words "
-             "or membership or outside_the_space or expectation_in_the_space")
+             "or membership or outside_the_space or expectation_in_the_space "
+             "or spin_flip or projection or probability_of_any_target or spin_coupled or numerator or stored_form")
 
 
 @pytest.mark.slow
@@ -62,6 +69,7 @@ def test_every_planted_mistake_is_caught():
         procs[name] = subprocess.Popen(
             [sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_pins.py"),
              os.path.join(ROOT, "tests", "test_oracle_rdm.py"), os.path.join(ROOT, "tests", "test_oracle_space.py"),
+             os.path.join(ROOT, "tests", "test_oracle_hphf.py"),
              "-x", "-q",
              "-p", "no:cacheprovider", "-k", FAST_PINS],
             env=env, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, cwd=ROOT)
