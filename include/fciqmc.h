@@ -101,6 +101,12 @@ typedef struct {
     int32_t max_seniority;       /* with FCIQMC_SPACE_SENIORITY */
     const uint64_t *frozen_occupied;  /* W words or NULL: spin orbitals every determinant keeps occupied */
     const uint64_t *frozen_empty;     /* W words or NULL: spin orbitals no determinant occupies */
+    /* Nonzero: walkers live on spin-coupled functions (Sec. VI C): |D> for closed shells and
+     * (|D> + sigma pi(D) |Dbar>) / sqrt(2) otherwise, Dbar the spin-flipped determinant, pi(D) =
+     * (-1)^(doubly occupied orbitals), sigma = pi(reference); each is stored on the smaller (as an
+     * unsigned number, last word most significant) of D and Dbar. Needs ms2 = 0 and a closed-shell
+     * reference (else FCIQMC_ERR_INVALID_ARG); loaded lists must hold stored determinants. */
+    int32_t hphf;
 } fciqmc_options;
 
 /* Per-iteration record. The estimators (nw_in .. num_in) describe the list at

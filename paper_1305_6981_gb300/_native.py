@@ -16,8 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfciqmc.so")
-SOURCES = ["fciqmc.cu", "fciqmc_static.cu", "fciqmc_rdm.cu"]
-DEPS = ["fciqmc.cu", "fciqmc_static.cu", "fciqmc_rdm.cu", "fciqmc_kernels.cuh", "fciqmc_device.cuh"]
+SOURCES = ["fciqmc.cu", "fciqmc_spawn_w1.cu", "fciqmc_spawn_w2.cu", "fciqmc_static.cu", "fciqmc_rdm.cu"]
+DEPS = SOURCES + ["fciqmc_kernels.cuh", "fciqmc_cycle.cuh", "fciqmc_device.cuh", "fciqmc_spawn.h", "fciqmc_spawn_impl.cuh"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
               "-Xcompiler", "-ffp-contract=off", "-fmad=false"]
@@ -43,13 +43,28 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and not _stale():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
-    tmp = LIB + f".tmp{os.getpid()}"
+    tag = f".tmp{os.getpid()}"
     extra = os.environ.get("FCIQMC_NVCC_FLAGS", "").split()  # tuning defines, e.g. -DFQ_SWEEP_MIN_BLOCKS=3
-    cmd = [nvcc(), ARCH, *NVCC_FLAGS, *extra, "-I" + INCLUDE, "-o", tmp] + [os.path.join(CSRC, s) for s in SOURCES]
-    if verbose:
-        print(" ".join(cmd))
-    subprocess.check_call(cmd)
-    os.replace(tmp, LIB)
+    compile_flags = [f for f in NVCC_FLAGS if f != "-shared"]
+    objs, procs = [], []
+    for src in SOURCES:  # one nvcc per translation unit, in parallel
+        obj = os.path.join(BUILD, os.path.splitext(src)[0] + tag + ".o")
+        cmd = [nvcc(), ARCH, *compile_flags, *extra, "-I" + INCLUDE, "-c", "-o", obj, os.path.join(CSRC, src)]
+        if verbose:
+            print(" ".join(cmd))
+        objs.append(obj)
+        procs.append((cmd, subprocess.Popen(cmd)))
+    failed = [cmd for cmd, p in procs if p.wait() != 0]
+    try:
+        if failed:
+            raise subprocess.CalledProcessError(1, failed[0])
+        tmp = LIB + tag
+        subprocess.check_call([nvcc(), ARCH, "-shared", "-o", tmp, *objs])
+        os.replace(tmp, LIB)
+    finally:
+        for obj in objs:
+            if os.path.exists(obj):
+                os.remove(obj)
     return LIB
 
 
@@ -62,7 +77,7 @@ class Options(ctypes.Structure):
                 ("grid_blocks", ctypes.c_int32), ("index_load", ctypes.c_double),
                 ("space_flags", ctypes.c_uint32), ("max_excitation", ctypes.c_int32),
                 ("max_seniority", ctypes.c_int32), ("frozen_occupied", ctypes.POINTER(ctypes.c_uint64)),
-                ("frozen_empty", ctypes.POINTER(ctypes.c_uint64))]
+                ("frozen_empty", ctypes.POINTER(ctypes.c_uint64)), ("hphf", ctypes.c_int32)]
 
 
 ROW_FIELDS = ["iteration", "shift", "nw_in", "nd_in", "c0_in", "num_in", "nw_out", "nd_out", "attempts", "nulls",

@@ -11,7 +11,8 @@
 #include <vector>
 
 #include "fciqmc.h"
-#include "fciqmc_kernels.cuh"
+#include "fciqmc_cycle.cuh"
+#include "fciqmc_spawn.h"
 
 using fq::DevState;
 using fq::Params;
@@ -145,7 +146,7 @@ int configure_kernels(fciqmc_handle *h) {
     int dev = 0, sms = 0, per_sm = 0;
     FQ_CUDA(cudaGetDevice(&dev));
     FQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    FQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fq::k_sweep<W, false>, fq::kTile, 0));
+    FQ_CUDA(W == 1 ? fq::sweep_occupancy_w1(&per_sm) : fq::sweep_occupancy_w2(&per_sm));
     h->sweep_grid = std::min(kMaxGrid, std::max(1, sms * std::max(per_sm, 1)));
     FQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fq::k_annihilate<W>, 256, h->smem_w));
     h->ann_grid = std::min(kMaxGrid, std::max(1, sms * std::max(per_sm, 1)));
@@ -164,15 +165,16 @@ int configure_kernels(fciqmc_handle *h) {
 }
 
 // The spawning kernels, instantiated with the permitted-space test only for runs that have one.
+int spawn_mode(const fciqmc_handle *h) { return (h->P.space ? 1 : 0) | (h->P.hphf ? 2 : 0); }
 template <int W>
 void launch_sweep(fciqmc_handle *h, cudaStream_t s) {
-    if (h->P.space) fq::k_sweep<W, true><<<h->sweep_grid, fq::kTile, 0, s>>>(h->P);
-    else fq::k_sweep<W, false><<<h->sweep_grid, fq::kTile, 0, s>>>(h->P);
+    if (W == 1) fq::launch_sweep_w1(spawn_mode(h), h->sweep_grid, s, h->P);
+    else fq::launch_sweep_w2(spawn_mode(h), h->sweep_grid, s, h->P);
 }
 template <int W>
 void launch_heavy(fciqmc_handle *h, cudaStream_t s) {
-    if (h->P.space) fq::k_heavy<W, true><<<h->heavy_grid, fq::kTile, 0, s>>>(h->P);
-    else fq::k_heavy<W, false><<<h->heavy_grid, fq::kTile, 0, s>>>(h->P);
+    if (W == 1) fq::launch_heavy_w1(spawn_mode(h), h->heavy_grid, s, h->P);
+    else fq::launch_heavy_w2(spawn_mode(h), h->heavy_grid, s, h->P);
 }
 template <int W>
 void launch_spawning(fciqmc_handle *h, cudaStream_t s) {
@@ -461,6 +463,12 @@ int fciqmc_create(const double *h1, const double *eri_s8, double e_core, int n_e
         if (((ref[w] & P.froz_emp[w]) | (~ref[w] & P.froz_occ[w])) != 0ull) { delete h; return FCIQMC_ERR_INVALID_ARG; }
     }
     if (((P.space & 1) && P.max_exc < 0) || ((P.space & 2) && P.max_sen < 0)) { delete h; return FCIQMC_ERR_INVALID_ARG; }
+    if (o.hphf) {  // spin-coupled functions: M_s = 0 and a closed-shell reference
+        if (ms2 != 0) { delete h; return FCIQMC_ERR_INVALID_ARG; }
+        for (int w = 0; w < z.W; ++w)
+            if (((ref[w] ^ (ref[w] >> 1)) & 0x5555555555555555ull) != 0ull) { delete h; return FCIQMC_ERR_INVALID_ARG; }
+        P.hphf = 1;
+    }
     if (P.space & 2) {
         int sen = 0;
         for (int w = 0; w < z.W; ++w) sen += __builtin_popcountll((ref[w] ^ (ref[w] >> 1)) & 0x5555555555555555ull);
@@ -519,6 +527,8 @@ int fciqmc_create(const double *h1, const double *eri_s8, double e_core, int n_e
         P.E0 = E0;
         P.cs = tau / p_single;
         P.cd = tau / p_double;
+        P.p_double_d = p_double;
+        P.p_single_d = p_single;
         P.cdn_f = (float)(P.cd * (double)z.npairs);
         P.d53_d = (double)d53;
         P.d53_f = (float)d53;

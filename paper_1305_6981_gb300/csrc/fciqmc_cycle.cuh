@@ -1,0 +1,513 @@
+// Kernels of one FCIQMC iteration after spawning (annihilation, finish, compaction) and of loading,
+// reading back and setting up a run. Included by the host translation unit only; the spawning kernels
+// are in fciqmc_kernels.cuh.
+#pragma once
+
+#include "fciqmc_kernels.cuh"
+
+namespace fq {
+
+template <int W>
+__global__ void __launch_bounds__(256) k_annihilate(Params P) {
+    extern __shared__ double s_w[];  // [2][M][M] pair terms, then M diagonal h_pp
+    __shared__ unsigned long long s_red[(256 / 32) * 4];
+    DevState *st = P.st;
+    if (st->status) return;
+    constexpr int S = Stride<W>::v;
+    const unsigned long long nm = st->n_merged;
+    const long long len = st->list_len;
+    // every block sees the same values, so either all blocks proceed or none changes anything
+    if (nm > (unsigned long long)(P.mt_cap / 4 * 3) || (long long)nm + len > P.cap ||
+        (long long)nm + len > P.idx_cap / 4 * 3) {
+        set_status(st, FCIQMC_ERR_CAPACITY);
+        return;
+    }
+    const int M = P.n_orb;
+    for (int k = threadIdx.x; k < 2 * M * M; k += blockDim.x) s_w[k] = P.wpair[k];
+    for (int k = threadIdx.x; k < M; k += blockDim.x) s_w[2 * M * M + k] = P.h[k * M + k];
+    __syncthreads();
+    const int lb = st->lb, pp = st->pp;
+    int *pop_out = P.pop[lb][pp ^ 1];
+    unsigned long long *det = P.det[lb];
+    const unsigned long long imask = (unsigned long long)P.idx_cap - 1ull;
+    unsigned long long dnw = 0, dnd = 0, aborted = 0, inserted = 0;
+
+    for (unsigned long long i0 = (unsigned long long)blockIdx.x * blockDim.x; i0 < nm;
+         i0 += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long i = i0 + threadIdx.x;
+        bool want = false;
+        unsigned long long key[W];
+        long long amt = 0;
+        unsigned long long h = 0;
+        if (i < nm) {
+            const unsigned pos = P.merged[i];
+            unsigned long long *e = P.mt + (unsigned long long)pos * S;
+#pragma unroll
+            for (int w = 0; w < W; ++w) key[w] = e[w];
+            const unsigned long long val = e[W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) e[w] = EMPTY;
+            e[W] = 0ull;
+            // payload = (#initiator spawns << 40) + signed amount
+            unsigned long long low = val & (kFlagUnit - 1ull);
+            amt = (low & (1ull << 39)) ? (long long)low - (long long)kFlagUnit : (long long)low;
+            const bool flag = ((val - (unsigned long long)amt) >> 40) != 0ull;
+            if (amt != 0) {
+                h = table_hash<W>(key, kSaltIndex) >> (64 - P.idx_bits);
+                long long slot = -1;
+                for (long long probe = 0; probe < P.idx_cap; ++probe) {
+                    const unsigned long long *x = P.idx + h * S;
+                    bool match = true, empty = true;
+#pragma unroll
+                    for (int w = 0; w < W; ++w) {
+                        unsigned long long kw = __ldcg(x + w);
+                        match = match && (kw == key[w]);
+                        empty = empty && (kw == EMPTY);
+                    }
+                    if (match) { slot = (long long)__ldcg(x + W); break; }
+                    if (empty) break;
+                    h = (h + 1ull) & imask;
+                }
+                const bool allow = P.init_thr < 0 || flag;
+                const unsigned long long aa = (unsigned long long)(amt < 0 ? -amt : amt);
+                if (slot >= 0) {
+                    const int old = pop_out[slot];
+                    if (old != 0) {
+                        long long nv = (long long)old + amt;
+                        if (nv > 2147483647LL || nv < -2147483647LL) set_status(st, FCIQMC_ERR_NUMERIC);
+                        pop_out[slot] = (int)nv;
+                        dnw += (unsigned long long)((nv < 0 ? -nv : nv) - (long long)(old < 0 ? -old : old));
+                        if (nv == 0) dnd += (unsigned long long)(-1LL);
+                    } else if (allow) {
+                        if (amt > 2147483647LL || amt < -2147483647LL) set_status(st, FCIQMC_ERR_NUMERIC);
+                        pop_out[slot] = (int)amt;
+                        dnw += aa;
+                        dnd += 1;
+                        inserted += 1;
+                    } else {
+                        aborted += aa;
+                    }
+                } else if (allow) {
+                    want = true;
+                } else {
+                    aborted += aa;
+                }
+            }
+        }
+        const long long ns = warp_append(&st->claim, want);
+        if (want) {
+            if (amt > 2147483647LL || amt < -2147483647LL) set_status(st, FCIQMC_ERR_NUMERIC);
+            double v = P.hphf ? hphf_hdiag<W>(P, key, s_w, s_w + 2 * M * M) : hdiag<W>(P, key, s_w, s_w + 2 * M * M);
+            double hdv = __dsub_rn(v, P.E0);
+#pragma unroll
+            for (int w = 0; w < W; ++w) det[ns * W + w] = key[w];
+            P.hd[lb][ns] = hdv;
+            P.hdf[lb][ns] = __double2float_rn(hdv);
+            pop_out[ns] = (int)amt;
+            // publish in the index (distinct keys only: no other thread inserts this determinant)
+            for (long long probe = 0; probe < P.idx_cap; ++probe) {
+                unsigned long long *x = P.idx + h * S;
+                bool claimed;
+                if (claim_key<W>(x, key, claimed)) {
+                    x[W] = (unsigned long long)ns;
+                    break;
+                }
+                h = (h + 1ull) & imask;
+            }
+            dnw += (unsigned long long)(amt < 0 ? -amt : amt);
+            dnd += 1;
+            inserted += 1;
+        }
+    }
+    unsigned long long accv[4] = {dnw, dnd, aborted, inserted};
+    unsigned long long *const dst[4] = {&st->d_nw, &st->d_nd, &st->cnt[C_ABORTED], &st->cnt[C_INSERTED]};
+    flush_counters<256, 4>(accv, dst, s_red);
+}
+
+// Natural logarithm from the atanh series (shift update); same operation order as the oracle's.
+__device__ double own_log(double x) {
+    const double LN2_HI = 0x1.62e42fe800000p-1;
+    const double LN2_LO = 0x1.e8e7bcd5e4f1ep-31;
+    const double SQRT2 = 0x1.6a09e667f3bcdp+0;
+    if (!(x > 0.0)) return x == 0.0 ? -CUDART_INF : CUDART_NAN;
+    if (isinf(x)) return x;
+    int e = 0;
+    if (x < 0x1.0p-1022) { x = __dmul_rn(x, 0x1.0p54); e = -54; }
+    unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    e += (int)((bits >> 52) & 0x7FFull) - 1023;
+    bits = (bits & 0x000FFFFFFFFFFFFFull) | 0x3FF0000000000000ull;
+    double m = __longlong_as_double((long long)bits);
+    if (m > SQRT2) { m = __dmul_rn(m, 0.5); e += 1; }
+    double s = __ddiv_rn(__dsub_rn(m, 1.0), __dadd_rn(m, 1.0));
+    double z = __dmul_rn(s, s);
+    double poly = __ddiv_rn(1.0, 23.0);
+    for (int k = 10; k >= 0; --k) poly = __dadd_rn(__dmul_rn(poly, z), __ddiv_rn(1.0, (double)(2 * k + 1)));
+    double t = __dmul_rn(s, poly);
+    double lnm = __dadd_rn(t, t);
+    double de = (double)e;
+    double r = __dadd_rn(lnm, __dmul_rn(de, LN2_LO));
+    return __dadd_rn(__dmul_rn(de, LN2_HI), r);
+}
+
+__global__ void k_finish(Params P) {
+    DevState *st = P.st;
+    if (threadIdx.x != 0 || st->status) return;
+    double num = 0.0;
+    for (int b = 0; b < P.sweep_grid; ++b) num = __dadd_rn(num, P.partial[b]);
+    const long long nw_in = (long long)st->nw_in, nd_in = (long long)st->nd_in;
+    const long long nw_out = nw_in + (long long)st->d_nw, nd_out = nd_in + (long long)st->d_nd;
+    fciqmc_row row;
+    row.iteration = st->iter;
+    row.shift = st->shift;
+    row.nw_in = nw_in;
+    row.nd_in = nd_in;
+    row.c0_in = st->c0_in;
+    row.num_in = num;
+    row.nw_out = nw_out;
+    row.nd_out = nd_out;
+    row.attempts = (long long)st->cnt[C_ATTEMPTS];
+    row.nulls = (long long)st->cnt[C_NULLS];
+    row.spawn_events = (long long)st->cnt[C_EVENTS];
+    row.spawned_walkers = (long long)st->cnt[C_SPAWNED];
+    row.death_walkers = (long long)st->cnt[C_DEATH];
+    row.clone_walkers = (long long)st->cnt[C_CLONE];
+    row.merged_entries = (long long)st->n_merged;
+    row.aborted_walkers = (long long)st->cnt[C_ABORTED];
+    row.inserted_dets = (long long)st->cnt[C_INSERTED];
+    row.heavy_attempts = (long long)st->cnt[C_HEAVY];
+    P.hist[st->hist_n % P.hist_cap] = row;
+    st->hist_n++;
+    // shift: S <- S - zeta/(A tau) ln(N_w(n) / N_w(n-A)) every A iterations once N_w reached the target
+    if (!st->vary) {
+        if (nw_out >= P.target) { st->vary = 1; st->nw_prev = nw_out; st->n_since = 0; }
+    } else {
+        st->n_since++;
+        if (st->n_since == P.period) {
+            double ratio = __ddiv_rn((double)nw_out, (double)st->nw_prev);
+            st->shift = __dsub_rn(st->shift, __dmul_rn(P.c_shift, own_log(ratio)));
+            st->nw_prev = nw_out;
+            st->n_since = 0;
+        }
+    }
+    const long long new_len = (long long)st->claim;
+    st->list_len = new_len;
+    st->pp ^= 1;
+    st->iter++;
+    const long long vacated = new_len - nd_out;
+    if ((vacated > 64 && vacated * 4 > new_len) || (vacated > 0 && new_len * 4 > P.cap * 3))
+        st->compact_pending = 1;
+    st->n_merged = 0;
+    st->heavy_packed = 0;
+    st->nw_in = st->nd_in = 0;
+    st->c0_in = 0;
+    st->d_nw = st->d_nd = 0;
+    for (int k = 0; k < NCNT; ++k) st->cnt[k] = 0;
+}
+
+// ---------------------------------------------------------------------------- compaction and index
+template <int W>
+__global__ void k_compact_copy(Params P) {
+    DevState *st = P.st;
+    if (!st->compact_pending || st->status) return;
+    const int lb = st->lb, pp = st->pp;
+    const long long len = st->list_len;
+    for (long long s0 = (long long)blockIdx.x * blockDim.x; s0 < len; s0 += (long long)gridDim.x * blockDim.x) {
+        const long long s = s0 + threadIdx.x;
+        int c = s < len ? P.pop[lb][pp][s] : 0;
+        const long long ns = warp_append(&st->new_len, c != 0);
+        if (c != 0) {
+#pragma unroll
+            for (int w = 0; w < W; ++w) P.det[lb ^ 1][ns * W + w] = P.det[lb][s * W + w];
+            P.hd[lb ^ 1][ns] = P.hd[lb][s];
+            P.hdf[lb ^ 1][ns] = P.hdf[lb][s];
+            P.pop[lb ^ 1][pp][ns] = c;
+        }
+    }
+}
+
+__global__ void k_index_clear(Params P, int force) {
+    DevState *st = P.st;
+    if (st->status || (!force && !st->compact_pending)) return;
+    const long long nwords = P.idx_cap * (P.idx_stride);
+    ulonglong2 *p = reinterpret_cast<ulonglong2 *>(P.idx);
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < nwords / 2; k += (long long)gridDim.x * blockDim.x)
+        p[k] = make_ulonglong2(EMPTY, EMPTY);
+}
+
+// Inserts slots [0, n) of a list buffer into the (cleared) index. force: rebuild the active list
+// (after set_walkers); otherwise the compacted list in the other buffer.
+template <int W>
+__global__ void k_index_fill(Params P, int force) {
+    DevState *st = P.st;
+    if (st->status || (!force && !st->compact_pending)) return;
+    constexpr int S = Stride<W>::v;
+    const int buf = force ? st->lb : (st->lb ^ 1);
+    const long long n = force ? st->list_len : (long long)st->new_len;
+    const unsigned long long imask = (unsigned long long)P.idx_cap - 1ull;
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
+        unsigned long long key[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) key[w] = P.det[buf][s * W + w];
+        unsigned long long h = table_hash<W>(key, kSaltIndex) >> (64 - P.idx_bits);
+        bool done = false;
+        for (long long probe = 0; probe < P.idx_cap; ++probe) {
+            unsigned long long *x = P.idx + h * S;
+            bool claimed;
+            if (claim_key<W>(x, key, claimed)) {
+                if (!claimed) set_status(st, FCIQMC_ERR_INVALID_ARG);  // duplicate determinant
+                else x[W] = (unsigned long long)s;
+                done = true;
+                break;
+            }
+            h = (h + 1ull) & imask;
+        }
+        if (!done) set_status(st, FCIQMC_ERR_CAPACITY);
+    }
+}
+
+// Empties the spawn merge table (EMPTY keys, zero payloads).
+__global__ void k_mt_clear(Params P, int W) {
+    const int S = P.idx_stride;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < P.mt_cap; e += (long long)gridDim.x * blockDim.x) {
+        for (int w = 0; w < W; ++w) P.mt[e * S + w] = EMPTY;
+        P.mt[e * S + W] = 0ull;
+    }
+}
+
+__global__ void k_compact_finish(Params P) {
+    DevState *st = P.st;
+    if (threadIdx.x != 0 || !st->compact_pending || st->status) return;
+    st->lb ^= 1;
+    st->list_len = (long long)st->new_len;
+    st->claim = st->new_len;
+    st->new_len = 0;
+    st->compact_pending = 0;
+    st->compactions++;
+}
+
+// ---------------------------------------------------------------------------- estimators, gather, setup
+template <int W>
+__global__ void __launch_bounds__(256) k_estimate(Params P) {
+    __shared__ unsigned long long s_red[16];
+    __shared__ double s_redf[8];
+    DevState *st = P.st;
+    const int lb = st->lb, pp = st->pp;
+    const long long len = st->list_len;
+    unsigned long long nw = 0, nd = 0;
+    double num = 0.0;
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < len; s += (long long)gridDim.x * blockDim.x) {
+        const int c = P.pop[lb][pp][s];
+        if (c == 0) continue;
+        unsigned long long d[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) d[w] = P.det[lb][s * W + w];
+        nw += (unsigned)(c < 0 ? -c : c);
+        nd += 1;
+        unsigned long long xd = 0;
+        int diff = 0;
+#pragma unroll
+        for (int w = 0; w < W; ++w) { xd |= d[w] ^ P.ref[w]; diff += __popcll(d[w] ^ P.ref[w]); }
+        if (xd == 0) st->est_c0 = c;
+        else if (diff == 2 || diff == 4) num = __dadd_rn(num, __dmul_rn(h0i<W>(P, d), (double)c));
+    }
+    unsigned long long accv[2] = {nw, nd};
+    unsigned long long *const dst[2] = {&st->est_nw, &st->est_nd};
+    flush_counters<256, 2>(accv, dst, s_red);
+    double bs = block_sum_f64<256>(num, s_redf);
+    if (threadIdx.x == 0) P.partial[blockIdx.x] = bs;
+}
+
+__global__ void k_estimate_finish(Params P, int nblocks) {
+    if (threadIdx.x != 0) return;
+    double num = 0.0;
+    for (int b = 0; b < nblocks; ++b) num = __dadd_rn(num, P.partial[b]);
+    P.st->est_num = num;
+}
+
+// Copies the occupied entries of the active list to the other buffer (for read-back), count in new_len.
+template <int W>
+__global__ void k_gather(Params P) {
+    DevState *st = P.st;
+    const int lb = st->lb, pp = st->pp;
+    const long long len = st->list_len;
+    for (long long s0 = (long long)blockIdx.x * blockDim.x; s0 < len; s0 += (long long)gridDim.x * blockDim.x) {
+        const long long s = s0 + threadIdx.x;
+        int c = s < len ? P.pop[lb][pp][s] : 0;
+        const long long ns = warp_append(&st->new_len, c != 0);
+        if (c != 0) {
+#pragma unroll
+            for (int w = 0; w < W; ++w) P.det[lb ^ 1][ns * W + w] = P.det[lb][s * W + w];
+            P.hd[lb ^ 1][ns] = P.hd[lb][s];
+            P.pop[lb ^ 1][pp][ns] = c;
+        }
+    }
+}
+
+// Checks slots [0, n) of list buffer b as loaded: n_elec occupied spin orbitals, none at or above n_so,
+// inside the permitted space, population neither 0 nor INT32_MIN. A failure sets st->check_bad.
+template <int W>
+__global__ void k_check_list(Params P, int b, long long n) {
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
+        int cnt = 0;
+        bool ok = true;
+        unsigned long long d[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) d[w] = P.det[b][s * W + w];
+        if (P.space && !in_space<W>(P, d)) ok = false;
+        if (P.hphf) {  // the stored (smaller) determinant of its spin-coupled pair, M_s = 0
+            unsigned long long db[W];
+            flip_spins<W>(d, db);
+            int na = 0;
+#pragma unroll
+            for (int w = 0; w < W; ++w) na += __popcll(d[w] & kEven);
+            if (det_less<W>(db, d) || 2 * na != P.n_elec) ok = false;
+        }
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            const unsigned long long x = d[w];
+            const int hi = P.n_so - 64 * w;
+            if (hi < 64 && (hi <= 0 ? x != 0ull : (x >> hi) != 0ull)) ok = false;
+            cnt += __popcll(x);
+        }
+        const int c = P.pop[b][0][s];
+        if (!ok || cnt != P.n_elec || c == 0 || c == (-2147483647 - 1)) atomicExch(&P.st->check_bad, 1);
+    }
+}
+
+// Index positions of the keys of slots [0, n) of list buffer b, into pos (-1 if absent). Lookups only:
+// entries are emptied afterwards by k_index_clear_at, so no probe chain is cut before every key is found.
+template <int W>
+__global__ void k_index_locate(Params P, int b, long long n, int *pos) {
+    constexpr int S = Stride<W>::v;
+    const unsigned long long imask = (unsigned long long)P.idx_cap - 1ull;
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
+        unsigned long long key[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) key[w] = P.det[b][s * W + w];
+        unsigned long long h = table_hash<W>(key, kSaltIndex) >> (64 - P.idx_bits);
+        int found = -1;
+        for (long long probe = 0; probe < P.idx_cap; ++probe) {
+            const unsigned long long *x = P.idx + h * S;
+            bool match = true, empty = true;
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                match = match && (x[w] == key[w]);
+                empty = empty && (x[w] == EMPTY);
+            }
+            if (match) { found = (int)h; break; }
+            if (empty) break;
+            h = (h + 1ull) & imask;
+        }
+        pos[s] = found;
+    }
+}
+
+// Empties the index entries at pos[0, n).
+__global__ void k_index_clear_at(Params P, const int *pos, long long n) {
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
+        const int h = pos[s];
+        if (h < 0) continue;
+        for (int w = 0; w < P.idx_stride; ++w) P.idx[(long long)h * P.idx_stride + w] = EMPTY;
+    }
+}
+
+// Diagonal elements of slots [0, n) of list buffer b: computed (compute != 0) or taken as given; the
+// float copy is the nearest float.
+template <int W>
+__global__ void __launch_bounds__(256) k_prepare_list(Params P, int b, long long n, int compute) {
+    extern __shared__ double s_w[];
+    const int M = P.n_orb;
+    for (int k = threadIdx.x; k < 2 * M * M; k += blockDim.x) s_w[k] = P.wpair[k];
+    for (int k = threadIdx.x; k < M; k += blockDim.x) s_w[2 * M * M + k] = P.h[k * M + k];
+    __syncthreads();
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
+        double v;
+        if (compute) {
+            unsigned long long d[W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) d[w] = P.det[b][s * W + w];
+            v = __dsub_rn(P.hphf ? hphf_hdiag<W>(P, d, s_w, s_w + 2 * M * M) : hdiag<W>(P, d, s_w, s_w + 2 * M * M),
+                          P.E0);
+            P.hd[b][s] = v;
+        } else {
+            v = P.hd[b][s];
+        }
+        P.hdf[b][s] = __double2float_rn(v);
+    }
+}
+
+// Setup tables and reference facts: float integrals, pair terms, orbital map (Philox, key
+// ("FCIQ", "MAP1"), counter (k, 0, 0, 0)), 1/L, E0 = H_00, and the reference's allowed single and
+// double excitation counts (for P_double, Sec. VI). One block.
+template <int W>
+__global__ void __launch_bounds__(256) k_setup(Params P, long long n_eri, unsigned long long *map1_out, double *wpair_out,
+                                               float *eri_f_out, double *recip_out, long long *facts, double *e0_out) {
+    const int M = P.n_orb;
+    for (long long k = threadIdx.x; k < n_eri; k += blockDim.x) eri_f_out[k] = __double2float_rn(P.eri[k]);
+    for (int k = threadIdx.x; k < P.n_so; k += blockDim.x) {
+        uint4 o = philox4x32_10(make_uint4((unsigned)k, 0u, 0u, 0u), make_uint2(0x46434951u, 0x4D415031u));
+        map1_out[k] = (unsigned long long)o.x | ((unsigned long long)o.y << 32);
+    }
+    for (int k = threadIdx.x; k < M * M; k += blockDim.x) {
+        int p = k / M, q = k % M;
+        double jpq = eri_d(P, p, p, q, q);
+        wpair_out[k] = jpq;
+        wpair_out[M * M + k] = __dsub_rn(jpq, eri_d(P, p, q, q, p));
+    }
+    for (int k = threadIdx.x; k < 2 * MAXSO + 2; k += blockDim.x) recip_out[k] = k == 0 ? 0.0 : __ddiv_rn(1.0, (double)k);
+    __syncthreads();
+    // reference excitation counts by enumeration
+    __shared__ unsigned long long s_ns, s_nd;
+    if (threadIdx.x == 0) { s_ns = 0; s_nd = 0; }
+    __syncthreads();
+    unsigned long long ref[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) ref[w] = P.ref[w];
+    const int N = P.n_elec, NS = P.n_so;
+    unsigned long long ns = 0, nd = 0;
+    for (int x = threadIdx.x; x < N; x += blockDim.x) {
+        int i = P.ref_occ[x];
+        for (int a = 0; a < NS; ++a)
+            if (!bit_of<W>(ref, a) && (a & 1) == (i & 1) && P.irrep[a >> 1] == P.irrep[i >> 1]) ns++;
+    }
+    for (int pq = threadIdx.x; pq < N * N; pq += blockDim.x) {
+        int x = pq / N, y = pq % N;
+        if (y <= x) continue;
+        int i = P.ref_occ[x], j = P.ref_occ[y];
+        int gij = P.irrep[i >> 1] ^ P.irrep[j >> 1];
+        for (int a = 0; a < NS; ++a) {
+            if (bit_of<W>(ref, a)) continue;
+            for (int b = a + 1; b < NS; ++b) {
+                if (bit_of<W>(ref, b)) continue;
+                if ((a & 1) + (b & 1) != (i & 1) + (j & 1)) continue;
+                if ((P.irrep[a >> 1] ^ P.irrep[b >> 1]) != gij) continue;
+                nd++;
+            }
+        }
+    }
+    atomicAdd(&s_ns, ns);
+    atomicAdd(&s_nd, nd);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        facts[0] = (long long)s_ns;
+        facts[1] = (long long)s_nd;
+    }
+}
+
+// E0 = H_00 of the reference (needs the pair table built by k_setup).
+template <int W>
+__global__ void k_reference_energy(Params P, double *e0_out) {
+    extern __shared__ double s_w[];
+    const int M = P.n_orb;
+    for (int k = threadIdx.x; k < 2 * M * M; k += blockDim.x) s_w[k] = P.wpair[k];
+    for (int k = threadIdx.x; k < M; k += blockDim.x) s_w[2 * M * M + k] = P.h[k * M + k];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long ref[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) ref[w] = P.ref[w];
+        *e0_out = hdiag<W>(P, ref, s_w, s_w + 2 * M * M);
+    }
+}
+
+}  // namespace fq

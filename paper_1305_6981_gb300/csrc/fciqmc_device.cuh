@@ -85,6 +85,8 @@ struct Params {
     // permitted space: bit 0 excitation limit, bit 1 seniority limit, bit 2 frozen spin orbitals
     int space, max_exc, max_sen;
     unsigned long long froz_occ[MAXW], froz_emp[MAXW];
+    int hphf;                         // walkers on spin-coupled functions (Sec. VI C)
+    double p_single_d, p_double_d;    // P_single, P_double as realised by the draw
     // main list, two buffers for compaction, two population arrays per buffer
     unsigned long long *det[2];
     double *hd[2];
@@ -314,6 +316,60 @@ __device__ double h0i(const Params &P, const unsigned long long (&d)[W]) {
     return 0.0;
 }
 
+// ---------------------------------------------------------------------------
+// spin-coupled functions (Sec. VI C). For M_s = 0 the spin flip F maps |D> to pi(D) |Dbar>, Dbar with spin
+// orbitals 2p and 2p + 1 exchanged, pi(D) = (-1)^(doubly occupied spatial orbitals); F commutes with H. A
+// function is |D> (closed shell) or (|D> + sigma pi(D) |Dbar>) / sqrt(2), sigma = pi(reference), stored
+// on the smaller of D, Dbar; sigma pi(D) = (-1)^(n_open / 2).
+constexpr double kSqrt2 = 0x1.6a09e667f3bcdp+0;  // sqrt(2) rounded to nearest
+constexpr unsigned long long kEven = 0x5555555555555555ull;
+
+template <int W>
+__device__ __forceinline__ void flip_spins(const unsigned long long (&d)[W], unsigned long long (&o)[W]) {
+#pragma unroll
+    for (int w = 0; w < W; ++w) o[w] = ((d[w] & kEven) << 1) | ((d[w] >> 1) & kEven);
+}
+template <int W>
+__device__ __forceinline__ int n_open(const unsigned long long (&d)[W]) {
+    int c = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) c += __popcll((d[w] ^ (d[w] >> 1)) & kEven);
+    return c;
+}
+template <int W>
+__device__ __forceinline__ bool det_less(const unsigned long long (&a)[W], const unsigned long long (&b)[W]) {
+    if (W == 2 && a[W - 1] != b[W - 1]) return a[W - 1] < b[W - 1];
+    return a[0] < b[0];
+}
+template <int W>
+__device__ __forceinline__ bool det_same(const unsigned long long (&a)[W], const unsigned long long (&b)[W]) {
+    bool e = true;
+#pragma unroll
+    for (int w = 0; w < W; ++w) e = e && a[w] == b[w];
+    return e;
+}
+__device__ __forceinline__ double pair_sign(int nopen) { return (nopen / 2) % 2 ? -1.0 : 1.0; }
+
+// <dst|H|src> for a single or double difference, evaluated from the source side; 0 otherwise
+// (occ: the source's ascending occupied list, for the spectator sum of a single).
+template <int W>
+__device__ double hij_any(const Params &P, const unsigned long long (&src)[W], const unsigned char *occ,
+                          const unsigned long long (&dst)[W]) {
+    unsigned long long holes[W], parts[W];
+    int nd = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        holes[w] = src[w] & ~dst[w];
+        parts[w] = dst[w] & ~src[w];
+        nd += __popcll(holes[w]);
+    }
+    if (nd == 1) return hij_single<W>(P, src, occ, select_bit<W>(holes, 0), select_bit<W>(parts, 0));
+    if (nd == 2)
+        return hij_double<W>(P, src, select_bit<W>(holes, 0), select_bit<W>(holes, 1), select_bit<W>(parts, 0),
+                             select_bit<W>(parts, 1));
+    return 0.0;
+}
+
 // Diagonal: sum_p h_pp (ascending) then, for p < q ascending, the pair term
 // (pp|qq) - delta_spin (pq|qp) added to the running sum. w: wpair table in shared memory.
 template <int W>
@@ -351,6 +407,20 @@ __device__ double hdiag(const Params &P, const unsigned long long (&d)[W], const
                 m2 = d[wb];
             }
         }
+    }
+    return v;
+}
+
+// <Phi_d|H|Phi_d> of a stored spin-coupled function: H_dd + sigma pi_d <d|H|dbar>, the second term only
+// for two open shells (d and dbar then differ by a double excitation).
+template <int W>
+__device__ double hphf_hdiag(const Params &P, const unsigned long long (&d)[W], const double *w, const double *hdiag_tab) {
+    double v = hdiag<W>(P, d, w, hdiag_tab);
+    const int no = n_open<W>(d);
+    if (no == 2) {
+        unsigned long long db[W];
+        flip_spins<W>(d, db);
+        v = __dadd_rn(v, __dmul_rn(pair_sign(no), hij_any<W>(P, d, nullptr, db)));
     }
     return v;
 }

@@ -285,12 +285,95 @@ __device__ __forceinline__ void emit_spawn(const Params &P, const DetView<W> &v,
     out.claimed = merge_insert<W>(P, child, val, out.pos);
 }
 
+// Probability that one attempt from v generates the determinant x (the closed forms the generator of
+// Sec. VI A, B realises; 0 when it cannot produce x), in the FP64 order
+//   single: P_single / (M_allow (N - delta_s)); double: (P_double (M^(b|a) + M^(a|b))) / (npairs G M^(b|a) M^(a|b)).
+template <int W>
+__device__ double gen_prob(const Params &P, const DetView<W> &v, const unsigned long long (&x)[W]) {
+    unsigned long long holes[W], parts[W];
+    int nh = 0, np = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        holes[w] = v.d[w] & ~x[w];
+        parts[w] = x[w] & ~v.d[w];
+        nh += __popcll(holes[w]);
+        np += __popcll(parts[w]);
+    }
+    if (nh != np || nh == 0 || nh > 2) return 0.0;
+    if (nh == 1) {
+        const int i = select_bit<W>(holes, 0), a = select_bit<W>(parts, 0);
+        const int ci = (int)__ldg(P.irrep + (i >> 1)) * 2 + (i & 1), ca = (int)__ldg(P.irrep + (a >> 1)) * 2 + (a & 1);
+        if (ci != ca) return 0.0;
+        return __ddiv_rn(P.p_single_d, (double)((long long)v.cnt[ci] * (long long)v.nok));
+    }
+    const int i = select_bit<W>(holes, 0), j = select_bit<W>(holes, 1);
+    const int a = select_bit<W>(parts, 0), b = select_bit<W>(parts, 1);
+    const int si = i & 1, sj = j & 1;
+    if ((a & 1) + (b & 1) != si + sj) return 0.0;
+    const int gi = __ldg(P.irrep + (i >> 1)), gj = __ldg(P.irrep + (j >> 1));
+    const int ga = __ldg(P.irrep + (a >> 1)), gb = __ldg(P.irrep + (b >> 1));
+    if ((ga ^ gb) != (gi ^ gj)) return 0.0;
+    if (si == sj && ((a & 1) != si || (b & 1) != si)) return 0.0;
+    unsigned long long gm[W];
+    const long long G = good_set<W>(P, v, si, sj, gi ^ gj, gm);
+    const int ca = ga * 2 + (a & 1), cb = gb * 2 + (b & 1);
+    const long long m_ba = (long long)v.cnt[cb] - (ca == cb ? 1 : 0);
+    const long long m_ab = (long long)v.cnt[ca] - (ca == cb ? 1 : 0);
+    return __ddiv_rn(__dmul_rn(P.p_double_d, (double)(m_ba + m_ab)), (double)((long long)P.npairs * G * m_ba * m_ab));
+}
+
+// <Phi_a|H|Phi_b> between the spin-coupled functions stored on v (a) and b != a: both open:
+// <a|H|b> + sigma pi_b <a|H|bbar>; one closed: sqrt(2) <a|H|b>; both closed: <a|H|b> (the flip symmetry folds
+// the four determinant couplings).
+template <int W>
+__device__ double hphf_hij(const Params &P, const DetView<W> &v, const unsigned long long (&b)[W]) {
+    unsigned long long ab[W], bb[W], a[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) a[w] = v.d[w];
+    flip_spins<W>(a, ab);
+    flip_spins<W>(b, bb);
+    const bool a_open = !det_same<W>(a, ab), b_open = !det_same<W>(b, bb);
+    const double hab = hij_any<W>(P, a, v.occ, b);
+    if (a_open && b_open) return __dadd_rn(hab, __dmul_rn(pair_sign(n_open<W>(b)), hij_any<W>(P, a, v.occ, bb)));
+    if (a_open || b_open) return __dmul_rn(hab, kSqrt2);
+    return hab;
+}
+
+// Completes an attempt on spin-coupled functions (Sec. VI C) that generated the determinant x from the
+// stored determinant v: the target function holds x and its flip, its generation probability is the sum
+// of theirs, p = tau |H_AB| / (P(x) + P(xbar)), the Bernoulli part from the type word as for determinants.
+template <int W, bool SP>
+__device__ void hphf_attempt_end(const Params &P, const DetView<W> &v, const unsigned long long (&x)[W],
+                                 unsigned long long t, bool single, unsigned long long *cnt, AttemptOut &out) {
+    unsigned long long xb[W], b[W];
+    flip_spins<W>(x, xb);
+    const bool fl_less = det_less<W>(xb, x);
+#pragma unroll
+    for (int w = 0; w < W; ++w) b[w] = fl_less ? xb[w] : x[w];
+    bool same = true;
+#pragma unroll
+    for (int w = 0; w < W; ++w) same = same && b[w] == v.d[w];
+    if (same || (SP && !in_space<W>(P, b))) { cnt[C_NULLS]++; return; }
+    const double hv = hphf_hij<W>(P, v, b);
+    if (hv == 0.0) return;
+    double g = gen_prob<W>(P, v, x);
+    if (!det_same<W>(xb, x)) g = __dadd_rn(g, gen_prob<W>(P, v, xb));
+    const double p = __ddiv_rn(__dmul_rn(P.tau, fabs(hv)), g);
+    const double fl = floor(p);
+    if (fl >= 2147483647.0) { set_status(P.st, FCIQMC_ERR_NUMERIC); return; }
+    const unsigned long long off = single ? P.d53 : 0ull;
+    const double range = single ? __dsub_rn(9007199254740992.0, P.d53_d) : P.d53_d;
+    const int n = (int)fl + (__ull2double_rn(t - off) < __dmul_rn(__dsub_rn(p, fl), range) ? 1 : 0);
+    if (n == 0) return;
+    emit_spawn<W>(P, v, b, n, hv > 0.0 ? 1 : -1, cnt, out);
+}
+
 // First part of attempt a from determinant v (Eq. 3 with the generator of Sec. VI). Random numbers:
 // two Philox blocks keyed by (seed, iteration), counter (a, tag 0/1, fingerprint). The type word r0
 // also realises the Bernoulli part of the spawn: given the type, t = r0 >> 11 is uniform on
 // [0, d53) for a double and on [d53, 2^53) for a single. A double is completed here; a single is
 // selected (electron i, virtual ao) and returned pending (true) for the warp to evaluate its element.
-template <int W, bool TAB, bool SP>
+template <int W, bool TAB, int MODE>
 __device__ __forceinline__ bool attempt_begin(const Params &P, const Tables &T, const DetView<W> &v,
                                               const HeavyTab *tab, const float *rcpf, unsigned a, unsigned iter,
                                               unsigned long long pol, unsigned long long *cnt, AttemptOut &out,
@@ -316,7 +399,16 @@ __device__ __forceinline__ bool attempt_begin(const Params &P, const Tables &T, 
             for (int w = 0; w < W; ++w) um[w] = ~v.d[w] & T.mask[ci * MAXW + w];
             ao = select_bit<W>(um, k2);
         }
-        if (SP) {  // outside the permitted space: a null excitation (Sec. VI)
+        if (MODE & 2) {  // spin-coupled functions: completed here in FP64
+            unsigned long long ch[W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) ch[w] = v.d[w];
+            flip<W>(ch, i);
+            flip<W>(ch, ao);
+            hphf_attempt_end<W, (MODE & 1) != 0>(P, v, ch, t, true, cnt, out);
+            return false;
+        }
+        if (MODE & 1) {  // outside the permitted space: a null excitation (Sec. VI)
             unsigned long long ch[W];
 #pragma unroll
             for (int w = 0; w < W; ++w) ch[w] = v.d[w];
@@ -368,7 +460,18 @@ __device__ __forceinline__ bool attempt_begin(const Params &P, const Tables &T, 
         clear_bit<W>(bm, ao);
         bo = select_bit<W>(bm, k3);
     }
-    if (SP) {  // outside the permitted space: a null excitation (Sec. VI)
+    if (MODE & 2) {  // spin-coupled functions: completed here in FP64
+        unsigned long long ch[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) ch[w] = v.d[w];
+        flip<W>(ch, i);
+        flip<W>(ch, j);
+        flip<W>(ch, ao);
+        flip<W>(ch, bo);
+        hphf_attempt_end<W, (MODE & 1) != 0>(P, v, ch, t, false, cnt, out);
+        return false;
+    }
+    if (MODE & 1) {  // outside the permitted space: a null excitation (Sec. VI)
         unsigned long long ch[W];
 #pragma unroll
         for (int w = 0; w < W; ++w) ch[w] = v.d[w];
@@ -504,7 +607,7 @@ __device__ __forceinline__ void attempt_single_end(const Params &P, const DetVie
 }
 
 // One spawning attempt per lane (active lanes only); called by all 32 lanes of a warp.
-template <int W, bool TAB, bool SP>
+template <int W, bool TAB, int MODE>
 __device__ __forceinline__ AttemptOut spawn_attempt(const Params &P, const Tables &T, const DetView<W> &v,
                                                      const HeavyTab *tab, const float *rcpf, bool active, unsigned a,
                                                      unsigned iter, unsigned long long *cnt) {
@@ -514,7 +617,7 @@ __device__ __forceinline__ AttemptOut spawn_attempt(const Params &P, const Table
     unsigned mallow = 0;
     unsigned long long q = 0;
     bool pend = false;
-    if (active) pend = attempt_begin<W, TAB, SP>(P, T, v, tab, rcpf, a, iter, pol, cnt, out, i, ao, mallow, q);
+    if (active) pend = attempt_begin<W, TAB, MODE>(P, T, v, tab, rcpf, a, iter, pol, cnt, out, i, ao, mallow, q);
     float hs = 0.f, hab = 0.f;
     single_elements_warp<W>(P, &v, pend, i, ao, pol, hs, hab);
     if (pend) attempt_single_end<W>(P, v, i, ao, mallow, q, hs, hab, cnt, out);
@@ -605,8 +708,9 @@ __device__ __forceinline__ void load_rcpf(const Params &P, float *s_rcpf) {
     for (int k = threadIdx.x; k < 2 * MAXSO + 2; k += blockDim.x) s_rcpf[k] = P.rcpf[k];
 }
 
-// SP: the run has a permitted space (its membership test is compiled in only then).
-template <int W, bool SP>
+// MODE bit 0: the run has a permitted space; bit 1: walkers on spin-coupled functions (the code of
+// each is compiled in only for runs that use it).
+template <int W, int MODE>
 __global__ void __launch_bounds__(kTile, FQ_SWEEP_MIN_BLOCKS) k_sweep(Params P) {
     DevState *st = P.st;
     if (st->status) return;
@@ -664,7 +768,11 @@ __global__ void __launch_bounds__(kTile, FQ_SWEEP_MIN_BLOCKS) k_sweep(Params P) 
 #pragma unroll
                 for (int w = 0; w < W; ++w) { xd |= v.d[w] ^ P.ref[w]; diff += __popcll(v.d[w] ^ P.ref[w]); }
                 if (xd == 0) st->c0_in = c;
-                else if (diff == 2 || diff == 4) num = __dadd_rn(num, __dmul_rn(h0i<W>(P, v.d), (double)c));
+                else if (diff == 2 || diff == 4) {
+                    double h0 = h0i<W>(P, v.d);
+                    if ((MODE & 2) && n_open<W>(v.d) > 0) h0 = __dmul_rn(h0, kSqrt2);  // closed reference, open function
+                    num = __dadd_rn(num, __dmul_rn(h0, (double)c));
+                }
                 const int nc = death_step<W>(P, v, hf, hd + s, S, S_f, iter, acc);
                 pop_out[s] = nc;
                 acc[NCNT + 2] += (unsigned long long)((long long)(nc < 0 ? -nc : nc) - (long long)ac);
@@ -723,7 +831,7 @@ __global__ void __launch_bounds__(kTile, FQ_SWEEP_MIN_BLOCKS) k_sweep(Params P) 
                     if (s_off[mid] <= k) lo = mid; else hi = mid - 1;
                 }
             }
-            const AttemptOut ao = spawn_attempt<W, false, SP>(P, T, s_dv[lo], nullptr, s_rcpf, act, k - s_off[lo], iter, acc);
+            const AttemptOut ao = spawn_attempt<W, false, MODE>(P, T, s_dv[lo], nullptr, s_rcpf, act, k - s_off[lo], iter, acc);
             long long slot = warp_append(&st->n_merged, ao.claimed);
             if (ao.claimed && slot < P.mt_cap) P.merged[slot] = ao.pos;
         }
@@ -740,7 +848,7 @@ __global__ void __launch_bounds__(kTile, FQ_SWEEP_MIN_BLOCKS) k_sweep(Params P) 
 // Attempts of heavily populated determinants, split into chunks of kChunk attempts: each warp takes a
 // contiguous range of chunks (so it meets few determinants) and builds a determinant's tables once
 // when it reaches it.
-template <int W, bool SP>
+template <int W, int MODE>
 __global__ void __launch_bounds__(kTile, 4) k_heavy(Params P) {
     DevState *st = P.st;
     if (st->status) return;
@@ -794,7 +902,7 @@ __global__ void __launch_bounds__(kTile, 4) k_heavy(Params P) {
         const unsigned a1 = min(a0 + (unsigned)kChunk, P.heavy_att[r]);
         for (unsigned base = a0; base < a1; base += 32) {
             const unsigned a = base + lane;
-            const AttemptOut ao = spawn_attempt<W, true, SP>(P, T, v, &tab, s_rcpf, a < a1, a, iter, cnt);
+            const AttemptOut ao = spawn_attempt<W, true, MODE>(P, T, v, &tab, s_rcpf, a < a1, a, iter, cnt);
             long long slot = warp_append(&st->n_merged, ao.claimed);
             if (ao.claimed && slot < P.mt_cap) P.merged[slot] = ao.pos;
         }
@@ -804,500 +912,6 @@ __global__ void __launch_bounds__(kTile, 4) k_heavy(Params P) {
                                            &st->cnt[5], &st->cnt[6], &st->cnt[7], &st->cnt[8], &st->cnt[9]};
     cnt[C_ATTEMPTS] = 0;  // attempts are counted by the sweep
     flush_counters<kTile, NCNT>(cnt, dst, s_red);
-}
-
-template <int W>
-__global__ void __launch_bounds__(256) k_annihilate(Params P) {
-    extern __shared__ double s_w[];  // [2][M][M] pair terms, then M diagonal h_pp
-    __shared__ unsigned long long s_red[(256 / 32) * 4];
-    DevState *st = P.st;
-    if (st->status) return;
-    constexpr int S = Stride<W>::v;
-    const unsigned long long nm = st->n_merged;
-    const long long len = st->list_len;
-    // every block sees the same values, so either all blocks proceed or none changes anything
-    if (nm > (unsigned long long)(P.mt_cap / 4 * 3) || (long long)nm + len > P.cap ||
-        (long long)nm + len > P.idx_cap / 4 * 3) {
-        set_status(st, FCIQMC_ERR_CAPACITY);
-        return;
-    }
-    const int M = P.n_orb;
-    for (int k = threadIdx.x; k < 2 * M * M; k += blockDim.x) s_w[k] = P.wpair[k];
-    for (int k = threadIdx.x; k < M; k += blockDim.x) s_w[2 * M * M + k] = P.h[k * M + k];
-    __syncthreads();
-    const int lb = st->lb, pp = st->pp;
-    int *pop_out = P.pop[lb][pp ^ 1];
-    unsigned long long *det = P.det[lb];
-    const unsigned long long imask = (unsigned long long)P.idx_cap - 1ull;
-    unsigned long long dnw = 0, dnd = 0, aborted = 0, inserted = 0;
-
-    for (unsigned long long i0 = (unsigned long long)blockIdx.x * blockDim.x; i0 < nm;
-         i0 += (unsigned long long)gridDim.x * blockDim.x) {
-        const unsigned long long i = i0 + threadIdx.x;
-        bool want = false;
-        unsigned long long key[W];
-        long long amt = 0;
-        unsigned long long h = 0;
-        if (i < nm) {
-            const unsigned pos = P.merged[i];
-            unsigned long long *e = P.mt + (unsigned long long)pos * S;
-#pragma unroll
-            for (int w = 0; w < W; ++w) key[w] = e[w];
-            const unsigned long long val = e[W];
-#pragma unroll
-            for (int w = 0; w < W; ++w) e[w] = EMPTY;
-            e[W] = 0ull;
-            // payload = (#initiator spawns << 40) + signed amount
-            unsigned long long low = val & (kFlagUnit - 1ull);
-            amt = (low & (1ull << 39)) ? (long long)low - (long long)kFlagUnit : (long long)low;
-            const bool flag = ((val - (unsigned long long)amt) >> 40) != 0ull;
-            if (amt != 0) {
-                h = table_hash<W>(key, kSaltIndex) >> (64 - P.idx_bits);
-                long long slot = -1;
-                for (long long probe = 0; probe < P.idx_cap; ++probe) {
-                    const unsigned long long *x = P.idx + h * S;
-                    bool match = true, empty = true;
-#pragma unroll
-                    for (int w = 0; w < W; ++w) {
-                        unsigned long long kw = __ldcg(x + w);
-                        match = match && (kw == key[w]);
-                        empty = empty && (kw == EMPTY);
-                    }
-                    if (match) { slot = (long long)__ldcg(x + W); break; }
-                    if (empty) break;
-                    h = (h + 1ull) & imask;
-                }
-                const bool allow = P.init_thr < 0 || flag;
-                const unsigned long long aa = (unsigned long long)(amt < 0 ? -amt : amt);
-                if (slot >= 0) {
-                    const int old = pop_out[slot];
-                    if (old != 0) {
-                        long long nv = (long long)old + amt;
-                        if (nv > 2147483647LL || nv < -2147483647LL) set_status(st, FCIQMC_ERR_NUMERIC);
-                        pop_out[slot] = (int)nv;
-                        dnw += (unsigned long long)((nv < 0 ? -nv : nv) - (long long)(old < 0 ? -old : old));
-                        if (nv == 0) dnd += (unsigned long long)(-1LL);
-                    } else if (allow) {
-                        if (amt > 2147483647LL || amt < -2147483647LL) set_status(st, FCIQMC_ERR_NUMERIC);
-                        pop_out[slot] = (int)amt;
-                        dnw += aa;
-                        dnd += 1;
-                        inserted += 1;
-                    } else {
-                        aborted += aa;
-                    }
-                } else if (allow) {
-                    want = true;
-                } else {
-                    aborted += aa;
-                }
-            }
-        }
-        const long long ns = warp_append(&st->claim, want);
-        if (want) {
-            if (amt > 2147483647LL || amt < -2147483647LL) set_status(st, FCIQMC_ERR_NUMERIC);
-            double v = hdiag<W>(P, key, s_w, s_w + 2 * M * M);
-            double hdv = __dsub_rn(v, P.E0);
-#pragma unroll
-            for (int w = 0; w < W; ++w) det[ns * W + w] = key[w];
-            P.hd[lb][ns] = hdv;
-            P.hdf[lb][ns] = __double2float_rn(hdv);
-            pop_out[ns] = (int)amt;
-            // publish in the index (distinct keys only: no other thread inserts this determinant)
-            for (long long probe = 0; probe < P.idx_cap; ++probe) {
-                unsigned long long *x = P.idx + h * S;
-                bool claimed;
-                if (claim_key<W>(x, key, claimed)) {
-                    x[W] = (unsigned long long)ns;
-                    break;
-                }
-                h = (h + 1ull) & imask;
-            }
-            dnw += (unsigned long long)(amt < 0 ? -amt : amt);
-            dnd += 1;
-            inserted += 1;
-        }
-    }
-    unsigned long long accv[4] = {dnw, dnd, aborted, inserted};
-    unsigned long long *const dst[4] = {&st->d_nw, &st->d_nd, &st->cnt[C_ABORTED], &st->cnt[C_INSERTED]};
-    flush_counters<256, 4>(accv, dst, s_red);
-}
-
-// Natural logarithm from the atanh series (shift update); same operation order as the oracle's.
-__device__ double own_log(double x) {
-    const double LN2_HI = 0x1.62e42fe800000p-1;
-    const double LN2_LO = 0x1.e8e7bcd5e4f1ep-31;
-    const double SQRT2 = 0x1.6a09e667f3bcdp+0;
-    if (!(x > 0.0)) return x == 0.0 ? -CUDART_INF : CUDART_NAN;
-    if (isinf(x)) return x;
-    int e = 0;
-    if (x < 0x1.0p-1022) { x = __dmul_rn(x, 0x1.0p54); e = -54; }
-    unsigned long long bits = (unsigned long long)__double_as_longlong(x);
-    e += (int)((bits >> 52) & 0x7FFull) - 1023;
-    bits = (bits & 0x000FFFFFFFFFFFFFull) | 0x3FF0000000000000ull;
-    double m = __longlong_as_double((long long)bits);
-    if (m > SQRT2) { m = __dmul_rn(m, 0.5); e += 1; }
-    double s = __ddiv_rn(__dsub_rn(m, 1.0), __dadd_rn(m, 1.0));
-    double z = __dmul_rn(s, s);
-    double poly = __ddiv_rn(1.0, 23.0);
-    for (int k = 10; k >= 0; --k) poly = __dadd_rn(__dmul_rn(poly, z), __ddiv_rn(1.0, (double)(2 * k + 1)));
-    double t = __dmul_rn(s, poly);
-    double lnm = __dadd_rn(t, t);
-    double de = (double)e;
-    double r = __dadd_rn(lnm, __dmul_rn(de, LN2_LO));
-    return __dadd_rn(__dmul_rn(de, LN2_HI), r);
-}
-
-__global__ void k_finish(Params P) {
-    DevState *st = P.st;
-    if (threadIdx.x != 0 || st->status) return;
-    double num = 0.0;
-    for (int b = 0; b < P.sweep_grid; ++b) num = __dadd_rn(num, P.partial[b]);
-    const long long nw_in = (long long)st->nw_in, nd_in = (long long)st->nd_in;
-    const long long nw_out = nw_in + (long long)st->d_nw, nd_out = nd_in + (long long)st->d_nd;
-    fciqmc_row row;
-    row.iteration = st->iter;
-    row.shift = st->shift;
-    row.nw_in = nw_in;
-    row.nd_in = nd_in;
-    row.c0_in = st->c0_in;
-    row.num_in = num;
-    row.nw_out = nw_out;
-    row.nd_out = nd_out;
-    row.attempts = (long long)st->cnt[C_ATTEMPTS];
-    row.nulls = (long long)st->cnt[C_NULLS];
-    row.spawn_events = (long long)st->cnt[C_EVENTS];
-    row.spawned_walkers = (long long)st->cnt[C_SPAWNED];
-    row.death_walkers = (long long)st->cnt[C_DEATH];
-    row.clone_walkers = (long long)st->cnt[C_CLONE];
-    row.merged_entries = (long long)st->n_merged;
-    row.aborted_walkers = (long long)st->cnt[C_ABORTED];
-    row.inserted_dets = (long long)st->cnt[C_INSERTED];
-    row.heavy_attempts = (long long)st->cnt[C_HEAVY];
-    P.hist[st->hist_n % P.hist_cap] = row;
-    st->hist_n++;
-    // shift: S <- S - zeta/(A tau) ln(N_w(n) / N_w(n-A)) every A iterations once N_w reached the target
-    if (!st->vary) {
-        if (nw_out >= P.target) { st->vary = 1; st->nw_prev = nw_out; st->n_since = 0; }
-    } else {
-        st->n_since++;
-        if (st->n_since == P.period) {
-            double ratio = __ddiv_rn((double)nw_out, (double)st->nw_prev);
-            st->shift = __dsub_rn(st->shift, __dmul_rn(P.c_shift, own_log(ratio)));
-            st->nw_prev = nw_out;
-            st->n_since = 0;
-        }
-    }
-    const long long new_len = (long long)st->claim;
-    st->list_len = new_len;
-    st->pp ^= 1;
-    st->iter++;
-    const long long vacated = new_len - nd_out;
-    if ((vacated > 64 && vacated * 4 > new_len) || (vacated > 0 && new_len * 4 > P.cap * 3))
-        st->compact_pending = 1;
-    st->n_merged = 0;
-    st->heavy_packed = 0;
-    st->nw_in = st->nd_in = 0;
-    st->c0_in = 0;
-    st->d_nw = st->d_nd = 0;
-    for (int k = 0; k < NCNT; ++k) st->cnt[k] = 0;
-}
-
-// ---------------------------------------------------------------------------- compaction and index
-template <int W>
-__global__ void k_compact_copy(Params P) {
-    DevState *st = P.st;
-    if (!st->compact_pending || st->status) return;
-    const int lb = st->lb, pp = st->pp;
-    const long long len = st->list_len;
-    for (long long s0 = (long long)blockIdx.x * blockDim.x; s0 < len; s0 += (long long)gridDim.x * blockDim.x) {
-        const long long s = s0 + threadIdx.x;
-        int c = s < len ? P.pop[lb][pp][s] : 0;
-        const long long ns = warp_append(&st->new_len, c != 0);
-        if (c != 0) {
-#pragma unroll
-            for (int w = 0; w < W; ++w) P.det[lb ^ 1][ns * W + w] = P.det[lb][s * W + w];
-            P.hd[lb ^ 1][ns] = P.hd[lb][s];
-            P.hdf[lb ^ 1][ns] = P.hdf[lb][s];
-            P.pop[lb ^ 1][pp][ns] = c;
-        }
-    }
-}
-
-__global__ void k_index_clear(Params P, int force) {
-    DevState *st = P.st;
-    if (st->status || (!force && !st->compact_pending)) return;
-    const long long nwords = P.idx_cap * (P.idx_stride);
-    ulonglong2 *p = reinterpret_cast<ulonglong2 *>(P.idx);
-    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < nwords / 2; k += (long long)gridDim.x * blockDim.x)
-        p[k] = make_ulonglong2(EMPTY, EMPTY);
-}
-
-// Inserts slots [0, n) of a list buffer into the (cleared) index. force: rebuild the active list
-// (after set_walkers); otherwise the compacted list in the other buffer.
-template <int W>
-__global__ void k_index_fill(Params P, int force) {
-    DevState *st = P.st;
-    if (st->status || (!force && !st->compact_pending)) return;
-    constexpr int S = Stride<W>::v;
-    const int buf = force ? st->lb : (st->lb ^ 1);
-    const long long n = force ? st->list_len : (long long)st->new_len;
-    const unsigned long long imask = (unsigned long long)P.idx_cap - 1ull;
-    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
-        unsigned long long key[W];
-#pragma unroll
-        for (int w = 0; w < W; ++w) key[w] = P.det[buf][s * W + w];
-        unsigned long long h = table_hash<W>(key, kSaltIndex) >> (64 - P.idx_bits);
-        bool done = false;
-        for (long long probe = 0; probe < P.idx_cap; ++probe) {
-            unsigned long long *x = P.idx + h * S;
-            bool claimed;
-            if (claim_key<W>(x, key, claimed)) {
-                if (!claimed) set_status(st, FCIQMC_ERR_INVALID_ARG);  // duplicate determinant
-                else x[W] = (unsigned long long)s;
-                done = true;
-                break;
-            }
-            h = (h + 1ull) & imask;
-        }
-        if (!done) set_status(st, FCIQMC_ERR_CAPACITY);
-    }
-}
-
-// Empties the spawn merge table (EMPTY keys, zero payloads).
-__global__ void k_mt_clear(Params P, int W) {
-    const int S = P.idx_stride;
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < P.mt_cap; e += (long long)gridDim.x * blockDim.x) {
-        for (int w = 0; w < W; ++w) P.mt[e * S + w] = EMPTY;
-        P.mt[e * S + W] = 0ull;
-    }
-}
-
-__global__ void k_compact_finish(Params P) {
-    DevState *st = P.st;
-    if (threadIdx.x != 0 || !st->compact_pending || st->status) return;
-    st->lb ^= 1;
-    st->list_len = (long long)st->new_len;
-    st->claim = st->new_len;
-    st->new_len = 0;
-    st->compact_pending = 0;
-    st->compactions++;
-}
-
-// ---------------------------------------------------------------------------- estimators, gather, setup
-template <int W>
-__global__ void __launch_bounds__(256) k_estimate(Params P) {
-    __shared__ unsigned long long s_red[16];
-    __shared__ double s_redf[8];
-    DevState *st = P.st;
-    const int lb = st->lb, pp = st->pp;
-    const long long len = st->list_len;
-    unsigned long long nw = 0, nd = 0;
-    double num = 0.0;
-    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < len; s += (long long)gridDim.x * blockDim.x) {
-        const int c = P.pop[lb][pp][s];
-        if (c == 0) continue;
-        unsigned long long d[W];
-#pragma unroll
-        for (int w = 0; w < W; ++w) d[w] = P.det[lb][s * W + w];
-        nw += (unsigned)(c < 0 ? -c : c);
-        nd += 1;
-        unsigned long long xd = 0;
-        int diff = 0;
-#pragma unroll
-        for (int w = 0; w < W; ++w) { xd |= d[w] ^ P.ref[w]; diff += __popcll(d[w] ^ P.ref[w]); }
-        if (xd == 0) st->est_c0 = c;
-        else if (diff == 2 || diff == 4) num = __dadd_rn(num, __dmul_rn(h0i<W>(P, d), (double)c));
-    }
-    unsigned long long accv[2] = {nw, nd};
-    unsigned long long *const dst[2] = {&st->est_nw, &st->est_nd};
-    flush_counters<256, 2>(accv, dst, s_red);
-    double bs = block_sum_f64<256>(num, s_redf);
-    if (threadIdx.x == 0) P.partial[blockIdx.x] = bs;
-}
-
-__global__ void k_estimate_finish(Params P, int nblocks) {
-    if (threadIdx.x != 0) return;
-    double num = 0.0;
-    for (int b = 0; b < nblocks; ++b) num = __dadd_rn(num, P.partial[b]);
-    P.st->est_num = num;
-}
-
-// Copies the occupied entries of the active list to the other buffer (for read-back), count in new_len.
-template <int W>
-__global__ void k_gather(Params P) {
-    DevState *st = P.st;
-    const int lb = st->lb, pp = st->pp;
-    const long long len = st->list_len;
-    for (long long s0 = (long long)blockIdx.x * blockDim.x; s0 < len; s0 += (long long)gridDim.x * blockDim.x) {
-        const long long s = s0 + threadIdx.x;
-        int c = s < len ? P.pop[lb][pp][s] : 0;
-        const long long ns = warp_append(&st->new_len, c != 0);
-        if (c != 0) {
-#pragma unroll
-            for (int w = 0; w < W; ++w) P.det[lb ^ 1][ns * W + w] = P.det[lb][s * W + w];
-            P.hd[lb ^ 1][ns] = P.hd[lb][s];
-            P.pop[lb ^ 1][pp][ns] = c;
-        }
-    }
-}
-
-// Checks slots [0, n) of list buffer b as loaded: n_elec occupied spin orbitals, none at or above n_so,
-// inside the permitted space, population neither 0 nor INT32_MIN. A failure sets st->check_bad.
-template <int W>
-__global__ void k_check_list(Params P, int b, long long n) {
-    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
-        int cnt = 0;
-        bool ok = true;
-        unsigned long long d[W];
-#pragma unroll
-        for (int w = 0; w < W; ++w) d[w] = P.det[b][s * W + w];
-        if (P.space && !in_space<W>(P, d)) ok = false;
-#pragma unroll
-        for (int w = 0; w < W; ++w) {
-            const unsigned long long x = d[w];
-            const int hi = P.n_so - 64 * w;
-            if (hi < 64 && (hi <= 0 ? x != 0ull : (x >> hi) != 0ull)) ok = false;
-            cnt += __popcll(x);
-        }
-        const int c = P.pop[b][0][s];
-        if (!ok || cnt != P.n_elec || c == 0 || c == (-2147483647 - 1)) atomicExch(&P.st->check_bad, 1);
-    }
-}
-
-// Index positions of the keys of slots [0, n) of list buffer b, into pos (-1 if absent). Lookups only:
-// entries are emptied afterwards by k_index_clear_at, so no probe chain is cut before every key is found.
-template <int W>
-__global__ void k_index_locate(Params P, int b, long long n, int *pos) {
-    constexpr int S = Stride<W>::v;
-    const unsigned long long imask = (unsigned long long)P.idx_cap - 1ull;
-    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
-        unsigned long long key[W];
-#pragma unroll
-        for (int w = 0; w < W; ++w) key[w] = P.det[b][s * W + w];
-        unsigned long long h = table_hash<W>(key, kSaltIndex) >> (64 - P.idx_bits);
-        int found = -1;
-        for (long long probe = 0; probe < P.idx_cap; ++probe) {
-            const unsigned long long *x = P.idx + h * S;
-            bool match = true, empty = true;
-#pragma unroll
-            for (int w = 0; w < W; ++w) {
-                match = match && (x[w] == key[w]);
-                empty = empty && (x[w] == EMPTY);
-            }
-            if (match) { found = (int)h; break; }
-            if (empty) break;
-            h = (h + 1ull) & imask;
-        }
-        pos[s] = found;
-    }
-}
-
-// Empties the index entries at pos[0, n).
-__global__ void k_index_clear_at(Params P, const int *pos, long long n) {
-    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
-        const int h = pos[s];
-        if (h < 0) continue;
-        for (int w = 0; w < P.idx_stride; ++w) P.idx[(long long)h * P.idx_stride + w] = EMPTY;
-    }
-}
-
-// Diagonal elements of slots [0, n) of list buffer b: computed (compute != 0) or taken as given; the
-// float copy is the nearest float.
-template <int W>
-__global__ void __launch_bounds__(256) k_prepare_list(Params P, int b, long long n, int compute) {
-    extern __shared__ double s_w[];
-    const int M = P.n_orb;
-    for (int k = threadIdx.x; k < 2 * M * M; k += blockDim.x) s_w[k] = P.wpair[k];
-    for (int k = threadIdx.x; k < M; k += blockDim.x) s_w[2 * M * M + k] = P.h[k * M + k];
-    __syncthreads();
-    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
-        double v;
-        if (compute) {
-            unsigned long long d[W];
-#pragma unroll
-            for (int w = 0; w < W; ++w) d[w] = P.det[b][s * W + w];
-            v = __dsub_rn(hdiag<W>(P, d, s_w, s_w + 2 * M * M), P.E0);
-            P.hd[b][s] = v;
-        } else {
-            v = P.hd[b][s];
-        }
-        P.hdf[b][s] = __double2float_rn(v);
-    }
-}
-
-// Setup tables and reference facts: float integrals, pair terms, orbital map (Philox, key
-// ("FCIQ", "MAP1"), counter (k, 0, 0, 0)), 1/L, E0 = H_00, and the reference's allowed single and
-// double excitation counts (for P_double, Sec. VI). One block.
-template <int W>
-__global__ void __launch_bounds__(256) k_setup(Params P, long long n_eri, unsigned long long *map1_out, double *wpair_out,
-                                               float *eri_f_out, double *recip_out, long long *facts, double *e0_out) {
-    const int M = P.n_orb;
-    for (long long k = threadIdx.x; k < n_eri; k += blockDim.x) eri_f_out[k] = __double2float_rn(P.eri[k]);
-    for (int k = threadIdx.x; k < P.n_so; k += blockDim.x) {
-        uint4 o = philox4x32_10(make_uint4((unsigned)k, 0u, 0u, 0u), make_uint2(0x46434951u, 0x4D415031u));
-        map1_out[k] = (unsigned long long)o.x | ((unsigned long long)o.y << 32);
-    }
-    for (int k = threadIdx.x; k < M * M; k += blockDim.x) {
-        int p = k / M, q = k % M;
-        double jpq = eri_d(P, p, p, q, q);
-        wpair_out[k] = jpq;
-        wpair_out[M * M + k] = __dsub_rn(jpq, eri_d(P, p, q, q, p));
-    }
-    for (int k = threadIdx.x; k < 2 * MAXSO + 2; k += blockDim.x) recip_out[k] = k == 0 ? 0.0 : __ddiv_rn(1.0, (double)k);
-    __syncthreads();
-    // reference excitation counts by enumeration
-    __shared__ unsigned long long s_ns, s_nd;
-    if (threadIdx.x == 0) { s_ns = 0; s_nd = 0; }
-    __syncthreads();
-    unsigned long long ref[W];
-#pragma unroll
-    for (int w = 0; w < W; ++w) ref[w] = P.ref[w];
-    const int N = P.n_elec, NS = P.n_so;
-    unsigned long long ns = 0, nd = 0;
-    for (int x = threadIdx.x; x < N; x += blockDim.x) {
-        int i = P.ref_occ[x];
-        for (int a = 0; a < NS; ++a)
-            if (!bit_of<W>(ref, a) && (a & 1) == (i & 1) && P.irrep[a >> 1] == P.irrep[i >> 1]) ns++;
-    }
-    for (int pq = threadIdx.x; pq < N * N; pq += blockDim.x) {
-        int x = pq / N, y = pq % N;
-        if (y <= x) continue;
-        int i = P.ref_occ[x], j = P.ref_occ[y];
-        int gij = P.irrep[i >> 1] ^ P.irrep[j >> 1];
-        for (int a = 0; a < NS; ++a) {
-            if (bit_of<W>(ref, a)) continue;
-            for (int b = a + 1; b < NS; ++b) {
-                if (bit_of<W>(ref, b)) continue;
-                if ((a & 1) + (b & 1) != (i & 1) + (j & 1)) continue;
-                if ((P.irrep[a >> 1] ^ P.irrep[b >> 1]) != gij) continue;
-                nd++;
-            }
-        }
-    }
-    atomicAdd(&s_ns, ns);
-    atomicAdd(&s_nd, nd);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        facts[0] = (long long)s_ns;
-        facts[1] = (long long)s_nd;
-    }
-}
-
-// E0 = H_00 of the reference (needs the pair table built by k_setup).
-template <int W>
-__global__ void k_reference_energy(Params P, double *e0_out) {
-    extern __shared__ double s_w[];
-    const int M = P.n_orb;
-    for (int k = threadIdx.x; k < 2 * M * M; k += blockDim.x) s_w[k] = P.wpair[k];
-    for (int k = threadIdx.x; k < M; k += blockDim.x) s_w[2 * M * M + k] = P.h[k * M + k];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long ref[W];
-#pragma unroll
-        for (int w = 0; w < W; ++w) ref[w] = P.ref[w];
-        *e0_out = hdiag<W>(P, ref, s_w, s_w + 2 * M * M);
-    }
 }
 
 }  // namespace fq

@@ -1,0 +1,12 @@
+// Spawning kernels for one-word determinants (up to 32 spatial orbitals).
+#include "fciqmc_spawn_impl.cuh"
+
+namespace fq {
+
+void launch_sweep_w1(int mode, int grid, cudaStream_t s, const Params &P) { launch_sweep_impl<1>(mode, grid, s, P); }
+void launch_heavy_w1(int mode, int grid, cudaStream_t s, const Params &P) { launch_heavy_impl<1>(mode, grid, s, P); }
+cudaError_t sweep_occupancy_w1(int *blocks_per_sm) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_sweep<1, 0>, kTile, 0);
+}
+
+}  // namespace fq

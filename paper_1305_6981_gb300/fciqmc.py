@@ -29,12 +29,13 @@ class Fciqmc:
     Options are the fields of fciqmc_options (shift_damping, shift_period, initial_population,
     initial_shift, target_walkers, seed, p_double, main_capacity, spawn_capacity, history_capacity,
     grid_blocks, index_load). The permitted space (Sec. VI) is given by max_excitation, max_seniority
-    (None: no limit), frozen_occupied and frozen_empty (W words or None).
+    (None: no limit), frozen_occupied and frozen_empty (W words or None); hphf=True puts the walkers
+    on spin-coupled functions (Sec. VI C).
     """
 
     def __init__(self, system, tau: float, initiator_threshold: int = -1, *, ms2: int = 0, reference=None,
                  device=None, stream=None, max_excitation=None, max_seniority=None, frozen_occupied=None,
-                 frozen_empty=None, **options):
+                 frozen_empty=None, hphf=False, **options):
         import torch
 
         self._L = L = _native.load()
@@ -44,9 +45,10 @@ class Fciqmc:
         L.fciqmc_default_options(ctypes.byref(o))
         for k, v in options.items():
             if not hasattr(o, k) or k in ("reference", "space_flags", "max_excitation", "max_seniority",
-                                          "frozen_occupied", "frozen_empty"):
+                                          "frozen_occupied", "frozen_empty", "hphf"):
                 raise TypeError(f"unknown option {k}")
             setattr(o, k, v)
+        o.hphf = 1 if hphf else 0
         if max_excitation is not None:
             o.space_flags |= 1
             o.max_excitation = int(max_excitation)
