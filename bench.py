@@ -60,6 +60,12 @@ WORKLOADS = {
                        space=dict(frozen_occupied=[(1 << 8) - 1, 0], frozen_empty=[0, ((1 << 32) - 1) << 24]),
                        desc="24e/60o active space CAS(16e,40o): spatial orbitals 0..3 frozen doubly occupied, "
                             "44..59 deleted (Sec. VI null excitations), initiator 3, tau 0.001, 1e8 target walkers"),
+    "24e60o-hphf": dict(system=synth.large_24e60o, tau=0.002, thr=3, target=50_000_000, main_capacity=100_000_000,
+                        spawn_capacity=1 << 26, initial_population=20_000, initial_shift=3.0, max_growth=40_000,
+                        equilibrate=50, space=dict(hphf=True),
+                        desc="24e/60o on spin-coupled functions (Sec. VI C: half the space, so half the walkers "
+                             "and twice the time step of the determinant run), initiator 3, tau 0.002, "
+                             "5e7 target walkers"),
     "12e24o": dict(system=synth.init_12e24o, tau=0.005, thr=3, target=1_000_000, main_capacity=4_000_000,
                    spawn_capacity=1 << 22, initial_population=2_000, initial_shift=1.0, max_growth=20_000,
                    equilibrate=50, desc="12e/24o (W=1), 8 irreps, initiator 3, tau 0.005, 1e6 target walkers"),
