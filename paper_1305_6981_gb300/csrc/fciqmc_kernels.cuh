@@ -339,12 +339,52 @@ __device__ double hphf_hij(const Params &P, const DetView<W> &v, const unsigned 
     return hab;
 }
 
+// Float bounds of the two quantities of a spin-coupled double-excitation attempt (the same forms as in
+// gen_prob and hij_double): the generation probability of a double excitation y of v (0 if the generator
+// cannot produce it), within 4 roundings of float, and the matrix element <y|H|v> for a double
+// difference, |H - value| <= err.
+template <int W>
+__device__ float gen_prob_double_f(const Params &P, const DetView<W> &v, const unsigned long long (&holes)[W],
+                                   const unsigned long long (&parts)[W]) {
+    const int i = select_bit<W>(holes, 0), j = select_bit<W>(holes, 1);
+    const int a = select_bit<W>(parts, 0), b = select_bit<W>(parts, 1);
+    const int si = i & 1, sj = j & 1;
+    if ((a & 1) + (b & 1) != si + sj) return 0.f;
+    const int gi = __ldg(P.irrep + (i >> 1)), gj = __ldg(P.irrep + (j >> 1));
+    const int ga = __ldg(P.irrep + (a >> 1)), gb = __ldg(P.irrep + (b >> 1));
+    if ((ga ^ gb) != (gi ^ gj)) return 0.f;
+    if (si == sj && ((a & 1) != si || (b & 1) != si)) return 0.f;
+    unsigned long long gm[W];
+    const long long G = good_set<W>(P, v, si, sj, gi ^ gj, gm);
+    const int ca = ga * 2 + (a & 1), cb = gb * 2 + (b & 1);
+    const long long m_ba = (long long)v.cnt[cb] - (ca == cb ? 1 : 0);
+    const long long m_ab = (long long)v.cnt[ca] - (ca == cb ? 1 : 0);
+    return __fdiv_rn(P.p_double_f * small_f((unsigned)(m_ba + m_ab)), (float)((long long)P.npairs * G * m_ba * m_ab));
+}
+template <int W>
+__device__ __forceinline__ float hdouble_f(const Params &P, const unsigned long long (&d)[W],
+                                           const unsigned long long (&holes)[W], const unsigned long long (&parts)[W],
+                                           unsigned long long pol, float &err) {
+    const int i = select_bit<W>(holes, 0), j = select_bit<W>(holes, 1);
+    const int a = select_bit<W>(parts, 0), b = select_bit<W>(parts, 1);
+    const float xf = ((i & 1) == (a & 1) && (j & 1) == (b & 1)) ? eri_f(P, i >> 1, a >> 1, j >> 1, b >> 1, pol) : 0.f;
+    const float yf = ((i & 1) == (b & 1) && (j & 1) == (a & 1)) ? eri_f(P, i >> 1, b >> 1, j >> 1, a >> 1, pol) : 0.f;
+    err = fmaf(fabsf(xf) + fabsf(yf), 0x1p-22f, 1e-30f);
+    const float h = xf - yf;
+    return double_parity<W>(d, i, j, a, b) ? -h : h;
+}
+
 // Completes an attempt on spin-coupled functions (Sec. VI C) that generated the determinant x from the
 // stored determinant v: the target function holds x and its flip, its generation probability is the sum
 // of theirs, p = tau |H_AB| / (P(x) + P(xbar)), the Bernoulli part from the type word as for determinants.
+// A double (gx: the float form of its generation probability) is first decided from float bounds of H_AB
+// and of the generation probability; singles, a flip that is a single of v, and undecided cases evaluate
+// everything in FP64. For a closed-shell v the flip of x has the same class counts, so the same
+// generation probability, and H_AB needs only the element to the stored determinant.
 template <int W, bool SP>
 __device__ void hphf_attempt_end(const Params &P, const DetView<W> &v, const unsigned long long (&x)[W],
-                                 unsigned long long t, bool single, unsigned long long *cnt, AttemptOut &out) {
+                                 unsigned long long t, bool single, float gx, unsigned long long *cnt,
+                                 AttemptOut &out) {
     unsigned long long xb[W], b[W];
     flip_spins<W>(x, xb);
     const bool fl_less = det_less<W>(xb, x);
@@ -354,6 +394,59 @@ __device__ void hphf_attempt_end(const Params &P, const DetView<W> &v, const uns
 #pragma unroll
     for (int w = 0; w < W; ++w) same = same && b[w] == v.d[w];
     if (same || (SP && !in_space<W>(P, b))) { cnt[C_NULLS]++; return; }
+    if (!single) {
+        unsigned long long hx[W], px[W], hb[W], pb[W], a[W], ab[W], bb[W];
+        int lb = 0;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            a[w] = v.d[w];
+            hx[w] = v.d[w] & ~x[w];
+            px[w] = x[w] & ~v.d[w];
+            hb[w] = v.d[w] & ~xb[w];
+            pb[w] = xb[w] & ~v.d[w];
+            lb += __popcll(hb[w]);
+        }
+        if (lb != 1) {
+            const unsigned long long pol = keep_policy();
+            flip_spins<W>(a, ab);
+            flip_spins<W>(b, bb);
+            const bool a_open = !det_same<W>(a, ab), b_open = !det_same<W>(b, bb);
+            float hab, habbar = 0.f, e1, e2 = 0.f;
+            if (a_open) {
+                float ex, exb = 0.f;
+                const float hxf = hdouble_f<W>(P, a, hx, px, pol, ex);
+                const float hxbf = lb == 2 ? hdouble_f<W>(P, a, hb, pb, pol, exb) : 0.f;  // beyond doubles: 0
+                hab = fl_less ? hxbf : hxf;
+                habbar = fl_less ? hxf : hxbf;
+                e1 = fl_less ? exb : ex;
+                e2 = fl_less ? ex : exb;
+            } else {  // only <a|H|b> enters
+                hab = fl_less ? hdouble_f<W>(P, a, hb, pb, pol, e1) : hdouble_f<W>(P, a, hx, px, pol, e1);
+            }
+            float vf, ev;
+            if (a_open && b_open) {
+                vf = hab + (float)pair_sign(n_open<W>(b)) * habbar;
+                ev = e1 + e2 + fabsf(vf) * 0x1p-21f;
+            } else if (a_open || b_open) {
+                vf = hab * (float)kSqrt2;
+                ev = 1.5f * e1 + fabsf(vf) * 0x1p-21f;
+            } else {
+                vf = hab;
+                ev = e1;
+            }
+            float g = gx;
+            if (lb == 2 && !det_same<W>(xb, x)) g = a_open ? g + gen_prob_double_f<W>(P, v, hb, pb) : g + g;
+            const float ah_lo = fabsf(vf) - ev, ah_hi = fabsf(vf) + ev;
+            const int n = decide_spawn(__fdiv_rn(ah_lo * P.tau_f, g) * kDown, __fdiv_rn(ah_hi * P.tau_f, g) * kUp, t,
+                                       P.d53_f);
+            if (n == 0) return;
+            if (n > 0) {
+                emit_spawn<W>(P, v, b, n, vf > 0.f ? 1 : -1, cnt, out);  // |vf| > ev: the sign of H_AB
+                return;
+            }
+            atomicAdd(&P.st->exact_spawn, 1ull);  // undecided by the float bounds
+        }
+    }
     const double hv = hphf_hij<W>(P, v, b);
     if (hv == 0.0) return;
     double g = gen_prob<W>(P, v, x);
@@ -405,7 +498,7 @@ __device__ __forceinline__ bool attempt_begin(const Params &P, const Tables &T, 
             for (int w = 0; w < W; ++w) ch[w] = v.d[w];
             flip<W>(ch, i);
             flip<W>(ch, ao);
-            hphf_attempt_end<W, (MODE & 1) != 0>(P, v, ch, t, true, cnt, out);
+            hphf_attempt_end<W, (MODE & 1) != 0>(P, v, ch, t, true, 0.f, cnt, out);
             return false;
         }
         if (MODE & 1) {  // outside the permitted space: a null excitation (Sec. VI)
@@ -460,7 +553,7 @@ __device__ __forceinline__ bool attempt_begin(const Params &P, const Tables &T, 
         clear_bit<W>(bm, ao);
         bo = select_bit<W>(bm, k3);
     }
-    if (MODE & 2) {  // spin-coupled functions: completed here in FP64
+    if (MODE & 2) {  // spin-coupled functions
         unsigned long long ch[W];
 #pragma unroll
         for (int w = 0; w < W; ++w) ch[w] = v.d[w];
@@ -468,7 +561,10 @@ __device__ __forceinline__ bool attempt_begin(const Params &P, const Tables &T, 
         flip<W>(ch, j);
         flip<W>(ch, ao);
         flip<W>(ch, bo);
-        hphf_attempt_end<W, (MODE & 1) != 0>(P, v, ch, t, false, cnt, out);
+        // generation probability of this double from the quantities of its selection (as gen_prob_double_f)
+        const float gx = __fdiv_rn(P.p_double_f * small_f(m_ba + m_ab),
+                                   (float)((long long)P.npairs * (long long)G * (long long)m_ba * (long long)m_ab));
+        hphf_attempt_end<W, (MODE & 1) != 0>(P, v, ch, t, false, gx, cnt, out);
         return false;
     }
     if (MODE & 1) {  // outside the permitted space: a null excitation (Sec. VI)
