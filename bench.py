@@ -226,6 +226,23 @@ def algorithmic_bytes(W, nd, slots, merged, inserted):
     return sweep, annih
 
 
+def replica_seed(rank: int) -> int:
+    """Random-number seed of the replica on a rank (independent replicas, one per GPU)."""
+    return 1 + rank
+
+
+def reduce_over_ranks(ms: float, attempts: float, world: int, device) -> tuple[float, float]:
+    """The timed region's length (the maximum over ranks) and the attempts of all ranks (their sum)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    a = torch.tensor([attempts], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(a, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(a.item())
+
+
 def grow(args, wl, rank):
     """Create the run and grow the population on the GPU until the shift starts varying (untimed)."""
     from paper_1305_6981_gb300 import Fciqmc
@@ -235,7 +252,7 @@ def grow(args, wl, rank):
     cap = wl["main_capacity"] if not args.target else max(2 * args.target, 1 << 16)
     scap = wl["spawn_capacity"] if not args.target else max(1 << 14, 1 << int(np.ceil(np.log2(args.target))))
     g = Fciqmc(system, wl["tau"], wl["thr"], target_walkers=target, initial_population=wl["initial_population"],
-               initial_shift=wl["initial_shift"], seed=1 + rank, main_capacity=cap, spawn_capacity=scap,
+               initial_shift=wl["initial_shift"], seed=replica_seed(rank), main_capacity=cap, spawn_capacity=scap,
                **wl.get("space", {}))
     t_grow = time.perf_counter()
     grown, chunk = 0, 50
@@ -309,13 +326,7 @@ def run_gpu(args, wl, rank, world, local_rank):
     nw_mean = float(np.mean([r["nw_in"] for r in rows]))
     merged_mean = float(np.mean([r["merged_entries"] for r in rows]))
     inserted_mean = float(np.mean([r["inserted_dets"] for r in rows]))
-    t = torch.tensor([ms, float(attempts)], dtype=torch.float64, device="cuda")
-    if world > 1:
-        tt = t.clone()
-        dist.all_reduce(tt[0:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(tt[1:2], op=dist.ReduceOp.SUM)
-        t = tt
-    ms_max, att_all = float(t[0]), float(t[1])
+    ms_max, att_all = reduce_over_ranks(ms, float(attempts), world, "cuda")
     # per-kernel times (same iterations, kernels launched one by one between events)
     est = g.estimates()
     exact = {"spawn_per_iter": (est["exact_spawns"] - e_before["exact_spawns"]) / args.steps,
