@@ -168,10 +168,54 @@ __device__ __forceinline__ void prepare_det(const Params &P, const Tables &T, De
 }
 
 // ---------------------------------------------------------------------------- one spawning attempt
-struct AttemptOut {
-    bool claimed;
-    unsigned pos;
+// Spawns accepted by the lanes of one warp, inserted into the merge table together (flush_queue) so that
+// the table's round trips are shared by the lanes instead of stalling the warp once per accepting lane.
+constexpr int kQueue = 48;       // capacity: flushed from 16 entries on; a round adds at most 32
+constexpr int kQueueFlush = 16;
+template <int W>
+struct SpawnQueue {
+    unsigned long long key[kQueue][W];
+    unsigned long long val[kQueue];
+    unsigned n;
+    unsigned pad[3];
 };
+
+// Inserts queued spawns into the merge table (all 32 lanes; every lane inserts one entry): everything
+// when all is set, else up to 32 entries once at least kQueueFlush are queued. Merge-table positions
+// newly claimed go to the merged list.
+template <int W>
+__device__ __forceinline__ void flush_queue(const Params &P, SpawnQueue<W> &q, bool all) {
+    __syncwarp();
+    const unsigned n = q.n;
+    if (n == 0 || (!all && n < (unsigned)kQueueFlush)) return;
+    const int lane = threadIdx.x & 31;
+    unsigned done = 0;
+    do {
+        const unsigned take = min(n - done, 32u);
+        const unsigned e = done + lane;
+        bool claimed = false;
+        unsigned pos = 0;
+        if (lane < (int)take) {
+            unsigned long long key[W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) key[w] = q.key[e][w];
+            claimed = merge_insert<W>(P, key, q.val[e], pos);
+        }
+        const long long slot = warp_append(&P.st->n_merged, claimed);
+        if (claimed && slot < P.mt_cap) P.merged[slot] = pos;
+        done += take;
+    } while (all && done < n);
+    __syncwarp();
+    const unsigned rest = n - done;  // fewer than kQueueFlush, below the entries just taken
+    if (lane < (int)rest) {
+#pragma unroll
+        for (int w = 0; w < W; ++w) q.key[lane][w] = q.key[done + lane][w];
+        q.val[lane] = q.val[done + lane];
+    }
+    __syncwarp();
+    if (lane == 0) q.n = rest;
+    __syncwarp();
+}
 
 // Exact float of a small nonnegative integer (x < 2^23) without a conversion instruction.
 __device__ __forceinline__ float small_f(unsigned x) { return __int_as_float(0x4B000000 | x) - 8388608.0f; }
@@ -274,15 +318,17 @@ __device__ __forceinline__ int decide_spawn(float p_lo, float p_hi, unsigned lon
     return -1;
 }
 
-// Counters and merge-table entry of an attempt that spawns n > 0 walkers onto child.
+// Counters and queued merge-table entry of an attempt that spawns n > 0 walkers onto child.
 template <int W>
 __device__ __forceinline__ void emit_spawn(const Params &P, const DetView<W> &v, const unsigned long long (&child)[W],
-                                           int n, int sgn_h, unsigned long long *cnt, AttemptOut &out) {
+                                           int n, int sgn_h, unsigned long long *cnt, SpawnQueue<W> &out) {
     cnt[C_EVENTS]++;
     cnt[C_SPAWNED] += (unsigned long long)n;
     const long long amt = -(long long)(v.c > 0 ? 1 : -1) * sgn_h * (long long)n;
-    const unsigned long long val = (v.flag ? kFlagUnit : 0ull) + (unsigned long long)amt;
-    out.claimed = merge_insert<W>(P, child, val, out.pos);
+    const unsigned slot = atomicAdd(&out.n, 1u);
+#pragma unroll
+    for (int w = 0; w < W; ++w) out.key[slot][w] = child[w];
+    out.val[slot] = (v.flag ? kFlagUnit : 0ull) + (unsigned long long)amt;
 }
 
 // Probability that one attempt from v generates the determinant x (the closed forms the generator of
@@ -384,7 +430,7 @@ __device__ __forceinline__ float hdouble_f(const Params &P, const unsigned long 
 template <int W, bool SP>
 __device__ void hphf_attempt_end(const Params &P, const DetView<W> &v, const unsigned long long (&x)[W],
                                  unsigned long long t, bool single, float gx, unsigned long long *cnt,
-                                 AttemptOut &out) {
+                                 SpawnQueue<W> &out) {
     unsigned long long xb[W], b[W];
     flip_spins<W>(x, xb);
     const bool fl_less = det_less<W>(xb, x);
@@ -469,7 +515,7 @@ __device__ void hphf_attempt_end(const Params &P, const DetView<W> &v, const uns
 template <int W, bool TAB, int MODE>
 __device__ __forceinline__ bool attempt_begin(const Params &P, const Tables &T, const DetView<W> &v,
                                               const HeavyTab *tab, const float *rcpf, unsigned a, unsigned iter,
-                                              unsigned long long pol, unsigned long long *cnt, AttemptOut &out,
+                                              unsigned long long pol, unsigned long long *cnt, SpawnQueue<W> &out,
                                               int &i_out, int &a_out, unsigned &mallow_out, unsigned long long &q_out) {
     unsigned long long r0, r1, r2, r3;
     draw2(a, 0u, v.fp, P.seed, iter, r0, r1);
@@ -671,7 +717,7 @@ __device__ __forceinline__ void single_elements_warp(const Params &P, const DetV
 template <int W>
 __device__ __forceinline__ void attempt_single_end(const Params &P, const DetView<W> &v, int i, int ao, unsigned mallow,
                                                    unsigned long long q, float hs, float hab, unsigned long long *cnt,
-                                                   AttemptOut &out) {
+                                                   SpawnQueue<W> &out) {
     const float eh = fmaf(hab, P.serr_f, 1e-30f);
     const float ah_lo = fabsf(hs) - eh, ah_hi = fabsf(hs) + eh;
     const float F = P.cs_f * small_f(mallow * v.nok);
@@ -704,10 +750,9 @@ __device__ __forceinline__ void attempt_single_end(const Params &P, const DetVie
 
 // One spawning attempt per lane (active lanes only); called by all 32 lanes of a warp.
 template <int W, bool TAB, int MODE>
-__device__ __forceinline__ AttemptOut spawn_attempt(const Params &P, const Tables &T, const DetView<W> &v,
-                                                     const HeavyTab *tab, const float *rcpf, bool active, unsigned a,
-                                                     unsigned iter, unsigned long long *cnt) {
-    AttemptOut out{false, 0u};
+__device__ __forceinline__ void spawn_attempt(const Params &P, const Tables &T, const DetView<W> &v,
+                                              const HeavyTab *tab, const float *rcpf, bool active, unsigned a,
+                                              unsigned iter, unsigned long long *cnt, SpawnQueue<W> &out) {
     const unsigned long long pol = keep_policy();
     int i = 0, ao = 0;
     unsigned mallow = 0;
@@ -717,7 +762,6 @@ __device__ __forceinline__ AttemptOut spawn_attempt(const Params &P, const Table
     float hs = 0.f, hab = 0.f;
     single_elements_warp<W>(P, &v, pend, i, ao, pol, hs, hab);
     if (pend) attempt_single_end<W>(P, v, i, ao, mallow, q, hs, hab, cnt, out);
-    return out;
 }
 
 // ---------------------------------------------------------------------------- death / cloning (Eq. 4)
@@ -810,6 +854,7 @@ template <int W, int MODE>
 __global__ void __launch_bounds__(kTile, FQ_SWEEP_MIN_BLOCKS) k_sweep(Params P) {
     DevState *st = P.st;
     if (st->status) return;
+    extern __shared__ __align__(16) unsigned char s_queue[];  // one SpawnQueue per warp
     __shared__ Tables T;
     __shared__ DetView<W> s_dv[kTile];
     __shared__ unsigned s_off[kTile + 1];
@@ -837,6 +882,9 @@ __global__ void __launch_bounds__(kTile, FQ_SWEEP_MIN_BLOCKS) k_sweep(Params P) 
     for (int k = 0; k < NCNT + 4; ++k) acc[k] = 0;
     double num = 0.0;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    SpawnQueue<W> &sq = reinterpret_cast<SpawnQueue<W> *>(s_queue)[warp];
+    if (lane == 0) sq.n = 0;
+    __syncwarp();
 
     for (long long tb = (long long)blockIdx.x * kTile; tb < len; tb += (long long)gridDim.x * kTile) {
         const long long s = tb + tid;
@@ -927,12 +975,12 @@ __global__ void __launch_bounds__(kTile, FQ_SWEEP_MIN_BLOCKS) k_sweep(Params P) 
                     if (s_off[mid] <= k) lo = mid; else hi = mid - 1;
                 }
             }
-            const AttemptOut ao = spawn_attempt<W, false, MODE>(P, T, s_dv[lo], nullptr, s_rcpf, act, k - s_off[lo], iter, acc);
-            long long slot = warp_append(&st->n_merged, ao.claimed);
-            if (ao.claimed && slot < P.mt_cap) P.merged[slot] = ao.pos;
+            spawn_attempt<W, false, MODE>(P, T, s_dv[lo], nullptr, s_rcpf, act, k - s_off[lo], iter, acc, sq);
+            flush_queue<W>(P, sq, false);
         }
         __syncthreads();
     }
+    flush_queue<W>(P, sq, true);
     unsigned long long *const dst[NCNT + 4] = {&st->cnt[0], &st->cnt[1], &st->cnt[2], &st->cnt[3], &st->cnt[4],
                                                &st->cnt[5], &st->cnt[6], &st->cnt[7], &st->cnt[8], &st->cnt[9],
                                                &st->nw_in, &st->nd_in, &st->d_nw, &st->d_nd};
@@ -948,6 +996,7 @@ template <int W, int MODE>
 __global__ void __launch_bounds__(kTile, 4) k_heavy(Params P) {
     DevState *st = P.st;
     if (st->status) return;
+    extern __shared__ __align__(16) unsigned char s_queue[];  // one SpawnQueue per warp
     constexpr int NW = kTile / 32;
     __shared__ Tables T;
     __shared__ DetView<W> s_v[NW];
@@ -972,6 +1021,9 @@ __global__ void __launch_bounds__(kTile, 4) k_heavy(Params P) {
     long long cur = -1;
     DetView<W> &v = s_v[warp];
     HeavyTab &tab = s_tab[warp];
+    SpawnQueue<W> &sq = reinterpret_cast<SpawnQueue<W> *>(s_queue)[warp];
+    if (lane == 0) sq.n = 0;
+    __syncwarp();
     for (unsigned long long q = q0; q < q1; ++q) {
         // record holding chunk q: last record whose first chunk is <= q
         long long r;
@@ -998,12 +1050,12 @@ __global__ void __launch_bounds__(kTile, 4) k_heavy(Params P) {
         const unsigned a1 = min(a0 + (unsigned)kChunk, P.heavy_att[r]);
         for (unsigned base = a0; base < a1; base += 32) {
             const unsigned a = base + lane;
-            const AttemptOut ao = spawn_attempt<W, true, MODE>(P, T, v, &tab, s_rcpf, a < a1, a, iter, cnt);
-            long long slot = warp_append(&st->n_merged, ao.claimed);
-            if (ao.claimed && slot < P.mt_cap) P.merged[slot] = ao.pos;
+            spawn_attempt<W, true, MODE>(P, T, v, &tab, s_rcpf, a < a1, a, iter, cnt, sq);
+            flush_queue<W>(P, sq, false);
         }
         __syncwarp();
     }
+    flush_queue<W>(P, sq, true);
     unsigned long long *const dst[NCNT] = {&st->cnt[0], &st->cnt[1], &st->cnt[2], &st->cnt[3], &st->cnt[4],
                                            &st->cnt[5], &st->cnt[6], &st->cnt[7], &st->cnt[8], &st->cnt[9]};
     cnt[C_ATTEMPTS] = 0;  // attempts are counted by the sweep
