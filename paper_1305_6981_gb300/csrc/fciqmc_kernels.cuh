@@ -20,7 +20,10 @@ constexpr int kTile = 256;          // determinants per sweep tile = threads per
 #ifndef FQ_SWEEP_MIN_BLOCKS
 #define FQ_SWEEP_MIN_BLOCKS 4          // resident sweep blocks per SM the register budget is sized for
 #endif
-constexpr int kHeavy = 1024;        // |C_i| above this: attempts go to the chunked heavy path
+#ifndef FQ_HEAVY_THRESHOLD
+#define FQ_HEAVY_THRESHOLD 256
+#endif
+constexpr int kHeavy = FQ_HEAVY_THRESHOLD;  // |C_i| above this: attempts go to the chunked heavy path
 constexpr int kChunk = 256;         // attempts per heavy chunk (one warp task)
 constexpr unsigned long long kSaltMerge = 0x5851F42D4C957F2Dull;
 constexpr unsigned long long kSaltIndex = 0x14057B7EF767814Full;
