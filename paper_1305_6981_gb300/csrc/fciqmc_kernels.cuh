@@ -411,16 +411,20 @@ __device__ float gen_prob_double_f(const Params &P, const DetView<W> &v, const u
     return __fdiv_rn(P.p_double_f * small_f((unsigned)(m_ba + m_ab)), (float)((long long)P.npairs * G * m_ba * m_ab));
 }
 template <int W>
-__device__ __forceinline__ float hdouble_f(const Params &P, const unsigned long long (&d)[W],
-                                           const unsigned long long (&holes)[W], const unsigned long long (&parts)[W],
-                                           unsigned long long pol, float &err) {
-    const int i = select_bit<W>(holes, 0), j = select_bit<W>(holes, 1);
-    const int a = select_bit<W>(parts, 0), b = select_bit<W>(parts, 1);
+__device__ __forceinline__ float hdouble_f_at(const Params &P, const unsigned long long (&d)[W], int i, int j, int a,
+                                              int b, unsigned long long pol, float &err) {
     const float xf = ((i & 1) == (a & 1) && (j & 1) == (b & 1)) ? eri_f(P, i >> 1, a >> 1, j >> 1, b >> 1, pol) : 0.f;
     const float yf = ((i & 1) == (b & 1) && (j & 1) == (a & 1)) ? eri_f(P, i >> 1, b >> 1, j >> 1, a >> 1, pol) : 0.f;
     err = fmaf(fabsf(xf) + fabsf(yf), 0x1p-22f, 1e-30f);
     const float h = xf - yf;
     return double_parity<W>(d, i, j, a, b) ? -h : h;
+}
+template <int W>
+__device__ __forceinline__ float hdouble_f(const Params &P, const unsigned long long (&d)[W],
+                                           const unsigned long long (&holes)[W], const unsigned long long (&parts)[W],
+                                           unsigned long long pol, float &err) {
+    return hdouble_f_at<W>(P, d, select_bit<W>(holes, 0), select_bit<W>(holes, 1), select_bit<W>(parts, 0),
+                           select_bit<W>(parts, 1), pol, err);
 }
 
 // Completes an attempt on spin-coupled functions (Sec. VI C) that generated the determinant x from the
@@ -432,8 +436,8 @@ __device__ __forceinline__ float hdouble_f(const Params &P, const unsigned long 
 // generation probability, and H_AB needs only the element to the stored determinant.
 template <int W, bool SP>
 __device__ void hphf_attempt_end(const Params &P, const DetView<W> &v, const unsigned long long (&x)[W],
-                                 unsigned long long t, bool single, float gx, unsigned long long *cnt,
-                                 SpawnQueue<W> &out) {
+                                 unsigned long long t, bool single, float gx, int oi, int oj, int oa, int ob,
+                                 unsigned long long *cnt, SpawnQueue<W> &out) {
     unsigned long long xb[W], b[W];
     flip_spins<W>(x, xb);
     const bool fl_less = det_less<W>(xb, x);
@@ -444,13 +448,11 @@ __device__ void hphf_attempt_end(const Params &P, const DetView<W> &v, const uns
     for (int w = 0; w < W; ++w) same = same && b[w] == v.d[w];
     if (same || (SP && !in_space<W>(P, b))) { cnt[C_NULLS]++; return; }
     if (!single) {
-        unsigned long long hx[W], px[W], hb[W], pb[W], a[W], ab[W], bb[W];
+        unsigned long long hb[W], pb[W], a[W], ab[W], bb[W];
         int lb = 0;
 #pragma unroll
         for (int w = 0; w < W; ++w) {
             a[w] = v.d[w];
-            hx[w] = v.d[w] & ~x[w];
-            px[w] = x[w] & ~v.d[w];
             hb[w] = v.d[w] & ~xb[w];
             pb[w] = xb[w] & ~v.d[w];
             lb += __popcll(hb[w]);
@@ -460,17 +462,21 @@ __device__ void hphf_attempt_end(const Params &P, const DetView<W> &v, const uns
             flip_spins<W>(a, ab);
             flip_spins<W>(b, bb);
             const bool a_open = !det_same<W>(a, ab), b_open = !det_same<W>(b, bb);
+            // (oi, oj) -> (oa, ob), ascending: the double that generated x
             float hab, habbar = 0.f, e1, e2 = 0.f;
             if (a_open) {
                 float ex, exb = 0.f;
-                const float hxf = hdouble_f<W>(P, a, hx, px, pol, ex);
+                const float hxf = hdouble_f_at<W>(P, a, oi, oj, oa, ob, pol, ex);
                 const float hxbf = lb == 2 ? hdouble_f<W>(P, a, hb, pb, pol, exb) : 0.f;  // beyond doubles: 0
                 hab = fl_less ? hxbf : hxf;
                 habbar = fl_less ? hxf : hxbf;
                 e1 = fl_less ? exb : ex;
                 e2 = fl_less ? ex : exb;
-            } else {  // only <a|H|b> enters
-                hab = fl_less ? hdouble_f<W>(P, a, hb, pb, pol, e1) : hdouble_f<W>(P, a, hx, px, pol, e1);
+            } else if (fl_less) {  // a = abar: the flip of x is the flipped double of a
+                const int fi = oi ^ 1, fj = oj ^ 1, fa = oa ^ 1, fb = ob ^ 1;
+                hab = hdouble_f_at<W>(P, a, min(fi, fj), max(fi, fj), min(fa, fb), max(fa, fb), pol, e1);
+            } else {
+                hab = hdouble_f_at<W>(P, a, oi, oj, oa, ob, pol, e1);
             }
             float vf, ev;
             if (a_open && b_open) {
@@ -547,7 +553,7 @@ __device__ __forceinline__ bool attempt_begin(const Params &P, const Tables &T, 
             for (int w = 0; w < W; ++w) ch[w] = v.d[w];
             flip<W>(ch, i);
             flip<W>(ch, ao);
-            hphf_attempt_end<W, (MODE & 1) != 0>(P, v, ch, t, true, 0.f, cnt, out);
+            hphf_attempt_end<W, (MODE & 1) != 0>(P, v, ch, t, true, 0.f, 0, 0, 0, 0, cnt, out);
             return false;
         }
         if (MODE & 1) {  // outside the permitted space: a null excitation (Sec. VI)
@@ -613,7 +619,7 @@ __device__ __forceinline__ bool attempt_begin(const Params &P, const Tables &T, 
         // generation probability of this double from the quantities of its selection (as gen_prob_double_f)
         const float gx = __fdiv_rn(P.p_double_f * small_f(m_ba + m_ab),
                                    (float)((long long)P.npairs * (long long)G * (long long)m_ba * (long long)m_ab));
-        hphf_attempt_end<W, (MODE & 1) != 0>(P, v, ch, t, false, gx, cnt, out);
+        hphf_attempt_end<W, (MODE & 1) != 0>(P, v, ch, t, false, gx, i, j, min(ao, bo), max(ao, bo), cnt, out);
         return false;
     }
     if (MODE & 1) {  // outside the permitted space: a null excitation (Sec. VI)
