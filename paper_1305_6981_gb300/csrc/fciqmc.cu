@@ -58,7 +58,8 @@ bool sizes_of(int n_elec, int n_orb, const fciqmc_options &o, Sizes &z) {
     z.idx_cap = next_pow2(std::max<long long>((long long)std::ceil((double)z.cap / load), 1 << 12));
     z.mt_cap = next_pow2(std::max<long long>(o.spawn_capacity > 0 ? o.spawn_capacity : z.cap / 2, 1 << 12));
     if (z.mt_cap > (1LL << 32)) return false;
-    z.heavy_cap = std::max<long long>(1 << 14, std::min<long long>(z.cap, 1 << 20));
+    // records of determinants with |C| > 256 (a run that needs more stops with FCIQMC_ERR_CAPACITY)
+    z.heavy_cap = std::max<long long>(1 << 14, std::min<long long>(z.cap / 2, 1 << 22));
     z.hist_cap = std::max<long long>(o.history_capacity > 0 ? o.history_capacity : (1LL << 16), 16);
     return true;
 }

@@ -393,10 +393,7 @@ __device__ double hphf_hij(const Params &P, const DetView<W> &v, const unsigned 
 // cannot produce it), within 4 roundings of float, and the matrix element <y|H|v> for a double
 // difference, |H - value| <= err.
 template <int W>
-__device__ float gen_prob_double_f(const Params &P, const DetView<W> &v, const unsigned long long (&holes)[W],
-                                   const unsigned long long (&parts)[W]) {
-    const int i = select_bit<W>(holes, 0), j = select_bit<W>(holes, 1);
-    const int a = select_bit<W>(parts, 0), b = select_bit<W>(parts, 1);
+__device__ float gen_prob_double_f(const Params &P, const DetView<W> &v, int i, int j, int a, int b) {
     const int si = i & 1, sj = j & 1;
     if ((a & 1) + (b & 1) != si + sj) return 0.f;
     const int gi = __ldg(P.irrep + (i >> 1)), gj = __ldg(P.irrep + (j >> 1));
@@ -418,13 +415,6 @@ __device__ __forceinline__ float hdouble_f_at(const Params &P, const unsigned lo
     err = fmaf(fabsf(xf) + fabsf(yf), 0x1p-22f, 1e-30f);
     const float h = xf - yf;
     return double_parity<W>(d, i, j, a, b) ? -h : h;
-}
-template <int W>
-__device__ __forceinline__ float hdouble_f(const Params &P, const unsigned long long (&d)[W],
-                                           const unsigned long long (&holes)[W], const unsigned long long (&parts)[W],
-                                           unsigned long long pol, float &err) {
-    return hdouble_f_at<W>(P, d, select_bit<W>(holes, 0), select_bit<W>(holes, 1), select_bit<W>(parts, 0),
-                           select_bit<W>(parts, 1), pol, err);
 }
 
 // Completes an attempt on spin-coupled functions (Sec. VI C) that generated the determinant x from the
@@ -464,10 +454,17 @@ __device__ void hphf_attempt_end(const Params &P, const DetView<W> &v, const uns
             const bool a_open = !det_same<W>(a, ab), b_open = !det_same<W>(b, bb);
             // (oi, oj) -> (oa, ob), ascending: the double that generated x
             float hab, habbar = 0.f, e1, e2 = 0.f;
+            int bi = 0, bj = 0, ba = 0, bbo = 0;  // a -> xbar when it is a double
+            if (a_open && lb == 2) {
+                bi = select_bit<W>(hb, 0);
+                bj = select_bit<W>(hb, 1);
+                ba = select_bit<W>(pb, 0);
+                bbo = select_bit<W>(pb, 1);
+            }
             if (a_open) {
                 float ex, exb = 0.f;
                 const float hxf = hdouble_f_at<W>(P, a, oi, oj, oa, ob, pol, ex);
-                const float hxbf = lb == 2 ? hdouble_f<W>(P, a, hb, pb, pol, exb) : 0.f;  // beyond doubles: 0
+                const float hxbf = lb == 2 ? hdouble_f_at<W>(P, a, bi, bj, ba, bbo, pol, exb) : 0.f;  // beyond doubles: 0
                 hab = fl_less ? hxbf : hxf;
                 habbar = fl_less ? hxf : hxbf;
                 e1 = fl_less ? exb : ex;
@@ -490,7 +487,7 @@ __device__ void hphf_attempt_end(const Params &P, const DetView<W> &v, const uns
                 ev = e1;
             }
             float g = gx;
-            if (lb == 2 && !det_same<W>(xb, x)) g = a_open ? g + gen_prob_double_f<W>(P, v, hb, pb) : g + g;
+            if (lb == 2 && !det_same<W>(xb, x)) g = a_open ? g + gen_prob_double_f<W>(P, v, bi, bj, ba, bbo) : g + g;
             const float ah_lo = fabsf(vf) - ev, ah_hi = fabsf(vf) + ev;
             const int n = decide_spawn(__fdiv_rn(ah_lo * P.tau_f, g) * kDown, __fdiv_rn(ah_hi * P.tau_f, g) * kUp, t,
                                        P.d53_f);
