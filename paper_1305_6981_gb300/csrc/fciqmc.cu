@@ -531,6 +531,7 @@ int fciqmc_create(const double *h1, const double *eri_s8, double e_core, int n_e
         P.p_double_d = p_double;
         P.p_single_d = p_single;
         P.p_double_f = (float)p_double;
+        P.p_single_f = (float)p_single;
         P.cdn_f = (float)(P.cd * (double)z.npairs);
         P.d53_d = (double)d53;
         P.d53_f = (float)d53;

@@ -87,7 +87,7 @@ struct Params {
     unsigned long long froz_occ[MAXW], froz_emp[MAXW];
     int hphf;                         // walkers on spin-coupled functions (Sec. VI C)
     double p_single_d, p_double_d;    // P_single, P_double as realised by the draw
-    float p_double_f;                 // nearest float of P_double
+    float p_double_f, p_single_f;     // nearest floats of P_double, P_single
     // main list, two buffers for compaction, two population arrays per buffer
     unsigned long long *det[2];
     double *hd[2];

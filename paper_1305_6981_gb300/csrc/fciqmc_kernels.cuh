@@ -417,6 +417,27 @@ __device__ __forceinline__ float hdouble_f_at(const Params &P, const unsigned lo
     return double_parity<W>(d, i, j, a, b) ? -h : h;
 }
 
+// The FP64 evaluation of a spin-coupled attempt that generated x (flip xb) from v, target function stored
+// on b: p = (tau |H_AB|) / (P(x) + P(xb)), then floor(p) plus one with the Bernoulli part of the type word.
+template <int W>
+__device__ __forceinline__ void hphf_exact(const Params &P, const DetView<W> &v, const unsigned long long (&x)[W],
+                                           const unsigned long long (&xb)[W], const unsigned long long (&b)[W],
+                                           unsigned long long t, bool single, unsigned long long *cnt,
+                                           SpawnQueue<W> &out) {
+    const double hv = hphf_hij<W>(P, v, b);
+    if (hv == 0.0) return;
+    double g = gen_prob<W>(P, v, x);
+    if (!det_same<W>(xb, x)) g = __dadd_rn(g, gen_prob<W>(P, v, xb));
+    const double p = __ddiv_rn(__dmul_rn(P.tau, fabs(hv)), g);
+    const double fl = floor(p);
+    if (fl >= 2147483647.0) { set_status(P.st, FCIQMC_ERR_NUMERIC); return; }
+    const unsigned long long off = single ? P.d53 : 0ull;
+    const double range = single ? __dsub_rn(9007199254740992.0, P.d53_d) : P.d53_d;
+    const int n = (int)fl + (__ull2double_rn(t - off) < __dmul_rn(__dsub_rn(p, fl), range) ? 1 : 0);
+    if (n == 0) return;
+    emit_spawn<W>(P, v, b, n, hv > 0.0 ? 1 : -1, cnt, out);
+}
+
 // Completes an attempt on spin-coupled functions (Sec. VI C) that generated the determinant x from the
 // stored determinant v: the target function holds x and its flip, its generation probability is the sum
 // of theirs, p = tau |H_AB| / (P(x) + P(xbar)), the Bernoulli part from the type word as for determinants.
@@ -499,18 +520,7 @@ __device__ void hphf_attempt_end(const Params &P, const DetView<W> &v, const uns
             atomicAdd(&P.st->exact_spawn, 1ull);  // undecided by the float bounds
         }
     }
-    const double hv = hphf_hij<W>(P, v, b);
-    if (hv == 0.0) return;
-    double g = gen_prob<W>(P, v, x);
-    if (!det_same<W>(xb, x)) g = __dadd_rn(g, gen_prob<W>(P, v, xb));
-    const double p = __ddiv_rn(__dmul_rn(P.tau, fabs(hv)), g);
-    const double fl = floor(p);
-    if (fl >= 2147483647.0) { set_status(P.st, FCIQMC_ERR_NUMERIC); return; }
-    const unsigned long long off = single ? P.d53 : 0ull;
-    const double range = single ? __dsub_rn(9007199254740992.0, P.d53_d) : P.d53_d;
-    const int n = (int)fl + (__ull2double_rn(t - off) < __dmul_rn(__dsub_rn(p, fl), range) ? 1 : 0);
-    if (n == 0) return;
-    emit_spawn<W>(P, v, b, n, hv > 0.0 ? 1 : -1, cnt, out);
+    hphf_exact<W>(P, v, x, xb, b, t, single, cnt, out);
 }
 
 // First part of attempt a from determinant v (Eq. 3 with the generator of Sec. VI). Random numbers:
@@ -522,7 +532,8 @@ template <int W, bool TAB, int MODE>
 __device__ __forceinline__ bool attempt_begin(const Params &P, const Tables &T, const DetView<W> &v,
                                               const HeavyTab *tab, const float *rcpf, unsigned a, unsigned iter,
                                               unsigned long long pol, unsigned long long *cnt, SpawnQueue<W> &out,
-                                              int &i_out, int &a_out, unsigned &mallow_out, unsigned long long &q_out) {
+                                              int &i_out, int &a_out, unsigned &mallow_out, unsigned long long &q_out,
+                                              int &i1_out, int &a1_out, int &i2_out, int &a2_out) {
     unsigned long long r0, r1, r2, r3;
     draw2(a, 0u, v.fp, P.seed, iter, r0, r1);
     draw2(a, 1u, v.fp, P.seed, iter, r2, r3);
@@ -544,14 +555,46 @@ __device__ __forceinline__ bool attempt_begin(const Params &P, const Tables &T, 
             for (int w = 0; w < W; ++w) um[w] = ~v.d[w] & T.mask[ci * MAXW + w];
             ao = select_bit<W>(um, k2);
         }
-        if (MODE & 2) {  // spin-coupled functions: completed here in FP64
-            unsigned long long ch[W];
+        if (MODE & 2) {  // spin-coupled functions: the single elements H_AB needs are evaluated by the warp
+            unsigned long long x[W], xb[W], b[W], sb[W];
 #pragma unroll
-            for (int w = 0; w < W; ++w) ch[w] = v.d[w];
-            flip<W>(ch, i);
-            flip<W>(ch, ao);
-            hphf_attempt_end<W, (MODE & 1) != 0>(P, v, ch, t, true, 0.f, 0, 0, 0, 0, cnt, out);
-            return false;
+            for (int w = 0; w < W; ++w) x[w] = v.d[w];
+            flip<W>(x, i);
+            flip<W>(x, ao);
+            flip_spins<W>(x, xb);
+            const bool fl_less = det_less<W>(xb, x);
+#pragma unroll
+            for (int w = 0; w < W; ++w) b[w] = fl_less ? xb[w] : x[w];
+            if (det_same<W>(b, v.d) || ((MODE & 1) && !in_space<W>(P, b))) { cnt[C_NULLS]++; return false; }
+            flip_spins<W>(v.d, sb);
+            i1_out = i;
+            a1_out = ao;
+            i2_out = -1;
+            a2_out = -1;
+            if (det_same<W>(v.d, sb)) {  // closed source: only the element to b, a single (flipped when b = xb)
+                if (fl_less) {
+                    i1_out = i ^ 1;
+                    a1_out = ao ^ 1;
+                }
+            } else if (!det_same<W>(x, xb)) {  // the element to x, and the one to xb when that is a single as well
+                unsigned long long hb[W], pb[W];
+                int lb = 0;
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    hb[w] = v.d[w] & ~xb[w];
+                    pb[w] = xb[w] & ~v.d[w];
+                    lb += __popcll(hb[w]);
+                }
+                if (lb == 1) {
+                    i2_out = select_bit<W>(hb, 0);
+                    a2_out = select_bit<W>(pb, 0);
+                }
+            }
+            i_out = i;
+            a_out = ao;
+            mallow_out = mallow;
+            q_out = t - P.d53;
+            return true;
         }
         if (MODE & 1) {  // outside the permitted space: a null excitation (Sec. VI)
             unsigned long long ch[W];
@@ -561,8 +604,9 @@ __device__ __forceinline__ bool attempt_begin(const Params &P, const Tables &T, 
             flip<W>(ch, ao);
             if (!in_space<W>(P, ch)) { cnt[C_NULLS]++; return false; }
         }
-        i_out = i;
-        a_out = ao;
+        i_out = i1_out = i;
+        a_out = a1_out = ao;
+        i2_out = a2_out = -1;
         mallow_out = mallow;
         q_out = t - P.d53;
         return true;
@@ -754,20 +798,103 @@ __device__ __forceinline__ void attempt_single_end(const Params &P, const DetVie
     emit_spawn<W>(P, v, child, n, sgn_h, cnt, out);
 }
 
+// Completes a pending spin-coupled single i -> ao from v (x and its flip xb; target stored on b) from the
+// warp's float sums of the single elements (i1, a1) and, for an open-shell v whose xb is a single as well,
+// (i2, a2): H_AB and the generation probability in float with error bounds, the same decision as for
+// determinants; undecided cases evaluate everything in FP64.
+template <int W>
+__device__ __forceinline__ void hphf_single_end(const Params &P, const DetView<W> &v, int i, int ao, int i1, int a1,
+                                                int i2, int a2, unsigned mallow, unsigned long long q, float hs,
+                                                float hab, float hs2, float hab2, unsigned long long *cnt,
+                                                SpawnQueue<W> &out) {
+    unsigned long long a[W], ab[W], x[W], xb[W], b[W], bb[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) a[w] = x[w] = v.d[w];
+    flip<W>(x, i);
+    flip<W>(x, ao);
+    flip_spins<W>(x, xb);
+    const bool fl_less = det_less<W>(xb, x);
+#pragma unroll
+    for (int w = 0; w < W; ++w) b[w] = fl_less ? xb[w] : x[w];
+    flip_spins<W>(a, ab);
+    flip_spins<W>(b, bb);
+    const bool a_open = !det_same<W>(a, ab), b_open = !det_same<W>(b, bb);
+    const float h1 = (count_between<W>(a, i1, a1) & 1) ? -hs : hs;  // signed element to (i1, a1)
+    const float e1 = fmaf(hab, P.serr_f, 1e-30f);
+    const float gx = __fdiv_rn(P.p_single_f, small_f(mallow * v.nok));
+    float vf, ev, g;
+    if (!a_open) {  // closed v: b is open, H_AB = sqrt(2) <a|H|b>, and P(xb) = P(x)
+        vf = h1 * (float)kSqrt2;
+        ev = 1.5f * e1 + fabsf(vf) * 0x1p-21f;
+        g = gx + gx;
+    } else {
+        float h2 = 0.f, e2 = 0.f, g2 = 0.f;  // the element to xb and its generation probability
+        if (i2 >= 0) {
+            h2 = (count_between<W>(a, i2, a2) & 1) ? -hs2 : hs2;
+            e2 = fmaf(hab2, P.serr_f, 1e-30f);
+            const int c2 = (int)__ldg(P.irrep + (i2 >> 1)) * 2 + (i2 & 1);
+            const int c2a = (int)__ldg(P.irrep + (a2 >> 1)) * 2 + (a2 & 1);
+            g2 = c2 == c2a ? __fdiv_rn(P.p_single_f, small_f((unsigned)v.cnt[c2] * v.nok)) : 0.f;
+        } else {
+            unsigned long long hb[W], pb[W];
+            int lb = 0;
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                hb[w] = a[w] & ~xb[w];
+                pb[w] = xb[w] & ~a[w];
+                lb += __popcll(hb[w]);
+            }
+            if (lb == 2) {  // beyond a double both stay 0
+                const int bi = select_bit<W>(hb, 0), bj = select_bit<W>(hb, 1);
+                const int ba = select_bit<W>(pb, 0), bbo = select_bit<W>(pb, 1);
+                h2 = hdouble_f_at<W>(P, a, bi, bj, ba, bbo, keep_policy(), e2);
+                g2 = gen_prob_double_f<W>(P, v, bi, bj, ba, bbo);
+            }
+        }
+        const float hb_f = fl_less ? h2 : h1, hbb_f = fl_less ? h1 : h2;
+        const float eb = fl_less ? e2 : e1, ebb = fl_less ? e1 : e2;
+        if (b_open) {
+            vf = hb_f + (float)pair_sign(n_open<W>(b)) * hbb_f;
+            ev = eb + ebb + fabsf(vf) * 0x1p-21f;
+        } else {
+            vf = hb_f * (float)kSqrt2;
+            ev = 1.5f * eb + fabsf(vf) * 0x1p-21f;
+        }
+        g = det_same<W>(xb, x) ? gx : gx + g2;
+    }
+    const float ah_lo = fabsf(vf) - ev, ah_hi = fabsf(vf) + ev;
+    const int n = decide_spawn(__fdiv_rn(ah_lo * P.tau_f, g) * kDown, __fdiv_rn(ah_hi * P.tau_f, g) * kUp, q,
+                               P.srange_f);
+    if (n == 0) return;
+    if (n > 0) {
+        emit_spawn<W>(P, v, b, n, vf > 0.f ? 1 : -1, cnt, out);  // |vf| > ev: the sign of H_AB
+        return;
+    }
+    atomicAdd(&P.st->exact_spawn, 1ull);  // undecided by the float bounds
+    hphf_exact<W>(P, v, x, xb, b, q + P.d53, true, cnt, out);
+}
+
 // One spawning attempt per lane (active lanes only); called by all 32 lanes of a warp.
 template <int W, bool TAB, int MODE>
 __device__ __forceinline__ void spawn_attempt(const Params &P, const Tables &T, const DetView<W> &v,
                                               const HeavyTab *tab, const float *rcpf, bool active, unsigned a,
                                               unsigned iter, unsigned long long *cnt, SpawnQueue<W> &out) {
     const unsigned long long pol = keep_policy();
-    int i = 0, ao = 0;
+    int i = 0, ao = 0, i1 = 0, a1 = 0, i2 = -1, a2 = -1;
     unsigned mallow = 0;
     unsigned long long q = 0;
     bool pend = false;
-    if (active) pend = attempt_begin<W, TAB, MODE>(P, T, v, tab, rcpf, a, iter, pol, cnt, out, i, ao, mallow, q);
+    if (active)
+        pend = attempt_begin<W, TAB, MODE>(P, T, v, tab, rcpf, a, iter, pol, cnt, out, i, ao, mallow, q, i1, a1, i2, a2);
     float hs = 0.f, hab = 0.f;
-    single_elements_warp<W>(P, &v, pend, i, ao, pol, hs, hab);
-    if (pend) attempt_single_end<W>(P, v, i, ao, mallow, q, hs, hab, cnt, out);
+    single_elements_warp<W>(P, &v, pend, i1, a1, pol, hs, hab);
+    if (MODE & 2) {
+        float hs2 = 0.f, hab2 = 0.f;
+        single_elements_warp<W>(P, &v, pend && i2 >= 0, i2, a2, pol, hs2, hab2);
+        if (pend) hphf_single_end<W>(P, v, i, ao, i1, a1, i2, a2, mallow, q, hs, hab, hs2, hab2, cnt, out);
+    } else if (pend) {
+        attempt_single_end<W>(P, v, i, ao, mallow, q, hs, hab, cnt, out);
+    }
 }
 
 // ---------------------------------------------------------------------------- death / cloning (Eq. 4)
