@@ -37,13 +37,17 @@
  *     (attempt, tag, fingerprint lo, fingerprint hi); fingerprint = Algorithm 1
  *     (p = 1099511628211, uint64 wraparound, no abs/mod) over the ascending
  *     occupied spin orbitals with a Philox-generated orbital map;
- *   - random choices among n options by rank selection, k = floor(r n / 2^64),
- *     instead of redraw loops (same distribution, fixed draw count);
+ *   - one Philox block (words r0, r1) per attempt: the top 53 bits of r0 make
+ *     the type word, the other 75 bits R = r1 2^11 + (r0 mod 2^11) the choices;
+ *   - random choices among n_1, n_2, ... options as the successive digits of R
+ *     in mixed radix, k = floor(R n / 2^75) and then R <- R n mod 2^75,
+ *     instead of redraw loops (the digits are uniform and independent within a
+ *     relative bias of n_1 n_2 ... / 2^75, below 2^-51 for every supported size);
  *   - single/double choice: double iff (r0 >> 11) < floor(P_double 2^53), and
  *     P_double itself is the double/single ratio of the reference rounded to a
  *     multiple of 2^-53 so that the draw realises it exactly; the same word,
  *     uniform within the chosen type's sub-range, realises the Bernoulli part
- *     of the spawn (two Philox blocks per attempt);
+ *     of the spawn;
  *   - initiator: |C_i| > threshold, or D_i is the reference;
  *   - shift: S <- S - zeta/(A tau) ln(N_w(n) / N_w(n-A)) every A iterations
  *     once N_w first reaches the target.
@@ -95,10 +99,26 @@ static void draw2(uint32_t a, uint32_t tag, uint64_t fp, uint32_t seed, uint32_t
     *w1 = (uint64_t)o[2] | ((uint64_t)o[3] << 32);
 }
 
-/* k = floor(r * n / 2^64): uniform choice in [0, n) from a 64-bit word. */
-static uint64_t rank_of(uint64_t r, uint64_t n)
+/* Next digit of the 75-bit choice word R in mixed radix: k = floor(R n / 2^75), uniform in [0, n);
+ * R keeps the remainder R n mod 2^75 for the next choice. */
+static uint64_t next_digit(unsigned __int128 *R, uint64_t n)
 {
-    return (uint64_t)(((unsigned __int128)r * (unsigned __int128)n) >> 64);
+    const unsigned __int128 x = *R * (unsigned __int128)n;
+    *R = x & ((((unsigned __int128)1) << 75) - 1);
+    return (uint64_t)(x >> 75);
+}
+
+/* The choice word of an attempt from its Philox words (r0, r1). */
+static unsigned __int128 choice_word(uint64_t r0, uint64_t r1)
+{
+    return ((unsigned __int128)r1 << 11) | (unsigned __int128)(r0 & 0x7FFu);
+}
+
+/* Digits k[0..m) of the choice word of (r0, r1) for the radices n[0..m) (tests). */
+void oq_digits(uint64_t r0, uint64_t r1, const uint64_t *n, int m, uint64_t *k)
+{
+    unsigned __int128 R = choice_word(r0, r1);
+    for (int x = 0; x < m; ++x) k[x] = next_digit(&R, n[x]);
 }
 
 /* u = (r >> 11) * 2^-53, exactly representable, in [0, 1). */
@@ -725,24 +745,24 @@ static void sbuf_push(sbuf_t *b, int W, const uint64_t *d, int64_t amt, int flag
 static int64_t attempt_one(const oq_t *q, const uint64_t *d, int32_t c, uint64_t fp, uint32_t a,
                            uint64_t *child, int *is_null, int *err)
 {
-    uint64_t r0, r1, r2, r3;
+    uint64_t r0, r1;
     *is_null = 0;
     draw2(a, 0u, fp, q->seed, q->iter, &r0, &r1);
-    draw2(a, 1u, fp, q->seed, q->iter, &r2, &r3);
+    unsigned __int128 R = choice_word(r0, r1);
     int type = (r0 >> 11) < q->d53 ? 2 : 1;
     int64_t info[10];
     /* stage option counts depend on the earlier choices, so the generator is queried stage by stage */
     oq_excite_ranks(q, d, type, 0, 0, 0, child, info);
     if (info[1] == 0) { *is_null = 1; return 0; }
-    uint64_t k1 = rank_of(r1, (uint64_t)info[1]);
+    uint64_t k1 = next_digit(&R, (uint64_t)info[1]);
     oq_excite_ranks(q, d, type, k1, 0, 0, child, info);
     if (info[2] == 0) { *is_null = 1; return 0; }
-    uint64_t k2 = rank_of(r2, (uint64_t)info[2]);
+    uint64_t k2 = next_digit(&R, (uint64_t)info[2]);
     uint64_t k3 = 0;
     if (type == 2) {
         oq_excite_ranks(q, d, type, k1, k2, 0, child, info);
         if (info[3] == 0) { *is_null = 1; return 0; }
-        k3 = rank_of(r3, (uint64_t)info[3]);
+        k3 = next_digit(&R, (uint64_t)info[3]);
     }
     int kind = oq_excite_ranks(q, d, type, k1, k2, k3, child, info);
     if (kind == 0) { *is_null = 1; return 0; }

@@ -52,6 +52,7 @@ def lib():
                                 ctypes.c_double, u64p]
         L.oq_destroy.argtypes = [ctypes.c_void_p]
         L.oq_philox.argtypes = [P(ctypes.c_uint32), P(ctypes.c_uint32), P(ctypes.c_uint32)]
+        L.oq_digits.argtypes = [ctypes.c_uint64, ctypes.c_uint64, u64p, ctypes.c_int, u64p]
         L.oq_log.restype = ctypes.c_double
         L.oq_log.argtypes = [ctypes.c_double]
         L.oq_fingerprint.restype = ctypes.c_uint64
@@ -109,6 +110,14 @@ def philox(ctr, key) -> list[int]:
     o = (ctypes.c_uint32 * 4)()
     lib().oq_philox(c, k, o)
     return list(o)
+
+
+def digits(r0: int, r1: int, radices) -> list[int]:
+    """Successive mixed-radix digits of the choice word of one attempt's Philox words (r0, r1)."""
+    n = np.ascontiguousarray(radices, dtype=np.uint64)
+    k = np.zeros(len(n), dtype=np.uint64)
+    lib().oq_digits(r0, r1, _p(n, ctypes.c_uint64), len(n), _p(k, ctypes.c_uint64))
+    return [int(x) for x in k]
 
 
 def log(x: float) -> float:

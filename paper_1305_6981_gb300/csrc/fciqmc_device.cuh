@@ -135,12 +135,21 @@ __device__ __forceinline__ void draw2(unsigned a, unsigned tag, unsigned long lo
     w1 = (unsigned long long)o.z | ((unsigned long long)o.w << 32);
 }
 
-// floor(r * n / 2^64): uniform rank in [0, n). With n < 2^32, r n = r_hi n 2^32 + r_lo n and the
-// low product only contributes floor(r_lo n / 2^32) to the carry, so two 32x32 products suffice.
-__device__ __forceinline__ unsigned rank_of(unsigned long long r, unsigned n) {
-    const unsigned long long hi = (unsigned long long)(unsigned)(r >> 32) * n;
-    const unsigned long long lo = __umulhi((unsigned)r, n);
-    return (unsigned)((hi + lo) >> 32);
+// The choices of an attempt are the successive digits of its 75-bit choice word R = rh 2^11 + rl (rl < 2^11)
+// in mixed radix: k = floor(R n / 2^75), uniform in [0, n), and R becomes R n mod 2^75. With
+// S = rh n + floor(rl n / 2^11) (at most 85 bits), k = floor(S / 2^64), the new rh = S mod 2^64 and the new
+// rl = rl n mod 2^11. Every radix is below 2^12 (at most MAXPAIRS = 2016 electron pairs, MAXSO spin
+// orbitals), so rl n fits 32 bits and (rh >> 32) n + 2^33 fits 64.
+static_assert(MAXPAIRS < 4096 && MAXSO < 4096, "choice radices must stay below 2^12");
+__device__ __forceinline__ unsigned rank_next(unsigned long long &rh, unsigned &rl, unsigned n) {
+    const unsigned long long lo = (unsigned long long)(unsigned)rh * n;
+    const unsigned long long hi = (unsigned long long)(unsigned)(rh >> 32) * n;
+    const unsigned q = rl * n;
+    const unsigned long long s0 = (lo & 0xFFFFFFFFull) + (q >> 11);
+    const unsigned long long sh = hi + (lo >> 32) + (s0 >> 32);
+    rh = (sh << 32) | (s0 & 0xFFFFFFFFull);
+    rl = q & 0x7FFu;
+    return (unsigned)(sh >> 32);
 }
 
 // ---------------------------------------------------------------------------

@@ -524,9 +524,10 @@ __device__ void hphf_attempt_end(const Params &P, const DetView<W> &v, const uns
 }
 
 // First part of attempt a from determinant v (Eq. 3 with the generator of Sec. VI). Random numbers:
-// two Philox blocks keyed by (seed, iteration), counter (a, tag 0/1, fingerprint). The type word r0
-// also realises the Bernoulli part of the spawn: given the type, t = r0 >> 11 is uniform on
-// [0, d53) for a double and on [d53, 2^53) for a single. A double is completed here; a single is
+// one Philox block keyed by (seed, iteration), counter (a, tag 0, fingerprint), words (r0, r1). The
+// type word t = r0 >> 11 also realises the Bernoulli part of the spawn: given the type, t is uniform on
+// [0, d53) for a double and on [d53, 2^53) for a single. The other 75 bits, r1 2^11 + (r0 mod 2^11),
+// give the choices as mixed-radix digits (rank_next). A double is completed here; a single is
 // selected (electron i, virtual ao) and returned pending (true) for the warp to evaluate its element.
 template <int W, bool TAB, int MODE>
 __device__ __forceinline__ bool attempt_begin(const Params &P, const Tables &T, const DetView<W> &v,
@@ -534,18 +535,18 @@ __device__ __forceinline__ bool attempt_begin(const Params &P, const Tables &T, 
                                               unsigned long long pol, unsigned long long *cnt, SpawnQueue<W> &out,
                                               int &i_out, int &a_out, unsigned &mallow_out, unsigned long long &q_out,
                                               int &i1_out, int &a1_out, int &i2_out, int &a2_out) {
-    unsigned long long r0, r1, r2, r3;
-    draw2(a, 0u, v.fp, P.seed, iter, r0, r1);
-    draw2(a, 1u, v.fp, P.seed, iter, r2, r3);
+    unsigned long long r0, rh;
+    draw2(a, 0u, v.fp, P.seed, iter, r0, rh);
     const unsigned long long t = r0 >> 11;
+    unsigned rl = (unsigned)r0 & 0x7FFu;  // choice word R = rh 2^11 + rl
     if (t >= P.d53) {
         // single excitation (Sec. VI A): i uniform over the N - delta_s electrons with M_allow > 0, a
         // uniform over the unoccupied spin orbitals of i's class
         if (v.nok == 0) { cnt[C_NULLS]++; return false; }
-        const int i = v.occ[select64(v.okm, (int)rank_of(r1, v.nok))];
+        const int i = v.occ[select64(v.okm, (int)rank_next(rh, rl, v.nok))];
         const int ci = T.irrep[i >> 1] * 2 + (i & 1);
         const unsigned mallow = v.cnt[ci];
-        const int k2 = (int)rank_of(r2, mallow);
+        const int k2 = (int)rank_next(rh, rl, mallow);
         int ao;
         if (TAB) {
             ao = tab->ulist[ci][k2];
@@ -614,7 +615,7 @@ __device__ __forceinline__ bool attempt_begin(const Params &P, const Tables &T, 
     // double excitation (Sec. VI B): pair by inverse triangular index, a among the "good" unoccupied
     // orbitals of allowed spin, b from the class fixed by symmetry (Eq. sym1) and spin
     if (P.npairs == 0) { cnt[C_NULLS]++; return false; }
-    const unsigned short pr = T.pairs[rank_of(r1, (unsigned)P.npairs)];
+    const unsigned short pr = T.pairs[rank_next(rh, rl, (unsigned)P.npairs)];
     const int i = v.occ[pr & 0xFF], j = v.occ[pr >> 8];
     const int si = i & 1, sj = j & 1;
     const int gij = T.irrep[i >> 1] ^ T.irrep[j >> 1];
@@ -624,12 +625,12 @@ __device__ __forceinline__ bool attempt_begin(const Params &P, const Tables &T, 
         const int e = (si == sj ? si : 2) * 8 + gij;
         G = tab->G[e];
         if (G == 0) { cnt[C_NULLS]++; return false; }
-        ao = tab->glist[e][rank_of(r2, G)];
+        ao = tab->glist[e][rank_next(rh, rl, G)];
     } else {
         unsigned long long gm[W];
         G = good_set<W>(P, v, si, sj, gij, gm);
         if (G == 0) { cnt[C_NULLS]++; return false; }
-        ao = select_bit<W>(gm, (int)rank_of(r2, G));
+        ao = select_bit<W>(gm, (int)rank_next(rh, rl, G));
     }
     const int ga = T.irrep[ao >> 1];
     const int ca = ga * 2 + (ao & 1);
@@ -637,7 +638,7 @@ __device__ __forceinline__ bool attempt_begin(const Params &P, const Tables &T, 
     const unsigned same = ca == cb ? 1u : 0u;
     const unsigned m_ba = v.cnt[cb] - same;
     const unsigned m_ab = v.cnt[ca] - same;
-    int k3 = (int)rank_of(r3, m_ba);
+    int k3 = (int)rank_next(rh, rl, m_ba);
     int bo;
     if (TAB) {
         if (same && k3 >= tab->urank[ao]) ++k3;  // the list of class cb still holds a

@@ -3,7 +3,8 @@ tau 0.001) grown on the GPU to ~1e8 walkers on ~4e6 determinants, in the launch 
 times (its workload table: 2e8-slot main list, 2^27-entry spawn table). From the grown list, one iteration
 on the GPU and one in the oracle: diagonal elements of the loaded list bit-identical, walker lists
 identical, every integer counter identical, the shift bit-identical, the projected-energy numerator within
-1e-11 relative. The oracle's iteration takes a minute or two on the host cores."""
+1e-11 relative. The oracle's iteration takes a minute or two on the host cores. The same for the
+active-space and spin-coupled workloads at 1e7 target walkers."""
 from __future__ import annotations
 
 import argparse
@@ -26,25 +27,23 @@ def _cuda():
     torch.cuda.set_device(0)
 
 
-def test_one_iteration_at_1e8_walkers():
+def one_iteration(workload: str, target: int = 0):
+    """Grow the benchmark workload on the GPU, then one iteration on the GPU and in the oracle from the
+    same list; returns the GPU row and the loaded list."""
     import bench
-    wl = bench.WORKLOADS["24e60o"]
-    g, _, _, _ = bench.grow(argparse.Namespace(target=0, workload="24e60o"), wl, 0)
+    wl = bench.WORKLOADS[workload]
+    g, _, _, _ = bench.grow(argparse.Namespace(target=target, workload=workload), wl, 0)
     g.step(3)
     d, p, h = g.walkers()
     st = g.state()
-    assert len(p) > 3_000_000 and int(np.abs(p.astype(np.int64)).sum()) > 80_000_000
-    assert int(np.abs(p).max()) > 1_000_000  # the reference: millions of attempts from one determinant
     g.step(1)
     rows_g = g.history(1)
     after = g.walkers()
     g.close()
-    r = rows_g[0]
-    assert r["heavy_attempts"] > r["attempts"] // 2 and r["spawn_events"] > 100_000
 
-    q = Oracle(wl["system"](), tau=wl["tau"], initiator_threshold=wl["thr"], target_walkers=wl["target"],
+    q = Oracle(wl["system"](), tau=wl["tau"], initiator_threshold=wl["thr"], target_walkers=target or wl["target"],
                initial_population=wl["initial_population"], initial_shift=wl["initial_shift"],
-               seed=bench.replica_seed(0))
+               seed=bench.replica_seed(0), **wl.get("space", {}))
     q.set_walkers(d, p, iteration=st["iteration"], shift=st["shift"], vary=bool(st["vary_shift"]),
                   nw_prev=st["nw_last_update"], n_since=st["shift_counter"])
     dq, pq, hq = q.walkers()
@@ -53,3 +52,21 @@ def test_one_iteration_at_1e8_walkers():
     rows_q = q.iterate(1)
     compare_rows(rows_g, rows_q)
     assert same_lists(after, q.walkers())
+    return rows_g[0], p
+
+
+def test_one_iteration_at_1e8_walkers():
+    r, p = one_iteration("24e60o")
+    assert len(p) > 3_000_000 and int(np.abs(p.astype(np.int64)).sum()) > 80_000_000
+    assert int(np.abs(p).max()) > 1_000_000  # the reference: millions of attempts from one determinant
+    assert r["heavy_attempts"] > r["attempts"] // 2 and r["spawn_events"] > 100_000
+
+
+@pytest.mark.parametrize("workload", ["24e60o-cas", "24e60o-hphf"])
+def test_one_iteration_at_1e7_walkers_with_space_or_spin_coupling(workload):
+    """The active-space and spin-coupled workloads of the benchmark at 1e7 target walkers."""
+    r, p = one_iteration(workload, 10_000_000)
+    assert int(np.abs(p.astype(np.int64)).sum()) > 5_000_000
+    assert r["heavy_attempts"] > r["attempts"] // 2 and r["spawn_events"] > 10_000
+    if workload.endswith("cas"):
+        assert r["nulls"] > 0

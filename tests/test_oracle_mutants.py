@@ -43,10 +43,12 @@ MUTANTS = [
     ("hphf_sqrt2_dropped", "if (a_open || b_open) return hab * SQRT2;", "if (a_open || b_open) return hab;"),
     ("hphf_diag_coupling_dropped", "if (!det_eq(q, a, ab)) v = v + pair_sign(q, a) * oq_hij(q, a, ab);", ""),
     ("hphf_projected_sqrt2", "if (q->hphf && n_open(q, d) > 0) h0 = h0 * SQRT2;", ""),
+    ("choice_word_not_advanced", "*R = x & ((((unsigned __int128)1) << 75) - 1);", ""),
+    ("choice_word_low_bits_dropped", " | (unsigned __int128)(r0 & 0x7FFu);", ";"),
     ("gen_prob_double_orders", "return (q->p_double * (double)(m_ba + m_ab)) /", "return (q->p_double * (double)(m_ba + m_ba)) /"),
 ]
 
-FAST_PINS = ("philox or own_log or second_quantisation or symmetry_and_spin or two_words and hamiltonian "
+FAST_PINS = ("philox or choice_digits or own_log or second_quantisation or symmetry_and_spin or two_words and hamiltonian "
              "or pdouble or normalised or eq1 or initiator_rule or on_a_subset or functional_two_words "
              "or membership or outside_the_space or expectation_in_the_space "
              "or spin_flip or projection or probability_of_any_target or spin_coupled or numerator or stored_form")

@@ -49,6 +49,57 @@ def test_philox_known_answers():
     assert n == 3
 
 
+def _split(R: int, top: int = 0) -> tuple[int, int]:
+    """Philox words (r0, r1) whose choice word is the 75-bit R; top fills the type bits of r0."""
+    return (top << 11) | (R & 0x7FF), R >> 11
+
+
+def test_choice_digits_are_the_mixed_radix_expansion():
+    """The attempt's choices are the digits of the uniform fraction x = R / 2^75 in mixed radix
+    (n1, n2, n3): the digits are (k1, k2, k3) exactly when x lies in [c, c + 1/(n1 n2 n3)) with
+    c = ((k1 n2 + k2) n3 + k3) / (n1 n2 n3). Checked at the first R of every cell and the R just below
+    it, with random type bits, in exact integer arithmetic."""
+    rng = np.random.default_rng(21)
+    for radices in ([3], [7, 5], [5, 1, 4], [276, 96, 47], [2016, 128, 64], [3, 2, 2, 5]):
+        total = math.prod(radices)
+        cells = range(total) if total <= 400 else rng.integers(0, total, 300)
+        for cell in cells:
+            cell = int(cell)
+            want, rest = [], cell
+            for n in reversed(radices):
+                want.append(rest % n)
+                rest //= n
+            want = want[::-1]
+            first = -((-cell << 75) // total)  # ceil(cell 2^75 / total)
+            top = int(rng.integers(0, 1 << 53))
+            assert O.digits(*_split(first, top), radices) == want, (radices, cell)
+            if cell > 0:
+                prev = cell - 1
+                got = O.digits(*_split(first - 1, top), radices)
+                exp, rest = [], prev
+                for n in reversed(radices):
+                    exp.append(rest % n)
+                    rest //= n
+                assert got == exp[::-1], (radices, cell)
+
+
+def test_choice_digits_uniform_and_independent():
+    """Over uniform Philox words the joint distribution of three digits is uniform (chi-square over
+    105 cells), so successive choices neither repeat nor correlate."""
+    rng = np.random.default_rng(5)
+    radices = [7, 5, 3]
+    counts = np.zeros(105, dtype=np.int64)
+    n = 60_000
+    words = rng.integers(0, 2**63, size=(n, 2), dtype=np.int64).astype(np.uint64) * np.uint64(2) \
+        + rng.integers(0, 2, size=(n, 2), dtype=np.int64).astype(np.uint64)
+    for r0, r1 in words:
+        k = O.digits(int(r0), int(r1), radices)
+        counts[(k[0] * 5 + k[1]) * 3 + k[2]] += 1
+    e = n / 105
+    chi2 = float(((counts - e) ** 2 / e).sum())
+    assert chi2 < 180.0, chi2  # 104 degrees of freedom: p < 1e-5 beyond 180
+
+
 def test_own_log_accuracy():
     """The shift's logarithm (atanh series) agrees with the correctly rounded ln to 2 ulp."""
     rng = np.random.default_rng(11)

@@ -110,7 +110,9 @@ def test_one_step_expectation_in_the_space(tiny, tiny_space, name):
     chosen = [cand[i] for i in pick] + [REF]
     pops = rng.integers(1, 6, len(chosen)) * rng.choice([-1, 1], len(chosen))
     pops[-1] = 60
-    tau, S = 0.05, -0.4
+    # tau small enough that a spawn rarely carries more than one walker (the variance floor below assumes
+    # outcomes of size one; a single excitation of 8e/8o can have tau |H| / P_gen of several at tau 0.05)
+    tau, S = 0.02, -0.4
     q = O.Oracle(tiny, tau=tau, initial_shift=S, **space)
     E0 = q.info()["E0"]
     c = np.zeros(len(dets))
