@@ -264,8 +264,9 @@ int fciqmc_get_info(const fciqmc_handle *h, fciqmc_info *info);
 #define FCIQMC_N_KERNELS 8
 /* 0 compact_copy, 1 index_clear, 2 index_fill, 3 compact_finish (no-ops unless
  * a compaction is due), 4 sweep (estimators, death, spawning), 5 heavy
- * (spawning from determinants with more than 1024 walkers), 6 annihilate,
- * 7 finish (reductions, shift). */
+ * (spawning from determinants with more than 256 walkers), 6 annihilate (with
+ * the diagonal elements of the determinants it placed in new slots: two
+ * launches), 7 finish (reductions, shift). */
 
 /* Synchronising: runs n_iterations iterations exactly as fciqmc_step does, but
  * launching each kernel individually between CUDA events on the run's stream,

@@ -123,7 +123,7 @@ struct fciqmc_handle {
     char *ws;
     cudaStream_t stream;
     fciqmc_info info;
-    int sweep_grid, heavy_grid, ann_grid, small_grid;
+    int sweep_grid, heavy_grid, ann_grid, diag_grid, small_grid;
     size_t smem_w;
     double e_core;
     cudaGraph_t graph_tmpl;  // one iteration, kept for composing batch graphs
@@ -141,7 +141,7 @@ T *at(fciqmc_handle *h, size_t off) {
 
 template <int W>
 int configure_kernels(fciqmc_handle *h) {
-    FQ_CUDA(cudaFuncSetAttribute(fq::k_annihilate<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem_w));
+    FQ_CUDA(cudaFuncSetAttribute(fq::k_new_diag<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem_w));
     FQ_CUDA(cudaFuncSetAttribute(fq::k_prepare_list<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem_w));
     FQ_CUDA(cudaFuncSetAttribute(fq::k_reference_energy<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem_w));
     int dev = 0, sms = 0, per_sm = 0;
@@ -149,13 +149,16 @@ int configure_kernels(fciqmc_handle *h) {
     FQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     FQ_CUDA(W == 1 ? fq::sweep_occupancy_w1(&per_sm) : fq::sweep_occupancy_w2(&per_sm));
     h->sweep_grid = std::min(kMaxGrid, std::max(1, sms * std::max(per_sm, 1)));
-    FQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fq::k_annihilate<W>, 256, h->smem_w));
+    FQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fq::k_annihilate<W>, 256, 0));
     h->ann_grid = std::min(kMaxGrid, std::max(1, sms * std::max(per_sm, 1)));
+    // k_new_diag: one block per SM (its blocks with no new slot return before loading the pair terms)
+    h->diag_grid = sms;
     h->heavy_grid = std::min(kMaxGrid, sms * 4);
     if (h->grid_request > 0) {
         const int g = std::min(kMaxGrid, h->grid_request);
         h->sweep_grid = std::min(h->sweep_grid, g);
         h->ann_grid = std::min(h->ann_grid, g);
+        h->diag_grid = std::min(h->diag_grid, g);
         h->heavy_grid = std::min(h->heavy_grid, g);
     }
     h->small_grid = std::min(kMaxGrid, sms * 8);
@@ -191,7 +194,8 @@ void enqueue_iteration(fciqmc_handle *h, cudaStream_t s) {
     fq::k_index_fill<W><<<h->small_grid, 256, 0, s>>>(P, 0);
     fq::k_compact_finish<<<1, 32, 0, s>>>(P);
     launch_spawning<W>(h, s);
-    fq::k_annihilate<W><<<h->ann_grid, 256, h->smem_w, s>>>(P);
+    fq::k_annihilate<W><<<h->ann_grid, 256, 0, s>>>(P);
+    fq::k_new_diag<W><<<h->diag_grid, 256, h->smem_w, s>>>(P);
     fq::k_finish<<<1, 32, 0, s>>>(P);
 }
 
@@ -620,7 +624,10 @@ int fciqmc_profile(fciqmc_handle *h, int32_t n_iterations, double *kernel_ms) {
                     case 3: fq::k_compact_finish<<<1, 32, 0, s>>>(P); break;
                     case 4: launch_sweep<1>(h, s); break;
                     case 5: launch_heavy<1>(h, s); break;
-                    case 6: fq::k_annihilate<1><<<h->ann_grid, 256, h->smem_w, s>>>(P); break;
+                    case 6:
+                        fq::k_annihilate<1><<<h->ann_grid, 256, 0, s>>>(P);
+                        fq::k_new_diag<1><<<h->diag_grid, 256, h->smem_w, s>>>(P);
+                        break;
                     default: fq::k_finish<<<1, 32, 0, s>>>(P); break;
                 }
             } else {
@@ -631,7 +638,10 @@ int fciqmc_profile(fciqmc_handle *h, int32_t n_iterations, double *kernel_ms) {
                     case 3: fq::k_compact_finish<<<1, 32, 0, s>>>(P); break;
                     case 4: launch_sweep<2>(h, s); break;
                     case 5: launch_heavy<2>(h, s); break;
-                    case 6: fq::k_annihilate<2><<<h->ann_grid, 256, h->smem_w, s>>>(P); break;
+                    case 6:
+                        fq::k_annihilate<2><<<h->ann_grid, 256, 0, s>>>(P);
+                        fq::k_new_diag<2><<<h->diag_grid, 256, h->smem_w, s>>>(P);
+                        break;
                     default: fq::k_finish<<<1, 32, 0, s>>>(P); break;
                 }
             }

@@ -7,9 +7,11 @@
 
 namespace fq {
 
+// New determinants get a slot, their population and an index entry here; their diagonal elements are
+// computed by k_new_diag over the list of new slots, where every lane of a warp has one (inserting lanes
+// are a minority of each warp here, and H_ii is a long FP64 sum).
 template <int W>
 __global__ void __launch_bounds__(256) k_annihilate(Params P) {
-    extern __shared__ double s_w[];  // [2][M][M] pair terms, then M diagonal h_pp
     __shared__ unsigned long long s_red[(256 / 32) * 4];
     DevState *st = P.st;
     if (st->status) return;
@@ -22,12 +24,9 @@ __global__ void __launch_bounds__(256) k_annihilate(Params P) {
         set_status(st, FCIQMC_ERR_CAPACITY);
         return;
     }
-    const int M = P.n_orb;
-    for (int k = threadIdx.x; k < 2 * M * M; k += blockDim.x) s_w[k] = P.wpair[k];
-    for (int k = threadIdx.x; k < M; k += blockDim.x) s_w[2 * M * M + k] = P.h[k * M + k];
-    __syncthreads();
     const int lb = st->lb, pp = st->pp;
     int *pop_out = P.pop[lb][pp ^ 1];
+    int *new_slots = P.pop[lb][pp];  // the iteration's input populations, no longer read after the sweep
     unsigned long long *det = P.det[lb];
     const unsigned long long imask = (unsigned long long)P.idx_cap - 1ull;
     unsigned long long dnw = 0, dnd = 0, aborted = 0, inserted = 0;
@@ -95,15 +94,13 @@ __global__ void __launch_bounds__(256) k_annihilate(Params P) {
             }
         }
         const long long ns = warp_append(&st->claim, want);
+        const long long nk = warp_append(&st->n_new, want);
         if (want) {
             if (amt > 2147483647LL || amt < -2147483647LL) set_status(st, FCIQMC_ERR_NUMERIC);
-            double v = P.hphf ? hphf_hdiag<W>(P, key, s_w, s_w + 2 * M * M) : hdiag<W>(P, key, s_w, s_w + 2 * M * M);
-            double hdv = __dsub_rn(v, P.E0);
 #pragma unroll
             for (int w = 0; w < W; ++w) det[ns * W + w] = key[w];
-            P.hd[lb][ns] = hdv;
-            P.hdf[lb][ns] = __double2float_rn(hdv);
             pop_out[ns] = (int)amt;
+            new_slots[nk] = (int)ns;
             // publish in the index (distinct keys only: no other thread inserts this determinant)
             for (long long probe = 0; probe < P.idx_cap; ++probe) {
                 unsigned long long *x = P.idx + h * S;
@@ -122,6 +119,33 @@ __global__ void __launch_bounds__(256) k_annihilate(Params P) {
     unsigned long long accv[4] = {dnw, dnd, aborted, inserted};
     unsigned long long *const dst[4] = {&st->d_nw, &st->d_nd, &st->cnt[C_ABORTED], &st->cnt[C_INSERTED]};
     flush_counters<256, 4>(accv, dst, s_red);
+}
+
+// H_ii - E0 (and its nearest float) of the slots placed by k_annihilate this iteration, one per thread in
+// the FP64 order of hdiag / hphf_hdiag, with the pair terms in shared memory.
+template <int W>
+__global__ void __launch_bounds__(256) k_new_diag(Params P) {
+    extern __shared__ double s_w[];  // [2][M][M] pair terms, then M diagonal h_pp
+    DevState *st = P.st;
+    if (st->status) return;
+    const long long n = (long long)st->n_new;
+    if ((long long)blockIdx.x * blockDim.x >= n) return;
+    const int M = P.n_orb;
+    for (int k = threadIdx.x; k < 2 * M * M; k += blockDim.x) s_w[k] = P.wpair[k];
+    for (int k = threadIdx.x; k < M; k += blockDim.x) s_w[2 * M * M + k] = P.h[k * M + k];
+    __syncthreads();
+    const int lb = st->lb, pp = st->pp;
+    const int *new_slots = P.pop[lb][pp];
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const long long s = new_slots[k];
+        unsigned long long key[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) key[w] = P.det[lb][s * W + w];
+        const double v = P.hphf ? hphf_hdiag<W>(P, key, s_w, s_w + 2 * M * M) : hdiag<W>(P, key, s_w, s_w + 2 * M * M);
+        const double hdv = __dsub_rn(v, P.E0);
+        P.hd[lb][s] = hdv;
+        P.hdf[lb][s] = __double2float_rn(hdv);
+    }
 }
 
 // Natural logarithm from the atanh series (shift update); same operation order as the oracle's.
@@ -151,9 +175,14 @@ __device__ double own_log(double x) {
 
 __global__ void k_finish(Params P) {
     DevState *st = P.st;
-    if (threadIdx.x != 0 || st->status) return;
-    double num = 0.0;
-    for (int b = 0; b < P.sweep_grid; ++b) num = __dadd_rn(num, P.partial[b]);
+    if (st->status) return;
+    // Eq. 2 numerator: the sweep blocks' partials summed by one warp in a fixed order (lane k takes
+    // blocks k, k + 32, ..., then a fixed shuffle tree), so the sum is the same in every run
+    const int lane = threadIdx.x & 31;
+    double part = 0.0;
+    for (int b = lane; b < P.sweep_grid; b += 32) part = __dadd_rn(part, P.partial[b]);
+    const double num = warp_sum_f64(part);  // lane 0 holds the total
+    if (threadIdx.x != 0) return;
     const long long nw_in = (long long)st->nw_in, nd_in = (long long)st->nd_in;
     const long long nw_out = nw_in + (long long)st->d_nw, nd_out = nd_in + (long long)st->d_nd;
     fciqmc_row row;
@@ -201,6 +230,7 @@ __global__ void k_finish(Params P) {
     st->nw_in = st->nd_in = 0;
     st->c0_in = 0;
     st->d_nw = st->d_nd = 0;
+    st->n_new = 0;
     for (int k = 0; k < NCNT; ++k) st->cnt[k] = 0;
 }
 

@@ -50,6 +50,7 @@ struct DevState {
     long long est_c0;
     double est_num;
     int check_bad;             // set by the check of a list being loaded
+    unsigned long long n_new;  // determinants placed in new slots this iteration (diagonal elements pending)
 };
 
 // Uniform parameters of a run, passed by value to every kernel.
