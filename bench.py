@@ -45,7 +45,7 @@ METRIC = "spawn attempts/s at 1e8 walkers (24e/60o, initiator, tau 0.001)"
 # those kernels change.
 WARP_INST_PER_ATTEMPT = {"heavy": 11.57, "sweep": 39.8}
 # DRAM bytes (read + write) per launch of each kernel at the full workload, from the same summary.
-DRAM_BYTES_PER_LAUNCH = {"heavy": 22_270_080, "sweep": 118_221_952, "annihilate": 52_127_104}
+DRAM_BYTES_PER_LAUNCH = {"heavy": 22_344_960, "sweep": 118_168_320, "annihilate": 52_243_072}
 ISSUE_PER_CLK_PER_SM = 4  # warp instructions: 4 schedulers per SM, one issue each per clock
 N_SMS = 152
 
