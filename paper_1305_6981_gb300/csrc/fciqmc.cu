@@ -264,7 +264,7 @@ int load_list(fciqmc_handle *h, const DevState &cur, DevState &st0, const uint64
         const unsigned ob = (unsigned)std::max<long long>(1, std::min<long long>((cur.list_len + 255) / 256, h->small_grid));
         int *pos = P.pop[cur.lb][cur.pp ^ 1];  // the old list's idle population buffer
         fq::k_index_locate<W><<<ob, 256, 0, s>>>(P, cur.lb, cur.list_len, pos);
-        fq::k_index_clear_at<<<ob, 256, 0, s>>>(P, pos, cur.list_len);
+        fq::k_index_clear_at<W><<<ob, 256, 0, s>>>(P, pos, cur.list_len);
     } else if (!sparse) {
         fq::k_index_clear<<<h->small_grid, 256, 0, s>>>(P, 1);
     }

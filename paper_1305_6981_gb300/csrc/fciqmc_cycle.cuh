@@ -417,13 +417,10 @@ __global__ void k_index_locate(Params P, int b, long long n, int *pos) {
         unsigned long long h = table_hash<W>(key, kSaltIndex) >> (64 - P.idx_bits);
         int found = -1;
         for (long long probe = 0; probe < P.idx_cap; ++probe) {
-            const unsigned long long *x = P.idx + h * S;
-            bool match = true, empty = true;
-#pragma unroll
-            for (int w = 0; w < W; ++w) {
-                match = match && (x[w] == key[w]);
-                empty = empty && (x[w] == EMPTY);
-            }
+            // the key words of an entry in one 16-byte load (entries are 16- or 32-byte aligned)
+            const ulonglong2 x = *reinterpret_cast<const ulonglong2 *>(P.idx + h * S);
+            const bool match = x.x == key[0] && (W == 1 || x.y == key[W - 1]);
+            const bool empty = x.x == EMPTY && (W == 1 || x.y == EMPTY);
             if (match) { found = (int)h; break; }
             if (empty) break;
             h = (h + 1ull) & imask;
@@ -432,12 +429,16 @@ __global__ void k_index_locate(Params P, int b, long long n, int *pos) {
     }
 }
 
-// Empties the index entries at pos[0, n).
+// Empties the index entries at pos[0, n) with 16-byte stores.
+template <int W>
 __global__ void k_index_clear_at(Params P, const int *pos, long long n) {
+    constexpr int S = Stride<W>::v;
     for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
         const int h = pos[s];
         if (h < 0) continue;
-        for (int w = 0; w < P.idx_stride; ++w) P.idx[(long long)h * P.idx_stride + w] = EMPTY;
+        ulonglong2 *e = reinterpret_cast<ulonglong2 *>(P.idx + (long long)h * S);
+#pragma unroll
+        for (int k = 0; k < S / 2; ++k) e[k] = make_ulonglong2(EMPTY, EMPTY);
     }
 }
 
