@@ -393,15 +393,21 @@ __device__ double hphf_hij(const Params &P, const DetView<W> &v, const unsigned 
 // cannot produce it), within 4 roundings of float, and the matrix element <y|H|v> for a double
 // difference, |H - value| <= err.
 template <int W>
-__device__ float gen_prob_double_f(const Params &P, const DetView<W> &v, int i, int j, int a, int b) {
+__device__ float gen_prob_double_f(const Params &P, const DetView<W> &v, const HeavyTab *tab, int i, int j, int a,
+                                   int b) {
     const int si = i & 1, sj = j & 1;
     if ((a & 1) + (b & 1) != si + sj) return 0.f;
     const int gi = __ldg(P.irrep + (i >> 1)), gj = __ldg(P.irrep + (j >> 1));
     const int ga = __ldg(P.irrep + (a >> 1)), gb = __ldg(P.irrep + (b >> 1));
     if ((ga ^ gb) != (gi ^ gj)) return 0.f;
     if (si == sj && ((a & 1) != si || (b & 1) != si)) return 0.f;
-    unsigned long long gm[W];
-    const long long G = good_set<W>(P, v, si, sj, gi ^ gj, gm);
+    long long G;
+    if (tab) {  // the determinant's tables hold the good-set sizes
+        G = tab->G[(si == sj ? si : 2) * 8 + (gi ^ gj)];
+    } else {
+        unsigned long long gm[W];
+        G = good_set<W>(P, v, si, sj, gi ^ gj, gm);
+    }
     const int ca = ga * 2 + (a & 1), cb = gb * 2 + (b & 1);
     const long long m_ba = (long long)v.cnt[cb] - (ca == cb ? 1 : 0);
     const long long m_ab = (long long)v.cnt[ca] - (ca == cb ? 1 : 0);
@@ -446,9 +452,9 @@ __device__ __forceinline__ void hphf_exact(const Params &P, const DetView<W> &v,
 // everything in FP64. For a closed-shell v the flip of x has the same class counts, so the same
 // generation probability, and H_AB needs only the element to the stored determinant.
 template <int W, bool SP>
-__device__ void hphf_attempt_end(const Params &P, const DetView<W> &v, const unsigned long long (&x)[W],
-                                 unsigned long long t, bool single, float gx, int oi, int oj, int oa, int ob,
-                                 unsigned long long *cnt, SpawnQueue<W> &out) {
+__device__ void hphf_attempt_end(const Params &P, const DetView<W> &v, const HeavyTab *tab,
+                                 const unsigned long long (&x)[W], unsigned long long t, bool single, float gx, int oi,
+                                 int oj, int oa, int ob, unsigned long long *cnt, SpawnQueue<W> &out) {
     unsigned long long xb[W], b[W];
     flip_spins<W>(x, xb);
     const bool fl_less = det_less<W>(xb, x);
@@ -508,7 +514,7 @@ __device__ void hphf_attempt_end(const Params &P, const DetView<W> &v, const uns
                 ev = e1;
             }
             float g = gx;
-            if (lb == 2 && !det_same<W>(xb, x)) g = a_open ? g + gen_prob_double_f<W>(P, v, bi, bj, ba, bbo) : g + g;
+            if (lb == 2 && !det_same<W>(xb, x)) g = a_open ? g + gen_prob_double_f<W>(P, v, tab, bi, bj, ba, bbo) : g + g;
             const float ah_lo = fabsf(vf) - ev, ah_hi = fabsf(vf) + ev;
             const int n = decide_spawn(__fdiv_rn(ah_lo * P.tau_f, g) * kDown, __fdiv_rn(ah_hi * P.tau_f, g) * kUp, t,
                                        P.d53_f);
@@ -661,7 +667,7 @@ __device__ __forceinline__ bool attempt_begin(const Params &P, const Tables &T, 
         // generation probability of this double from the quantities of its selection (as gen_prob_double_f)
         const float gx = __fdiv_rn(P.p_double_f * small_f(m_ba + m_ab),
                                    (float)((long long)P.npairs * (long long)G * (long long)m_ba * (long long)m_ab));
-        hphf_attempt_end<W, (MODE & 1) != 0>(P, v, ch, t, false, gx, i, j, min(ao, bo), max(ao, bo), cnt, out);
+        hphf_attempt_end<W, (MODE & 1) != 0>(P, v, tab, ch, t, false, gx, i, j, min(ao, bo), max(ao, bo), cnt, out);
         return false;
     }
     if (MODE & 1) {  // outside the permitted space: a null excitation (Sec. VI)
@@ -804,7 +810,8 @@ __device__ __forceinline__ void attempt_single_end(const Params &P, const DetVie
 // (i2, a2): H_AB and the generation probability in float with error bounds, the same decision as for
 // determinants; undecided cases evaluate everything in FP64.
 template <int W>
-__device__ __forceinline__ void hphf_single_end(const Params &P, const DetView<W> &v, int i, int ao, int i1, int a1,
+__device__ __forceinline__ void hphf_single_end(const Params &P, const DetView<W> &v, const HeavyTab *tab, int i,
+                                                int ao, int i1, int a1,
                                                 int i2, int a2, unsigned mallow, unsigned long long q, float hs,
                                                 float hab, float hs2, float hab2, unsigned long long *cnt,
                                                 SpawnQueue<W> &out) {
@@ -849,7 +856,7 @@ __device__ __forceinline__ void hphf_single_end(const Params &P, const DetView<W
                 const int bi = select_bit<W>(hb, 0), bj = select_bit<W>(hb, 1);
                 const int ba = select_bit<W>(pb, 0), bbo = select_bit<W>(pb, 1);
                 h2 = hdouble_f_at<W>(P, a, bi, bj, ba, bbo, keep_policy(), e2);
-                g2 = gen_prob_double_f<W>(P, v, bi, bj, ba, bbo);
+                g2 = gen_prob_double_f<W>(P, v, tab, bi, bj, ba, bbo);
             }
         }
         const float hb_f = fl_less ? h2 : h1, hbb_f = fl_less ? h1 : h2;
@@ -892,7 +899,7 @@ __device__ __forceinline__ void spawn_attempt(const Params &P, const Tables &T, 
     if (MODE & 2) {
         float hs2 = 0.f, hab2 = 0.f;
         single_elements_warp<W>(P, &v, pend && i2 >= 0, i2, a2, pol, hs2, hab2);
-        if (pend) hphf_single_end<W>(P, v, i, ao, i1, a1, i2, a2, mallow, q, hs, hab, hs2, hab2, cnt, out);
+        if (pend) hphf_single_end<W>(P, v, tab, i, ao, i1, a1, i2, a2, mallow, q, hs, hab, hs2, hab2, cnt, out);
     } else if (pend) {
         attempt_single_end<W>(P, v, i, ao, mallow, q, hs, hab, cnt, out);
     }
