@@ -109,7 +109,8 @@ class Info(ctypes.Structure):
                 ("reference", ctypes.c_uint64 * 2), ("main_capacity", ctypes.c_int64),
                 ("index_capacity", ctypes.c_int64), ("spawn_capacity", ctypes.c_int64),
                 ("history_capacity", ctypes.c_int64), ("workspace_bytes", ctypes.c_size_t),
-                ("grid_blocks", ctypes.c_int32), ("num_sms", ctypes.c_int32)]
+                ("grid_blocks", ctypes.c_int32), ("num_sms", ctypes.c_int32),
+                ("reference_excitations", ctypes.c_int64)]
 
 
 # every symbol declared in include/fciqmc.h

@@ -42,7 +42,7 @@ int log2_exact(long long x) {
 
 struct Sizes {
     int W, n_so, npairs;
-    long long n_eri, cap, idx_cap, mt_cap, hist_cap, heavy_cap;
+    long long n_eri, cap, idx_cap, mt_cap, hist_cap, heavy_cap, ref_cap;
 };
 
 bool sizes_of(int n_elec, int n_orb, const fciqmc_options &o, Sizes &z) {
@@ -61,12 +61,17 @@ bool sizes_of(int n_elec, int n_orb, const fciqmc_options &o, Sizes &z) {
     // records of determinants with |C| > 256 (a run that needs more stops with FCIQMC_ERR_CAPACITY)
     z.heavy_cap = std::max<long long>(1 << 14, std::min<long long>(z.cap / 2, 1 << 22));
     z.hist_cap = std::max<long long>(o.history_capacity > 0 ? o.history_capacity : (1LL << 16), 16);
+    // the reference's double excitations (plain runs): at most npairs x virtuals x virtuals choices
+    const bool plain = (o.space_flags & 3u) == 0 && !o.frozen_occupied && !o.frozen_empty && !o.hphf;
+    const long long nv = z.n_so - n_elec;
+    z.ref_cap = plain ? std::min<long long>((long long)z.npairs * nv * nv, 1LL << 22) : 0;
     return true;
 }
 
 struct Layout {
     size_t state, h, h_f, eri, eri_f, wpair, map1, cmask, unionm, irrep, pairs, recip, rcpf, ref_occ, facts, e0;
     size_t det[2], hd[2], hdf[2], pop[2][2], idx, mt, merged, heavy, heavy_base, heavy_att, partial, hist;
+    size_t ref_pinfo, ref_off2, ref_exc;
     size_t total;
 };
 
@@ -110,6 +115,9 @@ Layout layout_of(const Sizes &z, int n_orb) {
     L.heavy_att = take(sizeof(unsigned) * z.heavy_cap);
     L.partial = take(sizeof(double) * kMaxGrid);
     L.hist = take(sizeof(fciqmc_row) * z.hist_cap);
+    L.ref_pinfo = take(sizeof(unsigned) * std::max(z.npairs, 1));
+    L.ref_off2 = take(sizeof(unsigned) * std::max<long long>((long long)z.npairs * z.n_so, 1));
+    L.ref_exc = take(sizeof(fq::RefExc) * std::max<long long>(z.ref_cap, 1));
     L.total = off;
     return L;
 }
@@ -544,6 +552,26 @@ int fciqmc_create(const double *h1, const double *eri_s8, double e_core, int n_e
         // the float single-excitation element sums at most 2N - 1 terms, each rounded to float once
         // (relative 2^-24), with at most 2N - 2 float additions; the FP64 sum adds far less
         P.serr_f = (float)((2.0 * n_elec + 2.0) * 0x1.0p-24 * (1.0 + 0x1.0p-6));
+        // the reference's double excitations with their p (plain runs), read by its spawning attempts
+        P.ref_tab = 0;
+        long long n_ref_exc = 0;
+        if (z.ref_cap > 0 && z.npairs > 0) {
+            unsigned *pinfo = at<unsigned>(h, L.ref_pinfo), *off2 = at<unsigned>(h, L.ref_off2);
+            fq::RefExc *ex = at<fq::RefExc>(h, L.ref_exc);
+            if (z.W == 1) fq::k_ref_table<1><<<1, 256, 0, s>>>(P, pinfo, off2, ex, z.ref_cap, facts + 2);
+            else fq::k_ref_table<2><<<1, 256, 0, s>>>(P, pinfo, off2, ex, z.ref_cap, facts + 2);
+            FQ_TRY(cudaGetLastError());
+            FQ_TRY(cudaMemcpyAsync(&n_ref_exc, facts + 2, sizeof(long long), cudaMemcpyDeviceToHost, s));
+            FQ_TRY(cudaStreamSynchronize(s));
+            if (n_ref_exc >= 0) {
+                P.ref_pinfo = pinfo;
+                P.ref_off2 = off2;
+                P.ref_exc = ex;
+                P.ref_tab = 1;
+            } else {
+                n_ref_exc = 0;
+            }
+        }
         // initial state: the reference with the initial population
         DevState st0;
         std::memset(&st0, 0, sizeof(st0));
@@ -587,6 +615,7 @@ int fciqmc_create(const double *h1, const double *eri_s8, double e_core, int n_e
         I.spawn_capacity = z.mt_cap;
         I.history_capacity = z.hist_cap;
         I.workspace_bytes = L.total;
+        I.reference_excitations = n_ref_exc;
         build_graph(h);
     }
 #undef FQ_TRY

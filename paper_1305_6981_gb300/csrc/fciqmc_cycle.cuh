@@ -525,6 +525,101 @@ __global__ void __launch_bounds__(256) k_setup(Params P, long long n_eri, unsign
     }
 }
 
+// The reference table: every double excitation the generator can select from the reference, in the
+// order of attempt_begin (pair k1, the k2-th good a, the k3-th b of its class without a), with
+// p = ((|H| (tau / P_double)) (npairs G M^(b|a) M^(a|b))) (1 / (M^(b|a) + M^(a|b))) as the exact path
+// evaluates it. One block. out = number of excitations, or -1 when they exceed cap or the packing.
+template <int W>
+__global__ void __launch_bounds__(256) k_ref_table(Params P, unsigned *pinfo, unsigned *off2, RefExc *ex,
+                                                   long long cap, long long *out) {
+    __shared__ Tables T;
+    __shared__ DetView<W> v;
+    __shared__ unsigned s_g[MAXPAIRS], s_go[MAXPAIRS], s_eo[MAXPAIRS];
+    __shared__ int s_ok;
+    load_tables(P, T);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int w = 0; w < W; ++w) v.d[w] = P.ref[w];
+        prepare_det<W>(P, T, v, 1);
+    }
+    __syncthreads();
+    const int np = P.npairs;
+    // G and the number of (a, b) choices of every pair
+    for (int k = threadIdx.x; k < np; k += blockDim.x) {
+        const unsigned short pr = T.pairs[k];
+        const int i = v.occ[pr & 0xFF], j = v.occ[pr >> 8];
+        const int si = i & 1, sj = j & 1, gij = T.irrep[i >> 1] ^ T.irrep[j >> 1];
+        unsigned long long gm[W];
+        const unsigned G = (unsigned)good_set<W>(P, v, si, sj, gij, gm);
+        unsigned nx = 0;
+        for (unsigned k2 = 0; k2 < G; ++k2) {
+            const int ao = select_bit<W>(gm, (int)k2);
+            const int ga = T.irrep[ao >> 1];
+            const int ca = ga * 2 + (ao & 1), cb = (gij ^ ga) * 2 + (si + sj - (ao & 1));
+            nx += (unsigned)v.cnt[cb] - (ca == cb ? 1u : 0u);
+        }
+        s_g[k] = G;
+        s_eo[k] = nx;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {  // exclusive prefix sums
+        unsigned long long go = 0, eo = 0;
+        for (int k = 0; k < np; ++k) {
+            const unsigned g = s_g[k], e = s_eo[k];
+            s_go[k] = (unsigned)go;
+            s_eo[k] = (unsigned)eo;
+            go += g;
+            eo += e;
+        }
+        s_ok = (eo <= (unsigned long long)cap && eo < (1ull << 25) && go < (1ull << 24)) ? 1 : 0;
+        *out = s_ok ? (long long)eo : -1;
+    }
+    __syncthreads();
+    if (!s_ok) return;
+    for (int k = threadIdx.x; k < np; k += blockDim.x) {
+        const unsigned short pr = T.pairs[k];
+        const int i = v.occ[pr & 0xFF], j = v.occ[pr >> 8];
+        const int si = i & 1, sj = j & 1, gij = T.irrep[i >> 1] ^ T.irrep[j >> 1];
+        unsigned long long gm[W];
+        const unsigned G = (unsigned)good_set<W>(P, v, si, sj, gij, gm);
+        pinfo[k] = (s_go[k] << 8) | G;
+        unsigned e = s_eo[k];
+        for (unsigned k2 = 0; k2 < G; ++k2) {
+            const int ao = select_bit<W>(gm, (int)k2);
+            const int ga = T.irrep[ao >> 1];
+            const int ca = ga * 2 + (ao & 1), cb = (gij ^ ga) * 2 + (si + sj - (ao & 1));
+            const unsigned same = ca == cb ? 1u : 0u;
+            const unsigned m_ba = v.cnt[cb] - same, m_ab = v.cnt[ca] - same;
+            off2[s_go[k] + k2] = (e << 7) | m_ba;
+            unsigned long long bm[W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) bm[w] = ~v.d[w] & T.mask[cb * MAXW + w];
+            clear_bit<W>(bm, ao);
+            for (unsigned k3 = 0; k3 < m_ba; ++k3, ++e) {
+                const int bo = select_bit<W>(bm, (int)k3);
+                const int A = min(ao, bo), B = max(ao, bo);
+                const double hd = hij_double<W>(P, v.d, i, j, A, B);
+                double p = 0.0;
+                if (hd != 0.0) {
+                    const long long K = (long long)P.npairs * (long long)G * (long long)m_ba * (long long)m_ab;
+                    p = __dmul_rn(__dmul_rn(__dmul_rn(fabs(hd), P.cd), (double)K), P.recip[m_ba + m_ab]);
+                }
+                RefExc r;
+                r.p_lo = __double2float_rd(p);
+                r.p_hi = __double2float_ru(p);
+                r.ps = hd > 0.0 ? p : -p;
+                r.i = (unsigned char)i;
+                r.j = (unsigned char)j;
+                r.a = (unsigned char)ao;
+                r.b = (unsigned char)bo;
+                r.pad = 0;
+                ex[e] = r;
+            }
+        }
+    }
+}
+
 // E0 = H_00 of the reference (needs the pair table built by k_setup).
 template <int W>
 __global__ void k_reference_energy(Params P, double *e0_out) {

@@ -53,6 +53,16 @@ struct DevState {
     unsigned long long n_new;  // determinants placed in new slots this iteration (diagonal elements pending)
 };
 
+// One double excitation of the reference determinant as the generator selects it (pair, good a, b),
+// with its spawning probability p = tau |H| / P_gen in the FP64 order of the exact path: p_lo <= p <= p_hi
+// as floats, ps = p with the sign of H (0 when H = 0), and the spin orbitals i < j (occupied), a, b.
+struct RefExc {
+    float p_lo, p_hi;
+    double ps;
+    unsigned char i, j, a, b;
+    unsigned pad;
+};
+
 // Uniform parameters of a run, passed by value to every kernel.
 struct Params {
     int n_elec, n_orb, n_so, npairs, n_irrep_used;
@@ -88,6 +98,12 @@ struct Params {
     unsigned long long froz_occ[MAXW], froz_emp[MAXW];
     int hphf;                         // walkers on spin-coupled functions (Sec. VI C)
     double p_single_d, p_double_d;    // P_single, P_double as realised by the draw
+    // the reference's double excitations, for runs with neither a permitted space nor spin coupling:
+    // pair k -> (first good-a slot << 8) | G; good-a slot -> (first excitation << 7) | M^(b|a)
+    const unsigned *ref_pinfo;
+    const unsigned *ref_off2;
+    const RefExc *ref_exc;
+    int ref_tab;                      // 1 when those tables are built
     float p_double_f, p_single_f;     // nearest floats of P_double, P_single
     // main list, two buffers for compaction, two population arrays per buffer
     unsigned long long *det[2];

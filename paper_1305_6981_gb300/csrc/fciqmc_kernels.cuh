@@ -42,6 +42,7 @@ struct DetView {
     int c;
     unsigned char nok;          // electrons with at least one symmetry-allowed single (N - delta_s)
     unsigned char flag;         // initiator
+    unsigned char isref;        // the reference determinant
     unsigned char occ[MAXN];
 };
 
@@ -168,6 +169,7 @@ __device__ __forceinline__ void prepare_det(const Params &P, const Tables &T, De
     int ac = c < 0 ? -c : c;
     bool is_ref = det_eq<W>(v.d, P.ref);
     v.flag = (P.init_thr < 0 || ac > P.init_thr || is_ref) ? 1 : 0;
+    v.isref = is_ref ? 1 : 0;
 }
 
 // ---------------------------------------------------------------------------- one spawning attempt
@@ -540,7 +542,7 @@ __device__ __forceinline__ bool attempt_begin(const Params &P, const Tables &T, 
                                               const HeavyTab *tab, const float *rcpf, unsigned a, unsigned iter,
                                               unsigned long long pol, unsigned long long *cnt, SpawnQueue<W> &out,
                                               int &i_out, int &a_out, unsigned &mallow_out, unsigned long long &q_out,
-                                              int &i1_out, int &a1_out, int &i2_out, int &a2_out) {
+                                              int &i1_out, int &a1_out, int &i2_out, int &a2_out, bool rtab) {
     unsigned long long r0, rh;
     draw2(a, 0u, v.fp, P.seed, iter, r0, rh);
     const unsigned long long t = r0 >> 11;
@@ -621,6 +623,34 @@ __device__ __forceinline__ bool attempt_begin(const Params &P, const Tables &T, 
     // double excitation (Sec. VI B): pair by inverse triangular index, a among the "good" unoccupied
     // orbitals of allowed spin, b from the class fixed by symmetry (Eq. sym1) and spin
     if (P.npairs == 0) { cnt[C_NULLS]++; return false; }
+    if (TAB && MODE == 0 && rtab) {  // the reference: the same choices, read with p from its table
+        const unsigned pi = __ldg(P.ref_pinfo + rank_next(rh, rl, (unsigned)P.npairs));
+        const unsigned G = pi & 0xFFu;
+        if (G == 0) { cnt[C_NULLS]++; return false; }
+        const unsigned o2 = __ldg(P.ref_off2 + (pi >> 8) + rank_next(rh, rl, G));
+        const RefExc *e = P.ref_exc + (o2 >> 7) + rank_next(rh, rl, o2 & 0x7Fu);
+        const float2 pb = __ldg(reinterpret_cast<const float2 *>(e));
+        const double ps = __ldg(&e->ps);
+        int n = decide_spawn(pb.x, pb.y, t, P.d53_f);
+        if (n < 0) {
+            atomicAdd(&P.st->exact_spawn, 1ull);
+            const double p = fabs(ps);
+            const double fl = floor(p);
+            if (fl >= 2147483647.0) { set_status(P.st, FCIQMC_ERR_NUMERIC); return false; }
+            n = (int)fl + (__ull2double_rn(t) < __dmul_rn(__dsub_rn(p, fl), P.d53_d) ? 1 : 0);
+        }
+        if (n == 0) return false;
+        const uchar4 o = __ldg(reinterpret_cast<const uchar4 *>(&e->i));
+        unsigned long long child[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) child[w] = v.d[w];
+        flip<W>(child, o.x);
+        flip<W>(child, o.y);
+        flip<W>(child, o.z);
+        flip<W>(child, o.w);
+        emit_spawn<W>(P, v, child, n, ps > 0.0 ? 1 : -1, cnt, out);
+        return false;
+    }
     const unsigned short pr = T.pairs[rank_next(rh, rl, (unsigned)P.npairs)];
     const int i = v.occ[pr & 0xFF], j = v.occ[pr >> 8];
     const int si = i & 1, sj = j & 1;
@@ -886,14 +916,16 @@ __device__ __forceinline__ void hphf_single_end(const Params &P, const DetView<W
 template <int W, bool TAB, int MODE>
 __device__ __forceinline__ void spawn_attempt(const Params &P, const Tables &T, const DetView<W> &v,
                                               const HeavyTab *tab, const float *rcpf, bool active, unsigned a,
-                                              unsigned iter, unsigned long long *cnt, SpawnQueue<W> &out) {
+                                              unsigned iter, unsigned long long *cnt, SpawnQueue<W> &out,
+                                              bool rtab = false) {
     const unsigned long long pol = keep_policy();
     int i = 0, ao = 0, i1 = 0, a1 = 0, i2 = -1, a2 = -1;
     unsigned mallow = 0;
     unsigned long long q = 0;
     bool pend = false;
     if (active)
-        pend = attempt_begin<W, TAB, MODE>(P, T, v, tab, rcpf, a, iter, pol, cnt, out, i, ao, mallow, q, i1, a1, i2, a2);
+        pend = attempt_begin<W, TAB, MODE>(P, T, v, tab, rcpf, a, iter, pol, cnt, out, i, ao, mallow, q, i1, a1, i2, a2,
+                                           rtab);
     float hs = 0.f, hab = 0.f;
     single_elements_warp<W>(P, &v, pend, i1, a1, pol, hs, hab);
     if (MODE & 2) {
@@ -1189,9 +1221,10 @@ __global__ void __launch_bounds__(kTile, 4) k_heavy(Params P) {
         }
         const unsigned a0 = (unsigned)(q - P.heavy_base[r]) * kChunk;
         const unsigned a1 = min(a0 + (unsigned)kChunk, P.heavy_att[r]);
+        const bool rtab = MODE == 0 && P.ref_tab && v.isref;
         for (unsigned base = a0; base < a1; base += 32) {
             const unsigned a = base + lane;
-            spawn_attempt<W, true, MODE>(P, T, v, &tab, s_rcpf, a < a1, a, iter, cnt, sq);
+            spawn_attempt<W, true, MODE>(P, T, v, &tab, s_rcpf, a < a1, a, iter, cnt, sq, rtab);
             flush_queue<W>(P, sq, false);
         }
         __syncwarp();

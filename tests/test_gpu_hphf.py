@@ -70,6 +70,7 @@ def test_heavy_path_24e60o():
     """24e/60o (two words): 5000 walkers on the reference exercise the heavy-determinant path."""
     s = synth.large_24e60o()
     g, q = make_pair(s, 0.001, 3, initial_population=5000, initial_shift=2.0, seed=7, main_capacity=1 << 16)
+    assert g.info()["reference_excitations"] == 0  # tabulated only without spin coupling or a permitted space
     lockstep(g, q, 30)
     d, _, _ = g.walkers()
     assert all(stored(bf.from_words(w), 60) for w in d)

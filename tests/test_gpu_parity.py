@@ -91,6 +91,7 @@ def test_two_words_24e60o_heavy_reference():
     heavy-determinant path."""
     s = synth.large_24e60o()
     g, q = make_pair(s, 0.001, 3, initial_population=5000, initial_shift=2.0, seed=3, main_capacity=1 << 16)
+    assert g.info()["reference_excitations"] > 10_000  # the reference's attempts read its tabulated doubles
     rows_q = []
     for k in range(40):
         g.step(1)
@@ -103,6 +104,7 @@ def test_two_words_24e60o_heavy_reference():
 def test_heavy_path_one_word():
     s = synth.tiny_8e8o()
     g, q = make_pair(s, 0.01, 3, initial_population=20000, initial_shift=0.1, seed=9, main_capacity=1 << 13)
+    assert g.info()["reference_excitations"] > 0
     rows_q = []
     for k in range(30):
         g.step(1)
