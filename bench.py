@@ -216,7 +216,7 @@ def run_reference(args, wl, rank, world):
 
 # ---------------------------------------------------------------------------- GPU arm
 def algorithmic_bytes(W, nd, slots, merged, inserted):
-    """HBM bytes one iteration must move (see DESIGN.md): per occupied determinant its words, population
+    """HBM bytes one iteration must move: per occupied determinant its words, population
     and float diagonal read plus the new population written; per vacated slot its population read and
     written; per distinct spawned determinant the merge entry written and read back with its position,
     one index entry and one population read-modify-write; per insertion the new slot and index entry."""
