@@ -6,7 +6,11 @@ import numpy as np
 
 def canonical(dets: np.ndarray, pops: np.ndarray, hd: np.ndarray | None = None):
     """Walker list sorted by determinant (words as an unsigned big number)."""
-    dets = np.asarray(dets, dtype=np.uint64).reshape(len(pops), -1)
+    dets = np.asarray(dets, dtype=np.uint64)
+    if len(pops) == 0:  # an empty list
+        out = (dets.reshape(0, 0), np.asarray(pops)[:0])
+        return out + (np.asarray(hd)[:0],) if hd is not None else out
+    dets = dets.reshape(len(pops), -1)
     keys = [dets[:, w] for w in range(dets.shape[1])]
     order = np.lexsort(keys)
     out = (dets[order], np.asarray(pops)[order])
