@@ -73,6 +73,10 @@ WORKLOADS = {
                     initial_shift=1.0, max_growth=6000, equilibrate=20,
                     desc="64 independent runs, 8e/16o..16e/40o (seeded), targets log-uniform 1e4..2e6, tau 0.005, "
                          "initiator 3, one CUDA graph per launch vs the same runs advanced one at a time"),
+    "energy16e40o": dict(system=synth.rdm_16e40o, tau=0.0, thr=-1, target=0, main_capacity=0, spawn_capacity=0,
+                         initial_population=0, initial_shift=0.0, max_growth=0, equilibrate=0,
+                         desc="energy functional and density matrices over 1e6 sampled determinants of 16e/40o "
+                              "(--target overrides the number of determinants)"),
     "8e8o": dict(system=synth.tiny_8e8o, tau=0.01, thr=-1, target=1 << 14, main_capacity=1 << 14,
                  spawn_capacity=1 << 14, initial_population=1_000, initial_shift=0.5, max_growth=5_000,
                  equilibrate=50, desc="8e/8o (W=1), no symmetry, plain FCIQMC, tau 0.01, 2^14 target walkers"),
@@ -497,6 +501,7 @@ def energy_functional_timing(n_dets: int = 1_000_000):
     torch.cuda.synchronize()
     t_create = time.perf_counter() - t0
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    torch.cuda.nvtx.range_push("timed")
     ev[0].record()
     E = f.energy(h, v)
     ev[1].record()
@@ -505,6 +510,7 @@ def energy_functional_timing(n_dets: int = 1_000_000):
     f.energy(h, v)
     ev[3].record()
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     info = f.info()
     out = {"n_dets": n_dets, "system": "16e/40o (W=2), amplitudes exp(-level), levels 1..6",
            "energy": float(E), "create_ms": 1e3 * t_create, "forward_ms": ev[0].elapsed_time(ev[1]),
@@ -557,6 +563,15 @@ def main():
         return
     if args.ncu_case:
         run_ncu_case(args, wl)
+        return
+    if args.workload == "energy16e40o":
+        import torch
+        torch.cuda.set_device(0)
+        r = energy_functional_timing(args.target or 1_000_000)
+        print(json.dumps({"metric": "energy functional forward + first backward time (16e/40o sampled vector)",
+                          "value": r["forward_ms"] + r["backward_first_ms"], "unit": "ms", "n_gpus": 1,
+                          "higher_is_better": False, "dtype": "f64", "data": "synthetic",
+                          "config": {"workload": "energy16e40o", "n_dets": r["n_dets"]}, "detail": r}), flush=True)
         return
     if args.workload == "batch64":
         print(json.dumps(run_batch(args, wl)), flush=True)

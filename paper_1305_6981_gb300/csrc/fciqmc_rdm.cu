@@ -362,21 +362,45 @@ struct PairInfo {
     int i, j, a, b;
 };
 
-// Candidate pair t: bucket by binary search over pair offsets, (u < v) by inverse triangular index.
+// Last bucket b in [lo, hi] with poff[b] <= x.
+__device__ __forceinline__ long long bucket_search(const unsigned long long *poff, unsigned long long x, long long lo,
+                                                   long long hi) {
+    while (lo < hi) {
+        const long long mid = (lo + hi + 1) >> 1;
+        if (poff[mid] <= x) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Bucket of pair k * 2^kPairIndexShift for every k (the coarse index of the bucket search).
+constexpr int kPairIndexShift = 8;
+__global__ void k_pair_index(const unsigned long long *poff, long long nb, const RdmState *st, unsigned *idx) {
+    const unsigned long long nk = (st->n_pairs >> kPairIndexShift) + 1;
+    for (unsigned long long k = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; k < nk;
+         k += (unsigned long long)gridDim.x * blockDim.x)
+        idx[k] = (unsigned)bucket_search(poff, k << kPairIndexShift, 0, nb - 1);
+}
+
+// Candidate pair t: bucket by binary search over pair offsets, narrowed by the coarse index when there is
+// one, (u < v) by inverse triangular index (the float square root is a first guess that the integer
+// steps correct).
 template <int W>
-__device__ __forceinline__ PairInfo pair_of(unsigned long long t, long long nb, const unsigned long long *poff,
+__device__ __forceinline__ PairInfo pair_of(unsigned long long t, unsigned long long np, long long nb,
+                                            const unsigned long long *poff, const unsigned *pidx,
                                             const unsigned long long *moff, const unsigned long long *members,
                                             const unsigned long long *dets, unsigned long long (&dI)[W],
                                             unsigned long long (&dJ)[W]) {
     PairInfo P{};
-    long long lo = 0, hi = nb - 1;  // last bucket with poff <= t
-    while (lo < hi) {
-        const long long mid = (lo + hi + 1) >> 1;
-        if (poff[mid] <= t) lo = mid; else hi = mid - 1;
+    long long b_lo = 0, b_hi = nb - 1;
+    if (pidx) {
+        const unsigned long long k = t >> kPairIndexShift;
+        b_lo = pidx[k];
+        if (((k + 1) << kPairIndexShift) < np) b_hi = pidx[k + 1];
     }
+    const long long lo = bucket_search(poff, t, b_lo, b_hi);
     const unsigned long long l = t - poff[lo];
-    unsigned long long v = (unsigned long long)((1.0 + sqrt(1.0 + 8.0 * (double)l)) * 0.5);
-    while (v * (v - 1) / 2 > l) --v;
+    unsigned long long v = (unsigned long long)((1.0f + sqrtf(1.0f + 8.0f * (float)l)) * 0.5f);
+    while (v > 1 && v * (v - 1) / 2 > l) --v;
     while ((v + 1) * v / 2 <= l) ++v;
     const unsigned long long u = l - v * (v - 1) / 2;
     const unsigned long long mu = members[moff[lo] + u], mv = members[moff[lo] + v];
@@ -436,7 +460,7 @@ __device__ __forceinline__ double single_h(const Params &P, const unsigned long 
 template <int W>
 __global__ void __launch_bounds__(kThreads) k_pair_energy(Params P, const unsigned long long *dets, const double *c,
                                                           long long nb, const unsigned long long *poff,
-                                                          const unsigned long long *moff,
+                                                          const unsigned *pidx, const unsigned long long *moff,
                                                           const unsigned long long *members, const RdmState *st,
                                                           double *partial) {
     __shared__ CSum s[kThreads];
@@ -445,7 +469,7 @@ __global__ void __launch_bounds__(kThreads) k_pair_energy(Params P, const unsign
     for (unsigned long long t = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; t < np;
          t += (unsigned long long)gridDim.x * blockDim.x) {
         unsigned long long dI[W], dJ[W];
-        const PairInfo q = pair_of<W>(t, nb, poff, moff, members, dets, dI, dJ);
+        const PairInfo q = pair_of<W>(t, np, nb, poff, pidx, moff, members, dets, dI, dJ);
         if (q.kind == 0) continue;
         const double hv = q.kind == 1 ? single_h<W>(P, dI, q.i, q.a) : fq::hij_double<W>(P, dI, q.i, q.j, q.a, q.b);
         csum_add(acc, __dmul_rn(__dmul_rn(2.0, __dmul_rn(c[q.I], c[q.J])), hv));
@@ -508,14 +532,15 @@ __global__ void k_pair_wpair(Params P, double *wpair) {
 template <int W>
 __global__ void __launch_bounds__(kThreads) k_pair_grad(int n_orb, const unsigned long long *dets, const double *c,
                                                         long long nb, const unsigned long long *poff,
-                                                        const unsigned long long *moff, const unsigned long long *members,
-                                                        RdmState *st, double *gh, double *ge) {
+                                                        const unsigned *pidx, const unsigned long long *moff,
+                                                        const unsigned long long *members, RdmState *st, double *gh,
+                                                        double *ge) {
     const unsigned long long np = st->n_pairs;
     unsigned long long ns = 0, ndb = 0;
     for (unsigned long long t = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; t < np;
          t += (unsigned long long)gridDim.x * blockDim.x) {
         unsigned long long dI[W], dJ[W];
-        const PairInfo q = pair_of<W>(t, nb, poff, moff, members, dets, dI, dJ);
+        const PairInfo q = pair_of<W>(t, np, nb, poff, pidx, moff, members, dets, dI, dJ);
         if (q.kind == 0) continue;
         const double cc = c[q.I] * c[q.J];
         if (q.kind == 1) {
@@ -633,6 +658,7 @@ struct fciqmc_rdm {
     int grid;
     int sms;
     long long nb;  // buckets (host copy after construction)
+    bool pidx_ok;  // the coarse index of the bucket search is built (in the member-cursor buffer)
     RdmState host;
     bool rdm_ready;  // unscaled density matrices computed
 };
@@ -691,6 +717,13 @@ int construct(fciqmc_rdm *r) {
     if (cudaGetLastError() != cudaSuccess) return FCIQMC_ERR_CUDA;
     if (cudaMemcpyAsync(&r->host, st, sizeof(RdmState), cudaMemcpyDeviceToHost, s) != cudaSuccess) return FCIQMC_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return FCIQMC_ERR_CUDA;
+    // coarse index of the bucket search, in the member cursors (no longer needed)
+    r->pidx_ok = r->host.status == 0 && nb > 0 &&
+                 (long long)(r->host.n_pairs >> kPairIndexShift) + 2 <= d.n_keys;
+    if (r->pidx_ok) {
+        k_pair_index<<<g, kThreads, 0, s>>>(poff, nb, st, cursor);
+        if (cudaGetLastError() != cudaSuccess) return FCIQMC_ERR_CUDA;
+    }
     return r->host.status;
 }
 
@@ -706,8 +739,10 @@ void launch_energy(fciqmc_rdm *r, const Params &P, double *e) {
     k_pair_wpair<<<8, kThreads, 0, s>>>(P, const_cast<double *>(P.wpair));
     k_diag_energy<W><<<gd, kThreads, smem, s>>>(P, ptr<unsigned long long>(r, r->L.dets), ptr<double>(r, r->L.c), d.n,
                                                 partial);
+    const unsigned *pidx = r->pidx_ok ? ptr<unsigned>(r, r->L.cursor) : nullptr;
     k_pair_energy<W><<<gd, kThreads, 0, s>>>(P, ptr<unsigned long long>(r, r->L.dets), ptr<double>(r, r->L.c), r->nb,
-                                             ptr<unsigned long long>(r, r->L.poff), ptr<unsigned long long>(r, r->L.moff),
+                                             ptr<unsigned long long>(r, r->L.poff), pidx,
+                                             ptr<unsigned long long>(r, r->L.moff),
                                              ptr<unsigned long long>(r, r->L.members), st, partial + 2 * gd);
     k_energy_finish<<<1, 32, 0, s>>>(partial + 2 * gd, gd, partial, gd, st, e);
 }
@@ -723,8 +758,9 @@ void launch_rdm(fciqmc_rdm *r) {
     cudaMemsetAsync(gh, 0, sizeof(double) * d.n_orb * d.n_orb, s);
     cudaMemsetAsync(ge, 0, sizeof(double) * d.n_eri, s);
     cudaMemsetAsync(occ_pair, 0, sizeof(double) * 4 * d.n_orb * d.n_orb, s);
+    const unsigned *pidx = r->pidx_ok ? ptr<unsigned>(r, r->L.cursor) : nullptr;
     k_pair_grad<W><<<g, kThreads, 0, s>>>(d.n_orb, ptr<unsigned long long>(r, r->L.dets), ptr<double>(r, r->L.c), r->nb,
-                                          ptr<unsigned long long>(r, r->L.poff), ptr<unsigned long long>(r, r->L.moff),
+                                          ptr<unsigned long long>(r, r->L.poff), pidx, ptr<unsigned long long>(r, r->L.moff),
                                           ptr<unsigned long long>(r, r->L.members), st, gh, ge);
     k_diag_grad<W><<<std::min<long long>(g, (d.n + kThreads - 1) / kThreads), kThreads, 0, s>>>(
         2 * d.n_orb, ptr<unsigned long long>(r, r->L.dets), ptr<double>(r, r->L.c), d.n, occ_pair);
