@@ -456,6 +456,54 @@ __device__ __forceinline__ double single_h(const Params &P, const unsigned long 
     return (fq::count_between<W>(d, i, a) & 1) ? -v : v;
 }
 
+// Single-excitation pairs are a few percent of the candidates, and each costs an O(N) FP64 loop: a warp
+// queues its lanes' singles (pair I, J and orbitals i -> a) and evaluates them 32 at a time, so the loop
+// never runs for one lane while 31 wait. The queue order is fixed by the warp's schedule.
+struct SingleQueue {
+    unsigned long long ij[64];  // I | J << 32
+    unsigned short ia[64];      // i | a << 8
+    unsigned n;
+};
+__device__ __forceinline__ void queue_single(SingleQueue &q, bool single, const PairInfo &p) {
+    const unsigned m = __ballot_sync(0xFFFFFFFFu, single);
+    const int lane = threadIdx.x & 31;
+    const unsigned n = q.n;
+    if (single) {
+        const unsigned k = n + __popc(m & ((1u << lane) - 1u));
+        q.ij[k] = (unsigned long long)p.I | ((unsigned long long)p.J << 32);
+        q.ia[k] = (unsigned short)(p.i | (p.a << 8));
+    }
+    __syncwarp();
+    if (lane == 0) q.n = n + __popc(m);
+    __syncwarp();
+}
+// Takes up to 32 queued singles (all when `all`, else only once 32 are queued): lane k gets entry k
+// (take = false for the others); the rest moves to the front.
+__device__ __forceinline__ bool pop_single(SingleQueue &q, bool all, long long &I, long long &J, int &i, int &a) {
+    const int lane = threadIdx.x & 31;
+    const unsigned n = q.n;
+    if (n == 0 || (!all && n < 32)) return false;
+    const unsigned take = min(n, 32u);
+    bool got = false;
+    if ((unsigned)lane < take) {
+        I = (long long)(q.ij[lane] & 0xFFFFFFFFull);
+        J = (long long)(q.ij[lane] >> 32);
+        i = q.ia[lane] & 0xFF;
+        a = q.ia[lane] >> 8;
+        got = true;
+    }
+    __syncwarp();
+    const unsigned rest = n - take;
+    if ((unsigned)lane < rest) {
+        q.ij[lane] = q.ij[take + lane];
+        q.ia[lane] = q.ia[take + lane];
+    }
+    __syncwarp();
+    if (lane == 0) q.n = rest;
+    __syncwarp();
+    return got;
+}
+
 // 2 c_I c_J H_IJ summed over candidate pairs, per block in a fixed order (compensated).
 template <int W>
 __global__ void __launch_bounds__(kThreads) k_pair_energy(Params P, const unsigned long long *dets, const double *c,
@@ -464,16 +512,37 @@ __global__ void __launch_bounds__(kThreads) k_pair_energy(Params P, const unsign
                                                           const unsigned long long *members, const RdmState *st,
                                                           double *partial) {
     __shared__ CSum s[kThreads];
+    __shared__ SingleQueue s_q[kThreads / 32];
+    SingleQueue &sq = s_q[threadIdx.x >> 5];
+    if ((threadIdx.x & 31) == 0) sq.n = 0;
+    __syncwarp();
     const unsigned long long np = st->n_pairs;
     CSum acc{0.0, 0.0};
-    for (unsigned long long t = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; t < np;
-         t += (unsigned long long)gridDim.x * blockDim.x) {
-        unsigned long long dI[W], dJ[W];
-        const PairInfo q = pair_of<W>(t, np, nb, poff, pidx, moff, members, dets, dI, dJ);
-        if (q.kind == 0) continue;
-        const double hv = q.kind == 1 ? single_h<W>(P, dI, q.i, q.a) : fq::hij_double<W>(P, dI, q.i, q.j, q.a, q.b);
-        csum_add(acc, __dmul_rn(__dmul_rn(2.0, __dmul_rn(c[q.I], c[q.J])), hv));
+    auto add_single = [&](bool all) {
+        long long I = 0, J = 0;
+        int i = 0, a = 0;
+        if (pop_single(sq, all, I, J, i, a)) {
+            unsigned long long dI[W];
+            load_det<W>(dets, I, dI);
+            csum_add(acc, __dmul_rn(__dmul_rn(2.0, __dmul_rn(c[I], c[J])), single_h<W>(P, dI, i, a)));
+        }
+    };
+    // warp-uniform loop: lane k takes pair base + k
+    for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < np;
+         base += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long t = base + (threadIdx.x & 31);
+        PairInfo q{};
+        if (t < np) {
+            unsigned long long dI[W], dJ[W];
+            q = pair_of<W>(t, np, nb, poff, pidx, moff, members, dets, dI, dJ);
+            if (q.kind == 2)
+                csum_add(acc, __dmul_rn(__dmul_rn(2.0, __dmul_rn(c[q.I], c[q.J])),
+                                        fq::hij_double<W>(P, dI, q.i, q.j, q.a, q.b)));
+        }
+        queue_single(sq, q.kind == 1, q);
+        add_single(false);
     }
+    add_single(true);  // fewer than 32 remain
     s[threadIdx.x] = acc;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -535,18 +604,22 @@ __global__ void __launch_bounds__(kThreads) k_pair_grad(int n_orb, const unsigne
                                                         const unsigned *pidx, const unsigned long long *moff,
                                                         const unsigned long long *members, RdmState *st, double *gh,
                                                         double *ge) {
+    __shared__ SingleQueue s_q[kThreads / 32];
+    SingleQueue &sq = s_q[threadIdx.x >> 5];
+    if ((threadIdx.x & 31) == 0) sq.n = 0;
+    __syncwarp();
     const unsigned long long np = st->n_pairs;
     unsigned long long ns = 0, ndb = 0;
-    for (unsigned long long t = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; t < np;
-         t += (unsigned long long)gridDim.x * blockDim.x) {
-        unsigned long long dI[W], dJ[W];
-        const PairInfo q = pair_of<W>(t, np, nb, poff, pidx, moff, members, dets, dI, dJ);
-        if (q.kind == 0) continue;
-        const double cc = c[q.I] * c[q.J];
-        if (q.kind == 1) {
+    auto add_single = [&](bool all) {
+        long long Id = 0, Jd = 0;
+        int i = 0, a = 0;
+        if (pop_single(sq, all, Id, Jd, i, a)) {
             ++ns;
-            const double sg = (fq::count_between<W>(dI, q.i, q.a) & 1) ? -cc : cc;
-            const int I = q.i >> 1, A = q.a >> 1;
+            unsigned long long dI[W];
+            load_det<W>(dets, Id, dI);
+            const double cc = c[Id] * c[Jd];
+            const double sg = (fq::count_between<W>(dI, i, a) & 1) ? -cc : cc;
+            const int I = i >> 1, A = a >> 1;
             atomicAdd(&gh[I * n_orb + A], sg);
             atomicAdd(&gh[A * n_orb + I], sg);
 #pragma unroll
@@ -555,13 +628,25 @@ __global__ void __launch_bounds__(kThreads) k_pair_grad(int n_orb, const unsigne
                 while (m) {
                     const int j = 64 * w + __ffsll((long long)m) - 1;
                     m &= m - 1;
-                    if (j == q.i) continue;
+                    if (j == i) continue;
                     const int J = j >> 1;
                     atomicAdd(&ge[fq::eidx(I, A, J, J)], 2.0 * sg);
-                    if ((j & 1) == (q.i & 1)) atomicAdd(&ge[fq::eidx(I, J, J, A)], -2.0 * sg);
+                    if ((j & 1) == (i & 1)) atomicAdd(&ge[fq::eidx(I, J, J, A)], -2.0 * sg);
                 }
             }
-        } else {
+        }
+    };
+    // warp-uniform loop: lane k takes pair base + k
+    for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < np;
+         base += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long t = base + (threadIdx.x & 31);
+        PairInfo q{};
+        unsigned long long dI[W], dJ[W];
+        if (t < np) q = pair_of<W>(t, np, nb, poff, pidx, moff, members, dets, dI, dJ);
+        queue_single(sq, q.kind == 1, q);
+        add_single(false);
+        if (q.kind == 2) {
+            const double cc = c[q.I] * c[q.J];
             ++ndb;
             const double sg = fq::double_parity<W>(dI, q.i, q.j, q.a, q.b) ? -cc : cc;
             if ((q.i & 1) == (q.a & 1) && (q.j & 1) == (q.b & 1))
@@ -570,6 +655,7 @@ __global__ void __launch_bounds__(kThreads) k_pair_grad(int n_orb, const unsigne
                 atomicAdd(&ge[fq::eidx(q.i >> 1, q.b >> 1, q.j >> 1, q.a >> 1)], -2.0 * sg);
         }
     }
+    add_single(true);  // fewer than 32 remain
     if (ns) atomicAdd(&st->n_single, ns);
     if (ndb) atomicAdd(&st->n_double, ndb);
 }
