@@ -661,49 +661,49 @@ __global__ void __launch_bounds__(kThreads) k_pair_grad(int n_orb, const unsigne
 }
 
 // Diagonal contributions: occupation-pair sums O_pq = sum_I c_I^2 n_p n_q over spin orbitals p <= q
-// (p == q gives sum_I c_I^2 n_p), each thread accumulating a fixed strided set of (p, q) in registers
-// over tiles of determinants staged in shared memory, flushed once per block. O is stored at p * n_so + q.
+// (p == q gives sum_I c_I^2 n_p). Each thread walks the occupied pairs of its determinants and adds c_I^2
+// into a block copy of the triangle in shared memory (index q (q + 1) / 2 + p), flushed once per block.
+// O is stored at p * n_so + q.
 template <int W>
 __global__ void __launch_bounds__(kThreads) k_diag_grad(int n_so, const unsigned long long *dets, const double *c,
                                                         long long n, double *occ_pair) {
-    __shared__ unsigned long long s_d[kThreads][W];
-    __shared__ double s_c2[kThreads];
-    constexpr int PER = 33;  // 33 * 256 >= 128 * 129 / 2 triangular entries
+    extern __shared__ double s_o[];
     const int nent = n_so * (n_so + 1) / 2;
-    double acc[PER];
-    int ep[PER], eq[PER];
+    for (int k = threadIdx.x; k < nent; k += blockDim.x) s_o[k] = 0.0;
+    __syncthreads();
+    for (long long I = (long long)blockIdx.x * blockDim.x + threadIdx.x; I < n; I += (long long)gridDim.x * blockDim.x) {
+        unsigned long long d[W];
+        load_det<W>(dets, I, d);
+        const double c2 = c[I] * c[I];
 #pragma unroll
-    for (int r = 0; r < PER; ++r) {
-        acc[r] = 0.0;
-        const int e = threadIdx.x + r * kThreads;
-        int q = 0;
-        while ((q + 1) * (q + 2) / 2 <= e) ++q;  // e = q (q + 1) / 2 + p with p <= q
-        eq[r] = e < nent ? q : -1;
-        ep[r] = e < nent ? e - q * (q + 1) / 2 : -1;
-    }
-    for (long long base = (long long)blockIdx.x * kThreads; base < n; base += (long long)gridDim.x * kThreads) {
-        const long long I = base + threadIdx.x;
+        for (int wq = 0; wq < W; ++wq) {
+            unsigned long long mq = d[wq];
+            while (mq) {
+                const int q = 64 * wq + __ffsll((long long)mq) - 1;
+                mq &= mq - 1;
+                const int row = q * (q + 1) / 2;
 #pragma unroll
-        for (int w = 0; w < W; ++w) s_d[threadIdx.x][w] = I < n ? dets[I * W + w] : 0ull;
-        s_c2[threadIdx.x] = I < n ? c[I] * c[I] : 0.0;
-        __syncthreads();
-#pragma unroll
-        for (int r = 0; r < PER; ++r) {
-            const int p = ep[r], q = eq[r];
-            if (q < 0) continue;
-            double a = acc[r];
-            for (int k = 0; k < kThreads; ++k) {
-                const unsigned long long wp = (W == 1 || p < 64) ? s_d[k][0] : s_d[k][W - 1];
-                const unsigned long long wq = (W == 1 || q < 64) ? s_d[k][0] : s_d[k][W - 1];
-                if (((wp >> (p & 63)) & (wq >> (q & 63)) & 1ull) != 0ull) a += s_c2[k];
+                for (int wp = 0; wp <= wq; ++wp) {
+                    unsigned long long mp = d[wp];
+                    if (wp == wq) mp &= (q & 63) == 63 ? ~0ull : ((2ull << (q & 63)) - 1ull);  // p <= q
+                    while (mp) {
+                        const int p = 64 * wp + __ffsll((long long)mp) - 1;
+                        mp &= mp - 1;
+                        atomicAdd(&s_o[row + p], c2);
+                    }
+                }
             }
-            acc[r] = a;
         }
-        __syncthreads();
     }
-#pragma unroll
-    for (int r = 0; r < PER; ++r)
-        if (eq[r] >= 0 && acc[r] != 0.0) atomicAdd(&occ_pair[ep[r] * n_so + eq[r]], acc[r]);
+    __syncthreads();
+    for (int k = threadIdx.x; k < nent; k += blockDim.x) {
+        const double v = s_o[k];
+        if (v != 0.0) {
+            int q = 0;
+            while ((q + 1) * (q + 2) / 2 <= k) ++q;
+            atomicAdd(&occ_pair[(k - q * (q + 1) / 2) * n_so + q], v);
+        }
+    }
 }
 
 // Maps the occupation-pair sums onto h and the packed ERIs and scales the whole RDM by 1 / c^T c.
@@ -848,7 +848,8 @@ void launch_rdm(fciqmc_rdm *r) {
     k_pair_grad<W><<<g, kThreads, 0, s>>>(d.n_orb, ptr<unsigned long long>(r, r->L.dets), ptr<double>(r, r->L.c), r->nb,
                                           ptr<unsigned long long>(r, r->L.poff), pidx, ptr<unsigned long long>(r, r->L.moff),
                                           ptr<unsigned long long>(r, r->L.members), st, gh, ge);
-    k_diag_grad<W><<<std::min<long long>(g, (d.n + kThreads - 1) / kThreads), kThreads, 0, s>>>(
+    k_diag_grad<W><<<std::min<long long>(g, (d.n + kThreads - 1) / kThreads), kThreads,
+                     sizeof(double) * d.n_orb * (2 * d.n_orb + 1), s>>>(
         2 * d.n_orb, ptr<unsigned long long>(r, r->L.dets), ptr<double>(r, r->L.c), d.n, occ_pair);
     k_diag_finish<<<1, kThreads, 0, s>>>(d.n_orb, occ_pair, gh, ge, st);
 }
@@ -885,8 +886,11 @@ int fciqmc_rdm_create(int n_elec, int n_orb, const uint64_t *dets_dev, const dou
     }
     r->grid = std::min(kMaxGrid, r->sms * 8);
     const size_t smem = sizeof(double) * (2 * d.n_orb * d.n_orb + d.n_orb);
+    const size_t smem_o = sizeof(double) * d.n_orb * (2 * d.n_orb + 1);  // occupation-pair triangle
     if (cudaFuncSetAttribute(k_diag_energy<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
-        cudaFuncSetAttribute(k_diag_energy<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaFuncSetAttribute(k_diag_energy<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaFuncSetAttribute(k_diag_grad<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_o) != cudaSuccess ||
+        cudaFuncSetAttribute(k_diag_grad<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_o) != cudaSuccess) {
         delete r;
         return FCIQMC_ERR_CUDA;
     }
