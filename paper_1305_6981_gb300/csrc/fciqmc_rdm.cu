@@ -355,6 +355,30 @@ __device__ __forceinline__ void csum_merge(CSum &a, const CSum &b) {
     a.c = __dadd_rn(a.c, b.c);
 }
 
+// Fixed-tree merges (the same order in every run): lanes pairwise by shuffles, then the warps' results.
+__device__ __forceinline__ CSum warp_csum(CSum a) {
+    for (int o = 16; o > 0; o >>= 1) {
+        const CSum b{__shfl_down_sync(0xFFFFFFFFu, a.s, o), __shfl_down_sync(0xFFFFFFFFu, a.c, o)};
+        csum_merge(a, b);
+    }
+    return a;  // lane 0 holds the warp's sum
+}
+// Block sum of every thread's acc into out[0] (sum) and out[1] (running error); s: kThreads / 32 slots.
+__device__ __forceinline__ void block_csum(CSum acc, CSum *s, double *out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    acc = warp_csum(acc);
+    if (lane == 0) s[warp] = acc;
+    __syncthreads();
+    if (warp == 0) {
+        CSum x = lane < kThreads / 32 ? s[lane] : CSum{0.0, 0.0};
+        x = warp_csum(x);
+        if (lane == 0) {
+            out[0] = x.s;
+            out[1] = x.c;
+        }
+    }
+}
+
 // ------------------------------------------------------------------------------------ pairs
 struct PairInfo {
     long long I, J;
@@ -511,7 +535,7 @@ __global__ void __launch_bounds__(kThreads) k_pair_energy(Params P, const unsign
                                                           const unsigned *pidx, const unsigned long long *moff,
                                                           const unsigned long long *members, const RdmState *st,
                                                           double *partial) {
-    __shared__ CSum s[kThreads];
+    __shared__ CSum s[kThreads / 32];
     __shared__ SingleQueue s_q[kThreads / 32];
     SingleQueue &sq = s_q[threadIdx.x >> 5];
     if ((threadIdx.x & 31) == 0) sq.n = 0;
@@ -543,14 +567,7 @@ __global__ void __launch_bounds__(kThreads) k_pair_energy(Params P, const unsign
         add_single(false);
     }
     add_single(true);  // fewer than 32 remain
-    s[threadIdx.x] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        CSum tot{0.0, 0.0};
-        for (int k = 0; k < kThreads; ++k) csum_merge(tot, s[k]);
-        partial[2 * blockIdx.x] = tot.s;
-        partial[2 * blockIdx.x + 1] = tot.c;
-    }
+    block_csum(acc, s, partial + 2 * blockIdx.x);
 }
 
 // c_I^2 H_II per block (pair-term table in shared memory, compensated).
@@ -558,7 +575,7 @@ template <int W>
 __global__ void __launch_bounds__(kThreads) k_diag_energy(Params P, const unsigned long long *dets, const double *c,
                                                           long long n, double *partial) {
     extern __shared__ double s_w[];
-    __shared__ CSum s[kThreads];
+    __shared__ CSum s[kThreads / 32];
     const int M = P.n_orb;
     for (int k = threadIdx.x; k < 2 * M * M; k += blockDim.x) s_w[k] = P.wpair[k];
     for (int k = threadIdx.x; k < M; k += blockDim.x) s_w[2 * M * M + k] = P.h[k * M + k];
@@ -569,22 +586,18 @@ __global__ void __launch_bounds__(kThreads) k_diag_energy(Params P, const unsign
         load_det<W>(dets, I, d);
         csum_add(acc, __dmul_rn(__dmul_rn(c[I], c[I]), fq::hdiag<W>(P, d, s_w, s_w + 2 * M * M)));
     }
-    s[threadIdx.x] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        CSum tot{0.0, 0.0};
-        for (int k = 0; k < kThreads; ++k) csum_merge(tot, s[k]);
-        partial[2 * blockIdx.x] = tot.s;
-        partial[2 * blockIdx.x + 1] = tot.c;
-    }
+    block_csum(acc, s, partial + 2 * blockIdx.x);
 }
 
+// One warp: lane k merges the block partials k, k + 32, ... (diagonal, then pairs), then a fixed tree.
 __global__ void k_energy_finish(const double *pp, int npp, const double *pd, int npd, const RdmState *st, double *e) {
-    if (threadIdx.x != 0) return;
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x >= 32) return;
     CSum tot{0.0, 0.0};
-    for (int b = 0; b < npd; ++b) csum_merge(tot, CSum{pd[2 * b], pd[2 * b + 1]});
-    for (int b = 0; b < npp; ++b) csum_merge(tot, CSum{pp[2 * b], pp[2 * b + 1]});
-    *e = __ddiv_rn(__dadd_rn(tot.s, tot.c), st->norm);
+    for (int b = lane; b < npd; b += 32) csum_merge(tot, CSum{pd[2 * b], pd[2 * b + 1]});
+    for (int b = lane; b < npp; b += 32) csum_merge(tot, CSum{pp[2 * b], pp[2 * b + 1]});
+    tot = warp_csum(tot);
+    if (lane == 0) *e = __ddiv_rn(__dadd_rn(tot.s, tot.c), st->norm);
 }
 
 __global__ void k_pair_wpair(Params P, double *wpair) {
