@@ -43,9 +43,9 @@ METRIC = "spawn attempts/s at 1e8 walkers (24e/60o, initiator, tau 0.001)"
 # full-size launch in the timed region divided by the attempts that launch made), taken with the
 # one-pass command recorded in profiles/counters_24e60o_1e8.txt; they must be re-measured whenever
 # those kernels change.
-WARP_INST_PER_ATTEMPT = {"heavy": 10.68, "sweep": 39.9}
+WARP_INST_PER_ATTEMPT = {"heavy": 10.55, "sweep": 39.9}
 # DRAM bytes (read + write) per launch of each kernel at the full workload, from the same summary.
-DRAM_BYTES_PER_LAUNCH = {"heavy": 25_321_216, "sweep": 118_128_128, "annihilate": 52_217_984}
+DRAM_BYTES_PER_LAUNCH = {"heavy": 25_324_160, "sweep": 118_458_496, "annihilate": 52_211_584}
 ISSUE_PER_CLK_PER_SM = 4  # warp instructions: 4 schedulers per SM, one issue each per clock
 N_SMS = 152
 
