@@ -1,11 +1,13 @@
 """Batched runs (one CUDA graph advancing several independent runs) give exactly the results of the same
-runs advanced one at a time, and the launch-shape options the autotuner varies never change results."""
+runs advanced one at a time, each batched run matches the oracle, and the launch-shape options the autotuner
+varies never change results."""
 from __future__ import annotations
 
 import numpy as np
 import pytest
 
-from parity import same_lists
+from oracle.oracle import Oracle
+from parity import compare_rows, same_lists
 from paper_1305_6981_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -75,3 +77,27 @@ def test_launch_shape_options_do_not_change_results():
         assert same_lists(r1.walkers(), r2.walkers())
         r1.close()
         r2.close()
+
+
+def test_batched_runs_match_the_oracle():
+    """Four uneven runs advanced together by the batch graph: every run's history (counters, shift) and
+    final walker list equal the oracle's for the same system and options."""
+    from paper_1305_6981_gb300 import Batch
+    specs = synth.batch_systems(4, seed=7)
+    for sp in specs:
+        sp["target"] = 4000
+    runs = _runs(specs)
+    batch = Batch(runs, iterations_per_launch=5)
+    batch.step(6)  # 30 iterations each
+    for sp, r in zip(specs, runs):
+        assert r.sync() == 0
+        s = synth.make_system(sp["n_orb"], sp["n_elec"], seed=sp["sys_seed"] % 1000, n_chol=8)
+        q = Oracle(s, tau=0.005, initiator_threshold=3, target_walkers=sp["target"], initial_population=500,
+                   initial_shift=1.0, seed=sp["seed"])
+        rows_q = q.iterate(30)
+        compare_rows(r.history(30), rows_q)
+        assert same_lists(r.walkers(), q.walkers())
+        assert rows_q[-1]["nd_out"] > 20
+    batch.close()
+    for r in runs:
+        r.close()
