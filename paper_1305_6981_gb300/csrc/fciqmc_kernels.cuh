@@ -446,17 +446,18 @@ __device__ __forceinline__ void hphf_exact(const Params &P, const DetView<W> &v,
     emit_spawn<W>(P, v, b, n, hv > 0.0 ? 1 : -1, cnt, out);
 }
 
-// Completes an attempt on spin-coupled functions (Sec. VI C) that generated the determinant x from the
-// stored determinant v: the target function holds x and its flip, its generation probability is the sum
-// of theirs, p = tau |H_AB| / (P(x) + P(xbar)), the Bernoulli part from the type word as for determinants.
-// A double (gx: the float form of its generation probability) is first decided from float bounds of H_AB
-// and of the generation probability; singles, a flip that is a single of v, and undecided cases evaluate
+// Completes a double-excitation attempt on spin-coupled functions (Sec. VI C) that generated the
+// determinant x from the stored determinant v: the target function holds x and its flip, its generation
+// probability is the sum of theirs, p = tau |H_AB| / (P(x) + P(xbar)), the Bernoulli part from the type
+// word as for determinants. The attempt is first decided from float bounds of H_AB and of the generation
+// probability (gx: the float form of x's); a flip that is a single of v and undecided cases evaluate
 // everything in FP64. For a closed-shell v the flip of x has the same class counts, so the same
-// generation probability, and H_AB needs only the element to the stored determinant.
+// generation probability, and H_AB needs only the element to the stored determinant. (Singles are
+// completed by hphf_single_end.)
 template <int W, bool SP>
 __device__ void hphf_attempt_end(const Params &P, const DetView<W> &v, const HeavyTab *tab,
-                                 const unsigned long long (&x)[W], unsigned long long t, bool single, float gx, int oi,
-                                 int oj, int oa, int ob, unsigned long long *cnt, SpawnQueue<W> &out) {
+                                 const unsigned long long (&x)[W], unsigned long long t, float gx, int oi, int oj,
+                                 int oa, int ob, unsigned long long *cnt, SpawnQueue<W> &out) {
     unsigned long long xb[W], b[W];
     flip_spins<W>(x, xb);
     const bool fl_less = det_less<W>(xb, x);
@@ -466,7 +467,7 @@ __device__ void hphf_attempt_end(const Params &P, const DetView<W> &v, const Hea
 #pragma unroll
     for (int w = 0; w < W; ++w) same = same && b[w] == v.d[w];
     if (same || (SP && !in_space<W>(P, b))) { cnt[C_NULLS]++; return; }
-    if (!single) {
+    {
         unsigned long long hb[W], pb[W], a[W], ab[W], bb[W];
         int lb = 0;
 #pragma unroll
@@ -528,7 +529,7 @@ __device__ void hphf_attempt_end(const Params &P, const DetView<W> &v, const Hea
             atomicAdd(&P.st->exact_spawn, 1ull);  // undecided by the float bounds
         }
     }
-    hphf_exact<W>(P, v, x, xb, b, t, single, cnt, out);
+    hphf_exact<W>(P, v, x, xb, b, t, false, cnt, out);
 }
 
 // First part of attempt a from determinant v (Eq. 3 with the generator of Sec. VI). Random numbers:
@@ -697,7 +698,7 @@ __device__ __forceinline__ bool attempt_begin(const Params &P, const Tables &T, 
         // generation probability of this double from the quantities of its selection (as gen_prob_double_f)
         const float gx = __fdiv_rn(P.p_double_f * small_f(m_ba + m_ab),
                                    (float)((long long)P.npairs * (long long)G * (long long)m_ba * (long long)m_ab));
-        hphf_attempt_end<W, (MODE & 1) != 0>(P, v, tab, ch, t, false, gx, i, j, min(ao, bo), max(ao, bo), cnt, out);
+        hphf_attempt_end<W, (MODE & 1) != 0>(P, v, tab, ch, t, gx, i, j, min(ao, bo), max(ao, bo), cnt, out);
         return false;
     }
     if (MODE & 1) {  // outside the permitted space: a null excitation (Sec. VI)
