@@ -66,3 +66,28 @@ def test_product_package_does_not_import_the_oracle():
             src = open(os.path.join(ROOT, "paper_1305_6981_gb300", name)).read()
             assert not re.search(r"^\s*(from|import)\s+oracle", src, flags=re.M), name
             assert "liboracle" not in src and "fciqmc_oracle" not in src, name
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every public struct of include/fciqmc.h has the size and field offsets its ctypes mirror assumes
+    (compiled with the host C compiler; the header is plain C)."""
+    pairs = {"fciqmc_options": _native.Options, "fciqmc_row": _native.Row, "fciqmc_estimates": _native.Estimates,
+             "fciqmc_state": _native.State, "fciqmc_info": _native.Info}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "fciqmc.h"', "int main(void) {"]
+    for cname, py in pairs.items():
+        lines.append(f'    printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'    printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        cname, field, value = line.split()
+        got[(cname, field)] = int(value)
+    for cname, py in pairs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
