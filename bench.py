@@ -384,8 +384,8 @@ def run_gpu(args, wl, rank, world, local_rank):
             "clocks": clk,
             "status": st,
             "exact_path": exact,
-            "gpu_launches": 9 * args.steps,  # per iteration: 4 compaction kernels, sweep, heavy, annihilate,
-                                             # new-slot diagonal elements, finish
+            "gpu_launches": 11 * args.steps,  # per iteration: 6 compaction kernels, sweep, heavy, annihilate,
+                                              # new-slot diagonal elements, finish
         }
     return g, out, info
 

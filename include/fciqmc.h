@@ -265,7 +265,8 @@ int fciqmc_get_info(const fciqmc_handle *h, fciqmc_info *info);
 /* Kernels of one iteration, in launch order (indices into the kernel_ms array
  * of fciqmc_profile). */
 #define FCIQMC_N_KERNELS 8
-/* 0 compact_copy, 1 index_clear, 2 index_fill, 3 compact_finish (no-ops unless
+/* 0 compact_copy, 1 index_clear (three launches: the whole index, or the old
+ * list's entries located then emptied), 2 index_fill, 3 compact_finish (no-ops unless
  * a compaction is due), 4 sweep (estimators, death, spawning), 5 heavy
  * (spawning from determinants with more than 256 walkers), 6 annihilate (with
  * the diagonal elements of the determinants it placed in new slots: two

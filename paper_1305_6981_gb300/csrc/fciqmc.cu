@@ -199,6 +199,8 @@ void enqueue_iteration(fciqmc_handle *h, cudaStream_t s) {
     const Params &P = h->P;
     fq::k_compact_copy<W><<<h->small_grid, 256, 0, s>>>(P);
     fq::k_index_clear<<<h->small_grid, 256, 0, s>>>(P, 0);
+    fq::k_index_locate_old<W><<<h->small_grid, 256, 0, s>>>(P);
+    fq::k_index_clear_old<W><<<h->small_grid, 256, 0, s>>>(P);
     fq::k_index_fill<W><<<h->small_grid, 256, 0, s>>>(P, 0);
     fq::k_compact_finish<<<1, 32, 0, s>>>(P);
     launch_spawning<W>(h, s);
@@ -267,7 +269,8 @@ int load_list(fciqmc_handle *h, const DevState &cur, DevState &st0, const uint64
     st0.lb = b;
     st0.pp = 0;
     FQ_CUDA(cudaMemcpyAsync(P.st, &st0, sizeof(st0), cudaMemcpyHostToDevice, s));
-    const bool sparse = cur.status == 0 && cur.list_len >= 0 && cur.list_len * 16 <= h->z.idx_cap;
+    const bool sparse = cur.status == 0 && cur.list_len >= 0 && cur.list_len * 16 <= h->z.idx_cap &&
+                        h->z.idx_cap <= (1LL << 31);  // positions held as int
     if (sparse && cur.list_len > 0) {
         const unsigned ob = (unsigned)std::max<long long>(1, std::min<long long>((cur.list_len + 255) / 256, h->small_grid));
         int *pos = P.pop[cur.lb][cur.pp ^ 1];  // the old list's idle population buffer
@@ -648,7 +651,11 @@ int fciqmc_profile(fciqmc_handle *h, int32_t n_iterations, double *kernel_ms) {
             if (h->z.W == 1) {
                 switch (k) {
                     case 0: fq::k_compact_copy<1><<<h->small_grid, 256, 0, s>>>(P); break;
-                    case 1: fq::k_index_clear<<<h->small_grid, 256, 0, s>>>(P, 0); break;
+                    case 1:
+                        fq::k_index_clear<<<h->small_grid, 256, 0, s>>>(P, 0);
+                        fq::k_index_locate_old<1><<<h->small_grid, 256, 0, s>>>(P);
+                        fq::k_index_clear_old<1><<<h->small_grid, 256, 0, s>>>(P);
+                        break;
                     case 2: fq::k_index_fill<1><<<h->small_grid, 256, 0, s>>>(P, 0); break;
                     case 3: fq::k_compact_finish<<<1, 32, 0, s>>>(P); break;
                     case 4: launch_sweep<1>(h, s); break;
@@ -662,7 +669,11 @@ int fciqmc_profile(fciqmc_handle *h, int32_t n_iterations, double *kernel_ms) {
             } else {
                 switch (k) {
                     case 0: fq::k_compact_copy<2><<<h->small_grid, 256, 0, s>>>(P); break;
-                    case 1: fq::k_index_clear<<<h->small_grid, 256, 0, s>>>(P, 0); break;
+                    case 1:
+                        fq::k_index_clear<<<h->small_grid, 256, 0, s>>>(P, 0);
+                        fq::k_index_locate_old<2><<<h->small_grid, 256, 0, s>>>(P);
+                        fq::k_index_clear_old<2><<<h->small_grid, 256, 0, s>>>(P);
+                        break;
                     case 2: fq::k_index_fill<2><<<h->small_grid, 256, 0, s>>>(P, 0); break;
                     case 3: fq::k_compact_finish<<<1, 32, 0, s>>>(P); break;
                     case 4: launch_sweep<2>(h, s); break;

@@ -255,13 +255,66 @@ __global__ void k_compact_copy(Params P) {
     }
 }
 
+// Whether a due compaction empties the old list's index entries one by one (a short list: len * 16 <=
+// index capacity, positions held as int) rather than the whole index.
+__device__ __forceinline__ bool sparse_index_clear(const Params &P, const DevState *st) {
+    return st->list_len * 16 <= P.idx_cap && P.idx_cap <= (1LL << 31);
+}
+
+// Empties the whole index: forced (a rebuild), or for a due compaction whose list is too long for the
+// sparse clear below.
 __global__ void k_index_clear(Params P, int force) {
     DevState *st = P.st;
-    if (st->status || (!force && !st->compact_pending)) return;
+    if (st->status || (!force && (!st->compact_pending || sparse_index_clear(P, st)))) return;
     const long long nwords = P.idx_cap * (P.idx_stride);
     ulonglong2 *p = reinterpret_cast<ulonglong2 *>(P.idx);
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < nwords / 2; k += (long long)gridDim.x * blockDim.x)
         p[k] = make_ulonglong2(EMPTY, EMPTY);
+}
+
+// A due compaction with a short list (len * 16 <= index capacity): the old list's entries are emptied one
+// by one instead of clearing the whole index. First every old slot's entry is located (into the old
+// buffer's idle population array: no probe chain is cut before every key is found), then emptied.
+template <int W>
+__global__ void k_index_locate_old(Params P) {
+    DevState *st = P.st;
+    if (st->status || !st->compact_pending || !sparse_index_clear(P, st)) return;
+    constexpr int S = Stride<W>::v;
+    const int lb = st->lb;
+    const long long n = st->list_len;
+    int *pos = P.pop[lb][st->pp ^ 1];
+    const unsigned long long imask = (unsigned long long)P.idx_cap - 1ull;
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
+        unsigned long long key[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) key[w] = P.det[lb][s * W + w];
+        unsigned long long h = table_hash<W>(key, kSaltIndex) >> (64 - P.idx_bits);
+        int found = -1;
+        for (long long probe = 0; probe < P.idx_cap; ++probe) {
+            const ulonglong2 x = *reinterpret_cast<const ulonglong2 *>(P.idx + h * S);
+            const bool match = x.x == key[0] && (W == 1 || x.y == key[W - 1]);
+            const bool empty = x.x == EMPTY && (W == 1 || x.y == EMPTY);
+            if (match) { found = (int)h; break; }
+            if (empty) break;
+            h = (h + 1ull) & imask;
+        }
+        pos[s] = found;
+    }
+}
+template <int W>
+__global__ void k_index_clear_old(Params P) {
+    DevState *st = P.st;
+    if (st->status || !st->compact_pending || !sparse_index_clear(P, st)) return;
+    constexpr int S = Stride<W>::v;
+    const long long n = st->list_len;
+    const int *pos = P.pop[st->lb][st->pp ^ 1];
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
+        const int h = pos[s];
+        if (h < 0) continue;
+        ulonglong2 *e = reinterpret_cast<ulonglong2 *>(P.idx + (long long)h * S);
+#pragma unroll
+        for (int k = 0; k < S / 2; ++k) e[k] = make_ulonglong2(EMPTY, EMPTY);
+    }
 }
 
 // Inserts slots [0, n) of a list buffer into the (cleared) index. force: rebuild the active list
