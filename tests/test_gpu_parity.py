@@ -213,10 +213,13 @@ def test_gpu_run_is_deterministic():
                 assert a[k] == b[k]
 
 
-def test_compaction_preserves_parity():
-    """A run with heavy determinant turnover triggers main-list compaction; parity holds across it."""
+@pytest.mark.parametrize("cap", [1 << 13, 1 << 16])
+def test_compaction_preserves_parity(cap):
+    """A run with heavy determinant turnover triggers main-list compaction; parity holds across it. With
+    2^16 slots (an index of 2^17 entries) the list is always short enough for the old entries to be
+    emptied one by one; with 2^13 slots the longer lists clear the whole index."""
     s = synth.tiny_8e8o()
-    g, q = make_pair(s, 0.05, 3, initial_population=3000, initial_shift=0.0, seed=13, main_capacity=1 << 13)
+    g, q = make_pair(s, 0.05, 3, initial_population=3000, initial_shift=0.0, seed=13, main_capacity=cap)
     rows_q = []
     for k in range(150):
         g.step(1)
