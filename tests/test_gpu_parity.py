@@ -91,7 +91,16 @@ def test_two_words_24e60o_heavy_reference():
     heavy-determinant path."""
     s = synth.large_24e60o()
     g, q = make_pair(s, 0.001, 3, initial_population=5000, initial_shift=2.0, seed=3, main_capacity=1 << 16)
-    assert g.info()["reference_excitations"] > 10_000  # the reference's attempts read its tabulated doubles
+    # the reference's attempts read its tabulated doubles: one entry per choice path of the generator
+    ref = q.info()["ref"]
+    _, _, info = q.excite_ranks(ref, 2, 0, 0, 0)
+    paths = 0
+    for k1 in range(int(info[1])):
+        _, _, i1 = q.excite_ranks(ref, 2, k1, 0, 0)
+        for k2 in range(int(i1[2])):
+            _, _, i2 = q.excite_ranks(ref, 2, k1, k2, 0)
+            paths += int(i2[3])
+    assert g.info()["reference_excitations"] == paths > 100_000
     rows_q = []
     for k in range(40):
         g.step(1)
