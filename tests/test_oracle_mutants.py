@@ -48,7 +48,7 @@ MUTANTS = [
     ("gen_prob_double_orders", "return (q->p_double * (double)(m_ba + m_ab)) /", "return (q->p_double * (double)(m_ba + m_ba)) /"),
 ]
 
-FAST_PINS = ("philox or choice_digits or own_log or second_quantisation or symmetry_and_spin or two_words and hamiltonian "
+FAST_PINS = ("philox or choice_digits or keeps_the_invariants or own_log or second_quantisation or symmetry_and_spin or two_words and hamiltonian "
              "or pdouble or normalised or eq1 or initiator_rule or on_a_subset or functional_two_words "
              "or membership or outside_the_space or expectation_in_the_space "
              "or spin_flip or projection or probability_of_any_target or spin_coupled or numerator or stored_form")
@@ -72,6 +72,7 @@ def test_every_planted_mistake_is_caught():
             [sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_pins.py"),
              os.path.join(ROOT, "tests", "test_oracle_rdm.py"), os.path.join(ROOT, "tests", "test_oracle_space.py"),
              os.path.join(ROOT, "tests", "test_oracle_hphf.py"),
+             os.path.join(ROOT, "tests", "test_oracle_invariants.py"),
              "-x", "-q",
              "-p", "no:cacheprovider", "-k", FAST_PINS],
             env=env, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, cwd=ROOT)
