@@ -624,7 +624,7 @@ __device__ __forceinline__ bool attempt_begin(const Params &P, const Tables &T, 
     // double excitation (Sec. VI B): pair by inverse triangular index, a among the "good" unoccupied
     // orbitals of allowed spin, b from the class fixed by symmetry (Eq. sym1) and spin
     if (P.npairs == 0) { cnt[C_NULLS]++; return false; }
-    if (TAB && MODE == 0 && rtab) {  // the reference: the same choices, read with p from its table
+    if (TAB && (MODE & 1) == 0 && rtab) {  // the reference: the same choices, read with p from its table
         const unsigned pi = __ldg(P.ref_pinfo + rank_next(rh, rl, (unsigned)P.npairs));
         const unsigned G = pi & 0xFFu;
         if (G == 0) { cnt[C_NULLS]++; return false; }
@@ -1222,7 +1222,7 @@ __global__ void __launch_bounds__(kTile, 4) k_heavy(Params P) {
         }
         const unsigned a0 = (unsigned)(q - P.heavy_base[r]) * kChunk;
         const unsigned a1 = min(a0 + (unsigned)kChunk, P.heavy_att[r]);
-        const bool rtab = MODE == 0 && P.ref_tab && v.isref;
+        const bool rtab = (MODE & 1) == 0 && P.ref_tab && v.isref;
         for (unsigned base = a0; base < a1; base += 32) {
             const unsigned a = base + lane;
             spawn_attempt<W, true, MODE>(P, T, v, &tab, s_rcpf, a < a1, a, iter, cnt, sq, rtab);

@@ -70,7 +70,17 @@ def test_heavy_path_24e60o():
     """24e/60o (two words): 5000 walkers on the reference exercise the heavy-determinant path."""
     s = synth.large_24e60o()
     g, q = make_pair(s, 0.001, 3, initial_population=5000, initial_shift=2.0, seed=7, main_capacity=1 << 16)
-    assert g.info()["reference_excitations"] == 0  # tabulated only without spin coupling or a permitted space
+    # the closed-shell reference's attempts read its tabulated doubles (target function and p): one entry per
+    # choice path of the generator
+    ref = q.info()["ref"]
+    _, _, info = q.excite_ranks(ref, 2, 0, 0, 0)
+    paths = 0
+    for k1 in range(int(info[1])):
+        _, _, i1 = q.excite_ranks(ref, 2, k1, 0, 0)
+        for k2 in range(int(i1[2])):
+            _, _, i2 = q.excite_ranks(ref, 2, k1, k2, 0)
+            paths += int(i2[3])
+    assert g.info()["reference_excitations"] == paths > 100_000
     lockstep(g, q, 30)
     d, _, _ = g.walkers()
     assert all(stored(bf.from_words(w), 60) for w in d)

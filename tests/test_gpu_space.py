@@ -74,6 +74,7 @@ def test_active_space_24e60o_heavy_path():
     space = dict(frozen_occupied=core, frozen_empty=deleted, max_seniority=6)
     g, q = make_pair(s, 0.001, 3, space, initial_population=5000, initial_shift=2.0, seed=6,
                      main_capacity=1 << 16)
+    assert g.info()["reference_excitations"] == 0  # not tabulated with a permitted space
     rows = lockstep(g, q, 30)
     assert sum(r["nulls"] for r in rows) > 0
     d, _, _ = g.walkers()
