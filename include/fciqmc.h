@@ -171,9 +171,10 @@ typedef struct {
     int32_t grid_blocks;      /* persistent grid of the sweep kernels */
     int32_t num_sms;
     int64_t reference_excitations; /* double excitations of the reference tabulated with their spawning
-                                      probability (and, on spin-coupled functions, their target
-                                      function) in runs without a permitted space; 0 when not
-                                      tabulated: the reference's attempts read them */
+                                      probability (on spin-coupled functions with their target
+                                      function; with a permitted space those leaving it marked as
+                                      null excitations); 0 when not tabulated: the reference's
+                                      attempts read them */
 } fciqmc_info;
 
 /* Fills the defaults listed in fciqmc_options. */

@@ -61,11 +61,9 @@ bool sizes_of(int n_elec, int n_orb, const fciqmc_options &o, Sizes &z) {
     // records of determinants with |C| > 256 (a run that needs more stops with FCIQMC_ERR_CAPACITY)
     z.heavy_cap = std::max<long long>(1 << 14, std::min<long long>(z.cap / 2, 1 << 22));
     z.hist_cap = std::max<long long>(o.history_capacity > 0 ? o.history_capacity : (1LL << 16), 16);
-    // the reference's double excitations (runs without a permitted space): at most npairs x virtuals x
-    // virtuals choices
-    const bool plain = (o.space_flags & 3u) == 0 && !o.frozen_occupied && !o.frozen_empty;
+    // the reference's double excitations: at most npairs x virtuals x virtuals choices
     const long long nv = z.n_so - n_elec;
-    z.ref_cap = plain ? std::min<long long>((long long)z.npairs * nv * nv, 1LL << 22) : 0;
+    z.ref_cap = std::min<long long>((long long)z.npairs * nv * nv, 1LL << 22);
     return true;
 }
 

@@ -581,8 +581,9 @@ __global__ void __launch_bounds__(256) k_setup(Params P, long long n_eri, unsign
 // The reference table: every double excitation the generator can select from the reference, in the
 // order of attempt_begin (pair k1, the k2-th good a, the k3-th b of its class without a), with
 // p = ((|H| (tau / P_double)) (npairs G M^(b|a) M^(a|b))) (1 / (M^(b|a) + M^(a|b))) as the exact path
-// evaluates it, or for spin-coupled functions the target function and its p (hphf_exact's order). One
-// block. out = number of excitations, or -1 when they exceed cap or the packing.
+// evaluates it, or for spin-coupled functions the target function and its p (hphf_exact's order); with a
+// permitted space, excitations whose target lies outside it are marked as null excitations. One block.
+// out = number of excitations, or -1 when they exceed cap or the packing.
 template <int W>
 __global__ void __launch_bounds__(256) k_ref_table(Params P, unsigned *pinfo, unsigned *off2, RefExc *ex,
                                                    long long cap, long long *out) {
@@ -655,6 +656,7 @@ __global__ void __launch_bounds__(256) k_ref_table(Params P, unsigned *pinfo, un
                 const int A = min(ao, bo), B = max(ao, bo);
                 double hd, p = 0.0;
                 int fl = 0;  // 1: the target is stored on the flip of the generated determinant
+                bool outside = false;  // a null excitation: the target lies outside the permitted space
                 if (P.hphf) {
                     // spin-coupled functions (the reference is closed-shell): target stored on min(x, xbar),
                     // p = (tau |H_AB|) / (P(x) + P(xbar)) as the exact path evaluates it
@@ -669,22 +671,33 @@ __global__ void __launch_bounds__(256) k_ref_table(Params P, unsigned *pinfo, un
                     fl = det_less<W>(xb, x) ? 1 : 0;
 #pragma unroll
                     for (int w = 0; w < W; ++w) b[w] = fl ? xb[w] : x[w];
-                    hd = hphf_hij<W>(P, v, b);
+                    outside = P.space && !in_space<W>(P, b);
+                    hd = outside ? 0.0 : hphf_hij<W>(P, v, b);
                     if (hd != 0.0) {
                         double g = gen_prob<W>(P, v, x);
                         if (!det_same<W>(xb, x)) g = __dadd_rn(g, gen_prob<W>(P, v, xb));
                         p = __ddiv_rn(__dmul_rn(P.tau, fabs(hd)), g);
                     }
                 } else {
-                    hd = hij_double<W>(P, v.d, i, j, A, B);
+                    if (P.space) {
+                        unsigned long long x[W];
+#pragma unroll
+                        for (int w = 0; w < W; ++w) x[w] = v.d[w];
+                        flip<W>(x, i);
+                        flip<W>(x, j);
+                        flip<W>(x, ao);
+                        flip<W>(x, bo);
+                        outside = !in_space<W>(P, x);
+                    }
+                    hd = outside ? 0.0 : hij_double<W>(P, v.d, i, j, A, B);
                     if (hd != 0.0) {
                         const long long K = (long long)P.npairs * (long long)G * (long long)m_ba * (long long)m_ab;
                         p = __dmul_rn(__dmul_rn(__dmul_rn(fabs(hd), P.cd), (double)K), P.recip[m_ba + m_ab]);
                     }
                 }
                 RefExc r;
-                r.p_lo = __double2float_rd(p);
-                r.p_hi = __double2float_ru(p);
+                r.p_lo = outside ? -1.f : __double2float_rd(p);  // a negative bound marks a null excitation
+                r.p_hi = outside ? -1.f : __double2float_ru(p);
                 r.ps = hd > 0.0 ? p : -p;
                 r.i = (unsigned char)(i ^ fl);  // the orbitals whose flips on the reference give the target
                 r.j = (unsigned char)(j ^ fl);

@@ -624,13 +624,16 @@ __device__ __forceinline__ bool attempt_begin(const Params &P, const Tables &T, 
     // double excitation (Sec. VI B): pair by inverse triangular index, a among the "good" unoccupied
     // orbitals of allowed spin, b from the class fixed by symmetry (Eq. sym1) and spin
     if (P.npairs == 0) { cnt[C_NULLS]++; return false; }
-    if (TAB && (MODE & 1) == 0 && rtab) {  // the reference: the same choices, read with p from its table
+    if (TAB && rtab) {  // the reference: the same choices, read with p from its table
         const unsigned pi = __ldg(P.ref_pinfo + rank_next(rh, rl, (unsigned)P.npairs));
         const unsigned G = pi & 0xFFu;
         if (G == 0) { cnt[C_NULLS]++; return false; }
         const unsigned o2 = __ldg(P.ref_off2 + (pi >> 8) + rank_next(rh, rl, G));
         const RefExc *e = P.ref_exc + (o2 >> 7) + rank_next(rh, rl, o2 & 0x7Fu);
         const float2 pb = __ldg(reinterpret_cast<const float2 *>(e));
+        if (MODE & 1) {
+            if (pb.x < 0.f) { cnt[C_NULLS]++; return false; }  // the target lies outside the permitted space
+        }
         const double ps = __ldg(&e->ps);
         int n = decide_spawn(pb.x, pb.y, t, P.d53_f);
         if (n < 0) {
@@ -1222,7 +1225,7 @@ __global__ void __launch_bounds__(kTile, 4) k_heavy(Params P) {
         }
         const unsigned a0 = (unsigned)(q - P.heavy_base[r]) * kChunk;
         const unsigned a1 = min(a0 + (unsigned)kChunk, P.heavy_att[r]);
-        const bool rtab = (MODE & 1) == 0 && P.ref_tab && v.isref;
+        const bool rtab = P.ref_tab && v.isref;
         for (unsigned base = a0; base < a1; base += 32) {
             const unsigned a = base + lane;
             spawn_attempt<W, true, MODE>(P, T, v, &tab, s_rcpf, a < a1, a, iter, cnt, sq, rtab);

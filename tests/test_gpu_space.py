@@ -74,7 +74,17 @@ def test_active_space_24e60o_heavy_path():
     space = dict(frozen_occupied=core, frozen_empty=deleted, max_seniority=6)
     g, q = make_pair(s, 0.001, 3, space, initial_population=5000, initial_shift=2.0, seed=6,
                      main_capacity=1 << 16)
-    assert g.info()["reference_excitations"] == 0  # not tabulated with a permitted space
+    # the reference's attempts read its tabulated doubles, those leaving the space marked as null
+    # excitations: one entry per choice path of the (unrestricted) generator
+    ref = q.info()["ref"]
+    _, _, info = q.excite_ranks(ref, 2, 0, 0, 0)
+    paths = 0
+    for k1 in range(int(info[1])):
+        _, _, i1 = q.excite_ranks(ref, 2, k1, 0, 0)
+        for k2 in range(int(i1[2])):
+            _, _, i2 = q.excite_ranks(ref, 2, k1, k2, 0)
+            paths += int(i2[3])
+    assert g.info()["reference_excitations"] == paths > 100_000
     rows = lockstep(g, q, 30)
     assert sum(r["nulls"] for r in rows) > 0
     d, _, _ = g.walkers()
