@@ -184,7 +184,7 @@ def walker_snapshot(system: System, n_walkers: int, seed: int = 0, ref_fraction:
     aufbau reference holds `ref_fraction` of the walkers; the others sit on distinct determinants
     reached from it by 1..max_level random same-spin substitutions (level L drawn with weight 2^-L)
     that keep the reference's spatial symmetry, with random signs and geometric magnitudes (mean 3).
-    Returns (dets (n, W) uint64, pops (n,) int32)."""
+    A space too small to hold n_walkers that way yields fewer. Returns (dets (n, W) uint64, pops (n,) int32)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     M, N = system.n_orb, system.n_elec
     nh = N // 2
@@ -226,6 +226,7 @@ def walker_snapshot(system: System, n_walkers: int, seed: int = 0, ref_fraction:
         packed = np.packbits(bits, axis=1, bitorder="little")
         mags = rng.geometric(1.0 / 3.0, size=len(keep))
         sgns = np.where(rng.random(len(keep)) < 0.5, 1, -1)
+        added = 0
         for k in range(len(keep)):
             key = packed[k].tobytes()
             if key in seen:
@@ -234,8 +235,11 @@ def walker_snapshot(system: System, n_walkers: int, seed: int = 0, ref_fraction:
             rows.append(bits[k])
             pops.append(int(mags[k] * sgns[k]))
             total += int(mags[k])
+            added += 1
             if total >= n_walkers:
                 break
+        if added == 0 and B >= 1 << 16:
+            break  # a small space is exhausted: fewer walkers than asked for
         B = min(1 << 20, 2 * B)
     bits = np.array(rows)
     dets = np.packbits(bits, axis=1, bitorder="little").view("<u8").astype(np.uint64)

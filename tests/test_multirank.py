@@ -53,3 +53,23 @@ def test_reference_arm_runs_on_rank_zero_only(capsys):
     args = argparse.Namespace(workload="8e8o", steps=1, warmup=0, gpus=2)
     assert bench.run_reference(args, bench.WORKLOADS["8e8o"], 1, 2) is None
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_prints_one_contract_line(capsys):
+    """Rank 0 times the oracle on a sample of the workload and prints one JSON line with the keys the
+    benchmark contract asks of the reference arm."""
+    import json
+    import bench
+    args = argparse.Namespace(workload="8e8o", steps=1, warmup=0, gpus=1)
+    bench.run_reference(args, bench.WORKLOADS["8e8o"], 0, 1)
+    lines = [l for l in capsys.readouterr().out.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["value"] > 0 and d["config"]["workload"] == "8e8o"
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cores"] >= 1 and d["cpu_baseline"]["sample"]
+    assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
+    assert d["e2e"]["d2h_bytes_per_step"] == 0 and d["e2e"]["unit"] == d["unit"]
