@@ -179,8 +179,78 @@ def sample_list(dets, pops, n_walkers, seed=0):
 
 
 # ---------------------------------------------------------------------------- reference arm
+def _reference_line(args, metric, value, unit, higher, config, sample):
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"impl": "reference", "metric": metric, "value": value, "unit": unit, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": higher, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
+            "cpu_baseline": {"value": value, "unit": unit, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def run_reference_batch(args, wl):
+    """The oracle over the 64 uneven runs, one after another, each on a synthetic snapshot of its target
+    population capped at 2e4 walkers: aggregate attempts/s."""
+    from oracle.oracle import Oracle, lib
+    lib()
+    specs = synth.batch_systems(64, seed=3)
+    runs = []
+    for k, sp in enumerate(specs):
+        system = synth.make_system(sp["n_orb"], sp["n_elec"], seed=sp["sys_seed"] % 100000, n_chol=sp["n_orb"] // 2,
+                                   name=f"run{k}")
+        dets, pops = synth.walker_snapshot(system, min(int(sp["target"]), 20_000), seed=7)
+        runs.append((Oracle(system, tau=wl["tau"], initiator_threshold=wl["thr"], seed=sp["seed"]), dets, pops))
+    att, tsum = 0, 0.0
+    for k in range(args.warmup + args.steps):
+        for q, dets, pops in runs:
+            q.set_walkers(dets, pops, iteration=k, shift=0.0)
+            t0 = time.perf_counter()
+            rows = q.iterate(1)
+            if k >= args.warmup:
+                tsum += time.perf_counter() - t0
+                att += rows[0]["attempts"]
+    value = att / tsum
+    walkers = sum(int(np.abs(p).sum()) for _, _, p in runs)
+    out = _reference_line(args, "aggregate spawn attempts/s, 64 uneven independent runs (one graph per launch)",
+                          value, "attempts/s", True, {"workload": "batch64", "system": wl["desc"]},
+                          f"{args.steps} iterations of each of the 64 runs on snapshots of at most 2e4 walkers "
+                          f"({walkers} walkers in total)")
+    out["ms_per_step"] = 1e3 * tsum / max(args.steps, 1)
+    return out
+
+
+def run_reference_energy(args, wl):
+    """The oracle's energy functional and density matrices (one call gives both) on a 5000-determinant
+    sample of the 16e/40o vector: milliseconds per call (at most three timed calls: the oracle's pair
+    search is quadratic in the determinants)."""
+    from oracle.oracle import Oracle, lib
+    lib()
+    n = 5_000
+    s = wl["system"]()
+    dets, c = synth.sampled_vector(s, n, seed=5)
+    q = Oracle(s, tau=0.01)
+    for _ in range(min(args.warmup, 1)):
+        q.rdm_energy(dets, c)
+    calls = min(max(args.steps, 1), 3)
+    t0 = time.perf_counter()
+    for _ in range(calls):
+        q.rdm_energy(dets, c)
+    ms = 1e3 * (time.perf_counter() - t0) / calls
+    out = _reference_line(args, "energy functional forward + first backward time (16e/40o sampled vector)", ms,
+                          "ms", False, {"workload": "energy16e40o", "n_dets": n},
+                          f"{n} of the sampled determinants (the GPU arm uses 1e6)")
+    out["ms_per_step"] = ms
+    return out
+
+
 def run_reference(args, wl, rank, world):
     if rank != 0:
+        return
+    if args.workload == "batch64":
+        print(json.dumps(run_reference_batch(args, wl)), flush=True)
+        return
+    if args.workload == "energy16e40o":
+        print(json.dumps(run_reference_energy(args, wl)), flush=True)
         return
     system = wl["system"]()
     n_sample = 200_000 if args.workload.startswith("24e60o") else 50_000
