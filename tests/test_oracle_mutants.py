@@ -45,10 +45,12 @@ MUTANTS = [
     ("hphf_projected_sqrt2", "if (q->hphf && n_open(q, d) > 0) h0 = h0 * SQRT2;", ""),
     ("choice_word_not_advanced", "*R = x & ((((unsigned __int128)1) << 75) - 1);", ""),
     ("choice_word_low_bits_dropped", " | (unsigned __int128)(r0 & 0x7FFu);", ";"),
+    ("shift_update_sign", "q->shift = q->shift - q->c_shift * oq_log(ratio);",
+     "q->shift = q->shift + q->c_shift * oq_log(ratio);"),
     ("gen_prob_double_orders", "return (q->p_double * (double)(m_ba + m_ab)) /", "return (q->p_double * (double)(m_ba + m_ba)) /"),
 ]
 
-FAST_PINS = ("philox or choice_digits or keeps_the_invariants or own_log or second_quantisation or symmetry_and_spin or two_words and hamiltonian "
+FAST_PINS = ("philox or choice_digits or keeps_the_invariants or holds_the_population or own_log or second_quantisation or symmetry_and_spin or two_words and hamiltonian "
              "or pdouble or normalised or eq1 or initiator_rule or on_a_subset or functional_two_words "
              "or membership or outside_the_space or expectation_in_the_space "
              "or spin_flip or projection or probability_of_any_target or spin_coupled or numerator or stored_form")

@@ -358,6 +358,19 @@ def test_plain_dynamics_reach_fci_energy(tiny, tiny_space):
     assert 4000 <= nw.mean() < 4 * 4000
 
 
+def test_shift_holds_the_population():
+    """Once the walker number reaches the target the shift is varied (Sec. II) and holds the population
+    steady: over the last 300 of 800 iterations of 8e/8o it stays within a factor of two of the target and
+    does not drift."""
+    q = O.Oracle(synth.tiny_8e8o(), tau=0.02, target_walkers=2000, initial_population=500, initial_shift=0.1,
+                 seed=5)
+    rows = q.iterate(800)
+    assert q.state()["vary"]
+    nw = np.array([r["nw_out"] for r in rows[-300:]], dtype=float)
+    assert 1000 <= nw.min() and nw.max() <= 4000
+    assert abs(nw[150:].mean() / nw[:150].mean() - 1) < 0.2
+
+
 def test_invariants_with_initiator():
     """12e/24o initiator run: every determinant keeps N, Sz and the reference's irrep; list has no
     duplicates or empty entries; aborted spawns only occur with the initiator approximation on."""
