@@ -48,9 +48,14 @@ MUTANTS = [
     ("shift_update_sign", "q->shift = q->shift - q->c_shift * oq_log(ratio);",
      "q->shift = q->shift + q->c_shift * oq_log(ratio);"),
     ("gen_prob_double_orders", "return (q->p_double * (double)(m_ba + m_ab)) /", "return (q->p_double * (double)(m_ba + m_ba)) /"),
+    ("clone_sign", "else { nc = (int64_t)c + sc * nd; clone_w += nd; }", "else { nc = (int64_t)c - sc * nd; clone_w += nd; }"),
+    ("fingerprint_prime", "hsh = 1099511628211ull * hsh", "hsh = 1099511628213ull * hsh"),
+    ("fingerprint_zero_based", "q->map1[occ[i - 1]] * (uint64_t)i;", "q->map1[occ[i - 1]] * (uint64_t)(i - 1);"),
+    ("fingerprint_descending", "q->map1[occ[i - 1]] * (uint64_t)i;", "q->map1[occ[n - i]] * (uint64_t)i;"),
+    ("fingerprint_map_key", "key[2] = {0x46434951u, 0x4D415031u}", "key[2] = {0x46434951u, 0x4D415032u}"),
 ]
 
-FAST_PINS = ("philox or choice_digits or keeps_the_invariants or holds_the_population or own_log or second_quantisation or symmetry_and_spin or two_words and hamiltonian "
+FAST_PINS = ("philox or fingerprint_is_algorithm1 or choice_digits or keeps_the_invariants or holds_the_population or own_log or second_quantisation or symmetry_and_spin or two_words and hamiltonian "
              "or pdouble or normalised or eq1 or initiator_rule or on_a_subset or functional_two_words "
              "or membership or outside_the_space or expectation_in_the_space "
              "or spin_flip or projection or probability_of_any_target or spin_coupled or numerator or stored_form")

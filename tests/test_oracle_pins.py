@@ -285,14 +285,17 @@ def _random_state(rng, dets, n, ref):
     return chosen, pops
 
 
-def test_one_step_expectation_is_eq1(tiny, tiny_space):
-    """E[C^(n+1)] over independent random keys equals [1 - tau (H_ii - E0 - S)] C - tau H_offdiag C (Eq. 1)."""
+@pytest.mark.parametrize("S", [-0.4, 8.0])
+def test_one_step_expectation_is_eq1(tiny, tiny_space, S):
+    """E[C^(n+1)] over independent random keys equals [1 - tau (H_ii - E0 - S)] C - tau H_offdiag C (Eq. 1).
+    With S = -0.4 every determinant of the sample has H_ii - E0 - S > 0 (death only); with S = 8 the reference
+    and the sampled determinants with H_ii - E0 < 8 have r < 0 and clone (the second branch of Eq. 4)."""
     dets, H = tiny_space
     index = {d: i for i, d in enumerate(dets)}
     rng = np.random.default_rng(5)
     ref = 0xFF
     chosen, pops = _random_state(rng, dets, 25, ref)
-    tau, S = 0.05, -0.4
+    tau = 0.05
     q = O.Oracle(tiny, tau=tau, initial_shift=S)
     E0 = q.info()["E0"]
     c = np.zeros(len(dets))
@@ -303,9 +306,12 @@ def test_one_step_expectation_is_eq1(tiny, tiny_space):
     acc = np.zeros(len(dets))
     acc2 = np.zeros(len(dets))
     words = np.array([bf.to_words(d, 1) for d in chosen])
+    deaths = clones = 0
     for k in range(K):
         q.set_walkers(words, pops, iteration=k, shift=S)
-        q.iterate(1)
+        row = q.iterate(1)[0]
+        deaths += row["death_walkers"]
+        clones += row["clone_walkers"]
         dd, pp, _ = q.walkers()
         v = np.zeros(len(dets))
         for w, p in zip(dd, pp):
@@ -323,6 +329,7 @@ def test_one_step_expectation_is_eq1(tiny, tiny_space):
     assert np.all(np.isfinite(z))
     assert z.max() < 5.0, z.max()
     assert touched.sum() > 100
+    assert deaths > 0 and (clones > 0) == (S > 0), (deaths, clones)
 
 
 @pytest.mark.slow
@@ -461,6 +468,44 @@ def test_fingerprint_is_spread():
     counts = np.bincount(np.array(fps, dtype=np.uint64) & np.uint64(63), minlength=64)
     chi2 = ((counts - len(fps) / 64) ** 2 / (len(fps) / 64)).sum()
     assert chi2 < 130  # 63 degrees of freedom, p ~ 1e-6
+
+
+def _fingerprint_golden():
+    maps, cases = {}, []
+    with open(os.path.join(GOLDEN, "fingerprint_alg1.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            v = line.split()
+            if v[0] == "map":
+                maps[int(v[1])] = int(v[2], 16)
+            else:
+                cases.append(([int(x) for x in v[1].split(",")], [int(x, 16) for x in v[2:]]))
+    return maps, cases
+
+
+@pytest.mark.parametrize("n_orb", [16, 64])
+def test_fingerprint_is_algorithm1(n_orb):
+    """Algorithm 1 (Sec. V) against values worked step by step from its recurrence (tests/golden): the orbital
+    map is the keyed Philox of the random-number contract, a one-electron determinant hashes to its map value,
+    and every prefix of the occupied list (ascending, electrons counted from 1) gives the listed hash."""
+    maps, cases = _fingerprint_golden()
+    q = O.Oracle(synth.make_system(n_orb, 4, seed=0, n_chol=1), tau=0.01)
+    m = q.map1()
+    for k, v in maps.items():
+        if k < 2 * n_orb:
+            assert int(m[k]) == v, k
+    W = 1 if n_orb <= 32 else 2
+    checked = 0
+    for orbs, steps in cases:
+        if max(orbs) >= 2 * n_orb:
+            continue
+        for n in range(1, len(orbs) + 1):
+            d = sum(1 << k for k in orbs[:n])
+            assert q.fingerprint(bf.to_words(d, W)) == steps[n - 1], (orbs[:n], hex(steps[n - 1]))
+            checked += 1
+        assert steps[0] == maps[orbs[0]]
+    assert checked == (10 if n_orb == 16 else 18)
 
 
 def test_paper_storage_numbers():
