@@ -127,7 +127,7 @@ typedef struct {
     int64_t merged_entries;   /* distinct determinants spawned onto */
     int64_t aborted_walkers;  /* spawned walkers discarded by the initiator rule */
     int64_t inserted_dets;    /* determinants newly occupied by spawning */
-    int64_t heavy_attempts;   /* attempts from determinants with more than 1024 walkers, which the
+    int64_t heavy_attempts;   /* attempts from determinants with more than 256 walkers, which the
                                  chunked spawning kernel (k_heavy) carries out */
 } fciqmc_row;
 
@@ -203,9 +203,13 @@ int fciqmc_create(const double *h, const double *eri_s8, double e_core, int n_el
                   const fciqmc_options *opt, void *workspace, size_t workspace_bytes, void *cuda_stream,
                   fciqmc_handle **out);
 
-/* Enqueues n_iterations iterations (spawn + death, annihilation with the
- * initiator filter, estimators and shift) on the stream. Asynchronous: device
- * errors surface at the next synchronising call. */
+/* Enqueues n_iterations iterations on the stream. One iteration is the cycle of
+ * Sec. II: for every walker a spawning attempt with the generator of Sec. VI
+ * and the acceptance of Eq. 3, death/cloning of every determinant (Eq. 4), the
+ * spawned walkers merged per determinant and annihilated into the main list
+ * with the initiator filter (Sec. V A, V B), then the estimators (Eq. 2) and
+ * the shift update. Asynchronous: device errors surface at the next
+ * synchronising call. */
 int fciqmc_step(fciqmc_handle *h, int32_t n_iterations);
 
 /* Waits for the stream; returns the sticky device status. */
@@ -222,16 +226,22 @@ int fciqmc_history(fciqmc_handle *h, fciqmc_row *rows, int64_t max_rows, int64_t
 /* Synchronising: number of occupied determinants of the current list. */
 int fciqmc_n_dets(fciqmc_handle *h, int64_t *n_dets);
 
-/* Synchronising: copies the occupied determinants (W words each), their
- * populations and, if hdiag is not NULL, their stored H_ii - E0, into host
- * arrays of capacity cap entries, in unspecified order; *n receives the count.
+/* Synchronising: copies the main walker list (Sec. III: per occupied
+ * determinant its bit string and signed walker count, with the stored
+ * diagonal element) - the occupied determinants (W words each), their
+ * populations and, if hdiag is not NULL, their stored H_ii - E0 - into host
+ * arrays of capacity cap entries, in unspecified order (slot order of the
+ * device list, not sorted: sort on the host if an order is needed); *n
+ * receives the count.
  * Host arrays may be pinned or pageable. Returns FCIQMC_ERR_CAPACITY (with *n
  * set) if cap is too small. */
 int fciqmc_get_walkers(fciqmc_handle *h, uint64_t *dets, int32_t *pops, double *hdiag, int64_t cap,
                        int64_t *n);
 
-/* Synchronising: replaces the walker list and, if st is not NULL, the
- * dynamic state. dets: n x W words (host); pops: n nonzero populations;
+/* Synchronising: replaces the main walker list (Sec. III layout, as returned by
+ * fciqmc_get_walkers) and, if st is not NULL, the dynamic state, so a run
+ * resumes exactly (the random numbers are keyed by iteration and determinant,
+ * not by history). dets: n x W words (host); pops: n nonzero populations;
  * hdiag: H_ii - E0 per determinant as returned by fciqmc_get_walkers, or NULL
  * to compute it. Determinants must be distinct and carry the run's electron
  * count. Clears the history and the device status. */
@@ -324,8 +334,11 @@ void fciqmc_rdm_destroy(fciqmc_rdm *r);
 
 /* Largest walker list fciqmc_estimate_list_static accepts. Its scratch is one
  * static device array per device: FCIQMC_STATIC_MAX_DETS / 256 doubles (256 KiB)
- * and three 64-bit counters. */
+ * and four 64-bit counters. */
 #define FCIQMC_STATIC_MAX_DETS (1LL << 23)
+/* fciqmc_estimate_list_static flag: the list holds spin-coupled functions (the
+ * stored determinants of fciqmc_options.hphf runs). */
+#define FCIQMC_STATIC_SPIN_COUPLED 1
 
 /* The paper has no counterpart to this entry point: it is an allocation-free
  * form of fciqmc_estimators for callers that hold a walker list on the device
@@ -338,19 +351,27 @@ void fciqmc_rdm_destroy(fciqmc_rdm *r);
  * Computes, for the list (dets, pops) of n_dets entries (zero populations are
  * skipped): out[0] = sum |C_i|, out[1] = number of nonzero entries, out[2] =
  * C_0 (population of `reference`, 0 if absent), out[3] = sum_{i != 0}
- * <D_i|H|D_0> C_i (the Eq. 2 numerator; each term as in fciqmc_estimators,
- * summed per 256-entry tile and then over tiles in order, so the value agrees
- * with fciqmc_estimators to rounding).
+ * <D_i|H|D_0> C_i, the projected-energy numerator, each term as in
+ * fciqmc_estimators (with FCIQMC_STATIC_SPIN_COUPLED, sqrt(2) <D_i|H|D_0> for
+ * open-shell functions), summed per 256-entry tile and then over tiles in
+ * order, so the value agrees with fciqmc_estimators to rounding; out[4] = the
+ * number of nonzero entries skipped as invalid (a bit at or beyond spin
+ * orbital 2 n_orb, an electron count other than n_elec, a population of
+ * INT32_MIN; with FCIQMC_STATIC_SPIN_COUPLED also M_s != 0 or a determinant
+ * that is not the stored, smaller one of its spin-flip pair). Skipped entries
+ * contribute to nothing and never index the integrals.
  *   h_dev, eri_dev  device arrays in the layout of fciqmc_create (n_orb^2 and
  *                   the 8-fold packed ERIs), read only.
- *   reference       host array of W words with n_elec bits set.
+ *   reference       host array of W words with n_elec bits set, none at or
+ *                   beyond 2 n_orb (closed-shell with FCIQMC_STATIC_SPIN_COUPLED).
  *   dets_dev        device, n_dets x W words; pops_dev device, n_dets int32.
- *   out_dev         device, 4 doubles, written by the last kernel.
+ *   flags           0 or FCIQMC_STATIC_SPIN_COUPLED.
+ *   out_dev         device, 5 doubles, written by the last kernel.
  *   cuda_stream     stream the three kernels are enqueued on (asynchronous).
  * Returns FCIQMC_ERR_CAPACITY, before launching anything, if n_dets >
  * FCIQMC_STATIC_MAX_DETS; FCIQMC_ERR_UNSUPPORTED for sizes beyond the
- * library's limits; FCIQMC_ERR_INVALID_ARG for null pointers or a reference
- * with the wrong electron count.
+ * library's limits; FCIQMC_ERR_INVALID_ARG for null pointers, unknown flags or
+ * a reference that is not a determinant of the basis with n_elec electrons.
  * Scratch: the first call on each device looks up the device address of the
  * static array (cudaGetSymbolAddress, with that device current) and caches
  * it, so that first call should come before any stream capture. The array
@@ -361,7 +382,7 @@ void fciqmc_rdm_destroy(fciqmc_rdm *r);
  * Allocates no memory: no cudaMalloc, no cudaFree, no allocating library call. */
 int fciqmc_estimate_list_static(const double *h_dev, const double *eri_dev, int n_elec, int n_orb,
                                 const uint64_t *reference, const uint64_t *dets_dev, const int32_t *pops_dev,
-                                int64_t n_dets, double *out_dev, void *cuda_stream);
+                                int64_t n_dets, int32_t flags, double *out_dev, void *cuda_stream);
 
 /* Releases host-side resources (graphs, events). Synchronising. The
  * workspace stays the caller's. Accepts NULL. */

@@ -121,6 +121,7 @@ SYMBOLS = ["fciqmc_default_options", "fciqmc_workspace_bytes", "fciqmc_create", 
            "fciqmc_rdm_gradient", "fciqmc_rdm_info", "fciqmc_rdm_destroy", "fciqmc_batch_create",
            "fciqmc_batch_step", "fciqmc_batch_destroy"]
 STATIC_MAX_DETS = 1 << 23
+STATIC_SPIN_COUPLED = 1
 N_KERNELS = 8
 KERNEL_NAMES = ["compact_copy", "index_clear", "index_fill", "compact_finish", "sweep", "heavy", "annihilate",
                 "finish"]
@@ -149,7 +150,7 @@ def _declare(L):
     L.fciqmc_get_state.argtypes = [vp, P(State)]
     L.fciqmc_get_info.argtypes = [vp, P(Info)]
     L.fciqmc_profile.argtypes = [vp, i32, f64p]
-    L.fciqmc_estimate_list_static.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, u64p, vp, vp, i64, vp, vp]
+    L.fciqmc_estimate_list_static.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, u64p, vp, vp, i64, i32, vp, vp]
     L.fciqmc_estimate_list_static.restype = ctypes.c_int
     L.fciqmc_rdm_workspace_bytes.argtypes = [ctypes.c_int, ctypes.c_int, i64]
     L.fciqmc_rdm_workspace_bytes.restype = ctypes.c_size_t
