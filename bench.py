@@ -4,8 +4,10 @@
 Workload (default "24e60o"): 24 electrons in 60 spatial orbitals (two uint64 words per
 determinant), 8 irreps, synthetic decaying-Cholesky integrals with a near-degenerate frontier,
 initiator threshold 3, tau = 0.001, 1e8 target walkers, main list of 2e8 slots. The walker
-population is grown on the GPU from the reference (untimed), the shift starts varying at the
-target, and after warm-up iterations K iterations are timed with CUDA events on the run's stream.
+population is grown on the GPU from the reference at a moderate initial shift (untimed), the shift
+starts varying at the target, the run settles for 4000 more iterations (the shift, N_w and N_d are
+then flat to a few per mille per 500 iterations), and after warm-up iterations K iterations are
+timed with CUDA events on the run's stream.
 One "step" is one full iteration: spawning, death, annihilation with the initiator filter,
 estimators and shift. The main list (GBs) is far larger than L2, so no L2 flush is needed.
 
@@ -39,11 +41,13 @@ from paper_1305_6981_gb300 import synth  # noqa: E402
 METRIC = "spawn attempts/s at 1e8 walkers (24e/60o, initiator, tau 0.001)"
 
 # Instruction-issue roofline of the spawning kernels (they are bound by their instruction stream, not
-# by HBM). Per-unit figures are warp instructions per attempt from ncu (smsp__inst_executed.sum of a
-# full-size launch in the timed region divided by the attempts that launch made), taken with the
-# one-pass command recorded in profiles/counters_24e60o_1e8.txt; they must be re-measured whenever
-# those kernels change.
+# by HBM). Per-unit figures are warp instructions per attempt from ncu: smsp__inst_executed.sum of one
+# launch divided by the attempts of that launch, captured one kernel at a time (-k, -c 1) on the medium
+# steady-state case (--ncu-case --target 5000000, a few GB on the device) with the command recorded in
+# the profile summary named in WARP_INST_SOURCE; full-size runs are timed with CUDA events and
+# gpu__time_duration.sum only. They must be re-measured whenever those kernels change.
 WARP_INST_PER_ATTEMPT = {"heavy": 10.55, "sweep": 39.9}
+WARP_INST_SOURCE = "profiles/counters_24e60o_1e8.txt (taken on the growth-phase list at ~1.2e8 walkers)"
 # DRAM bytes (read + write) per launch of each kernel at the full workload, from the same summary.
 DRAM_BYTES_PER_LAUNCH = {"heavy": 25_324_160, "sweep": 118_458_496, "annihilate": 52_211_584}
 ISSUE_PER_CLK_PER_SM = 4  # warp instructions: 4 schedulers per SM, one issue each per clock
@@ -51,18 +55,19 @@ N_SMS = 152
 
 WORKLOADS = {
     "24e60o": dict(system=synth.large_24e60o, tau=0.001, thr=3, target=100_000_000, main_capacity=200_000_000,
-                   spawn_capacity=1 << 27, initial_population=20_000, initial_shift=3.0, max_growth=40_000,
-                   equilibrate=50,
-                   desc="24e/60o (W=2), 8 irreps, initiator 3, tau 0.001, 1e8 target walkers, 2e8-slot main list"),
+                   spawn_capacity=1 << 27, initial_population=20_000, initial_shift=0.5, max_growth=40_000,
+                   equilibrate=4000,
+                   desc="24e/60o (W=2), 8 irreps, initiator 3, tau 0.001, 1e8 target walkers, 2e8-slot main list, "
+                        "timed at steady state (grown at shift 0.5, 4000 iterations after the shift starts varying)"),
     "24e60o-cas": dict(system=synth.large_24e60o, tau=0.001, thr=3, target=100_000_000, main_capacity=200_000_000,
-                       spawn_capacity=1 << 27, initial_population=20_000, initial_shift=3.0, max_growth=40_000,
-                       equilibrate=50,
+                       spawn_capacity=1 << 27, initial_population=20_000, initial_shift=0.5, max_growth=40_000,
+                       equilibrate=4000,
                        space=dict(frozen_occupied=[(1 << 8) - 1, 0], frozen_empty=[0, ((1 << 32) - 1) << 24]),
                        desc="24e/60o active space CAS(16e,40o): spatial orbitals 0..3 frozen doubly occupied, "
                             "44..59 deleted (Sec. VI null excitations), initiator 3, tau 0.001, 1e8 target walkers"),
     "24e60o-hphf": dict(system=synth.large_24e60o, tau=0.002, thr=3, target=50_000_000, main_capacity=100_000_000,
-                        spawn_capacity=1 << 26, initial_population=20_000, initial_shift=3.0, max_growth=40_000,
-                        equilibrate=50, space=dict(hphf=True),
+                        spawn_capacity=1 << 26, initial_population=20_000, initial_shift=0.5, max_growth=40_000,
+                        equilibrate=2000, space=dict(hphf=True),
                         desc="24e/60o on spin-coupled functions (Sec. VI C: half the space, so half the walkers "
                              "and twice the time step of the determinant run), initiator 3, tau 0.002, "
                              "5e7 target walkers"),
@@ -93,8 +98,9 @@ def parse():
     ap.add_argument("--target", type=int, default=0, help="override target walkers (smaller runs)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle baseline")
     ap.add_argument("--growth-log", default="")
+    ap.add_argument("--settle", type=int, default=-1,
+                    help="iterations after the shift starts varying before warm-up (default: the workload's)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-runs and energy-functional measurements appended to the default line")
     ap.add_argument("--ncu-case", action="store_true",
@@ -151,31 +157,84 @@ class Clocks:
 
 
 # ---------------------------------------------------------------------------- oracle baseline
-def oracle_rate(system, wl, dets, pops, seconds: float, seed: int = 1):
-    """The CPU oracle as it stands on this host's cores: spawn attempts/s of whole iterations on a
-    bounded sample of the workload's walker list."""
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def _stored_forms(dets, pops):
+    """Spin-coupled functions are stored on the smaller of a determinant and its spin flip: map each
+    determinant of a synthetic snapshot to that form and merge the populations of a pair."""
+    even = np.uint64(0x5555555555555555)
+    flip = ((dets & even) << np.uint64(1)) | ((dets >> np.uint64(1)) & even)
+    keys = [tuple(r[::-1]) for r in dets.tolist()]
+    fkeys = [tuple(r[::-1]) for r in flip.tolist()]
+    merged = {}
+    for k, fk, c in zip(keys, fkeys, pops.tolist()):
+        m = min(k, fk)
+        merged[m] = merged.get(m, 0) + c
+    items = [(k, c) for k, c in merged.items() if c != 0]
+    d = np.array([k[::-1] for k, _ in items], dtype=np.uint64).reshape(-1, dets.shape[1])
+    return d, np.array([c for _, c in items], dtype=np.int32)
+
+
+def oracle_sample(wl, system):
+    """The bounded sample that both the CPU baseline of the GPU arm and the reference arm time: a synthetic
+    snapshot of the workload (2e5 walkers for the 24e/60o workloads, 5e4 otherwise; the reference holds 5%,
+    the rest sit on random 1..4-fold excitations), restricted to the permitted space."""
     from oracle.oracle import Oracle, lib
     lib()
-    q = Oracle(system, tau=wl["tau"], initiator_threshold=wl["thr"], seed=seed, **wl.get("space", {}))
-    att, it, elapsed = 0, 0, 0.0
-    while elapsed < seconds and it < 1000:
-        q.set_walkers(dets, pops, iteration=1000 + it, shift=0.0)
-        t1 = time.perf_counter()
-        rows = q.iterate(1)
-        elapsed += time.perf_counter() - t1
-        att += rows[0]["attempts"]
-        it += 1
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return att / elapsed, cores, it, att
+    n = 200_000 if wl["desc"].startswith("24e/60o") else 50_000
+    dets, pops = synth.walker_snapshot(system, n, seed=7)
+    q = Oracle(system, tau=wl["tau"], initiator_threshold=wl["thr"], seed=1, **wl.get("space", {}))
+    if wl.get("space", {}).get("hphf"):
+        dets, pops = _stored_forms(dets, pops)
+    keep = np.array([q.in_space(d) for d in dets])
+    return q, dets[keep], pops[keep]
 
 
-def sample_list(dets, pops, n_walkers, seed=0):
-    """Uniform sample of determinants holding about n_walkers walkers (populations unchanged)."""
-    rng = np.random.default_rng(seed)
-    tot = int(np.abs(pops).sum())
-    p = min(1.0, n_walkers / max(tot, 1))
-    keep = rng.random(len(pops)) < p
-    return dets[keep], pops[keep]
+def oracle_baseline(wl, system, steps: int, warmup: int, one_thread_steps: int = 2):
+    """The CPU oracle as it stands, timed on this host on the bounded sample of oracle_sample: whole
+    iterations (spawning, death, merge, annihilation, estimators) restarted from the sample each time, on
+    all cores and on one thread. Returns a dict with both rates, the cores used and the CPU model."""
+    from oracle import oracle as O
+    q, dets, pops = oracle_sample(wl, system)
+    cores = O.set_threads(os.cpu_count() or 1)
+
+    def timed(n_steps, first_iter):
+        att, tsum = 0, 0.0
+        for k in range(n_steps):
+            q.set_walkers(dets, pops, iteration=first_iter + k, shift=0.0)
+            t0 = time.perf_counter()
+            rows = q.iterate(1)
+            tsum += time.perf_counter() - t0
+            att += rows[0]["attempts"]
+        return att, tsum
+
+    timed(warmup, 0)
+    att, tsum = timed(steps, warmup)
+    O.set_threads(1)
+    att1, tsum1 = timed(one_thread_steps, warmup + steps)
+    O.set_threads(cores)
+    return {"value": att / tsum, "unit": "attempts/s", "cores": cores, "kind": "oracle",
+            "one_thread": att1 / tsum1, "cpu_model": cpu_model(), "ms_per_step": 1e3 * tsum / max(steps, 1),
+            "sample": f"{steps} oracle iterations on all {cores} cores (and {one_thread_steps} on one thread) of a "
+                      f"synthetic snapshot of the workload: {len(pops)} determinants / {int(np.abs(pops).sum())} "
+                      f"walkers (reference 5%, random 1..4-fold excitations); the same sample as the reference arm"}
 
 
 # ---------------------------------------------------------------------------- reference arm
@@ -219,10 +278,32 @@ def run_reference_batch(args, wl):
     return out
 
 
+ENERGY_METRIC = ("energy functional forward + first backward: connected determinant pairs per second "
+                 "(16e/40o sampled vector)")
+
+
+def connected_pairs(dets) -> int:
+    """Unordered pairs of distinct determinants that differ by a single or a double excitation (the pairs
+    whose matrix elements and density-matrix terms the energy functional evaluates)."""
+    def popcount(x):  # 64-bit population count, lane-parallel on uint64 arrays
+        x = x - ((x >> np.uint64(1)) & np.uint64(0x5555555555555555))
+        x = (x & np.uint64(0x3333333333333333)) + ((x >> np.uint64(2)) & np.uint64(0x3333333333333333))
+        x = (x + (x >> np.uint64(4))) & np.uint64(0x0F0F0F0F0F0F0F0F)
+        return ((x * np.uint64(0x0101010101010101)) >> np.uint64(56)).astype(np.int64)
+
+    d = np.ascontiguousarray(dets, dtype=np.uint64).reshape(len(dets), -1)
+    n = 0
+    for i in range(len(d) - 1):
+        x = d[i + 1:] ^ d[i]
+        c = sum(popcount(x[:, w]) for w in range(d.shape[1]))
+        n += int(((c == 2) | (c == 4)).sum())
+    return n
+
+
 def run_reference_energy(args, wl):
     """The oracle's energy functional and density matrices (one call gives both) on a 5000-determinant
-    sample of the 16e/40o vector: milliseconds per call (at most three timed calls: the oracle's pair
-    search is quadratic in the determinants)."""
+    sample of the 16e/40o vector, in connected determinant pairs per second like the GPU arm (at most three
+    timed calls: the oracle's pair search is quadratic in the determinants)."""
     from oracle.oracle import Oracle, lib
     lib()
     n = 5_000
@@ -235,11 +316,12 @@ def run_reference_energy(args, wl):
     t0 = time.perf_counter()
     for _ in range(calls):
         q.rdm_energy(dets, c)
-    ms = 1e3 * (time.perf_counter() - t0) / calls
-    out = _reference_line(args, "energy functional forward + first backward time (16e/40o sampled vector)", ms,
-                          "ms", False, {"workload": "energy16e40o", "n_dets": n},
-                          f"{n} of the sampled determinants (the GPU arm uses 1e6)")
-    out["ms_per_step"] = ms
+    sec = (time.perf_counter() - t0) / calls
+    pairs = connected_pairs(dets)
+    out = _reference_line(args, ENERGY_METRIC, pairs / sec, "pairs/s", True,
+                          {"workload": "energy16e40o", "n_dets": n, "connected_pairs": pairs},
+                          f"{n} of the sampled determinants (the GPU arm uses 1e6); {pairs} connected pairs")
+    out["ms_per_step"] = 1e3 * sec
     return out
 
 
@@ -253,38 +335,11 @@ def run_reference(args, wl, rank, world):
         print(json.dumps(run_reference_energy(args, wl)), flush=True)
         return
     system = wl["system"]()
-    n_sample = 200_000 if args.workload.startswith("24e60o") else 50_000
-    dets, pops = synth.walker_snapshot(system, n_sample, seed=7)
-    from oracle.oracle import Oracle, lib
-    lib()
-    q = Oracle(system, tau=wl["tau"], initiator_threshold=wl["thr"], seed=1, **wl.get("space", {}))
-    if "space" in wl:
-        keep = np.array([q.in_space(d) for d in dets])
-        dets, pops = dets[keep], pops[keep]
-    for k in range(args.warmup):
-        q.set_walkers(dets, pops, iteration=k, shift=0.0)
-        q.iterate(1)
-    att, tsum = 0, 0.0
-    for k in range(args.steps):
-        q.set_walkers(dets, pops, iteration=args.warmup + k, shift=0.0)
-        t0 = time.perf_counter()
-        rows = q.iterate(1)
-        tsum += time.perf_counter() - t0
-        att += rows[0]["attempts"]
-    value = att / tsum
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    out = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": "attempts/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tsum / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic",
-        "config": {"workload": args.workload, "system": wl["desc"],
-                   "sample": f"{len(pops)} determinants / {int(np.abs(pops).sum())} walkers of a synthetic "
-                             f"snapshot (reference + random symmetry-conserving excitations)"},
-        "cpu_baseline": {"value": value, "unit": "attempts/s", "cores": cores, "kind": "oracle",
-                         "sample": f"{args.steps} oracle iterations on a {int(np.abs(pops).sum())}-walker sample"},
-        "e2e": {"value": value, "unit": "attempts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-    }
+    b = oracle_baseline(wl, system, max(args.steps, 1), args.warmup)
+    out = _reference_line(args, METRIC, b["value"], "attempts/s", True,
+                          {"workload": args.workload, "system": wl["desc"], "sample": b["sample"]}, b["sample"])
+    out["ms_per_step"] = b["ms_per_step"]
+    out["cpu_baseline"].update({"cores": b["cores"], "one_thread": b["one_thread"], "cpu_model": b["cpu_model"]})
     print(json.dumps(out), flush=True)
 
 
@@ -340,8 +395,16 @@ def grow(args, wl, rank):
             raise RuntimeError(f"device status {e['status']} during growth at {grown}: {log[-1]}")
         if e["vary_shift"] or grown >= wl["max_growth"]:
             break
-    g.step(wl["equilibrate"])
-    grown += wl["equilibrate"]
+    settle = wl["equilibrate"] if args.settle < 0 else args.settle
+    while settle > 0:  # settle towards the steady state of the varying shift
+        k = min(settle, 500)
+        g.step(k)
+        settle -= k
+        grown += k
+        e = g.estimates()
+        log.append((grown, e["n_walkers"], e["n_dets"], e["shift"], e["list_slots"]))
+        if e["status"] != 0:
+            raise RuntimeError(f"device status {e['status']} while settling at {grown}: {log[-1]}")
     return g, grown, time.perf_counter() - t_grow, log
 
 
@@ -395,6 +458,9 @@ def run_gpu(args, wl, rank, world, local_rank):
     ms = ev0.elapsed_time(ev1)
     st = g.sync()
     rows = g.history(args.steps)
+    # the rate no attempt stream can exceed: one Philox4x32-10 block per attempt (measured after the window)
+    from paper_1305_6981_gb300 import rng_throughput
+    rng_rate = rng_throughput(1 << 31, g.stream)
     attempts = sum(r["attempts"] for r in rows)
     nd_mean = float(np.mean([r["nd_in"] for r in rows]))
     nw_mean = float(np.mean([r["nw_in"] for r in rows]))
@@ -437,19 +503,31 @@ def run_gpu(args, wl, rank, world, local_rank):
                        "dets_mean": nd_mean, "list_slots": slots, "merged_per_iter": merged_mean,
                        "inserted_per_iter": inserted_mean, "growth_iterations": grown,
                        "growth_seconds": round(t_grow, 1), "l2": "inputs larger than L2 (main list ~GBs)",
-                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                       "steady_state": {"shift_at_timing": rows[0]["shift"] if rows else None,
+                                        "shift_at_end": rows[-1]["shift"] if rows else None,
+                                        "nw_first": rows[0]["nw_in"] if rows else None,
+                                        "nw_last": rows[-1]["nw_out"] if rows else None,
+                                        "nw_drift": (rows[-1]["nw_out"] / rows[0]["nw_in"] - 1.0) if rows else None,
+                                        "dets_first": rows[0]["nd_in"] if rows else None,
+                                        "heavy_share": (sum(r["heavy_attempts"] for r in rows)
+                                                        / max(1, sum(r["attempts"] for r in rows))),
+                                        "c0_first": rows[0]["c0_in"] if rows else None}},
             # the per-unit instruction counts were measured on the default workload's kernels
             "roofline": ({"bound": "alu", "kernel": f"k_{dom}", "achieved": achieved, "peak": issue_peak,
                           "unit": "Gwarp-inst/s", "frac": achieved / issue_peak,
                           "traffic": DRAM_BYTES_PER_LAUNCH.get(dom),
-                          "per_unit": f"{WARP_INST_PER_ATTEMPT[dom]} warp instructions per attempt (ncu, full-size "
-                                      f"launch)",
+                          "per_unit": f"{WARP_INST_PER_ATTEMPT[dom]} warp instructions per attempt (ncu, "
+                                      f"{WARP_INST_SOURCE})",
                           "units_per_launch": units[dom], "launch_ms": dom_ms,
                           "peak_derivation": f"{ISSUE_PER_CLK_PER_SM} warp-inst/clk/SM x {N_SMS} SMs x "
                                              f"{sm_mhz:.0f} MHz"}
                          if args.workload == "24e60o" and not args.target else None),
             "hbm": {"cycle_algorithmic_gbs": cycle_gbs, "peak": hbm_peak, "frac": cycle_gbs / hbm_peak,
                     "peak_source": peak_src, "bytes_per_iter": sweep_b + annih_b},
+            # attempts/s against the Philox4x32-10 rate measured live on this GPU (one block per attempt)
+            "alu_floor": {"philox_blocks_per_s": rng_rate, "attempts_per_s": att_all / (ms_max * 1e-3),
+                          "frac": att_all / (ms_max * 1e-3) / rng_rate / world},
             "kernel_ms_per_iter": {k: v / 5.0 for k, v in prof.items()},
             "clocks": clk,
             "status": st,
@@ -638,10 +716,13 @@ def main():
         import torch
         torch.cuda.set_device(0)
         r = energy_functional_timing(args.target or 1_000_000)
-        print(json.dumps({"metric": "energy functional forward + first backward time (16e/40o sampled vector)",
-                          "value": r["forward_ms"] + r["backward_first_ms"], "unit": "ms", "n_gpus": 1,
-                          "higher_is_better": False, "dtype": "f64", "data": "synthetic",
-                          "config": {"workload": "energy16e40o", "n_dets": r["n_dets"]}, "detail": r}), flush=True)
+        pairs = r["single_pairs"] + r["double_pairs"]
+        ms = r["forward_ms"] + r["backward_first_ms"]
+        print(json.dumps({"metric": ENERGY_METRIC, "value": pairs / (ms * 1e-3), "unit": "pairs/s", "n_gpus": 1,
+                          "steps": 1, "warmup": 1, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                          "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                          "config": {"workload": "energy16e40o", "n_dets": r["n_dets"], "connected_pairs": pairs},
+                          "detail": r}), flush=True)
         return
     if args.workload == "batch64":
         print(json.dumps(run_batch(args, wl)), flush=True)
@@ -658,13 +739,9 @@ def main():
             dets, pops, _ = g.walkers()
             out["e2e"] = None
         if not args.no_cpu_baseline and world == 1:
-            system = wl["system"]()
-            sd, sp = sample_list(dets, pops, 300_000 if args.workload.startswith("24e60o") else 50_000)
-            rate, cores, its, att = oracle_rate(system, wl, sd, sp, args.cpu_seconds)
-            out["cpu_baseline"] = {"value": rate, "unit": "attempts/s", "cores": cores, "kind": "oracle",
-                                   "sample": f"{its} oracle iterations on {len(sp)} determinants / "
-                                             f"{int(np.abs(sp).sum())} walkers sampled uniformly from the "
-                                             f"GPU list ({att} attempts)"}
+            b = oracle_baseline(wl, wl["system"](), 20, 3)
+            b.pop("ms_per_step")
+            out["cpu_baseline"] = b
         if not args.no_extras and world == 1 and args.workload == "24e60o":
             g.close()
             bargs = argparse.Namespace(**vars(args))

@@ -384,6 +384,16 @@ int fciqmc_estimate_list_static(const double *h_dev, const double *eri_dev, int 
                                 const uint64_t *reference, const uint64_t *dets_dev, const int32_t *pops_dev,
                                 int64_t n_dets, int32_t flags, double *out_dev, void *cuda_stream);
 
+/* Measurement utility (the paper has no counterpart): throughput of the random numbers every spawning
+ * attempt draws, one Philox4x32-10 block keyed like an attempt's (the random-number contract of the
+ * library: counter (attempt, tag, fingerprint), key (seed, iteration)). Evaluates about n_blocks blocks
+ * over a grid that fills every SM of the current device (after a shorter warm-up launch), on cuda_stream,
+ * timed with CUDA events, and writes blocks per second into *blocks_per_s (host). No spawning attempt can
+ * take less than one block, so attempts/s of the walker cycle is at most this rate. Synchronising.
+ * Returns FCIQMC_ERR_INVALID_ARG for n_blocks < 1 or a NULL output, FCIQMC_ERR_CUDA if a launch fails.
+ * Allocates no device memory. */
+int fciqmc_rng_throughput(int64_t n_blocks, void *cuda_stream, double *blocks_per_s);
+
 /* Releases host-side resources (graphs, events). Synchronising. The
  * workspace stays the caller's. Accepts NULL. */
 void fciqmc_destroy(fciqmc_handle *h);

@@ -62,6 +62,7 @@
 
 #define OQ_MAXW 2
 #define OQ_MAXSO 128
+#define OQ_CHUNK 4096   /* spawning attempts per parallel work unit */
 
 /* ------------------------------------------------------------------------- */
 /* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy
@@ -806,10 +807,11 @@ static int64_t attempt_one(const oq_t *q, const uint64_t *d, int32_t c, uint64_t
     return -(int64_t)sgn_c * sgn_h * nsp;
 }
 
-static void spawn_from(const oq_t *q, const uint64_t *d, int32_t c, uint64_t fp, int flag, sbuf_t *b)
+/* Spawning attempts a0 <= a < a1 of determinant d (Eq. 3 once per walker). */
+static void spawn_range(const oq_t *q, const uint64_t *d, int32_t c, uint64_t fp, int flag, uint32_t a0, uint32_t a1,
+                        sbuf_t *b)
 {
-    uint32_t na = (uint32_t)(c < 0 ? -(int64_t)c : c);
-    for (uint32_t a = 0; a < na; ++a) {
+    for (uint32_t a = a0; a < a1; ++a) {
         uint64_t child[OQ_MAXW];
         int is_null = 0;
         int64_t amt = attempt_one(q, d, c, fp, a, child, &is_null, &b->err);
@@ -875,20 +877,41 @@ int oq_iterate(oq_t *q, int n_iter, oq_row *rows)
         int32_t *newpop = malloc(sizeof(int32_t) * (q->n ? q->n : 1));
         int64_t death_w = 0, clone_w = 0;
         int numeric = 0;
-#pragma omp parallel for schedule(dynamic, 64) reduction(+ : death_w, clone_w) reduction(| : numeric)
+        /* Work units: the attempts of each determinant in chunks of at most OQ_CHUNK (the attempt index is
+         * a counter of the random numbers and the spawned list is sorted before it is merged, so how a
+         * determinant's attempts are split across threads does not change the result); the first chunk of a
+         * determinant also takes its death/cloning step. */
+        int64_t n_units = 0;
         for (int64_t x = 0; x < q->n; ++x) {
+            int64_t ac = q->pop[x] < 0 ? -(int64_t)q->pop[x] : q->pop[x];
+            newpop[x] = q->pop[x];
+            if (ac > 0) n_units += (ac + OQ_CHUNK - 1) / OQ_CHUNK;
+        }
+        int64_t *units = malloc(sizeof(int64_t) * 2 * (n_units ? n_units : 1));
+        n_units = 0;
+        for (int64_t x = 0; x < q->n; ++x) {
+            int64_t ac = q->pop[x] < 0 ? -(int64_t)q->pop[x] : q->pop[x];
+            for (int64_t a0 = 0; a0 < ac; a0 += OQ_CHUNK) {
+                units[2 * n_units] = x;
+                units[2 * n_units + 1] = a0;
+                n_units++;
+            }
+        }
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : death_w, clone_w) reduction(| : numeric)
+        for (int64_t u = 0; u < n_units; ++u) {
             int tid = 0;
 #ifdef _OPENMP
             tid = omp_get_thread_num();
 #endif
+            const int64_t x = units[2 * u], a0 = units[2 * u + 1];
             const uint64_t *d = q->det + x * W;
             int32_t c = q->pop[x];
-            newpop[x] = c;
-            if (c == 0) continue;
             uint64_t fp = oq_fingerprint(q, d);
             int64_t ac = c < 0 ? -(int64_t)c : c;
             int flag = q->init_thr < 0 || ac > q->init_thr || det_eq(q, d, q->ref);
-            spawn_from(q, d, c, fp, flag, &bufs[tid]);
+            int64_t a1 = a0 + OQ_CHUNK < ac ? a0 + OQ_CHUNK : ac;
+            spawn_range(q, d, c, fp, flag, (uint32_t)a0, (uint32_t)a1, &bufs[tid]);
+            if (a0 != 0) continue;
             /* death / cloning, Eq. 4: r = tau (H_ii - E0 - S) |C_i| */
             double r = (q->tau * (q->hd[x] - q->shift)) * (double)ac;
             double ar = fabs(r);
@@ -904,6 +927,7 @@ int oq_iterate(oq_t *q, int n_iter, oq_row *rows)
             if (nc > 2147483647LL || nc < -2147483647LL) { numeric = 1; continue; }
             newpop[x] = (int32_t)nc;
         }
+        free(units);
         /* concatenate, sort and compress the spawned list (Sec. V A) */
         int64_t ns = 0;
         for (int t = 0; t < nthreads; ++t) {
@@ -1018,6 +1042,25 @@ int oq_iterate(oq_t *q, int n_iter, oq_row *rows)
 /* ---------------- accessors ---------------- */
 int64_t oq_n_dets(const oq_t *q) { return q->n; }
 int oq_words(const oq_t *q) { return q->W; }
+
+/* Threads of the parallel loops (the timing harness compares one thread with all cores); the results do
+ * not depend on the count. */
+void oq_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+int oq_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 void oq_get_walkers(const oq_t *q, uint64_t *dets, int32_t *pops, double *hd)
 {
     memcpy(dets, q->det, sizeof(uint64_t) * q->W * q->n);

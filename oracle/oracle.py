@@ -26,7 +26,7 @@ class Row(ctypes.Structure):
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (no FMA contraction, OpenMP over determinants)."""
+    """Compile the oracle with gcc (no FMA contraction, OpenMP over chunks of spawning attempts)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
@@ -96,6 +96,9 @@ def lib():
         L.oq_hphf_hij.argtypes = [ctypes.c_void_p, u64p, u64p]
         L.oq_hphf_hdiag.restype = ctypes.c_double
         L.oq_hphf_hdiag.argtypes = [ctypes.c_void_p, u64p]
+        L.oq_set_threads.argtypes = [ctypes.c_int]
+        L.oq_set_threads.restype = None
+        L.oq_max_threads.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -122,6 +125,12 @@ def digits(r0: int, r1: int, radices) -> list[int]:
 
 def log(x: float) -> float:
     return lib().oq_log(x)
+
+
+def set_threads(n: int) -> int:
+    """Threads of the oracle's parallel loops (results do not depend on it); returns the count in effect."""
+    lib().oq_set_threads(int(n))
+    return int(lib().oq_max_threads())
 
 
 class Oracle:

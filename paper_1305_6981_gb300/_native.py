@@ -119,7 +119,7 @@ SYMBOLS = ["fciqmc_default_options", "fciqmc_workspace_bytes", "fciqmc_create", 
            "fciqmc_get_state", "fciqmc_get_info", "fciqmc_profile", "fciqmc_estimate_list_static", "fciqmc_destroy",
            "fciqmc_strerror", "fciqmc_rdm_workspace_bytes", "fciqmc_rdm_create", "fciqmc_rdm_energy",
            "fciqmc_rdm_gradient", "fciqmc_rdm_info", "fciqmc_rdm_destroy", "fciqmc_batch_create",
-           "fciqmc_batch_step", "fciqmc_batch_destroy"]
+           "fciqmc_batch_step", "fciqmc_batch_destroy", "fciqmc_rng_throughput"]
 STATIC_MAX_DETS = 1 << 23
 STATIC_SPIN_COUPLED = 1
 N_KERNELS = 8
@@ -168,6 +168,8 @@ def _declare(L):
     L.fciqmc_batch_step.restype = ctypes.c_int
     L.fciqmc_batch_destroy.argtypes = [vp]
     L.fciqmc_batch_destroy.restype = None
+    L.fciqmc_rng_throughput.argtypes = [i64, vp, P(ctypes.c_double)]
+    L.fciqmc_rng_throughput.restype = ctypes.c_int
     L.fciqmc_destroy.argtypes = [vp]
     L.fciqmc_destroy.restype = None
     L.fciqmc_strerror.argtypes = [ctypes.c_int]

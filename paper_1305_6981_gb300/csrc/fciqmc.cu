@@ -846,6 +846,54 @@ void fciqmc_destroy(fciqmc_handle *h) {
 
 }  // extern "C"
 
+// ---------------------------------------------------------------------------------------------------------
+// Throughput of the attempt's random numbers: one Philox4x32-10 block per (thread, k), keyed like a spawning
+// attempt's block. The accumulated words are stored only if they hit a value the generator's output cannot
+// be forced to (so the blocks are not optimised away and nothing is written in practice).
+namespace {
+__device__ unsigned long long g_rng_sink;
+
+__global__ void __launch_bounds__(256) k_rng_throughput(long long per_thread) {
+    const unsigned tid = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long acc = 0;
+    for (long long k = 0; k < per_thread; ++k) {
+        unsigned long long w0, w1;
+        fq::draw2((unsigned)k, 0u, 0x9E3779B97F4A7C15ull ^ tid, 1u, tid, w0, w1);
+        acc ^= w0 + w1;
+    }
+    if (acc == 0x0123456789ABCDEFull) g_rng_sink = acc;
+}
+}  // namespace
+
+extern "C" int fciqmc_rng_throughput(int64_t n_blocks, void *cuda_stream, double *blocks_per_s) {
+    if (!blocks_per_s || n_blocks < 1) return FCIQMC_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    int dev = 0, sms = 0, per_sm = 0;
+    FQ_CUDA(cudaGetDevice(&dev));
+    FQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    FQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rng_throughput, 256, 0));
+    const long long threads = (long long)sms * std::max(per_sm, 1) * 256;
+    const long long per_thread = std::max<long long>(1, (n_blocks + threads - 1) / threads);
+    const unsigned grid = (unsigned)(threads / 256);
+    cudaEvent_t e0, e1;
+    FQ_CUDA(cudaEventCreate(&e0));
+    FQ_CUDA(cudaEventCreate(&e1));
+    k_rng_throughput<<<grid, 256, 0, s>>>(std::max<long long>(1, per_thread / 8));  // warm-up
+    cudaEventRecord(e0, s);
+    k_rng_throughput<<<grid, 256, 0, s>>>(per_thread);
+    cudaEventRecord(e1, s);
+    int rc = FCIQMC_OK;
+    float ms = 0.f;
+    if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess || !(ms > 0.f))
+        rc = FCIQMC_ERR_CUDA;
+    else
+        *blocks_per_s = (double)per_thread * (double)threads / (ms * 1e-3);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
+}
+
 struct fciqmc_batch {
     std::vector<fciqmc_handle *> runs;
     std::vector<cudaEvent_t> run_events;

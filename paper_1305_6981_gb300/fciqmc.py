@@ -221,3 +221,16 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def rng_throughput(n_blocks: int = 1 << 31, stream=None) -> float:
+    """Philox4x32-10 blocks per second on the current device, keyed like spawning attempts
+    (fciqmc_rng_throughput): the rate no walker cycle's attempts/s can exceed."""
+    import torch
+
+    L = _native.load()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    out = ctypes.c_double()
+    check(L.fciqmc_rng_throughput(int(n_blocks), ctypes.c_void_p(s.cuda_stream), ctypes.byref(out)),
+          "fciqmc_rng_throughput")
+    return out.value

@@ -9,10 +9,13 @@ walkers minus those the initiator rule aborted).
 """
 from __future__ import annotations
 
+import os
+
 import numpy as np
 import pytest
 
 import bruteforce as bf
+from oracle import oracle as O
 from oracle.oracle import Oracle
 from paper_1305_6981_gb300 import synth
 
@@ -55,3 +58,24 @@ def test_every_iteration_keeps_the_invariants(thr):
         aborted += r["aborted_walkers"]
     assert r["nd_out"] > 50 and r["iter"] == n_iter - 1
     assert (aborted > 0) == (thr >= 0)  # the initiator rule is active only when it is on
+
+
+def test_thread_count_does_not_change_results():
+    """The oracle splits a determinant's attempts into chunks spread over threads; one thread and several
+    threads give identical lists and counters (the reference holds several chunks' worth of walkers)."""
+    s = synth.init_12e24o()
+    dets, pops = synth.walker_snapshot(s, 60_000, seed=3, ref_fraction=0.5)
+    out = []
+    for threads in (1, 6):
+        O.set_threads(threads)
+        q = O.Oracle(s, tau=0.005, initiator_threshold=3, seed=9)
+        q.set_walkers(dets, pops, iteration=40, shift=0.3)
+        rows = q.iterate(3)
+        d, p, _ = q.walkers()
+        out.append((rows, sorted(zip(map(tuple, d.tolist()), p.tolist()))))
+    O.set_threads(os.cpu_count() or 1)
+    assert max(abs(int(x)) for x in pops) > 4 * 4096
+    assert out[0][1] == out[1][1]
+    for a, b in zip(out[0][0], out[1][0]):
+        assert {k: v for k, v in a.items() if k != "num_in"} == {k: v for k, v in b.items() if k != "num_in"}
+        assert abs(a["num_in"] - b["num_in"]) <= 1e-12 * max(1.0, abs(a["num_in"]))
