@@ -99,6 +99,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--growth-log", default="")
+    ap.add_argument("--save-state", default="",
+                    help="after growth and settling, save the walker list and run state to this .npz file")
+    ap.add_argument("--load-state", default="",
+                    help="start from a list saved by --save-state instead of growing (few launches before the "
+                         "timed region, for profiler captures)")
     ap.add_argument("--settle", type=int, default=-1,
                     help="iterations after the shift starts varying before warm-up (default: the workload's)")
     ap.add_argument("--no-extras", action="store_true",
@@ -176,22 +181,6 @@ def cpu_model() -> str:
     return "unknown"
 
 
-def _stored_forms(dets, pops):
-    """Spin-coupled functions are stored on the smaller of a determinant and its spin flip: map each
-    determinant of a synthetic snapshot to that form and merge the populations of a pair."""
-    even = np.uint64(0x5555555555555555)
-    flip = ((dets & even) << np.uint64(1)) | ((dets >> np.uint64(1)) & even)
-    keys = [tuple(r[::-1]) for r in dets.tolist()]
-    fkeys = [tuple(r[::-1]) for r in flip.tolist()]
-    merged = {}
-    for k, fk, c in zip(keys, fkeys, pops.tolist()):
-        m = min(k, fk)
-        merged[m] = merged.get(m, 0) + c
-    items = [(k, c) for k, c in merged.items() if c != 0]
-    d = np.array([k[::-1] for k, _ in items], dtype=np.uint64).reshape(-1, dets.shape[1])
-    return d, np.array([c for _, c in items], dtype=np.int32)
-
-
 def oracle_sample(wl, system):
     """The bounded sample that both the CPU baseline of the GPU arm and the reference arm time: a synthetic
     snapshot of the workload (2e5 walkers for the 24e/60o workloads, 5e4 otherwise; the reference holds 5%,
@@ -202,7 +191,7 @@ def oracle_sample(wl, system):
     dets, pops = synth.walker_snapshot(system, n, seed=7)
     q = Oracle(system, tau=wl["tau"], initiator_threshold=wl["thr"], seed=1, **wl.get("space", {}))
     if wl.get("space", {}).get("hphf"):
-        dets, pops = _stored_forms(dets, pops)
+        dets, pops = synth.stored_pairs(dets, pops)
     keep = np.array([q.in_space(d) for d in dets])
     return q, dets[keep], pops[keep]
 
@@ -386,6 +375,14 @@ def grow(args, wl, rank):
     t_grow = time.perf_counter()
     grown, chunk = 0, 50
     log = []
+    if args.load_state:
+        z = np.load(args.load_state)
+        st = {k: z["state"][i] for i, k in enumerate(("iteration", "shift", "vary_shift", "shift_counter",
+                                                       "nw_last_update"))}
+        g.set_walkers(z["dets"], z["pops"], z["hdiag"], iteration=int(st["iteration"]), shift=float(st["shift"]),
+                      vary=int(st["vary_shift"]), shift_counter=int(st["shift_counter"]),
+                      nw_last_update=int(st["nw_last_update"]))
+        return g, int(st["iteration"]), time.perf_counter() - t_grow, log
     while True:
         g.step(chunk)
         grown += chunk
@@ -405,6 +402,12 @@ def grow(args, wl, rank):
         log.append((grown, e["n_walkers"], e["n_dets"], e["shift"], e["list_slots"]))
         if e["status"] != 0:
             raise RuntimeError(f"device status {e['status']} while settling at {grown}: {log[-1]}")
+    if args.save_state:
+        d, p, hd = g.walkers()
+        st = g.state()
+        np.savez(args.save_state, dets=d, pops=p, hdiag=hd,
+                 state=np.array([st["iteration"], st["shift"], st["vary_shift"], st["shift_counter"],
+                                 st["nw_last_update"]], dtype=np.float64))
     return g, grown, time.perf_counter() - t_grow, log
 
 

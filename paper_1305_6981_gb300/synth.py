@@ -246,6 +246,22 @@ def walker_snapshot(system: System, n_walkers: int, seed: int = 0, ref_fraction:
     return dets.reshape(len(rows), W), np.array(pops, dtype=np.int32)
 
 
+def stored_pairs(dets: np.ndarray, pops: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """A snapshot on spin-coupled functions: each determinant of (dets, pops) is replaced by the smaller (last
+    word most significant) of itself and its spin flip (bits 2p and 2p + 1 exchanged), populations of a pair
+    are added, and entries that cancel are dropped. The determinants must have M_s = 0."""
+    dets = np.ascontiguousarray(dets, dtype=np.uint64).reshape(len(pops), -1)
+    even = np.uint64(0x5555555555555555)
+    flip = ((dets & even) << np.uint64(1)) | ((dets >> np.uint64(1)) & even)
+    merged: dict = {}
+    for k, fk, c in zip(map(tuple, dets[:, ::-1].tolist()), map(tuple, flip[:, ::-1].tolist()), pops.tolist()):
+        m = min(k, fk)
+        merged[m] = merged.get(m, 0) + int(c)
+    items = [(k, c) for k, c in merged.items() if c != 0]
+    out = np.array([k[::-1] for k, _ in items], dtype=np.uint64).reshape(-1, dets.shape[1])
+    return out, np.array([c for _, c in items], dtype=np.int32)
+
+
 def sampled_vector(system: System, n_dets: int, seed: int = 5, max_level: int = 6) -> tuple[np.ndarray, np.ndarray]:
     """A fixed amplitude vector with the structure of a time-averaged FCIQMC wavefunction: the aufbau
     reference (amplitude 1) plus distinct S_z-conserving excitations of it whose level L (electrons

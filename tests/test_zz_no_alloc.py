@@ -48,15 +48,16 @@ def _run_and_list(which):
         d0, p0 = synth.walker_snapshot(system, 100_000, seed=11)
         g.set_walkers(d0, p0)
         g.step(3)
-    else:  # spin-coupled functions, grown from the reference
-        system = synth.init_12e24o()
-        g = Fciqmc(system, 0.005, 3, main_capacity=1 << 18, seed=3, hphf=True, initial_population=4000,
-                   initial_shift=1.0)
-        g.step(150)
+    else:  # spin-coupled functions: a snapshot mapped to the stored determinants of its pairs
+        system = synth.large_24e60o()
+        g = Fciqmc(system, 0.005, 3, main_capacity=1 << 18, seed=3, hphf=True)
+        d0, p0 = synth.stored_pairs(*synth.walker_snapshot(system, 100_000, seed=11))
+        g.set_walkers(d0, p0)
+        g.step(3)
     return system, g
 
 
-@pytest.mark.parametrize("which", ["12e24o", "24e60o", "12e24o-spin-coupled"])
+@pytest.mark.parametrize("which", ["12e24o", "24e60o", "24e60o-spin-coupled"])
 def test_static_estimator_matches_run_and_oracle_twice(which):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -71,7 +72,7 @@ def test_static_estimator_matches_run_and_oracle_twice(which):
     dets, pops, _ = g.walkers()
     assert len(pops) > 300 and ref["c0"] != 0 and ref["proj_num"] != 0.0
     if spin:  # open-shell functions carry the sqrt(2) of the spin coupling: some must be present
-        assert any((int(x) ^ (int(x) >> 1)) & 0x5555555555555555 for x in dets[:, 0])
+        assert any((int(x) ^ (int(x) >> 1)) & 0x5555555555555555 for x in dets.reshape(-1))
     q = Oracle(system, tau=0.005, initiator_threshold=3, hphf=spin)
     q.set_walkers(dets, pops)
     est_q = q.estimate()
