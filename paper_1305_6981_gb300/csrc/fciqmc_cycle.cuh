@@ -390,8 +390,13 @@ __global__ void __launch_bounds__(256) k_estimate(Params P) {
         int diff = 0;
 #pragma unroll
         for (int w = 0; w < W; ++w) { xd |= d[w] ^ P.ref[w]; diff += __popcll(d[w] ^ P.ref[w]); }
-        if (xd == 0) st->est_c0 = c;
-        else if (diff == 2 || diff == 4) num = __dadd_rn(num, __dmul_rn(h0i<W>(P, d), (double)c));
+        if (xd == 0) {
+            st->est_c0 = c;
+        } else if (diff == 2 || diff == 4) {
+            double h0 = h0i<W>(P, d);
+            if (P.hphf && n_open<W>(d) > 0) h0 = __dmul_rn(h0, kSqrt2);  // closed reference, open function
+            num = __dadd_rn(num, __dmul_rn(h0, (double)c));
+        }
     }
     unsigned long long accv[2] = {nw, nd};
     unsigned long long *const dst[2] = {&st->est_nw, &st->est_nd};

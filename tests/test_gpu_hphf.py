@@ -38,6 +38,10 @@ def lockstep(g, q, n_iter):
         rows_q += q.iterate(1)
         assert same_lists(g.walkers(), q.walkers()), f"walker lists differ after iteration {k + 1}"
     compare_rows(g.history(n_iter), rows_q)
+    # the estimators of the final list (fciqmc_estimators), open-shell functions with their sqrt(2)
+    e, est = g.estimates(), q.estimate()
+    assert e["n_walkers"] == est["nw"] and e["n_dets"] == est["nd"] and e["c0"] == est["c0"]
+    assert abs(e["proj_num"] - est["num"]) <= 1e-11 * max(abs(est["num"]), 1e-300)
     return rows_q
 
 
