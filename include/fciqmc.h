@@ -107,6 +107,18 @@ typedef struct {
      * unsigned number, last word most significant) of D and Dbar. Needs ms2 = 0 and a closed-shell
      * reference (else FCIQMC_ERR_INVALID_ARG); loaded lists must hold stored determinants. */
     int32_t hphf;
+    /* Hash-partitioned runs (Sec. V A, Algorithm 1): with n_partitions = P > 1 the handle holds partition
+     * partition_index (0 <= index < P <= 64) of a run: the determinants whose Algorithm 1 fingerprint (the
+     * one that keys the random numbers, see fciqmc_owner) is congruent to the index mod P. Its spawns onto
+     * determinants of other partitions go to one outbox per destination of outbox_capacity entries (0: a
+     * quarter of the spawn table); an overflowing outbox stops the iteration with FCIQMC_ERR_CAPACITY. A
+     * partition is advanced only through fciqmc_group_* with the run's other partitions (fciqmc_step,
+     * fciqmc_profile and fciqmc_batch_create refuse it); the reference's initial walkers are placed by its
+     * own partition; loaded lists may hold only the partition's determinants. The random numbers do not
+     * depend on the partitioning, so a run gives the same walkers for every P. 0 or 1: not partitioned. */
+    int32_t n_partitions;
+    int32_t partition_index;
+    int64_t outbox_capacity;
 } fciqmc_options;
 
 /* Per-iteration record. The estimators (nw_in .. num_in) describe the list at
@@ -267,6 +279,55 @@ int fciqmc_batch_step(fciqmc_batch *b, int32_t n_launches, void *cuda_stream);
 
 /* Releases the graph and events (synchronising on the last batch stream). Accepts NULL. */
 void fciqmc_batch_destroy(fciqmc_batch *b);
+
+/* ---------------------------------------------------------------------------
+ * Hash-partitioned runs (Sec. V A): the determinants of one run are divided among P partitions by
+ * hash (Algorithm 1 fingerprint mod P), each partition a handle with its own main list, hash index, spawn
+ * table and workspace (created with fciqmc_options.n_partitions = P and partition_index = r). An iteration
+ * of the group is the paper's scheme: every partition spawns from its own determinants and routes each
+ * spawn onto another partition's determinant into that partition's outbox (the spawned array ordered by
+ * destination, Fig. 2); in the exchange each partition merges the entries bound for it; then every
+ * partition annihilates its merged list against its own main list, and the run's N_w, C_0, numerator and
+ * counters are summed over partitions for one row and one shift update, applied to all partitions. Here
+ * the partitions share one GPU and the exchange reads the outboxes in device memory; the results are those
+ * of the unpartitioned run (same random numbers), which the tests check against the oracle. */
+typedef struct fciqmc_group fciqmc_group;
+
+/* Device bytes fciqmc_group_create needs for n_partitions partitions and history_capacity rows (0: 2^16).
+ * Returns 0 for n_partitions outside [2, 64]. */
+size_t fciqmc_group_workspace_bytes(int32_t n_partitions, int64_t history_capacity);
+
+/* Groups parts[0..n_partitions) (part r created with partition_index r, all with the same problem, time
+ * step, initiator threshold and options, on the current device) into one run. workspace: device memory of
+ * fciqmc_group_workspace_bytes(n_partitions, history_capacity) bytes, 256-byte aligned, owned by the caller.
+ * cuda_stream: the stream the group's iterations are enqueued on. The group does not own the partitions;
+ * they must outlive it. Synchronising. Returns FCIQMC_ERR_INVALID_ARG for mismatched partitions. */
+int fciqmc_group_create(fciqmc_handle *const *parts, int32_t n_partitions, int64_t history_capacity, void *workspace,
+                        size_t workspace_bytes, void *cuda_stream, fciqmc_group **out);
+
+/* Enqueues n_iterations iterations of the partitioned run on the group's stream (ordered after work
+ * previously enqueued on the partitions' streams, which are made to wait for it). Asynchronous. */
+int fciqmc_group_step(fciqmc_group *g, int32_t n_iterations);
+
+/* Waits for the group's stream; returns the group's sticky status (the first error of any partition, which
+ * stops every partition before the failing iteration changes any committed list). */
+int fciqmc_group_sync(fciqmc_group *g);
+
+/* Synchronising: copies up to max_rows of the run's most recent rows (sums over the partitions; the
+ * numerator added in partition order), oldest first, into rows (host); *n_rows receives the count. Each
+ * partition's fciqmc_history holds its own list's rows. */
+int fciqmc_group_history(fciqmc_group *g, fciqmc_row *rows, int64_t max_rows, int64_t *n_rows);
+
+/* Releases the group's graph and events (synchronising). Accepts NULL. */
+void fciqmc_group_destroy(fciqmc_group *g);
+
+/* Host only, no GPU needed: the partition of each of n determinants (W = ceil(2 n_orb / 64) words each) in
+ * a run of n_partitions partitions, owner[k] = fingerprint(D_k) mod n_partitions with the fingerprint of
+ * Algorithm 1 (Sec. V): hash <- 1099511628211 hash + map(orbital_i) i over the occupied spin orbitals in
+ * ascending order, i from 1, modulo 2^64, map(k) = the first two words of Philox4x32-10 with key
+ * (0x46434951, 0x4D415031) and counter (k, 0, 0, 0). Returns FCIQMC_ERR_INVALID_ARG for a bad size,
+ * partition count or NULL arrays. */
+int fciqmc_owner(int n_orb, const uint64_t *dets, int64_t n, int32_t n_partitions, int32_t *owner);
 
 /* Synchronising: dynamic state of the run. */
 int fciqmc_get_state(fciqmc_handle *h, fciqmc_state *st);

@@ -77,7 +77,9 @@ class Options(ctypes.Structure):
                 ("grid_blocks", ctypes.c_int32), ("index_load", ctypes.c_double),
                 ("space_flags", ctypes.c_uint32), ("max_excitation", ctypes.c_int32),
                 ("max_seniority", ctypes.c_int32), ("frozen_occupied", ctypes.POINTER(ctypes.c_uint64)),
-                ("frozen_empty", ctypes.POINTER(ctypes.c_uint64)), ("hphf", ctypes.c_int32)]
+                ("frozen_empty", ctypes.POINTER(ctypes.c_uint64)), ("hphf", ctypes.c_int32),
+                ("n_partitions", ctypes.c_int32), ("partition_index", ctypes.c_int32),
+                ("outbox_capacity", ctypes.c_int64)]
 
 
 ROW_FIELDS = ["iteration", "shift", "nw_in", "nd_in", "c0_in", "num_in", "nw_out", "nd_out", "attempts", "nulls",
@@ -119,7 +121,9 @@ SYMBOLS = ["fciqmc_default_options", "fciqmc_workspace_bytes", "fciqmc_create", 
            "fciqmc_get_state", "fciqmc_get_info", "fciqmc_profile", "fciqmc_estimate_list_static", "fciqmc_destroy",
            "fciqmc_strerror", "fciqmc_rdm_workspace_bytes", "fciqmc_rdm_create", "fciqmc_rdm_energy",
            "fciqmc_rdm_gradient", "fciqmc_rdm_info", "fciqmc_rdm_destroy", "fciqmc_batch_create",
-           "fciqmc_batch_step", "fciqmc_batch_destroy", "fciqmc_rng_throughput"]
+           "fciqmc_batch_step", "fciqmc_batch_destroy", "fciqmc_rng_throughput", "fciqmc_group_workspace_bytes",
+           "fciqmc_group_create", "fciqmc_group_step", "fciqmc_group_sync", "fciqmc_group_history",
+           "fciqmc_group_destroy", "fciqmc_owner"]
 STATIC_MAX_DETS = 1 << 23
 STATIC_SPIN_COUPLED = 1
 N_KERNELS = 8
@@ -168,6 +172,18 @@ def _declare(L):
     L.fciqmc_batch_step.restype = ctypes.c_int
     L.fciqmc_batch_destroy.argtypes = [vp]
     L.fciqmc_batch_destroy.restype = None
+    L.fciqmc_group_workspace_bytes.argtypes = [i32, i64]
+    L.fciqmc_group_workspace_bytes.restype = ctypes.c_size_t
+    L.fciqmc_group_create.argtypes = [P(vp), i32, i64, vp, ctypes.c_size_t, vp, P(vp)]
+    L.fciqmc_group_step.argtypes = [vp, i32]
+    L.fciqmc_group_sync.argtypes = [vp]
+    L.fciqmc_group_history.argtypes = [vp, P(Row), i64, P(i64)]
+    L.fciqmc_group_destroy.argtypes = [vp]
+    L.fciqmc_group_destroy.restype = None
+    L.fciqmc_owner.argtypes = [ctypes.c_int, u64p, i64, i32, i32p]
+    for name in ("fciqmc_group_create", "fciqmc_group_step", "fciqmc_group_sync", "fciqmc_group_history",
+                 "fciqmc_owner"):
+        getattr(L, name).restype = ctypes.c_int
     L.fciqmc_rng_throughput.argtypes = [i64, vp, P(ctypes.c_double)]
     L.fciqmc_rng_throughput.restype = ctypes.c_int
     L.fciqmc_destroy.argtypes = [vp]

@@ -41,8 +41,8 @@ int log2_exact(long long x) {
 }
 
 struct Sizes {
-    int W, n_so, npairs;
-    long long n_eri, cap, idx_cap, mt_cap, hist_cap, heavy_cap, ref_cap;
+    int W, n_so, npairs, n_parts, part;
+    long long n_eri, cap, idx_cap, mt_cap, hist_cap, heavy_cap, ref_cap, ob_cap;
 };
 
 bool sizes_of(int n_elec, int n_orb, const fciqmc_options &o, Sizes &z) {
@@ -64,13 +64,17 @@ bool sizes_of(int n_elec, int n_orb, const fciqmc_options &o, Sizes &z) {
     // the reference's double excitations: at most npairs x virtuals x virtuals choices
     const long long nv = z.n_so - n_elec;
     z.ref_cap = std::min<long long>((long long)z.npairs * nv * nv, 1LL << 22);
+    // hash partitioning: one outbox per destination partition
+    z.n_parts = o.n_partitions > 1 ? o.n_partitions : 1;
+    z.part = o.n_partitions > 1 ? o.partition_index : 0;
+    z.ob_cap = z.n_parts > 1 ? (o.outbox_capacity > 0 ? o.outbox_capacity : std::max<long long>(z.mt_cap / 4, 1024)) : 0;
     return true;
 }
 
 struct Layout {
     size_t state, h, h_f, eri, eri_f, wpair, map1, cmask, unionm, irrep, pairs, recip, rcpf, ref_occ, facts, e0;
     size_t det[2], hd[2], hdf[2], pop[2][2], idx, mt, merged, heavy, heavy_base, heavy_att, partial, hist;
-    size_t ref_pinfo, ref_off2, ref_exc;
+    size_t ref_pinfo, ref_off2, ref_exc, outbox;
     size_t total;
 };
 
@@ -117,8 +121,42 @@ Layout layout_of(const Sizes &z, int n_orb) {
     L.ref_pinfo = take(sizeof(unsigned) * std::max(z.npairs, 1));
     L.ref_off2 = take(sizeof(unsigned) * std::max<long long>((long long)z.npairs * z.n_so, 1));
     L.ref_exc = take(sizeof(fq::RefExc) * std::max<long long>(z.ref_cap, 1));
+    L.outbox = take(sizeof(unsigned long long) * stride * z.n_parts * z.ob_cap);
     L.total = off;
     return L;
+}
+
+// Host copies of the orbital map and fingerprint of Algorithm 1 (the device computes the same in k_setup and
+// fingerprint<W>): Philox4x32-10 (Salmon et al., SC'11) with 64-bit products.
+void host_philox(const unsigned ctr_in[4], const unsigned key_in[2], unsigned out[4]) {
+    unsigned c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3], k0 = key_in[0], k1 = key_in[1];
+    for (int r = 0; r < 10; ++r) {
+        const unsigned long long p0 = 0xD2511F53ull * c0, p1 = 0xCD9E8D57ull * c2;
+        const unsigned n0 = (unsigned)(p1 >> 32) ^ c1 ^ k0, n2 = (unsigned)(p0 >> 32) ^ c3 ^ k1;
+        c0 = n0;
+        c1 = (unsigned)p1;
+        c2 = n2;
+        c3 = (unsigned)p0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = c0;
+    out[1] = c1;
+    out[2] = c2;
+    out[3] = c3;
+}
+unsigned long long host_map1(int k) {
+    const unsigned ctr[4] = {(unsigned)k, 0u, 0u, 0u}, key[2] = {0x46434951u, 0x4D415031u};
+    unsigned o[4];
+    host_philox(ctr, key, o);
+    return (unsigned long long)o[0] | ((unsigned long long)o[1] << 32);
+}
+unsigned long long host_fingerprint(const uint64_t *d, int W, const unsigned long long *map1) {
+    unsigned long long h = 0, n = 0;
+    for (int w = 0; w < W; ++w)
+        for (int b = 0; b < 64; ++b)
+            if ((d[w] >> b) & 1ull) h = 1099511628211ull * h + map1[64 * w + b] * (++n);
+    return h;
 }
 
 }  // namespace
@@ -137,6 +175,9 @@ struct fciqmc_handle {
     cudaGraphExec_t graph;
     bool graph_ready;
     int grid_request;
+    fciqmc_options opt;      // as created (checked when partitions are grouped)
+    double tau;
+    int32_t init_thr;
 };
 
 namespace {
@@ -345,6 +386,9 @@ int fciqmc_create(const double *h1, const double *eri_s8, double e_core, int n_e
     if (opt) o = *opt;
     else fciqmc_default_options(&o);
     if (o.shift_period < 1 || o.initial_population == 0 || o.target_walkers < 0) return FCIQMC_ERR_INVALID_ARG;
+    if (o.n_partitions < 0 || o.n_partitions > fq::MAXPARTS || o.outbox_capacity < 0 ||
+        (o.n_partitions > 1 && (o.partition_index < 0 || o.partition_index >= o.n_partitions)))
+        return FCIQMC_ERR_INVALID_ARG;
     Sizes z;
     if (!sizes_of(n_elec, n_orb, o, z)) return FCIQMC_ERR_UNSUPPORTED;
     Layout L = layout_of(z, n_orb);
@@ -381,6 +425,9 @@ int fciqmc_create(const double *h1, const double *eri_s8, double e_core, int n_e
     h->graph_tmpl = nullptr;
     h->grid_request = o.grid_blocks;
     h->smem_w = sizeof(double) * (2 * n_orb * n_orb + n_orb);
+    h->opt = o;
+    h->tau = tau;
+    h->init_thr = initiator_threshold < 0 ? -1 : initiator_threshold;
 
     Params &P = h->P;
     std::memset(&P, 0, sizeof(P));
@@ -435,6 +482,10 @@ int fciqmc_create(const double *h1, const double *eri_s8, double e_core, int n_e
     P.hist = at<fciqmc_row>(h, L.hist);
     P.hist_cap = z.hist_cap;
     P.st = at<DevState>(h, L.state);
+    P.n_parts = z.n_parts;
+    P.part = z.part;
+    P.outbox = z.n_parts > 1 ? at<unsigned long long>(h, L.outbox) : nullptr;
+    P.ob_cap = z.ob_cap;
 
     int rc = FCIQMC_OK;
     cudaStream_t s = h->stream;
@@ -574,13 +625,21 @@ int fciqmc_create(const double *h1, const double *eri_s8, double e_core, int n_e
                 n_ref_exc = 0;
             }
         }
-        // initial state: the reference with the initial population
+        // initial state: the reference with the initial population (in a partitioned run, on the reference's
+        // own partition; the others start empty)
+        bool owns_ref = true;
+        if (z.n_parts > 1) {
+            std::vector<unsigned long long> m1(z.n_so);
+            FQ_TRY(cudaMemcpyAsync(m1.data(), P.map1, sizeof(unsigned long long) * z.n_so, cudaMemcpyDeviceToHost, s));
+            FQ_TRY(cudaStreamSynchronize(s));
+            owns_ref = (int)(host_fingerprint(ref, z.W, m1.data()) % (unsigned long long)z.n_parts) == z.part;
+        }
         DevState st0;
         std::memset(&st0, 0, sizeof(st0));
         st0.iter = 0;
         st0.shift = o.initial_shift;
-        st0.list_len = 1;
-        st0.claim = 1;
+        st0.list_len = owns_ref ? 1 : 0;
+        st0.claim = owns_ref ? 1 : 0;
         FQ_TRY(cudaMemcpyAsync(P.st, &st0, sizeof(st0), cudaMemcpyHostToDevice, s));
         FQ_TRY(cudaMemcpyAsync(P.det[0], ref, sizeof(uint64_t) * z.W, cudaMemcpyHostToDevice, s));
         int p0 = o.initial_population;
@@ -629,7 +688,7 @@ fail:
 }
 
 int fciqmc_step(fciqmc_handle *h, int32_t n_iterations) {
-    if (!h || n_iterations < 0) return FCIQMC_ERR_INVALID_ARG;
+    if (!h || n_iterations < 0 || h->z.n_parts > 1) return FCIQMC_ERR_INVALID_ARG;
     for (int i = 0; i < n_iterations; ++i) {
         if (h->graph_ready) FQ_CUDA(cudaGraphLaunch(h->graph, h->stream));
         else enqueue(h, h->stream);
@@ -639,7 +698,7 @@ int fciqmc_step(fciqmc_handle *h, int32_t n_iterations) {
 }
 
 int fciqmc_profile(fciqmc_handle *h, int32_t n_iterations, double *kernel_ms) {
-    if (!h || !kernel_ms || n_iterations < 0) return FCIQMC_ERR_INVALID_ARG;
+    if (!h || !kernel_ms || n_iterations < 0 || h->z.n_parts > 1) return FCIQMC_ERR_INVALID_ARG;
     cudaEvent_t ev[FCIQMC_N_KERNELS + 1];
     for (int k = 0; k <= FCIQMC_N_KERNELS; ++k) FQ_CUDA(cudaEventCreate(&ev[k]));
     const Params &P = h->P;
@@ -909,7 +968,8 @@ int fciqmc_batch_create(fciqmc_handle *const *runs, int n_runs, int32_t iteratio
     if (!out || !runs || n_runs < 1 || iterations_per_launch < 1) return FCIQMC_ERR_INVALID_ARG;
     *out = nullptr;
     for (int r = 0; r < n_runs; ++r) {
-        if (!runs[r] || !runs[r]->graph_ready || !runs[r]->graph_tmpl) return FCIQMC_ERR_INVALID_ARG;
+        if (!runs[r] || !runs[r]->graph_ready || !runs[r]->graph_tmpl || runs[r]->z.n_parts > 1)
+            return FCIQMC_ERR_INVALID_ARG;
         for (int q = 0; q < r; ++q)
             if (runs[q] == runs[r]) return FCIQMC_ERR_INVALID_ARG;
     }
@@ -974,6 +1034,222 @@ void fciqmc_batch_destroy(fciqmc_batch *b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     delete b;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------------------------
+// Hash-partitioned runs (Sec. V A).
+struct fciqmc_group {
+    std::vector<fciqmc_handle *> parts;
+    std::vector<cudaEvent_t> part_events;
+    cudaEvent_t done;
+    cudaStream_t stream;
+    fq::PartLink *links;      // device
+    fq::GroupDev *gdev;       // device
+    fciqmc_row *ghist;        // device ring
+    long long hist_cap;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+};
+
+namespace {
+
+struct GroupLayout {
+    size_t gdev, links, hist, total;
+};
+GroupLayout group_layout(int n, long long hist_cap) {
+    GroupLayout L{};
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = align_up(off + bytes);
+        return o;
+    };
+    L.gdev = take(sizeof(fq::GroupDev));
+    L.links = take(sizeof(fq::PartLink) * n);
+    L.hist = take(sizeof(fciqmc_row) * hist_cap);
+    L.total = off;
+    return L;
+}
+
+template <int W>
+void enqueue_group_iteration(fciqmc_group *g, cudaStream_t s) {
+    const int n = (int)g->parts.size();
+    for (fciqmc_handle *h : g->parts) {
+        const Params &P = h->P;
+        fq::k_compact_copy<W><<<h->small_grid, 256, 0, s>>>(P);
+        fq::k_index_clear<<<h->small_grid, 256, 0, s>>>(P, 0);
+        fq::k_index_locate_old<W><<<h->small_grid, 256, 0, s>>>(P);
+        fq::k_index_clear_old<W><<<h->small_grid, 256, 0, s>>>(P);
+        fq::k_index_fill<W><<<h->small_grid, 256, 0, s>>>(P, 0);
+        fq::k_compact_finish<<<1, 32, 0, s>>>(P);
+    }
+    for (fciqmc_handle *h : g->parts) launch_spawning<W>(h, s);
+    // the exchange: each partition merges the spawns the others routed to it
+    for (fciqmc_handle *h : g->parts) fq::k_receive<W><<<h->ann_grid, 256, 0, s>>>(h->P, g->links);
+    for (fciqmc_handle *h : g->parts) {
+        fq::k_annihilate<W><<<h->ann_grid, 256, 0, s>>>(h->P);
+        fq::k_new_diag<W><<<h->diag_grid, 256, h->smem_w, s>>>(h->P);
+    }
+    const Params &P0 = g->parts[0]->P;
+    fq::k_group_finish<<<1, 32, 0, s>>>(g->links, n, g->gdev, g->ghist, g->hist_cap, P0.target, P0.period, P0.c_shift);
+}
+
+bool same_run(const fciqmc_handle *a, const fciqmc_handle *b) {
+    const fciqmc_options &x = a->opt, &y = b->opt;
+    return a->z.W == b->z.W && a->P.n_elec == b->P.n_elec && a->P.n_orb == b->P.n_orb && a->tau == b->tau &&
+           a->init_thr == b->init_thr && a->P.d53 == b->P.d53 && a->P.E0 == b->P.E0 && a->P.ref[0] == b->P.ref[0] &&
+           a->P.ref[1] == b->P.ref[1] && x.shift_damping == y.shift_damping && x.shift_period == y.shift_period &&
+           x.initial_shift == y.initial_shift && x.target_walkers == y.target_walkers &&
+           (x.seed & 0xFFFFFFFFull) == (y.seed & 0xFFFFFFFFull) && a->P.space == b->P.space &&
+           a->P.max_exc == b->P.max_exc && a->P.max_sen == b->P.max_sen && a->P.hphf == b->P.hphf &&
+           a->P.froz_occ[0] == b->P.froz_occ[0] && a->P.froz_occ[1] == b->P.froz_occ[1] &&
+           a->P.froz_emp[0] == b->P.froz_emp[0] && a->P.froz_emp[1] == b->P.froz_emp[1] &&
+           a->z.n_parts == b->z.n_parts;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t fciqmc_group_workspace_bytes(int32_t n_partitions, int64_t history_capacity) {
+    if (n_partitions < 2 || n_partitions > fq::MAXPARTS || history_capacity < 0) return 0;
+    return group_layout(n_partitions, history_capacity > 0 ? history_capacity : (1LL << 16)).total;
+}
+
+int fciqmc_group_create(fciqmc_handle *const *parts, int32_t n_partitions, int64_t history_capacity, void *workspace,
+                        size_t workspace_bytes, void *cuda_stream, fciqmc_group **out) {
+    if (!out) return FCIQMC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!parts || n_partitions < 2 || n_partitions > fq::MAXPARTS || history_capacity < 0) return FCIQMC_ERR_INVALID_ARG;
+    for (int r = 0; r < n_partitions; ++r) {
+        const fciqmc_handle *h = parts[r];
+        if (!h || h->z.n_parts != n_partitions || h->z.part != r || !same_run(h, parts[0])) return FCIQMC_ERR_INVALID_ARG;
+    }
+    const long long hist_cap = history_capacity > 0 ? history_capacity : (1LL << 16);
+    const GroupLayout L = group_layout(n_partitions, hist_cap);
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0 || workspace_bytes < L.total)
+        return FCIQMC_ERR_WORKSPACE;
+    fciqmc_group *g = new (std::nothrow) fciqmc_group();
+    if (!g) return FCIQMC_ERR_INVALID_ARG;
+    char *ws = static_cast<char *>(workspace);
+    g->parts.assign(parts, parts + n_partitions);
+    g->stream = static_cast<cudaStream_t>(cuda_stream);
+    g->gdev = reinterpret_cast<fq::GroupDev *>(ws + L.gdev);
+    g->links = reinterpret_cast<fq::PartLink *>(ws + L.links);
+    g->ghist = reinterpret_cast<fciqmc_row *>(ws + L.hist);
+    g->hist_cap = hist_cap;
+    g->graph = nullptr;
+    g->exec = nullptr;
+    std::vector<fq::PartLink> links(n_partitions);
+    for (int r = 0; r < n_partitions; ++r) {
+        const Params &P = parts[r]->P;
+        links[r].st = P.st;
+        links[r].outbox = P.outbox;
+        links[r].ob_cap = P.ob_cap;
+        links[r].partial = P.partial;
+        links[r].sweep_grid = P.sweep_grid;
+        links[r].hist = P.hist;
+        links[r].hist_cap = P.hist_cap;
+        links[r].cap = P.cap;
+    }
+    int rc = FCIQMC_OK;
+    cudaStream_t cs = nullptr;
+    do {
+        // the partitions' own streams finish their work (creation, loads) before the group starts
+        for (fciqmc_handle *h : g->parts)
+            if (cudaStreamSynchronize(h->stream) != cudaSuccess) { rc = FCIQMC_ERR_CUDA; break; }
+        if (rc != FCIQMC_OK) break;
+        if (cudaMemsetAsync(g->gdev, 0, sizeof(fq::GroupDev), g->stream) != cudaSuccess ||
+            cudaMemcpyAsync(g->links, links.data(), sizeof(fq::PartLink) * n_partitions, cudaMemcpyHostToDevice,
+                            g->stream) != cudaSuccess ||
+            cudaStreamSynchronize(g->stream) != cudaSuccess) { rc = FCIQMC_ERR_CUDA; break; }
+        if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) { rc = FCIQMC_ERR_CUDA; break; }
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            if (parts[0]->z.W == 1) enqueue_group_iteration<1>(g, cs);
+            else enqueue_group_iteration<2>(g, cs);
+            e = cudaStreamEndCapture(cs, &graph);
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&g->exec, graph, 0);
+        if (e == cudaSuccess) g->graph = graph;
+        else if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) { rc = FCIQMC_ERR_CUDA; break; }
+        g->part_events.resize(n_partitions);
+        for (int r = 0; r < n_partitions && rc == FCIQMC_OK; ++r)
+            if (cudaEventCreateWithFlags(&g->part_events[r], cudaEventDisableTiming) != cudaSuccess) rc = FCIQMC_ERR_CUDA;
+        if (rc == FCIQMC_OK && cudaEventCreateWithFlags(&g->done, cudaEventDisableTiming) != cudaSuccess)
+            rc = FCIQMC_ERR_CUDA;
+    } while (false);
+    if (cs) cudaStreamDestroy(cs);
+    if (rc != FCIQMC_OK) {
+        cudaGetLastError();
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        if (g->graph) cudaGraphDestroy(g->graph);
+        delete g;
+        return rc;
+    }
+    *out = g;
+    return FCIQMC_OK;
+}
+
+int fciqmc_group_step(fciqmc_group *g, int32_t n_iterations) {
+    if (!g || n_iterations < 0) return FCIQMC_ERR_INVALID_ARG;
+    for (size_t r = 0; r < g->parts.size(); ++r) {
+        FQ_CUDA(cudaEventRecord(g->part_events[r], g->parts[r]->stream));
+        FQ_CUDA(cudaStreamWaitEvent(g->stream, g->part_events[r], 0));
+    }
+    for (int k = 0; k < n_iterations; ++k) FQ_CUDA(cudaGraphLaunch(g->exec, g->stream));
+    FQ_CUDA(cudaEventRecord(g->done, g->stream));
+    for (fciqmc_handle *h : g->parts) FQ_CUDA(cudaStreamWaitEvent(h->stream, g->done, 0));
+    return FCIQMC_OK;
+}
+
+int fciqmc_group_sync(fciqmc_group *g) {
+    if (!g) return FCIQMC_ERR_INVALID_ARG;
+    fq::GroupDev d;
+    FQ_CUDA(cudaMemcpyAsync(&d, g->gdev, sizeof(d), cudaMemcpyDeviceToHost, g->stream));
+    FQ_CUDA(cudaStreamSynchronize(g->stream));
+    return d.status;
+}
+
+int fciqmc_group_history(fciqmc_group *g, fciqmc_row *rows, int64_t max_rows, int64_t *n_rows) {
+    if (!g || !n_rows || max_rows < 0 || (max_rows > 0 && !rows)) return FCIQMC_ERR_INVALID_ARG;
+    fq::GroupDev d;
+    FQ_CUDA(cudaMemcpyAsync(&d, g->gdev, sizeof(d), cudaMemcpyDeviceToHost, g->stream));
+    FQ_CUDA(cudaStreamSynchronize(g->stream));
+    const long long avail = std::min<long long>(d.hist_n, g->hist_cap);
+    const long long n = std::min<long long>(avail, max_rows);
+    for (long long k = 0; k < n; ++k) {
+        const long long idx = (d.hist_n - n + k) % g->hist_cap;
+        FQ_CUDA(cudaMemcpyAsync(rows + k, g->ghist + idx, sizeof(fciqmc_row), cudaMemcpyDeviceToHost, g->stream));
+    }
+    FQ_CUDA(cudaStreamSynchronize(g->stream));
+    *n_rows = n;
+    return FCIQMC_OK;
+}
+
+void fciqmc_group_destroy(fciqmc_group *g) {
+    if (!g) return;
+    cudaStreamSynchronize(g->stream);
+    for (cudaEvent_t e : g->part_events) cudaEventDestroy(e);
+    if (!g->part_events.empty()) cudaEventDestroy(g->done);
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
+}
+
+int fciqmc_owner(int n_orb, const uint64_t *dets, int64_t n, int32_t n_partitions, int32_t *owner) {
+    if (n_orb < 1 || n_orb > 64 || n < 0 || n_partitions < 1 || (n > 0 && (!dets || !owner))) return FCIQMC_ERR_INVALID_ARG;
+    const int W = (2 * n_orb + 63) / 64;
+    unsigned long long map1[fq::MAXSO];
+    for (int k = 0; k < 2 * n_orb; ++k) map1[k] = host_map1(k);
+    for (int k = 2 * n_orb; k < fq::MAXSO; ++k) map1[k] = 0ull;
+    for (int64_t x = 0; x < n; ++x)
+        owner[x] = (int32_t)(host_fingerprint(dets + x * W, W, map1) % (unsigned long long)n_partitions);
+    return FCIQMC_OK;
 }
 
 }  // extern "C"

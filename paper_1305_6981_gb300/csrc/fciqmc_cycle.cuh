@@ -173,27 +173,19 @@ __device__ double own_log(double x) {
     return __dadd_rn(__dmul_rn(de, LN2_HI), r);
 }
 
-__global__ void k_finish(Params P) {
-    DevState *st = P.st;
-    if (st->status) return;
-    // Eq. 2 numerator: the sweep blocks' partials summed by one warp in a fixed order (lane k takes
-    // blocks k, k + 32, ..., then a fixed shuffle tree), so the sum is the same in every run
-    const int lane = threadIdx.x & 31;
-    double part = 0.0;
-    for (int b = lane; b < P.sweep_grid; b += 32) part = __dadd_rn(part, P.partial[b]);
-    const double num = warp_sum_f64(part);  // lane 0 holds the total
-    if (threadIdx.x != 0) return;
-    const long long nw_in = (long long)st->nw_in, nd_in = (long long)st->nd_in;
-    const long long nw_out = nw_in + (long long)st->d_nw, nd_out = nd_in + (long long)st->d_nd;
+// The iteration's row for one list: its estimators (start of the iteration) and counters; num is the
+// Eq. 2 numerator of the list.
+__device__ __forceinline__ fciqmc_row list_row(const DevState *st, double num) {
     fciqmc_row row;
+    const long long nw_in = (long long)st->nw_in, nd_in = (long long)st->nd_in;
     row.iteration = st->iter;
     row.shift = st->shift;
     row.nw_in = nw_in;
     row.nd_in = nd_in;
     row.c0_in = st->c0_in;
     row.num_in = num;
-    row.nw_out = nw_out;
-    row.nd_out = nd_out;
+    row.nw_out = nw_in + (long long)st->d_nw;
+    row.nd_out = nd_in + (long long)st->d_nd;
     row.attempts = (long long)st->cnt[C_ATTEMPTS];
     row.nulls = (long long)st->cnt[C_NULLS];
     row.spawn_events = (long long)st->cnt[C_EVENTS];
@@ -204,26 +196,34 @@ __global__ void k_finish(Params P) {
     row.aborted_walkers = (long long)st->cnt[C_ABORTED];
     row.inserted_dets = (long long)st->cnt[C_INSERTED];
     row.heavy_attempts = (long long)st->cnt[C_HEAVY];
-    P.hist[st->hist_n % P.hist_cap] = row;
-    st->hist_n++;
-    // shift: S <- S - zeta/(A tau) ln(N_w(n) / N_w(n-A)) every A iterations once N_w reached the target
+    return row;
+}
+
+// Shift update of the run: S <- S - zeta/(A tau) ln(N_w(n) / N_w(n-A)) every A iterations once N_w reached
+// the target (nw_out: the whole run's walkers after the iteration).
+__device__ __forceinline__ void shift_update(DevState *st, long long nw_out, long long target, int period, double c_shift) {
     if (!st->vary) {
-        if (nw_out >= P.target) { st->vary = 1; st->nw_prev = nw_out; st->n_since = 0; }
+        if (nw_out >= target) { st->vary = 1; st->nw_prev = nw_out; st->n_since = 0; }
     } else {
         st->n_since++;
-        if (st->n_since == P.period) {
+        if (st->n_since == period) {
             double ratio = __ddiv_rn((double)nw_out, (double)st->nw_prev);
-            st->shift = __dsub_rn(st->shift, __dmul_rn(P.c_shift, own_log(ratio)));
+            st->shift = __dsub_rn(st->shift, __dmul_rn(c_shift, own_log(ratio)));
             st->nw_prev = nw_out;
             st->n_since = 0;
         }
     }
+}
+
+// Makes the iteration's list the current one (new slots included, populations' parity flipped), decides a
+// compaction for the next iteration and clears the per-iteration counters.
+__device__ __forceinline__ void commit_list(DevState *st, long long nd_out, long long cap) {
     const long long new_len = (long long)st->claim;
     st->list_len = new_len;
     st->pp ^= 1;
     st->iter++;
     const long long vacated = new_len - nd_out;
-    if ((vacated > 64 && vacated * 4 > new_len) || (vacated > 0 && new_len * 4 > P.cap * 3))
+    if ((vacated > 64 && vacated * 4 > new_len) || (vacated > 0 && new_len * 4 > cap * 3))
         st->compact_pending = 1;
     st->n_merged = 0;
     st->heavy_packed = 0;
@@ -232,6 +232,122 @@ __global__ void k_finish(Params P) {
     st->d_nw = st->d_nd = 0;
     st->n_new = 0;
     for (int k = 0; k < NCNT; ++k) st->cnt[k] = 0;
+    for (int k = 0; k < MAXPARTS; ++k) st->ob_n[k] = 0;
+}
+
+// Eq. 2 numerator of one list: its sweep blocks' partials summed by one warp in a fixed order (lane k takes
+// blocks k, k + 32, ..., then a fixed shuffle tree), so the sum is the same in every run; lane 0 holds it.
+__device__ __forceinline__ double list_numerator(const double *partial, int n_blocks) {
+    const int lane = threadIdx.x & 31;
+    double part = 0.0;
+    for (int b = lane; b < n_blocks; b += 32) part = __dadd_rn(part, partial[b]);
+    return warp_sum_f64(part);
+}
+
+__global__ void k_finish(Params P) {
+    DevState *st = P.st;
+    if (st->status) return;
+    const double num = list_numerator(P.partial, P.sweep_grid);
+    if (threadIdx.x != 0) return;
+    const fciqmc_row row = list_row(st, num);
+    P.hist[st->hist_n % P.hist_cap] = row;
+    st->hist_n++;
+    shift_update(st, row.nw_out, P.target, P.period, P.c_shift);
+    commit_list(st, row.nd_out, P.cap);
+}
+
+// ---------------------------------------------------------------------------- hash-partitioned runs
+// What a partition's kernels need of the other partitions of its run (device array, one entry per partition).
+struct PartLink {
+    DevState *st;
+    unsigned long long *outbox;  // [n_parts][ob_cap] entries
+    long long ob_cap;
+    const double *partial;       // sweep partials of the numerator
+    int sweep_grid;
+    fciqmc_row *hist;            // the partition's own rows (its list's counters)
+    long long hist_cap, cap;
+};
+struct GroupDev {
+    long long hist_n;            // rows written to hist
+    int status;                  // first error of any partition (sticky)
+};
+
+// The exchange of Sec. V A, receiving side: the entries the other partitions routed to this one are merged
+// into its spawn table (sum of signed amounts, initiator flags counted) as its own spawns were.
+template <int W>
+__global__ void __launch_bounds__(256) k_receive(Params P, const PartLink *links) {
+    DevState *st = P.st;
+    if (st->status) return;
+    constexpr int S = Stride<W>::v;
+    for (int r = 0; r < P.n_parts; ++r) {
+        if (r == P.part) continue;
+        const long long n = min((long long)links[r].st->ob_n[P.part], links[r].ob_cap);
+        const unsigned long long *src = links[r].outbox + (unsigned long long)P.part * (unsigned long long)links[r].ob_cap * S;
+        for (long long i0 = (long long)blockIdx.x * blockDim.x; i0 < n; i0 += (long long)gridDim.x * blockDim.x) {
+            const long long i = i0 + threadIdx.x;
+            bool claimed = false;
+            unsigned pos = 0;
+            if (i < n) {
+                unsigned long long key[W];
+#pragma unroll
+                for (int w = 0; w < W; ++w) key[w] = src[i * S + w];
+                claimed = merge_insert<W>(P, key, src[i * S + W], pos);
+            }
+            const long long slot = warp_append(&st->n_merged, claimed);
+            if (claimed && slot < P.mt_cap) P.merged[slot] = pos;
+        }
+    }
+}
+
+// End of an iteration of a hash-partitioned run (one warp): the partitions' rows, the run's row (counters and
+// estimators summed over partitions, numerators added in partition order), one shift update from the run's
+// N_w applied to every partition, and each partition's list committed. An error in any partition stops the
+// iteration in all of them before any list is committed.
+__global__ void k_group_finish(const PartLink *links, int n_parts, GroupDev *g, fciqmc_row *ghist, long long ghist_cap,
+                               long long target, int period, double c_shift) {
+    int bad = g->status;
+    for (int r = 0; r < n_parts && !bad; ++r) bad = links[r].st->status;
+    if (bad) {
+        if (threadIdx.x == 0) {
+            g->status = bad;
+            for (int r = 0; r < n_parts; ++r) atomicCAS(&links[r].st->status, 0, bad);
+        }
+        return;
+    }
+    double nums[MAXPARTS];
+    for (int r = 0; r < n_parts; ++r) nums[r] = list_numerator(links[r].partial, links[r].sweep_grid);
+    if (threadIdx.x != 0) return;
+    fciqmc_row tot = list_row(links[0].st, nums[0]);
+    for (int r = 0; r < n_parts; ++r) {
+        const fciqmc_row row = list_row(links[r].st, nums[r]);
+        DevState *st = links[r].st;
+        links[r].hist[st->hist_n % links[r].hist_cap] = row;
+        st->hist_n++;
+        if (r == 0) continue;
+        tot.nw_in += row.nw_in;
+        tot.nd_in += row.nd_in;
+        tot.c0_in += row.c0_in;
+        tot.num_in = __dadd_rn(tot.num_in, row.num_in);
+        tot.nw_out += row.nw_out;
+        tot.nd_out += row.nd_out;
+        tot.attempts += row.attempts;
+        tot.nulls += row.nulls;
+        tot.spawn_events += row.spawn_events;
+        tot.spawned_walkers += row.spawned_walkers;
+        tot.death_walkers += row.death_walkers;
+        tot.clone_walkers += row.clone_walkers;
+        tot.merged_entries += row.merged_entries;
+        tot.aborted_walkers += row.aborted_walkers;
+        tot.inserted_dets += row.inserted_dets;
+        tot.heavy_attempts += row.heavy_attempts;
+    }
+    ghist[g->hist_n % ghist_cap] = tot;
+    g->hist_n++;
+    for (int r = 0; r < n_parts; ++r) {
+        DevState *st = links[r].st;
+        shift_update(st, tot.nw_out, target, period, c_shift);  // the same state and input in every partition
+        commit_list(st, (long long)st->nd_in + (long long)st->d_nd, links[r].cap);
+    }
 }
 
 // ---------------------------------------------------------------------------- compaction and index
@@ -432,7 +548,8 @@ __global__ void k_gather(Params P) {
 }
 
 // Checks slots [0, n) of list buffer b as loaded: n_elec occupied spin orbitals, none at or above n_so,
-// inside the permitted space, population neither 0 nor INT32_MIN. A failure sets st->check_bad.
+// inside the permitted space, owned by this partition, population neither 0 nor INT32_MIN. A failure sets
+// st->check_bad.
 template <int W>
 __global__ void k_check_list(Params P, int b, long long n) {
     for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
@@ -457,6 +574,8 @@ __global__ void k_check_list(Params P, int b, long long n) {
             if (hi < 64 && (hi <= 0 ? x != 0ull : (x >> hi) != 0ull)) ok = false;
             cnt += __popcll(x);
         }
+        if (P.n_parts > 1 && fingerprint<W>(d, P.map1) % (unsigned long long)P.n_parts != (unsigned long long)P.part)
+            ok = false;  // a determinant of another partition
         const int c = P.pop[b][0][s];
         if (!ok || cnt != P.n_elec || c == 0 || c == (-2147483647 - 1)) atomicExch(&P.st->check_bad, 1);
     }

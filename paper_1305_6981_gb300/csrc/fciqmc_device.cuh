@@ -22,6 +22,7 @@ constexpr int NCLASS = 16;   // 8 irreps x 2 spins
 constexpr int MAXPAIRS = MAXN * (MAXN - 1) / 2;
 constexpr unsigned long long EMPTY = ~0ull;
 constexpr int NCNT = 10;     // per-iteration counters, same order as fciqmc_row from `attempts`
+constexpr int MAXPARTS = 64; // partitions of a hash-partitioned run
 
 // ---------------------------------------------------------------------------
 // Shared state of one run, in device memory.
@@ -51,6 +52,7 @@ struct DevState {
     double est_num;
     int check_bad;             // set by the check of a list being loaded
     unsigned long long n_new;  // determinants placed in new slots this iteration (diagonal elements pending)
+    unsigned long long ob_n[MAXPARTS];  // partitioned runs: spawns routed to each other partition this iteration
 };
 
 // One double excitation of the reference determinant as the generator selects it (pair, good a, b),
@@ -128,6 +130,11 @@ struct Params {
     fciqmc_row *hist;
     long long hist_cap;
     DevState *st;
+    // hash-partitioned runs (Sec. V A): this list holds the determinants whose fingerprint mod n_parts is
+    // part; spawns onto the others go to outbox[dest][ob_cap] (entries of Stride<W> words: key, payload)
+    int n_parts, part;
+    unsigned long long *outbox;
+    long long ob_cap;
 };
 
 // ---------------------------------------------------------------------------
@@ -238,6 +245,25 @@ __device__ __forceinline__ bool det_eq(const unsigned long long (&a)[W], const u
 #pragma unroll
     for (int w = 0; w < W; ++w) e = e && (a[w] == b[w]);
     return e;
+}
+
+// Algorithm 1 (Sec. V) over the occupied spin orbitals in ascending order, electrons counted from 1, uint64
+// wraparound: the fingerprint that keys the random numbers and, mod the partition count, a determinant's
+// partition (map1: the orbital map).
+template <int W>
+__device__ __forceinline__ unsigned long long fingerprint(const unsigned long long (&d)[W], const unsigned long long *map1) {
+    unsigned long long h = 0;
+    unsigned n = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        unsigned long long m = d[w];
+        while (m) {
+            const int k = 64 * w + __ffsll((long long)m) - 1;
+            h = 1099511628211ull * h + map1[k] * (unsigned long long)(++n);
+            m &= m - 1;
+        }
+    }
+    return h;
 }
 
 // Permitted space (Sec. VI): at most max_exc reference spin orbitals empty, at most max_sen spatial

@@ -187,9 +187,12 @@ struct SpawnQueue {
 
 // Inserts queued spawns into the merge table (all 32 lanes; every lane inserts one entry): everything
 // when all is set, else up to 32 entries once at least kQueueFlush are queued. Merge-table positions
-// newly claimed go to the merged list.
+// newly claimed go to the merged list. In a hash-partitioned run (Sec. V A) an entry whose determinant
+// belongs to another partition (its fingerprint mod the partition count; map1 the orbital map) is
+// appended to that partition's outbox instead, to be merged there after the exchange.
 template <int W>
-__device__ __forceinline__ void flush_queue(const Params &P, SpawnQueue<W> &q, bool all) {
+__device__ __forceinline__ void flush_queue(const Params &P, SpawnQueue<W> &q, bool all,
+                                            const unsigned long long *map1) {
     __syncwarp();
     const unsigned n = q.n;
     if (n == 0 || (!all && n < (unsigned)kQueueFlush)) return;
@@ -204,7 +207,22 @@ __device__ __forceinline__ void flush_queue(const Params &P, SpawnQueue<W> &q, b
             unsigned long long key[W];
 #pragma unroll
             for (int w = 0; w < W; ++w) key[w] = q.key[e][w];
-            claimed = merge_insert<W>(P, key, q.val[e], pos);
+            const unsigned long long val = q.val[e];
+            int dest = P.part;
+            if (P.n_parts > 1) dest = (int)(fingerprint<W>(key, map1) % (unsigned long long)P.n_parts);
+            if (dest == P.part) {
+                claimed = merge_insert<W>(P, key, val, pos);
+            } else {
+                const unsigned long long slot = atomicAdd(&P.st->ob_n[dest], 1ull);
+                if (slot < (unsigned long long)P.ob_cap) {
+                    unsigned long long *o = P.outbox + ((unsigned long long)dest * (unsigned long long)P.ob_cap + slot) * Stride<W>::v;
+#pragma unroll
+                    for (int w = 0; w < W; ++w) o[w] = key[w];
+                    o[W] = val;
+                } else {
+                    set_status(P.st, FCIQMC_ERR_CAPACITY);
+                }
+            }
         }
         const long long slot = warp_append(&P.st->n_merged, claimed);
         if (claimed && slot < P.mt_cap) P.merged[slot] = pos;
@@ -1153,11 +1171,11 @@ __global__ void __launch_bounds__(kTile, FQ_SWEEP_MIN_BLOCKS) k_sweep(Params P) 
                 }
             }
             spawn_attempt<W, false, MODE>(P, T, s_dv[lo], nullptr, s_rcpf, act, k - s_off[lo], iter, acc, sq);
-            flush_queue<W>(P, sq, false);
+            flush_queue<W>(P, sq, false, T.map1);
         }
         __syncthreads();
     }
-    flush_queue<W>(P, sq, true);
+    flush_queue<W>(P, sq, true, T.map1);
     unsigned long long *const dst[NCNT + 4] = {&st->cnt[0], &st->cnt[1], &st->cnt[2], &st->cnt[3], &st->cnt[4],
                                                &st->cnt[5], &st->cnt[6], &st->cnt[7], &st->cnt[8], &st->cnt[9],
                                                &st->nw_in, &st->nd_in, &st->d_nw, &st->d_nd};
@@ -1229,11 +1247,11 @@ __global__ void __launch_bounds__(kTile, 4) k_heavy(Params P) {
         for (unsigned base = a0; base < a1; base += 32) {
             const unsigned a = base + lane;
             spawn_attempt<W, true, MODE>(P, T, v, &tab, s_rcpf, a < a1, a, iter, cnt, sq, rtab);
-            flush_queue<W>(P, sq, false);
+            flush_queue<W>(P, sq, false, T.map1);
         }
         __syncwarp();
     }
-    flush_queue<W>(P, sq, true);
+    flush_queue<W>(P, sq, true, T.map1);
     unsigned long long *const dst[NCNT] = {&st->cnt[0], &st->cnt[1], &st->cnt[2], &st->cnt[3], &st->cnt[4],
                                            &st->cnt[5], &st->cnt[6], &st->cnt[7], &st->cnt[8], &st->cnt[9]};
     cnt[C_ATTEMPTS] = 0;  // attempts are counted by the sweep

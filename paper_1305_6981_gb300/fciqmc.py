@@ -234,3 +234,98 @@ def rng_throughput(n_blocks: int = 1 << 31, stream=None) -> float:
     check(L.fciqmc_rng_throughput(int(n_blocks), ctypes.c_void_p(s.cuda_stream), ctypes.byref(out)),
           "fciqmc_rng_throughput")
     return out.value
+
+
+def owners(n_orb: int, dets, n_partitions: int) -> np.ndarray:
+    """Partition of each determinant in a run of n_partitions partitions (fciqmc_owner: the Algorithm 1
+    fingerprint mod n_partitions); host only."""
+    W = words_for(n_orb)
+    d = np.ascontiguousarray(np.asarray(dets, dtype=np.uint64).reshape(-1, W))
+    out = np.zeros(len(d), dtype=np.int32)
+    check(_native.load().fciqmc_owner(int(n_orb), _ptr(d, ctypes.c_uint64), len(d), int(n_partitions),
+                                      _ptr(out, ctypes.c_int32)), "fciqmc_owner")
+    return out
+
+
+class Partitioned:
+    """One run divided among n_partitions hash partitions on one GPU (Sec. V A; fciqmc_group_*): each
+    partition is an Fciqmc handle holding the determinants that fciqmc_owner assigns to it, and an
+    iteration spawns in every partition, exchanges the spawns onto other partitions' determinants, annihilates
+    and takes one shift update from the run's N_w. Arguments as for Fciqmc (options apply to every
+    partition); outbox_capacity sets the entries of each per-destination outbox."""
+
+    def __init__(self, system, tau: float, initiator_threshold: int = -1, *, n_partitions: int = 2,
+                 history_capacity: int = 1 << 16, stream=None, **kw):
+        import torch
+
+        self._L = L = _native.load()
+        self.n_orb = int(system.n_orb)
+        self.n = int(n_partitions)
+        self.parts = [Fciqmc(system, tau, initiator_threshold, n_partitions=self.n, partition_index=r,
+                             stream=stream, **kw) for r in range(self.n)]
+        self.stream = self.parts[0].stream
+        nbytes = L.fciqmc_group_workspace_bytes(self.n, int(history_capacity))
+        if nbytes == 0:
+            raise ValueError("unsupported number of partitions")
+        self.workspace = torch.empty(int(nbytes), dtype=torch.uint8, device=self.parts[0].device)
+        arr = (ctypes.c_void_p * self.n)(*[p.handle.value for p in self.parts])
+        h = ctypes.c_void_p()
+        check(L.fciqmc_group_create(arr, self.n, int(history_capacity), ctypes.c_void_p(self.workspace.data_ptr()),
+                                    int(nbytes), ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)),
+              "fciqmc_group_create")
+        self.handle = h
+
+    def step(self, n: int = 1):
+        check(self._L.fciqmc_group_step(self.handle, int(n)), "fciqmc_group_step")
+
+    def sync(self) -> int:
+        return check(self._L.fciqmc_group_sync(self.handle), "fciqmc_group_sync")
+
+    def history(self, max_rows: int = 1 << 16) -> list[dict]:
+        rows = (Row * max_rows)()
+        n = ctypes.c_int64()
+        check(self._L.fciqmc_group_history(self.handle, rows, max_rows, ctypes.byref(n)), "fciqmc_group_history")
+        return [{f: getattr(rows[k], f) for f in ROW_FIELDS} for k in range(n.value)]
+
+    def walkers(self):
+        """The run's list: the partitions' lists concatenated (dets, pops, H_ii - E0)."""
+        parts = [p.walkers() for p in self.parts]
+        return tuple(np.concatenate([x[k] for x in parts]) for k in range(3))
+
+    def estimates(self) -> dict:
+        """Estimators of the run's list: walkers, determinants, C_0 and numerator summed over the partitions
+        (numerators in partition order); shift and status of partition 0 (the same in every partition)."""
+        es = [p.estimates() for p in self.parts]
+        out = dict(es[0])
+        for k in ("n_walkers", "n_dets", "c0"):
+            out[k] = sum(e[k] for e in es)
+        num = 0.0
+        for e in es:
+            num += e["proj_num"]
+        out["proj_num"] = num
+        out["e_proj"] = out["e_ref"] + num / out["c0"] if out["c0"] else float("nan")
+        out["status"] = next((e["status"] for e in es if e["status"]), 0)
+        return out
+
+    def set_walkers(self, dets, pops, hdiag=None, **state):
+        """Loads a list, each determinant into its partition; state keywords as for Fciqmc.set_walkers."""
+        W = self.parts[0].W
+        dets = np.asarray(dets, dtype=np.uint64).reshape(-1, W)
+        pops = np.asarray(pops, dtype=np.int32)
+        own = owners(self.n_orb, dets, self.n)
+        for r, p in enumerate(self.parts):
+            m = own == r
+            p.set_walkers(dets[m], pops[m], None if hdiag is None else np.asarray(hdiag)[m], **state)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._L.fciqmc_group_destroy(self.handle)
+            self.handle = None
+        for p in self.parts:
+            p.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
