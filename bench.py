@@ -375,7 +375,7 @@ def grow(args, wl, rank):
     t_grow = time.perf_counter()
     grown, chunk = 0, 50
     log = []
-    if args.load_state:
+    if getattr(args, "load_state", ""):
         z = np.load(args.load_state)
         st = {k: z["state"][i] for i, k in enumerate(("iteration", "shift", "vary_shift", "shift_counter",
                                                        "nw_last_update"))}
@@ -392,7 +392,7 @@ def grow(args, wl, rank):
             raise RuntimeError(f"device status {e['status']} during growth at {grown}: {log[-1]}")
         if e["vary_shift"] or grown >= wl["max_growth"]:
             break
-    settle = wl["equilibrate"] if args.settle < 0 else args.settle
+    settle = wl["equilibrate"] if getattr(args, "settle", -1) < 0 else args.settle
     while settle > 0:  # settle towards the steady state of the varying shift
         k = min(settle, 500)
         g.step(k)
@@ -402,7 +402,7 @@ def grow(args, wl, rank):
         log.append((grown, e["n_walkers"], e["n_dets"], e["shift"], e["list_slots"]))
         if e["status"] != 0:
             raise RuntimeError(f"device status {e['status']} while settling at {grown}: {log[-1]}")
-    if args.save_state:
+    if getattr(args, "save_state", ""):
         d, p, hd = g.walkers()
         st = g.state()
         np.savez(args.save_state, dets=d, pops=p, hdiag=hd,

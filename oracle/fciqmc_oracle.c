@@ -213,6 +213,10 @@ typedef struct {
     int max_exc, max_sen;
     uint64_t froz_occ[OQ_MAXW], froz_emp[OQ_MAXW];  /* spin orbitals that stay occupied / empty */
     int hphf;                  /* walkers live on spin-coupled functions (Sec. VI C) */
+    /* real/integer hybrid walkers: populations are integers in units of 2^-frac_bits walkers */
+    int frac_bits;
+    int64_t occ_units;         /* occupation threshold in units (1: none) */
+    double tau_s;              /* time step of the spawning probabilities, in units: tau 2^frac_bits */
 } oq_t;
 
 /* ---------------- bit-string helpers ---------------- */
@@ -521,6 +525,7 @@ oq_t *oq_create(const double *h, const double *eri_s8, double e_core, int n_elec
         for (int p = 0; p < q->n_beta; ++p) det_flip(q->ref, 2 * p + 1);
     }
     q->tau = tau; q->init_thr = initiator_threshold; q->target = target_walkers;
+    q->frac_bits = 0; q->occ_units = 1; q->tau_s = tau;
     q->zeta = shift_damping; q->period = shift_period;
     q->c_shift = shift_damping / ((double)shift_period * tau);
     q->seed = (uint32_t)seed;
@@ -779,7 +784,7 @@ static int64_t attempt_one(const oq_t *q, const uint64_t *d, int32_t c, uint64_t
         if (hv == 0.0) return 0;
         double g = oq_gen_prob(q, d, child);
         if (!det_eq(q, xb, child)) g = g + oq_gen_prob(q, d, xb);
-        p = (q->tau * fabs(hv)) / g;
+        p = (q->tau_s * fabs(hv)) / g;
         memcpy(child, b, sizeof(uint64_t) * q->W);
     } else {
         if (!in_space(q, child)) { *is_null = 1; return 0; }
@@ -805,6 +810,22 @@ static int64_t attempt_one(const oq_t *q, const uint64_t *d, int32_t c, uint64_t
     if (nsp == 0) return 0;
     int sgn_c = c > 0 ? 1 : -1, sgn_h = hv > 0.0 ? 1 : -1;
     return -(int64_t)sgn_c * sgn_h * nsp;
+}
+
+/* Spawning attempts of a determinant with population c: one per walker (Eq. 3). With populations in units
+ * of 2^-b walkers the |c| 2^-b walkers are rounded stochastically, floor plus one with the probability of
+ * the fraction, drawn with tag 4 (counter (0, 4, fingerprint), key (seed, iteration)). */
+static int64_t attempts_of(const oq_t *q, const uint64_t *d, int32_t c)
+{
+    int64_t ac = c < 0 ? -(int64_t)c : c;
+    if (q->frac_bits == 0) return ac;
+    int64_t n = ac >> q->frac_bits, frac = ac & (((int64_t)1 << q->frac_bits) - 1);
+    if (frac) {
+        uint64_t u, unused;
+        draw2(0u, 4u, oq_fingerprint(q, d), q->seed, q->iter, &u, &unused);
+        if (unit53(u) < (double)frac * ldexp(1.0, -q->frac_bits)) n++;
+    }
+    return n;
 }
 
 /* Spawning attempts a0 <= a < a1 of determinant d (Eq. 3 once per walker). */
@@ -866,7 +887,6 @@ int oq_iterate(oq_t *q, int n_iter, oq_row *rows)
         row->iter = q->iter;
         row->shift = q->shift;
         oq_estimate(q, &row->nw_in, &row->nd_in, &row->c0_in, &row->num_in);
-        row->attempts = row->nw_in;
 
         /* spawning from start-of-iteration populations (thread-local buffers, merged by sorting) */
         int nthreads = 1;
@@ -881,21 +901,27 @@ int oq_iterate(oq_t *q, int n_iter, oq_row *rows)
          * a counter of the random numbers and the spawned list is sorted before it is merged, so how a
          * determinant's attempts are split across threads does not change the result); the first chunk of a
          * determinant also takes its death/cloning step. */
+        int64_t *natt = malloc(sizeof(int64_t) * (q->n ? q->n : 1));
+#pragma omp parallel for schedule(static)
+        for (int64_t x = 0; x < q->n; ++x) natt[x] = attempts_of(q, q->det + x * W, q->pop[x]);
         int64_t n_units = 0;
         for (int64_t x = 0; x < q->n; ++x) {
-            int64_t ac = q->pop[x] < 0 ? -(int64_t)q->pop[x] : q->pop[x];
             newpop[x] = q->pop[x];
-            if (ac > 0) n_units += (ac + OQ_CHUNK - 1) / OQ_CHUNK;
+            if (q->pop[x] == 0) continue;
+            n_units += natt[x] > 0 ? (natt[x] + OQ_CHUNK - 1) / OQ_CHUNK : 1;  /* the first also takes the death step */
+            row->attempts += natt[x];
         }
         int64_t *units = malloc(sizeof(int64_t) * 2 * (n_units ? n_units : 1));
         n_units = 0;
         for (int64_t x = 0; x < q->n; ++x) {
-            int64_t ac = q->pop[x] < 0 ? -(int64_t)q->pop[x] : q->pop[x];
-            for (int64_t a0 = 0; a0 < ac; a0 += OQ_CHUNK) {
+            if (q->pop[x] == 0) continue;
+            int64_t a0 = 0;
+            do {
                 units[2 * n_units] = x;
                 units[2 * n_units + 1] = a0;
                 n_units++;
-            }
+                a0 += OQ_CHUNK;
+            } while (a0 < natt[x]);
         }
 #pragma omp parallel for schedule(dynamic, 16) reduction(+ : death_w, clone_w) reduction(| : numeric)
         for (int64_t u = 0; u < n_units; ++u) {
@@ -909,7 +935,7 @@ int oq_iterate(oq_t *q, int n_iter, oq_row *rows)
             uint64_t fp = oq_fingerprint(q, d);
             int64_t ac = c < 0 ? -(int64_t)c : c;
             int flag = q->init_thr < 0 || ac > q->init_thr || det_eq(q, d, q->ref);
-            int64_t a1 = a0 + OQ_CHUNK < ac ? a0 + OQ_CHUNK : ac;
+            int64_t a1 = a0 + OQ_CHUNK < natt[x] ? a0 + OQ_CHUNK : natt[x];
             spawn_range(q, d, c, fp, flag, (uint32_t)a0, (uint32_t)a1, &bufs[tid]);
             if (a0 != 0) continue;
             /* death / cloning, Eq. 4: r = tau (H_ii - E0 - S) |C_i| */
@@ -928,6 +954,7 @@ int oq_iterate(oq_t *q, int n_iter, oq_row *rows)
             newpop[x] = (int32_t)nc;
         }
         free(units);
+        free(natt);
         /* concatenate, sort and compress the spawned list (Sec. V A) */
         int64_t ns = 0;
         for (int t = 0; t < nthreads; ++t) {
@@ -1016,6 +1043,27 @@ int oq_iterate(oq_t *q, int n_iter, oq_row *rows)
         q->det = nd_det; q->pop = nd_pop; q->hd = nd_hd;
         q->n = out; q->cap = cap_new ? cap_new : 1;
         if (numeric) q->error = 1;
+        /* occupation threshold of hybrid walkers: an amplitude below occ_units units is rounded stochastically
+         * to +-occ_units (probability |C| / occ_units, draw tag 4 + 1) or removed; unbiased */
+        if (q->occ_units > 1) {
+            int64_t m = 0;
+            for (int64_t x = 0; x < q->n; ++x) {
+                int32_t c = q->pop[x];
+                int64_t ac = c < 0 ? -(int64_t)c : c;
+                if (ac < q->occ_units) {
+                    uint64_t u, unused;
+                    draw2(0u, 5u, oq_fingerprint(q, q->det + x * W), q->seed, q->iter, &u, &unused);
+                    int keep = unit53(u) < (double)ac / (double)q->occ_units;
+                    c = keep ? (int32_t)(c > 0 ? q->occ_units : -q->occ_units) : 0;
+                }
+                if (c == 0) continue;
+                memmove(q->det + m * W, q->det + x * W, sizeof(uint64_t) * W);
+                q->pop[m] = c;
+                q->hd[m] = q->hd[x];
+                m++;
+            }
+            q->n = m;
+        }
 
         int64_t nw_out = 0;
         for (int64_t x = 0; x < q->n; ++x) nw_out += q->pop[x] < 0 ? -(int64_t)q->pop[x] : q->pop[x];
