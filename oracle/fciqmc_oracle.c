@@ -661,6 +661,34 @@ static int stored_form(const oq_t *q, const uint64_t *d)
 }
 
 /* Switches to spin-coupled functions; needs M_s = 0 and a closed-shell reference. */
+/* Real/integer hybrid walkers (the multi-scale representation Sec. II mentions and defers): populations
+ * become integers in units of 2^-bits walkers (the current list is rescaled); spawning probabilities are
+ * formed with tau 2^bits, so the count drawn for a spawn is in units (Eq. 3 at resolution 2^-bits); death
+ * (Eq. 4) is unchanged in units; a determinant's attempts are its walkers rounded stochastically; after
+ * annihilation an amplitude below occ walkers is rounded stochastically to +-occ or removed. The initiator
+ * threshold and the target stay in walkers (compared in units). Returns 0, or -1 for bits outside [0, 20], an
+ * occupation threshold below one unit or above 2^31 units, a population or threshold that leaves int32, or
+ * a second call. */
+int oq_set_real(oq_t *q, int bits, double occ)
+{
+    if (bits < 0 || bits > 20 || q->frac_bits != 0) return -1;
+    const double R = ldexp(1.0, bits);
+    const double ou = nearbyint(occ * R);
+    if (!(ou >= 1.0) || ou > 2147483647.0) return -1;
+    for (int64_t x = 0; x < q->n; ++x)
+        if (fabs((double)q->pop[x]) * R > 2147483647.0) return -1;
+    if (q->init_thr >= 0 && (double)q->init_thr * R > 2147483647.0) return -1;
+    for (int64_t x = 0; x < q->n; ++x) q->pop[x] = (int32_t)((int64_t)q->pop[x] << bits);
+    if (q->init_thr >= 0) q->init_thr = (int32_t)((int64_t)q->init_thr << bits);
+    q->target = q->target > (INT64_MAX >> bits) ? INT64_MAX : q->target << bits;
+    q->frac_bits = bits;
+    q->occ_units = (int64_t)ou;
+    q->tau_s = q->tau * R;
+    q->cs = q->tau_s / q->p_single;
+    q->cd = q->tau_s / q->p_double;
+    return 0;
+}
+
 int oq_set_hphf(oq_t *q, int on)
 {
     if (on) {

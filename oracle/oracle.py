@@ -96,6 +96,8 @@ def lib():
         L.oq_hphf_hij.argtypes = [ctypes.c_void_p, u64p, u64p]
         L.oq_hphf_hdiag.restype = ctypes.c_double
         L.oq_hphf_hdiag.argtypes = [ctypes.c_void_p, u64p]
+        L.oq_set_real.restype = ctypes.c_int
+        L.oq_set_real.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double]
         L.oq_set_threads.argtypes = [ctypes.c_int]
         L.oq_set_threads.restype = None
         L.oq_max_threads.restype = ctypes.c_int
@@ -139,7 +141,8 @@ class Oracle:
     def __init__(self, system, *, tau, initiator_threshold=-1, target_walkers=1 << 62,
                  shift_damping=0.05, shift_period=10, initial_shift=0.0, initial_population=10,
                  seed=1, p_double=0.0, ms2=0, reference=None, max_excitation=None, max_seniority=None,
-                 frozen_occupied=None, frozen_empty=None, hphf=False):
+                 frozen_occupied=None, frozen_empty=None, hphf=False, walker_fraction_bits=0,
+                 occupation_threshold=1.0):
         L = lib()
         self.system = system
         self.n_orb, self.n_elec = system.n_orb, system.n_elec
@@ -170,6 +173,9 @@ class Oracle:
                 raise ValueError("oracle: the reference lies outside the permitted space")
         if hphf and L.oq_set_hphf(self.h, 1) != 0:
             raise ValueError("oracle: spin-coupled functions need M_s = 0 and a closed-shell reference")
+        self.frac_bits = int(walker_fraction_bits)
+        if self.frac_bits and L.oq_set_real(self.h, self.frac_bits, float(occupation_threshold)) != 0:
+            raise ValueError("oracle: invalid hybrid-walker resolution or occupation threshold")
 
     def __del__(self):
         if getattr(self, "h", None):

@@ -1,6 +1,6 @@
 """The walker cycle at full size against the oracle: 24e/60o (two-word determinants, 8 irreps, initiator 3,
-tau 0.001) grown on the GPU to ~1e8 walkers on ~4e6 determinants, in the launch configuration the benchmark
-times (its workload table: 2e8-slot main list, 2^27-entry spawn table). From the grown list, one iteration
+tau 0.001) grown on the GPU and settled to the steady state the benchmark times (~1.4e8 walkers on ~6e6
+determinants), in its launch configuration (its workload table: 2e8-slot main list, 2^27-entry spawn table). From the grown list, one iteration
 on the GPU and one in the oracle: diagonal elements of the loaded list bit-identical, walker lists
 identical, every integer counter identical, the shift bit-identical, the projected-energy numerator within
 1e-11 relative. The oracle's iteration takes a minute or two on the host cores. The same for the
@@ -58,7 +58,7 @@ def one_iteration(workload: str, target: int = 0):
 def test_one_iteration_at_1e8_walkers():
     r, p = one_iteration("24e60o")
     assert len(p) > 3_000_000 and int(np.abs(p.astype(np.int64)).sum()) > 80_000_000
-    assert int(np.abs(p).max()) > 1_000_000  # the reference: millions of attempts from one determinant
+    assert int(np.abs(p).max()) > 1_000_000  # millions of attempts from one determinant (heavy path)
     assert r["heavy_attempts"] > r["attempts"] // 2 and r["spawn_events"] > 100_000
 
 

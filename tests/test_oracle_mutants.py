@@ -53,9 +53,15 @@ MUTANTS = [
     ("fingerprint_zero_based", "q->map1[occ[i - 1]] * (uint64_t)i;", "q->map1[occ[i - 1]] * (uint64_t)(i - 1);"),
     ("fingerprint_descending", "q->map1[occ[i - 1]] * (uint64_t)i;", "q->map1[occ[n - i]] * (uint64_t)i;"),
     ("fingerprint_map_key", "key[2] = {0x46434951u, 0x4D415031u}", "key[2] = {0x46434951u, 0x4D415032u}"),
+    ("hybrid_attempts_floored", "        if (unit53(u) < (double)frac * ldexp(1.0, -q->frac_bits)) n++;\n", ""),
+    ("hybrid_threshold_inverted", "int keep = unit53(u) < (double)ac / (double)q->occ_units;",
+     "int keep = unit53(u) >= (double)ac / (double)q->occ_units;"),
+    ("hybrid_spawn_unscaled", "    q->tau_s = q->tau * R;", "    q->tau_s = q->tau;"),
+    ("hybrid_death_scaled", "double r = (q->tau * (q->hd[x] - q->shift)) * (double)ac;",
+     "double r = (q->tau_s * (q->hd[x] - q->shift)) * (double)ac;"),
 ]
 
-FAST_PINS = ("philox or fingerprint_is_algorithm1 or choice_digits or keeps_the_invariants or holds_the_population or own_log or second_quantisation or symmetry_and_spin or two_words and hamiltonian "
+FAST_PINS = ("philox or fingerprint_is_algorithm1 or hybrid_one_step or hybrid_attempts or choice_digits or keeps_the_invariants or holds_the_population or own_log or second_quantisation or symmetry_and_spin or two_words and hamiltonian "
              "or pdouble or normalised or eq1 or initiator_rule or on_a_subset or functional_two_words "
              "or membership or outside_the_space or expectation_in_the_space "
              "or spin_flip or projection or probability_of_any_target or spin_coupled or numerator or stored_form")
@@ -80,6 +86,7 @@ def test_every_planted_mistake_is_caught():
              os.path.join(ROOT, "tests", "test_oracle_rdm.py"), os.path.join(ROOT, "tests", "test_oracle_space.py"),
              os.path.join(ROOT, "tests", "test_oracle_hphf.py"),
              os.path.join(ROOT, "tests", "test_oracle_invariants.py"),
+             os.path.join(ROOT, "tests", "test_oracle_real.py"),
              "-x", "-q",
              "-p", "no:cacheprovider", "-k", FAST_PINS],
             env=env, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, cwd=ROOT)
