@@ -119,6 +119,16 @@ typedef struct {
     int32_t n_partitions;
     int32_t partition_index;
     int64_t outbox_capacity;
+    /* Real/integer hybrid walkers (the multi-scale representation Sec. II mentions and defers): with
+     * walker_fraction_bits = b in [1, 20] populations are integers in units of 2^-b walkers (the int32 values
+     * of fciqmc_get_walkers / fciqmc_set_walkers, the static estimator and the N_w and C_0 of the rows are in
+     * units). A determinant makes |C| 2^-b spawning attempts rounded stochastically; a spawn's count is drawn
+     * in units (Eq. 3 with tau 2^b); death (Eq. 4) acts on units; after annihilation an amplitude below
+     * occupation_threshold walkers (<= 0: 1) is rounded stochastically to +-threshold or removed. Every step
+     * keeps the expectation of Eq. 1. initial_population, target_walkers and the initiator threshold stay in
+     * walkers. 0: integer walkers. */
+    int32_t walker_fraction_bits;
+    double occupation_threshold;
 } fciqmc_options;
 
 /* Per-iteration record. The estimators (nw_in .. num_in) describe the list at

@@ -79,7 +79,8 @@ class Options(ctypes.Structure):
                 ("max_seniority", ctypes.c_int32), ("frozen_occupied", ctypes.POINTER(ctypes.c_uint64)),
                 ("frozen_empty", ctypes.POINTER(ctypes.c_uint64)), ("hphf", ctypes.c_int32),
                 ("n_partitions", ctypes.c_int32), ("partition_index", ctypes.c_int32),
-                ("outbox_capacity", ctypes.c_int64)]
+                ("outbox_capacity", ctypes.c_int64), ("walker_fraction_bits", ctypes.c_int32),
+                ("occupation_threshold", ctypes.c_double)]
 
 
 ROW_FIELDS = ["iteration", "shift", "nw_in", "nd_in", "c0_in", "num_in", "nw_out", "nd_out", "attempts", "nulls",

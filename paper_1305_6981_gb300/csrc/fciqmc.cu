@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstddef>
 #include <cstdint>
@@ -246,6 +247,7 @@ void enqueue_iteration(fciqmc_handle *h, cudaStream_t s) {
     launch_spawning<W>(h, s);
     fq::k_annihilate<W><<<h->ann_grid, 256, 0, s>>>(P);
     fq::k_new_diag<W><<<h->diag_grid, 256, h->smem_w, s>>>(P);
+    if (P.occ_units > 1) fq::k_round<W><<<h->small_grid, 256, 0, s>>>(P);
     fq::k_finish<<<1, 32, 0, s>>>(P);
 }
 
@@ -389,6 +391,15 @@ int fciqmc_create(const double *h1, const double *eri_s8, double e_core, int n_e
     if (o.n_partitions < 0 || o.n_partitions > fq::MAXPARTS || o.outbox_capacity < 0 ||
         (o.n_partitions > 1 && (o.partition_index < 0 || o.partition_index >= o.n_partitions)))
         return FCIQMC_ERR_INVALID_ARG;
+    // hybrid walkers: populations, the initiator threshold and the target in units of 2^-bits walkers
+    if (o.walker_fraction_bits < 0 || o.walker_fraction_bits > 20) return FCIQMC_ERR_INVALID_ARG;
+    const int fbits = o.walker_fraction_bits;
+    const double unit_scale = std::ldexp(1.0, fbits);
+    const double occ_units = std::nearbyint((o.occupation_threshold > 0.0 ? o.occupation_threshold : 1.0) * unit_scale);
+    if (!(occ_units >= 1.0) || occ_units > 2147483647.0 ||
+        std::fabs((double)o.initial_population) * unit_scale > 2147483647.0 ||
+        (initiator_threshold >= 0 && (double)initiator_threshold * unit_scale > 2147483647.0))
+        return FCIQMC_ERR_INVALID_ARG;
     Sizes z;
     if (!sizes_of(n_elec, n_orb, o, z)) return FCIQMC_ERR_UNSUPPORTED;
     Layout L = layout_of(z, n_orb);
@@ -436,13 +447,18 @@ int fciqmc_create(const double *h1, const double *eri_s8, double e_core, int n_e
     P.n_so = z.n_so;
     P.npairs = z.npairs;
     P.n_irrep_used = max_irrep + 1;
-    P.init_thr = initiator_threshold < 0 ? -1 : initiator_threshold;
+    P.init_thr = initiator_threshold < 0 ? -1 : (int)((long long)initiator_threshold << fbits);
     P.seed = (unsigned)(o.seed & 0xFFFFFFFFull);
-    P.tau = tau;
+    P.tau = tau * unit_scale;  // spawning probabilities in units (exact: a power of two)
     P.period = o.shift_period;
-    P.target = o.target_walkers;
+    P.target = o.target_walkers > (LLONG_MAX >> fbits) ? LLONG_MAX : (o.target_walkers << fbits);
     P.c_shift = o.shift_damping / ((double)o.shift_period * tau);
-    P.tau_f = (float)tau;
+    P.tau_f = (float)P.tau;
+    P.tau_death = tau;
+    P.tau_death_f = (float)tau;
+    P.frac_bits = fbits;
+    P.frac_scale = std::ldexp(1.0, -fbits);
+    P.occ_units = (int)occ_units;
     P.h = at<double>(h, L.h);
     P.eri = at<double>(h, L.eri);
     P.eri_f = at<float>(h, L.eri_f);
@@ -591,8 +607,8 @@ int fciqmc_create(const double *h1, const double *eri_s8, double e_core, int n_e
         double p_single = 1.0 - p_double;
         P.d53 = d53;
         P.E0 = E0;
-        P.cs = tau / p_single;
-        P.cd = tau / p_double;
+        P.cs = P.tau / p_single;
+        P.cd = P.tau / p_double;
         P.p_double_d = p_double;
         P.p_single_d = p_single;
         P.p_double_f = (float)p_double;
@@ -642,7 +658,7 @@ int fciqmc_create(const double *h1, const double *eri_s8, double e_core, int n_e
         st0.claim = owns_ref ? 1 : 0;
         FQ_TRY(cudaMemcpyAsync(P.st, &st0, sizeof(st0), cudaMemcpyHostToDevice, s));
         FQ_TRY(cudaMemcpyAsync(P.det[0], ref, sizeof(uint64_t) * z.W, cudaMemcpyHostToDevice, s));
-        int p0 = o.initial_population;
+        int p0 = (int)((long long)o.initial_population << fbits);
         FQ_TRY(cudaMemcpyAsync(P.pop[0][0], &p0, sizeof(int), cudaMemcpyHostToDevice, s));
         if (z.W == 1) {
             launch_prepare<1>(h, 0, 1, 1);
@@ -721,6 +737,7 @@ int fciqmc_profile(fciqmc_handle *h, int32_t n_iterations, double *kernel_ms) {
                     case 6:
                         fq::k_annihilate<1><<<h->ann_grid, 256, 0, s>>>(P);
                         fq::k_new_diag<1><<<h->diag_grid, 256, h->smem_w, s>>>(P);
+                        if (P.occ_units > 1) fq::k_round<1><<<h->small_grid, 256, 0, s>>>(P);
                         break;
                     default: fq::k_finish<<<1, 32, 0, s>>>(P); break;
                 }
@@ -739,6 +756,7 @@ int fciqmc_profile(fciqmc_handle *h, int32_t n_iterations, double *kernel_ms) {
                     case 6:
                         fq::k_annihilate<2><<<h->ann_grid, 256, 0, s>>>(P);
                         fq::k_new_diag<2><<<h->diag_grid, 256, h->smem_w, s>>>(P);
+                        if (P.occ_units > 1) fq::k_round<2><<<h->small_grid, 256, 0, s>>>(P);
                         break;
                     default: fq::k_finish<<<1, 32, 0, s>>>(P); break;
                 }
@@ -1091,6 +1109,7 @@ void enqueue_group_iteration(fciqmc_group *g, cudaStream_t s) {
     for (fciqmc_handle *h : g->parts) {
         fq::k_annihilate<W><<<h->ann_grid, 256, 0, s>>>(h->P);
         fq::k_new_diag<W><<<h->diag_grid, 256, h->smem_w, s>>>(h->P);
+        if (h->P.occ_units > 1) fq::k_round<W><<<h->small_grid, 256, 0, s>>>(h->P);
     }
     const Params &P0 = g->parts[0]->P;
     fq::k_group_finish<<<1, 32, 0, s>>>(g->links, n, g->gdev, g->ghist, g->hist_cap, P0.target, P0.period, P0.c_shift);
@@ -1106,7 +1125,7 @@ bool same_run(const fciqmc_handle *a, const fciqmc_handle *b) {
            a->P.max_exc == b->P.max_exc && a->P.max_sen == b->P.max_sen && a->P.hphf == b->P.hphf &&
            a->P.froz_occ[0] == b->P.froz_occ[0] && a->P.froz_occ[1] == b->P.froz_occ[1] &&
            a->P.froz_emp[0] == b->P.froz_emp[0] && a->P.froz_emp[1] == b->P.froz_emp[1] &&
-           a->z.n_parts == b->z.n_parts;
+           a->z.n_parts == b->z.n_parts && a->P.frac_bits == b->P.frac_bits && a->P.occ_units == b->P.occ_units;
 }
 
 }  // namespace

@@ -148,6 +148,38 @@ __global__ void __launch_bounds__(256) k_new_diag(Params P) {
     }
 }
 
+// Occupation threshold of hybrid walkers: after annihilation every amplitude below occ_units units is rounded
+// stochastically to +-occ_units (probability |C| / occ_units, draw tag 5) or removed, which keeps the list's
+// expectation (Eq. 1). Launched only for runs with a threshold above one unit.
+template <int W>
+__global__ void __launch_bounds__(256) k_round(Params P) {
+    __shared__ unsigned long long s_red[(256 / 32) * 2];
+    DevState *st = P.st;
+    if (st->status) return;
+    const int lb = st->lb, pp = st->pp;
+    int *pop_out = P.pop[lb][pp ^ 1];
+    const long long n = (long long)st->claim;
+    const unsigned iter = (unsigned)st->iter;
+    unsigned long long dnw = 0, dnd = 0;
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
+        const int c = pop_out[s];
+        const unsigned ac = (unsigned)(c < 0 ? -c : c);
+        if (c == 0 || ac >= (unsigned)P.occ_units) continue;
+        unsigned long long d[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) d[w] = P.det[lb][s * W + w];
+        unsigned long long u, unused;
+        draw2(0u, 5u, fingerprint<W>(d, P.map1), P.seed, iter, u, unused);
+        const bool keep = unit53(u) < __ddiv_rn((double)ac, (double)P.occ_units);
+        pop_out[s] = keep ? (c > 0 ? P.occ_units : -P.occ_units) : 0;
+        dnw += (unsigned long long)((long long)(keep ? P.occ_units : 0) - (long long)ac);
+        if (!keep) dnd += (unsigned long long)(-1LL);
+    }
+    unsigned long long accv[2] = {dnw, dnd};
+    unsigned long long *const dst[2] = {&st->d_nw, &st->d_nd};
+    flush_counters<256, 2>(accv, dst, s_red);
+}
+
 // Natural logarithm from the atanh series (shift update); same operation order as the oracle's.
 __device__ double own_log(double x) {
     const double LN2_HI = 0x1.62e42fe800000p-1;

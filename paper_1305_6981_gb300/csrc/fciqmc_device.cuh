@@ -135,6 +135,13 @@ struct Params {
     int n_parts, part;
     unsigned long long *outbox;
     long long ob_cap;
+    // real/integer hybrid walkers: populations in units of 2^-frac_bits walkers; tau, tau_f, cs, cd, cs_f and
+    // cdn_f above carry the factor 2^frac_bits (spawn counts in units), death uses tau_death
+    int frac_bits;
+    double frac_scale;                // 2^-frac_bits
+    int occ_units;                    // occupation threshold in units (1: none)
+    double tau_death;
+    float tau_death_f;
 };
 
 // ---------------------------------------------------------------------------

@@ -972,7 +972,7 @@ __device__ __forceinline__ int death_step(const Params &P, const DetView<W> &v, 
     const float et = fmaf(fabsf(hdf) + fabsf(S_f), 0x1p-22f, 1e-30f);  // >= |(H_ii - E0 - S) - tf|
     const float acf = __uint2float_rn(ac);
     const float at_lo = fabsf(tf) - et, at_hi = fabsf(tf) + et;
-    const float r_hi = at_hi * P.tau_f * acf * kUp, r_lo = at_lo * P.tau_f * acf * kDown;
+    const float r_hi = at_hi * P.tau_death_f * acf * kUp, r_lo = at_lo * P.tau_death_f * acf * kDown;
     const int dec = decide_death(r_lo, r_hi, u);
     int nd;
     bool positive;
@@ -984,7 +984,7 @@ __device__ __forceinline__ int death_step(const Params &P, const DetView<W> &v, 
     } else {
         atomicAdd(&P.st->exact_death, 1ull);
         double hd = *hd_ptr;
-        double r = __dmul_rn(__dmul_rn(P.tau, __dsub_rn(hd, S)), (double)ac);
+        double r = __dmul_rn(__dmul_rn(P.tau_death, __dsub_rn(hd, S)), (double)ac);
         double arr = fabs(r);
         double fl = floor(arr);
         if (fl >= 2147483647.0) { set_status(P.st, FCIQMC_ERR_NUMERIC); return c; }
@@ -1116,13 +1116,25 @@ __global__ void __launch_bounds__(kTile, FQ_SWEEP_MIN_BLOCKS) k_sweep(Params P) 
                 pop_out[s] = nc;
                 acc[NCNT + 2] += (unsigned long long)((long long)(nc < 0 ? -nc : nc) - (long long)ac);
                 if (nc == 0) acc[NCNT + 3] += (unsigned long long)(-1LL);
-                acc[C_ATTEMPTS] += ac;
-                if (ac > (unsigned)kHeavy) {
+                // attempts: one per walker; with hybrid walkers the |C| 2^-b walkers rounded stochastically
+                // (floor, plus one with the probability of the fraction; draw tag 4)
+                unsigned natt = ac;
+                if (P.frac_bits) {
+                    natt = ac >> P.frac_bits;
+                    const unsigned frac = ac & ((1u << P.frac_bits) - 1u);
+                    if (frac) {
+                        unsigned long long u, unused;
+                        draw2(0u, 4u, v.fp, P.seed, iter, u, unused);
+                        if (unit53(u) < __dmul_rn((double)frac, P.frac_scale)) ++natt;
+                    }
+                }
+                acc[C_ATTEMPTS] += natt;
+                if (natt > (unsigned)kHeavy) {
                     // heavily populated determinant: a record for k_heavy, whose warps take chunks of kChunk
                     // attempts; record index and first chunk are claimed by one atomic, so the first
                     // chunks are nondecreasing in the record index
-                    acc[C_HEAVY] += ac;
-                    const unsigned nch = (ac + kChunk - 1) / kChunk;
+                    acc[C_HEAVY] += natt;
+                    const unsigned nch = (natt + kChunk - 1) / kChunk;
                     const unsigned long long old = atomicAdd(&st->heavy_packed, (1ull << 40) | nch);
                     const unsigned long long hidx = old >> 40;
                     if (hidx >= (unsigned long long)P.heavy_cap) {
@@ -1130,10 +1142,10 @@ __global__ void __launch_bounds__(kTile, FQ_SWEEP_MIN_BLOCKS) k_sweep(Params P) 
                     } else {
                         heavy[hidx] = v;
                         P.heavy_base[hidx] = (unsigned)(old & ((1ull << 40) - 1ull));
-                        P.heavy_att[hidx] = ac;
+                        P.heavy_att[hidx] = natt;
                     }
                 } else {
-                    att = ac;
+                    att = natt;
                 }
             }
         }
