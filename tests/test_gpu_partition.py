@@ -68,14 +68,16 @@ def test_partitioned_24e60o_heavy_two_words():
 def test_partitioned_outbox_overflow_stops_every_partition():
     """An outbox too small for the iteration's routed spawns stops the iteration in every partition before
     any list changes, and the error stays set."""
-    from paper_1305_6981_gb300 import Partitioned
+    from paper_1305_6981_gb300 import Partitioned, _native
     s = synth.large_24e60o()
     g = Partitioned(s, 0.005, 3, n_partitions=2, main_capacity=1 << 18, outbox_capacity=8, seed=3)
     d0, p0 = synth.walker_snapshot(s, 100_000, seed=11)
     g.set_walkers(d0, p0)
     before = g.walkers()
     g.step(2)
-    assert g.sync() == -2  # FCIQMC_ERR_CAPACITY
+    with pytest.raises(_native.FciqmcError) as err:
+        g.sync()
+    assert err.value.status == -2  # FCIQMC_ERR_CAPACITY
     assert all(p.estimates()["status"] == -2 for p in g.parts)
     assert same_lists(g.walkers(), before)
     assert g.history(10) == []
