@@ -547,31 +547,24 @@ def run_batch(args, wl):
     import torch
 
     from paper_1305_6981_gb300 import Batch, Fciqmc
-    from paper_1305_6981_gb300.autotune import tune
+    from paper_1305_6981_gb300.autotune import bucket_of, tune_buckets
 
     torch.cuda.set_device(0)
     specs = synth.batch_systems(64, seed=3)
     systems = [synth.make_system(sp["n_orb"], sp["n_elec"], seed=sp["sys_seed"] % 100000, n_chol=sp["n_orb"] // 2,
                                  name=f"run{k}") for k, sp in enumerate(specs)]
     targets = np.array([sp["target"] for sp in specs])
-    # autotune three representative runs (smallest, median and largest target); each run takes the options of
-    # the representative nearest in log(target)
-    reps = [int(np.argmin(targets)), int(np.argsort(targets)[len(targets) // 2]), int(np.argmax(targets))]
-    tuned = {}
+    # autotune one representative per size bucket (one octave of target walkers): block count, index load factor
+    # and spawn-table size; every run takes its bucket's choice, scaled to its own target
     t_tune = time.perf_counter()
-    for r in reps:
-        tuned[r] = tune(systems[r], wl["tau"], wl["thr"], int(targets[r]), trial_iterations=10,
-                        candidates={"grid_blocks": [0, 38, 152], "index_load": [0.5], "spawn_factor": [0.5]})
+    per_run, tuned = tune_buckets(systems, [int(t) for t in targets], wl["tau"], wl["thr"], trial_iterations=10)
     t_tune = time.perf_counter() - t_tune
 
-    def opts_for(k):
-        r = min(reps, key=lambda q: abs(np.log(targets[q]) - np.log(targets[k])))
-        return dict(tuned[r]["best"])
-
     def make(k):
-        o = opts_for(k)
+        rep_target = int(targets[tuned[bucket_of(int(targets[k]))]["representative"]])
+        o = dict(per_run[k])
         o["main_capacity"] = max(4 * int(targets[k]), 1 << 14)
-        o["spawn_capacity"] = max(1 << 12, int(targets[k]) // 2)
+        o["spawn_capacity"] = max(1 << 12, int(o["spawn_capacity"] * targets[k] / rep_target))
         return Fciqmc(systems[k], wl["tau"], wl["thr"], target_walkers=int(targets[k]),
                       initial_population=max(100, int(targets[k]) // 100), initial_shift=wl["initial_shift"],
                       seed=specs[k]["seed"], **o)
@@ -617,7 +610,8 @@ def run_batch(args, wl):
         "config": {"workload": "batch64", "system": wl["desc"], "iterations_per_launch": L,
                    "walkers_total": int(sum(r.estimates()["n_walkers"] for r in runs)),
                    "growth_iterations": grown, "growth_seconds": round(t_grow, 1), "tune_seconds": round(t_tune, 1),
-                   "tuned": {str(k): tuned[k]["best"] for k in reps}},
+                   "tuned": {f"2^{b}..2^{b + 1} walkers ({r['members']} runs)":
+                             dict(r["best"], ms_per_iteration=r["ms_per_iteration"]) for b, r in tuned.items()}},
         "sequential": {"value": att_seq / (ms_seq * 1e-3), "unit": "attempts/s", "ms_total": ms_seq},
         "speedup_vs_sequential": (att_batch / ms_batch) / (att_seq / ms_seq),
         "status": status,

@@ -18,9 +18,9 @@ import numpy as np
 from .fciqmc import Fciqmc
 
 DEFAULT_CANDIDATES = {
-    "grid_blocks": [0, 152, 304],
-    "index_load": [0.5, 0.25],
-    "spawn_factor": [0.25, 1.0],
+    "grid_blocks": [0, 38, 152],
+    "index_load": [0.25, 0.5, 0.75],
+    "spawn_factor": [0.25, 0.5, 1.0],
 }
 
 
@@ -80,3 +80,26 @@ def tune(system, tau: float, thr: int, target: int, *, trial_iterations: int = 2
         with open(cache_path, "w") as f:
             json.dump(cache, f, indent=1)
     return result
+
+
+def bucket_of(target: int, width: float = 1.0) -> int:
+    """Size bucket of a run: its target walker number on a log2 scale, `width` octaves per bucket."""
+    return int(np.floor(np.log2(max(int(target), 2)) / width))
+
+
+def tune_buckets(systems, targets, tau: float, thr: int, *, width: float = 1.0, **kw) -> tuple[list, dict]:
+    """Tunes one representative run per size bucket (the run with the median target of the bucket) and gives
+    every run its bucket's options. Returns (options per run, {bucket: tune() result with the representative's
+    index})."""
+    buckets: dict = {}
+    for k, t in enumerate(targets):
+        buckets.setdefault(bucket_of(t, width), []).append(k)
+    results = {}
+    for b, members in sorted(buckets.items()):
+        order = sorted(members, key=lambda k: targets[k])
+        rep = order[len(order) // 2]
+        r = tune(systems[rep], tau, thr, int(targets[rep]), **kw)
+        r = dict(r, representative=rep, members=len(members))
+        results[b] = r
+    per_run = [dict(results[bucket_of(t, width)]["best"]) for t in targets]
+    return per_run, results

@@ -101,3 +101,33 @@ def test_batched_runs_match_the_oracle():
     batch.close()
     for r in runs:
         r.close()
+
+
+def test_tuner_chooses_a_candidate_whose_run_matches_the_oracle():
+    """The autotuner times every candidate (block count, index load factor, spawn-table size) from one grown
+    snapshot and returns the fastest one; a run created with its choice matches the oracle iteration for
+    iteration (launch shapes never change results). Bucketed tuning gives each run its bucket's choice."""
+    from paper_1305_6981_gb300 import Fciqmc
+    from paper_1305_6981_gb300.autotune import DEFAULT_CANDIDATES, bucket_of, tune, tune_buckets
+    s = synth.make_system(12, 6, seed=3, n_chol=8)
+    r = tune(s, 0.005, 3, 5000, trial_iterations=5)
+    n_cand = 1
+    for v in DEFAULT_CANDIDATES.values():
+        n_cand *= len(v)
+    assert len(r["trials"]) == n_cand and all(t["status"] == 0 for t in r["trials"])
+    best = r["best"]
+    assert best["grid_blocks"] in DEFAULT_CANDIDATES["grid_blocks"]
+    assert best["index_load"] in DEFAULT_CANDIDATES["index_load"]
+    assert r["ms_per_iteration"] == min(t["ms_per_iteration"] for t in r["trials"])
+    g = Fciqmc(s, 0.005, 3, target_walkers=5000, initial_population=300, initial_shift=1.0, seed=9, **best)
+    q = Oracle(s, tau=0.005, initiator_threshold=3, target_walkers=5000, initial_population=300,
+               initial_shift=1.0, seed=9)
+    g.step(40)
+    compare_rows(g.history(40), q.iterate(40))
+    assert same_lists(g.walkers(), q.walkers())
+    g.close()
+    small = dict(grid_blocks=[0, 38], index_load=[0.5], spawn_factor=[0.5])
+    targets = [3000, 3500, 9000]
+    per_run, buckets = tune_buckets([s, s, s], targets, 0.005, 3, trial_iterations=3, candidates=small)
+    assert set(buckets) == {bucket_of(t) for t in targets} and len(buckets) == 2
+    assert per_run[0] == per_run[1] == buckets[bucket_of(3000)]["best"]
