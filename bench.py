@@ -46,10 +46,11 @@ METRIC = "spawn attempts/s at 1e8 walkers (24e/60o, initiator, tau 0.001)"
 # steady-state case (--ncu-case --target 5000000, a few GB on the device) with the command recorded in
 # the profile summary named in WARP_INST_SOURCE; full-size runs are timed with CUDA events and
 # gpu__time_duration.sum only. They must be re-measured whenever those kernels change.
-WARP_INST_PER_ATTEMPT = {"heavy": 10.55, "sweep": 39.9}
-WARP_INST_SOURCE = "profiles/counters_24e60o_1e8.txt (taken on the growth-phase list at ~1.2e8 walkers)"
-# DRAM bytes (read + write) per launch of each kernel at the full workload, from the same summary.
-DRAM_BYTES_PER_LAUNCH = {"heavy": 25_324_160, "sweep": 118_458_496, "annihilate": 52_211_584}
+WARP_INST_PER_ATTEMPT = {"heavy": 15.17, "sweep": 39.19}
+WARP_INST_SOURCE = "profiles/counters_24e60o_steady_5e6.txt (medium steady-state case)"
+# DRAM bytes (read + write) per launch at the full workload; None where no capture of the current kernel at
+# full size exists (the medium case's traffic does not scale with the attempts, see the summary).
+DRAM_BYTES_PER_LAUNCH = {"heavy": None, "sweep": None, "annihilate": None}
 ISSUE_PER_CLK_PER_SM = 4  # warp instructions: 4 schedulers per SM, one issue each per clock
 N_SMS = 152
 
