@@ -41,16 +41,15 @@ from paper_1305_6981_gb300 import synth  # noqa: E402
 METRIC = "spawn attempts/s at 1e8 walkers (24e/60o, initiator, tau 0.001)"
 
 # Instruction-issue roofline of the spawning kernels (they are bound by their instruction stream, not
-# by HBM). Per-unit figures are warp instructions per attempt from ncu: smsp__inst_executed.sum of one
-# launch divided by the attempts of that launch, captured one kernel at a time (-k, -c 1) on the medium
-# steady-state case (--ncu-case --target 5000000, a few GB on the device) with the command recorded in
-# the profile summary named in WARP_INST_SOURCE; full-size runs are timed with CUDA events and
-# gpu__time_duration.sum only. They must be re-measured whenever those kernels change.
-WARP_INST_PER_ATTEMPT = {"heavy": 15.17, "sweep": 39.19}
-WARP_INST_SOURCE = "profiles/counters_24e60o_steady_5e6.txt (medium steady-state case)"
-# DRAM bytes (read + write) per launch at the full workload; None where no capture of the current kernel at
-# full size exists (the medium case's traffic does not scale with the attempts, see the summary).
-DRAM_BYTES_PER_LAUNCH = {"heavy": None, "sweep": None, "annihilate": None}
+# by HBM). Per-unit figures are warp instructions per attempt from ncu: smsp__inst_executed.sum of a launch
+# divided by the attempts of that launch. Metrics collected at full size must be a one-pass set, checked on
+# the medium case first (--ncu-case --target 5000000); multi-pass sets (--set full) stay on that medium case,
+# one kernel and one launch. The commands are in the profile summary named in WARP_INST_SOURCE. The figures
+# must be re-measured whenever those kernels change.
+WARP_INST_PER_ATTEMPT = {"heavy": 11.55, "sweep": 36.3}
+WARP_INST_SOURCE = "profiles/counters_24e60o_steady.txt (full size, steady state, one-pass capture)"
+# DRAM bytes (read + write) per launch at the full workload, from the same capture.
+DRAM_BYTES_PER_LAUNCH = {"heavy": 35_800_000, "sweep": 186_300_000, "annihilate": 87_800_000}
 ISSUE_PER_CLK_PER_SM = 4  # warp instructions: 4 schedulers per SM, one issue each per clock
 N_SMS = 152
 

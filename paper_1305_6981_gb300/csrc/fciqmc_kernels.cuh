@@ -248,9 +248,11 @@ __device__ __forceinline__ float small_f(unsigned x) { return __int_as_float(0x4
 // 1 beta beta, 2 mixed; times 8, plus the irrep product of the pair) the "good" first virtuals a of
 // Sec. VI B in ascending order and their number G; for each (irrep, spin) class its unoccupied spin
 // orbitals in ascending order, and the position of each unoccupied spin orbital in its class list.
+// Rows are padded by one 32-bit word so that the same position in different rows falls in different
+// shared-memory banks (the lanes of a warp read random rows).
 struct HeavyTab {
-    unsigned char glist[24][MAXSO];
-    unsigned char ulist[NCLASS][MAXSO / 2];
+    unsigned char glist[24][MAXSO + 4];
+    unsigned char ulist[NCLASS][MAXSO / 2 + 4];
     unsigned char urank[MAXSO];
     unsigned short G[24];
 };
