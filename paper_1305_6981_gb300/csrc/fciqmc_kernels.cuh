@@ -24,7 +24,10 @@ constexpr int kTile = 256;          // determinants per sweep tile = threads per
 #define FQ_HEAVY_THRESHOLD 256
 #endif
 constexpr int kHeavy = FQ_HEAVY_THRESHOLD;  // |C_i| above this: attempts go to the chunked heavy path
-constexpr int kChunk = 512;         // attempts per heavy chunk (one warp task; 512 measured against 128 to 2048)
+#ifndef FQ_HEAVY_CHUNK
+#define FQ_HEAVY_CHUNK 512
+#endif
+constexpr int kChunk = FQ_HEAVY_CHUNK;  // attempts per heavy chunk (one warp task; 512 measured against 128 to 2048)
 constexpr unsigned long long kSaltMerge = 0x5851F42D4C957F2Dull;
 constexpr unsigned long long kSaltIndex = 0x14057B7EF767814Full;
 constexpr unsigned long long kFlagUnit = 1ull << 40;  // merge payload: (#initiator spawns << 40) + amount
@@ -175,8 +178,11 @@ __device__ __forceinline__ void prepare_det(const Params &P, const Tables &T, De
 // ---------------------------------------------------------------------------- one spawning attempt
 // Spawns accepted by the lanes of one warp, inserted into the merge table together (flush_queue) so that
 // the table's round trips are shared by the lanes instead of stalling the warp once per accepting lane.
-constexpr int kQueue = 48;       // capacity: flushed from 16 entries on; a round adds at most 32
-constexpr int kQueueFlush = 16;
+#ifndef FQ_QUEUE_FLUSH
+#define FQ_QUEUE_FLUSH 16
+#endif
+constexpr int kQueueFlush = FQ_QUEUE_FLUSH;  // flushed from this many entries on
+constexpr int kQueue = kQueueFlush + 32;     // capacity: a round adds at most 32 to fewer than kQueueFlush
 template <int W>
 struct SpawnQueue {
     unsigned long long key[kQueue][W];

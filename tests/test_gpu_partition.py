@@ -65,6 +65,17 @@ def test_partitioned_24e60o_heavy_two_words():
     assert sum(r["heavy_attempts"] for r in rows) > 0
 
 
+@pytest.mark.parametrize("mode", ["spin-coupled", "cisd"])
+def test_partitioned_with_spin_coupling_or_space(mode):
+    """Spin-coupled functions are routed by the fingerprint of their stored determinant; excitations outside
+    a permitted space stay null excitations in every partition."""
+    kw = dict(hphf=True) if mode == "spin-coupled" else dict(max_excitation=2)
+    rows = _lockstep(synth.init_12e24o(), 0.005, 3, 2, 80, dict(main_capacity=1 << 17),
+                     target_walkers=100000, initial_population=3000, initial_shift=1.0, seed=11, **kw)
+    if mode == "cisd":
+        assert sum(r["nulls"] for r in rows) > 0
+
+
 def test_partitioned_outbox_overflow_stops_every_partition():
     """An outbox too small for the iteration's routed spawns stops the iteration in every partition before
     any list changes, and the error stays set."""
