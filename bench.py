@@ -71,6 +71,18 @@ WORKLOADS = {
                         desc="24e/60o on spin-coupled functions (Sec. VI C: half the space, so half the walkers "
                              "and twice the time step of the determinant run), initiator 3, tau 0.002, "
                              "5e7 target walkers"),
+    "24e60o-real": dict(system=synth.large_24e60o, tau=0.001, thr=3, target=100_000_000, main_capacity=200_000_000,
+                        spawn_capacity=1 << 27, initial_population=20_000, initial_shift=0.5, max_growth=40_000,
+                        equilibrate=4000, space=dict(walker_fraction_bits=4, occupation_threshold=1.0),
+                        desc="24e/60o with real/integer hybrid walkers (populations in units of 1/16 walker, "
+                             "occupation threshold 1 walker), initiator 3, tau 0.001, 1e8 target walkers, steady state"),
+    "24e60o-part4": dict(system=synth.large_24e60o, tau=0.001, thr=3, target=100_000_000, main_capacity=75_000_000,
+                         spawn_capacity=1 << 25, initial_population=20_000, initial_shift=0.5, max_growth=40_000,
+                         equilibrate=4000, partitions=4, outbox_capacity=1 << 20,
+                         desc="24e/60o divided among 4 hash partitions on one GPU (Sec. V A: owner = Algorithm 1 "
+                              "fingerprint mod 4, spawns routed through per-destination outboxes), initiator 3, "
+                              "tau 0.001, 1e8 target walkers, steady state; beside it the unpartitioned run from "
+                              "the same list"),
     "12e24o": dict(system=synth.init_12e24o, tau=0.005, thr=3, target=1_000_000, main_capacity=4_000_000,
                    spawn_capacity=1 << 22, initial_population=2_000, initial_shift=1.0, max_growth=20_000,
                    equilibrate=50, desc="12e/24o (W=1), 8 irreps, initiator 3, tau 0.005, 1e6 target walkers"),
@@ -193,7 +205,8 @@ def oracle_sample(wl, system):
     if wl.get("space", {}).get("hphf"):
         dets, pops = synth.stored_pairs(dets, pops)
     keep = np.array([q.in_space(d) for d in dets])
-    return q, dets[keep], pops[keep]
+    bits = wl.get("space", {}).get("walker_fraction_bits", 0)
+    return q, dets[keep], (pops[keep].astype(np.int64) << bits).astype(np.int32)  # hybrid walkers: units
 
 
 def oracle_baseline(wl, system, steps: int, warmup: int, one_thread_steps: int = 2):
@@ -541,6 +554,83 @@ def run_gpu(args, wl, rank, world, local_rank):
     return g, out, info
 
 
+def run_partitioned(args, wl):
+    """The workload divided among hash partitions on one GPU (fciqmc_group_*): grown and settled as the
+    default workload, then K timed iterations of the group; beside it, an unpartitioned run loaded with the
+    same list and state and timed over the same number of iterations (the cost of the decomposition)."""
+    import torch
+
+    from paper_1305_6981_gb300 import Fciqmc, Partitioned
+
+    torch.cuda.set_device(0)
+    system = wl["system"]()
+    n_parts = wl["partitions"]
+    target = args.target or wl["target"]
+    g = Partitioned(system, wl["tau"], wl["thr"], n_partitions=n_parts, target_walkers=target,
+                    initial_population=wl["initial_population"], initial_shift=wl["initial_shift"], seed=1,
+                    main_capacity=wl["main_capacity"], spawn_capacity=wl["spawn_capacity"],
+                    outbox_capacity=wl["outbox_capacity"])
+    t_grow = time.perf_counter()
+    grown = 0
+    while grown < wl["max_growth"]:
+        g.step(50)
+        grown += 50
+        e = g.estimates()
+        if e["status"] != 0:
+            raise RuntimeError(f"device status {e['status']} during growth at {grown}")
+        if e["vary_shift"]:
+            break
+    settle = wl["equilibrate"] if args.settle < 0 else args.settle
+    g.step(settle)
+    grown += settle
+    g.step(args.warmup)
+    g.sync()
+    t_grow = time.perf_counter() - t_grow
+
+    def timed(run, stream):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        run.step(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1)
+
+    d, p, hd = g.walkers()
+    st = g.parts[0].state()
+    clocks = Clocks(0)
+    clocks.start()
+    time.sleep(0.3)
+    ms = timed(g, g.stream)
+    clk = clocks.stop()
+    status = g.sync()
+    rows = g.history(args.steps)
+    att = sum(r["attempts"] for r in rows)
+    per_part = [len(x.walkers()[1]) for x in g.parts]
+    g.close()
+    # the same list, unpartitioned
+    u = Fciqmc(system, wl["tau"], wl["thr"], target_walkers=target, seed=1, main_capacity=2 * len(p) + (1 << 20),
+               spawn_capacity=wl["spawn_capacity"] * n_parts)
+    u.set_walkers(d, p, hd, iteration=st["iteration"], shift=st["shift"], vary=st["vary_shift"],
+                  shift_counter=st["shift_counter"], nw_last_update=st["nw_last_update"])
+    u.step(args.warmup)
+    ms_u = timed(u, u.stream)
+    rows_u = u.history(args.steps)
+    att_u = sum(r["attempts"] for r in rows_u)
+    u.close()
+    return {"metric": METRIC, "value": att / (ms * 1e-3), "unit": "attempts/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "system": wl["desc"], "partitions": n_parts,
+                       "walkers_mean": float(np.mean([r["nw_in"] for r in rows])), "dets": int(len(p)),
+                       "dets_per_partition": per_part, "growth_iterations": grown,
+                       "growth_seconds": round(t_grow, 1), "parallelism": f"{n_parts} partitions on 1 GPU"},
+            "unpartitioned_same_state": {"value": att_u / (ms_u * 1e-3), "unit": "attempts/s",
+                                         "ms_per_step": ms_u / args.steps},
+            "partition_cost": (ms / args.steps) / (ms_u / args.steps),
+            "clocks": clk, "status": status, "gpu_launches": (11 * n_parts + 1) * args.steps}
+
+
 def run_batch(args, wl):
     """Aggregate spawn attempts/s of 64 uneven runs advanced by one graph per launch, against the same
     runs advanced one at a time (each with its own graph launches on its own stream, in sequence)."""
@@ -723,6 +813,9 @@ def main():
         return
     if args.workload == "batch64":
         print(json.dumps(run_batch(args, wl)), flush=True)
+        return
+    if wl.get("partitions"):
+        print(json.dumps(run_partitioned(args, wl)), flush=True)
         return
     import torch.distributed as dist
     if world > 1:
