@@ -70,3 +70,39 @@ def test_one_iteration_at_1e7_walkers_with_space_or_spin_coupling(workload):
     assert r["heavy_attempts"] > r["attempts"] // 2 and r["spawn_events"] > 10_000
     if workload.endswith("cas"):
         assert r["nulls"] > 0
+
+
+def test_one_iteration_partitioned_at_1e7_walkers():
+    """The grown 24e/60o list (1e7 target, settled) loaded into a run of three hash partitions: one iteration of
+    the group against one oracle iteration from the same list, every counter, the shift and the union of the
+    partitions' lists identical."""
+    import bench
+    from paper_1305_6981_gb300 import Partitioned
+    wl = bench.WORKLOADS["24e60o"]
+    g0, _, _, _ = bench.grow(argparse.Namespace(target=10_000_000, workload="24e60o"), wl, 0)
+    d, p, h = g0.walkers()
+    st = g0.state()
+    g0.close()
+    g = Partitioned(wl["system"](), wl["tau"], wl["thr"], n_partitions=3, target_walkers=10_000_000,
+                    main_capacity=2 * len(p), spawn_capacity=1 << 23, outbox_capacity=1 << 20, seed=1)
+    g.set_walkers(d, p, h, iteration=st["iteration"], shift=st["shift"], vary=st["vary_shift"],
+                  shift_counter=st["shift_counter"], nw_last_update=st["nw_last_update"])
+    g.step(1)
+    rows_g = g.history(1)
+    after = g.walkers()
+    g.close()
+    q = Oracle(wl["system"](), tau=wl["tau"], initiator_threshold=wl["thr"], target_walkers=10_000_000, seed=1)
+    q.set_walkers(d, p, iteration=st["iteration"], shift=st["shift"], vary=bool(st["vary_shift"]),
+                  nw_prev=st["nw_last_update"], n_since=st["shift_counter"])
+    compare_rows(rows_g, q.iterate(1))
+    assert same_lists(after, q.walkers())
+    assert int(np.abs(p.astype(np.int64)).sum()) > 5_000_000 and rows_g[0]["spawn_events"] > 10_000
+
+
+def test_one_iteration_hybrid_at_1e7_walkers():
+    """The hybrid-walker workload of the benchmark (units of 1/16 walker) grown to a 1e7 target and settled: one
+    iteration on the GPU and in the oracle from the same list, identical."""
+    r, p = one_iteration("24e60o-real", 10_000_000)
+    a = np.abs(p.astype(np.int64))
+    assert a.sum() > 5_000_000 * 16 and np.all(a >= 16) and np.any(a % 16 != 0)
+    assert r["heavy_attempts"] > r["attempts"] // 2
