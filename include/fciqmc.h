@@ -61,7 +61,10 @@ enum {
     FCIQMC_ERR_TIMEOUT = -4,       /* a bounded device wait gave up */
     FCIQMC_ERR_CUDA = -5,          /* a CUDA runtime call failed */
     FCIQMC_ERR_UNSUPPORTED = -6,   /* size beyond the limits above */
-    FCIQMC_ERR_WORKSPACE = -7      /* workspace too small or misaligned (256 B) */
+    FCIQMC_ERR_WORKSPACE = -7,     /* workspace too small or misaligned (256 B) */
+    FCIQMC_ERR_BOUNDS = -8         /* a device table index out of range; reported only by the debug build
+                                      (compiled with -DFCIQMC_DEBUG), which checks every index the
+                                      algorithm keeps in range by construction and skips the access */
 };
 
 typedef struct fciqmc_handle fciqmc_handle;

@@ -15,7 +15,10 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
-LIB = os.path.join(BUILD, "libfciqmc.so")
+# FCIQMC_DEBUG_BUILD=1 selects the debug build (-DFCIQMC_DEBUG: device table indices checked, a violation
+# reported as FCIQMC_ERR_BOUNDS), built and loaded as its own library beside the normal one.
+DEBUG = os.environ.get("FCIQMC_DEBUG_BUILD", "") == "1"
+LIB = os.path.join(BUILD, "libfciqmc_debug.so" if DEBUG else "libfciqmc.so")
 SOURCES = ["fciqmc.cu", "fciqmc_spawn_w1.cu", "fciqmc_spawn_w2.cu", "fciqmc_static.cu", "fciqmc_rdm.cu"]
 DEPS = SOURCES + ["fciqmc_kernels.cuh", "fciqmc_cycle.cuh", "fciqmc_device.cuh", "fciqmc_spawn.h", "fciqmc_spawn_impl.cuh"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
@@ -43,8 +46,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and not _stale():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
-    tag = f".tmp{os.getpid()}"
+    tag = f".tmp{os.getpid()}" + ("d" if DEBUG else "")
     extra = os.environ.get("FCIQMC_NVCC_FLAGS", "").split()  # tuning defines, e.g. -DFQ_SWEEP_MIN_BLOCKS=3
+    if DEBUG:
+        extra.append("-DFCIQMC_DEBUG")
     compile_flags = [f for f in NVCC_FLAGS if f != "-shared"]
     objs, procs = [], []
     for src in SOURCES:  # one nvcc per translation unit, in parallel

@@ -1,6 +1,7 @@
 // C ABI of the FCIQMC walker cycle: workspace layout, setup, iteration launch, read-back.
 // The declarations and the contract of every entry point are in include/fciqmc.h.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <climits>
@@ -25,6 +26,15 @@ namespace {
         cudaError_t e_ = (call);                          \
         if (e_ != cudaSuccess) return FCIQMC_ERR_CUDA;    \
     } while (0)
+
+// NVTX range over a library call (a no-op unless a profiler is attached), so a timeline attributes the
+// graph launches, loads and read-backs to the call that issued them.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 constexpr size_t kAlign = 256;
 constexpr int kMaxGrid = 4096;
@@ -374,6 +384,7 @@ const char *fciqmc_strerror(int status) {
         case FCIQMC_ERR_CUDA: return "CUDA runtime error";
         case FCIQMC_ERR_UNSUPPORTED: return "unsupported size (n_orb <= 64, n_elec <= 64)";
         case FCIQMC_ERR_WORKSPACE: return "workspace too small or not 256-byte aligned";
+        case FCIQMC_ERR_BOUNDS: return "device index out of range (debug build check)";
         default: return "unknown status";
     }
 }
@@ -498,6 +509,7 @@ int fciqmc_create(const double *h1, const double *eri_s8, double e_core, int n_e
     P.hist = at<fciqmc_row>(h, L.hist);
     P.hist_cap = z.hist_cap;
     P.st = at<DevState>(h, L.state);
+    P.n_eri = z.n_eri;
     P.n_parts = z.n_parts;
     P.part = z.part;
     P.outbox = z.n_parts > 1 ? at<unsigned long long>(h, L.outbox) : nullptr;
@@ -633,6 +645,7 @@ int fciqmc_create(const double *h1, const double *eri_s8, double e_core, int n_e
             FQ_TRY(cudaMemcpyAsync(&n_ref_exc, facts + 2, sizeof(long long), cudaMemcpyDeviceToHost, s));
             FQ_TRY(cudaStreamSynchronize(s));
             if (n_ref_exc >= 0) {
+                P.ref_n = n_ref_exc;
                 P.ref_pinfo = pinfo;
                 P.ref_off2 = off2;
                 P.ref_exc = ex;
@@ -705,6 +718,7 @@ fail:
 
 int fciqmc_step(fciqmc_handle *h, int32_t n_iterations) {
     if (!h || n_iterations < 0 || h->z.n_parts > 1) return FCIQMC_ERR_INVALID_ARG;
+    NvtxRange range("fciqmc_step");
     for (int i = 0; i < n_iterations; ++i) {
         if (h->graph_ready) FQ_CUDA(cudaGraphLaunch(h->graph, h->stream));
         else enqueue(h, h->stream);
@@ -719,9 +733,12 @@ int fciqmc_profile(fciqmc_handle *h, int32_t n_iterations, double *kernel_ms) {
     for (int k = 0; k <= FCIQMC_N_KERNELS; ++k) FQ_CUDA(cudaEventCreate(&ev[k]));
     const Params &P = h->P;
     cudaStream_t s = h->stream;
+    static const char *const kNames[FCIQMC_N_KERNELS] = {"compact_copy", "index_clear", "index_fill", "compact_finish",
+                                                         "sweep", "heavy", "annihilate", "finish"};
     for (int it = 0; it < n_iterations; ++it) {
         cudaEventRecord(ev[0], s);
         for (int k = 0; k < FCIQMC_N_KERNELS; ++k) {
+            NvtxRange range(kNames[k]);
             if (h->z.W == 1) {
                 switch (k) {
                     case 0: fq::k_compact_copy<1><<<h->small_grid, 256, 0, s>>>(P); break;
@@ -785,6 +802,7 @@ int fciqmc_sync(fciqmc_handle *h) {
 
 int fciqmc_estimators(fciqmc_handle *h, fciqmc_estimates *out) {
     if (!h || !out) return FCIQMC_ERR_INVALID_ARG;
+    NvtxRange range("fciqmc_estimators");
     DevState *st = h->P.st;
     FQ_CUDA(cudaMemsetAsync(&st->est_nw, 0, sizeof(unsigned long long) * 2 + sizeof(long long), h->stream));
     const int blocks = std::min(h->small_grid, kMaxGrid);
@@ -839,6 +857,7 @@ int fciqmc_n_dets(fciqmc_handle *h, int64_t *n_dets) {
 
 int fciqmc_get_walkers(fciqmc_handle *h, uint64_t *dets, int32_t *pops, double *hdiag, int64_t cap, int64_t *n) {
     if (!h || !n || cap < 0 || (cap > 0 && (!dets || !pops))) return FCIQMC_ERR_INVALID_ARG;
+    NvtxRange range("fciqmc_get_walkers");
     DevState *st = h->P.st;
     FQ_CUDA(cudaMemsetAsync(&st->new_len, 0, sizeof(unsigned long long), h->stream));
     if (h->z.W == 1) fq::k_gather<1><<<h->small_grid, 256, 0, h->stream>>>(h->P);
@@ -869,6 +888,7 @@ int fciqmc_set_walkers(fciqmc_handle *h, const uint64_t *dets, const int32_t *po
                        const fciqmc_state *stin) {
     if (!h || n < 0 || (n > 0 && (!dets || !pops))) return FCIQMC_ERR_INVALID_ARG;
     if (n > h->z.cap) return FCIQMC_ERR_CAPACITY;
+    NvtxRange range("fciqmc_set_walkers");
     DevState cur;
     int rc = read_state(h, cur);
     if (rc != FCIQMC_OK) return rc;
@@ -1032,6 +1052,7 @@ int fciqmc_batch_create(fciqmc_handle *const *runs, int n_runs, int32_t iteratio
 
 int fciqmc_batch_step(fciqmc_batch *b, int32_t n_launches, void *cuda_stream) {
     if (!b || n_launches < 0) return FCIQMC_ERR_INVALID_ARG;
+    NvtxRange range("fciqmc_batch_step");
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     for (size_t r = 0; r < b->runs.size(); ++r) {
         FQ_CUDA(cudaEventRecord(b->run_events[r], b->runs[r]->stream));
@@ -1216,6 +1237,7 @@ int fciqmc_group_create(fciqmc_handle *const *parts, int32_t n_partitions, int64
 
 int fciqmc_group_step(fciqmc_group *g, int32_t n_iterations) {
     if (!g || n_iterations < 0) return FCIQMC_ERR_INVALID_ARG;
+    NvtxRange range("fciqmc_group_step");
     for (size_t r = 0; r < g->parts.size(); ++r) {
         FQ_CUDA(cudaEventRecord(g->part_events[r], g->parts[r]->stream));
         FQ_CUDA(cudaStreamWaitEvent(g->stream, g->part_events[r], 0));

@@ -135,6 +135,7 @@ struct Params {
     int n_parts, part;
     unsigned long long *outbox;
     long long ob_cap;
+    long long n_eri, ref_n;           // packed ERIs; entries of the reference's table (debug checks)
     // real/integer hybrid walkers: populations in units of 2^-frac_bits walkers; tau, tau_f, cs, cd, cs_f and
     // cdn_f above carry the factor 2^frac_bits (spawn counts in units), death uses tau_death
     int frac_bits;
@@ -143,6 +144,17 @@ struct Params {
     double tau_death;
     float tau_death_f;
 };
+
+__device__ __forceinline__ void set_status(DevState *st, int code) { atomicCAS(&st->status, 0, code); }
+
+// Debug build (-DFCIQMC_DEBUG): indices that the algorithm keeps in range by construction are checked before
+// the access they guard; a violation sets FCIQMC_ERR_BOUNDS (sticky like the other device errors) and the
+// access is skipped. In the normal build the check is the constant true.
+#ifdef FCIQMC_DEBUG
+#define FQ_CHECK(cond, st) ((cond) ? true : (::fq::set_status((st), FCIQMC_ERR_BOUNDS), false))
+#else
+#define FQ_CHECK(cond, st) true
+#endif
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).
@@ -312,7 +324,9 @@ __device__ __forceinline__ float ld_keep(const float *p, unsigned long long pol)
     return v;
 }
 __device__ __forceinline__ float eri_f(const Params &P, int p, int q, int r, int s, unsigned long long pol) {
-    return ld_keep(P.eri_f + eidx(p, q, r, s), pol);
+    const int k = eidx(p, q, r, s);
+    if (!FQ_CHECK(k >= 0 && k < P.n_eri, P.st)) return 0.f;
+    return ld_keep(P.eri_f + k, pol);
 }
 
 // Slater-Condon, single i -> a from source d (occupied list occ of d), exact FP64 in ascending order.
@@ -564,6 +578,6 @@ __device__ __forceinline__ long long warp_append(unsigned long long *ctr, bool w
     return (long long)(base + __popc(m & ((1u << lane) - 1u)));
 }
 
-__device__ __forceinline__ void set_status(DevState *st, int code) { atomicCAS(&st->status, 0, code); }
+
 
 }  // namespace fq

@@ -158,6 +158,7 @@ __device__ __forceinline__ void prepare_det(const Params &P, const Tables &T, De
         while (m) {
             const int b = __ffsll((long long)m) - 1;
             const int k = 64 * w + b;
+            if (!FQ_CHECK(n < MAXN, P.st)) break;
             v.occ[n] = (unsigned char)k;
             okm |= ((ok[w] >> b) & 1ull) << n;
             h = 1099511628211ull * h + T.map1[k] * (unsigned long long)(n + 1);
@@ -357,6 +358,7 @@ __device__ __forceinline__ void emit_spawn(const Params &P, const DetView<W> &v,
     cnt[C_SPAWNED] += (unsigned long long)n;
     const long long amt = -(long long)(v.c > 0 ? 1 : -1) * sgn_h * (long long)n;
     const unsigned slot = atomicAdd(&out.n, 1u);
+    if (!FQ_CHECK(slot < (unsigned)kQueue, P.st)) return;
 #pragma unroll
     for (int w = 0; w < W; ++w) out.key[slot][w] = child[w];
     out.val[slot] = (v.flag ? kFlagUnit : 0ull) + (unsigned long long)amt;
@@ -655,7 +657,9 @@ __device__ __forceinline__ bool attempt_begin(const Params &P, const Tables &T, 
         const unsigned G = pi & 0xFFu;
         if (G == 0) { cnt[C_NULLS]++; return false; }
         const unsigned o2 = __ldg(P.ref_off2 + (pi >> 8) + rank_next(rh, rl, G));
-        const RefExc *e = P.ref_exc + (o2 >> 7) + rank_next(rh, rl, o2 & 0x7Fu);
+        const unsigned ei = (o2 >> 7) + rank_next(rh, rl, o2 & 0x7Fu);
+        if (!FQ_CHECK((long long)ei < P.ref_n, P.st)) return false;
+        const RefExc *e = P.ref_exc + ei;
         const float2 pb = __ldg(reinterpret_cast<const float2 *>(e));
         if (MODE & 1) {
             if (pb.x < 0.f) { cnt[C_NULLS]++; return false; }  // the target lies outside the permitted space
@@ -691,7 +695,9 @@ __device__ __forceinline__ bool attempt_begin(const Params &P, const Tables &T, 
         const int e = (si == sj ? si : 2) * 8 + gij;
         G = tab->G[e];
         if (G == 0) { cnt[C_NULLS]++; return false; }
-        ao = tab->glist[e][rank_next(rh, rl, G)];
+        const unsigned k2 = rank_next(rh, rl, G);
+        if (!FQ_CHECK(k2 < (unsigned)MAXSO, P.st)) return false;
+        ao = tab->glist[e][k2];
     } else {
         unsigned long long gm[W];
         G = good_set<W>(P, v, si, sj, gij, gm);
@@ -708,6 +714,7 @@ __device__ __forceinline__ bool attempt_begin(const Params &P, const Tables &T, 
     int bo;
     if (TAB) {
         if (same && k3 >= tab->urank[ao]) ++k3;  // the list of class cb still holds a
+        if (!FQ_CHECK(k3 < MAXSO / 2, P.st)) return false;
         bo = tab->ulist[cb][k3];
     } else {
         unsigned long long bm[W];
