@@ -60,7 +60,7 @@ def test_full_space_ground_state_8e8o():
     f.close()
 
 
-@pytest.mark.parametrize("n", [600, 3000])
+@pytest.mark.parametrize("n", [600, 3000, 10000])
 def test_sampled_vector_16e40o_matches_oracle(n):
     s = synth.rdm_16e40o()
     dets, c = synth.sampled_vector(s, n, seed=5)
