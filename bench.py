@@ -840,6 +840,8 @@ def main():
             out["batched_64_runs"] = {k: b[k] for k in ("value", "unit", "sequential", "speedup_vs_sequential",
                                                          "ms_per_step", "status")}
             out["batched_64_runs"]["walkers_total"] = b["config"]["walkers_total"]
+            out["batched_64_runs"]["tuned"] = b["config"]["tuned"]
+            out["batched_64_runs"]["tune_seconds"] = b["config"]["tune_seconds"]
             out["energy_functional"] = energy_functional_timing()
         print(json.dumps(out), flush=True)
     if getattr(g, "handle", None):
