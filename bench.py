@@ -548,8 +548,9 @@ def run_gpu(args, wl, rank, world, local_rank):
             "clocks": clk,
             "status": st,
             "exact_path": exact,
-            "gpu_launches": 11 * args.steps,  # per iteration: 6 compaction kernels, sweep, heavy, annihilate,
-                                              # new-slot diagonal elements, finish
+            # per iteration: 6 compaction kernels, sweep, tile sums, heavy, annihilate, new-slot diagonal
+            # elements, finish (and the occupation threshold with hybrid walkers)
+            "gpu_launches": (12 + (1 if wl.get("space", {}).get("walker_fraction_bits") else 0)) * args.steps,
         }
     return g, out, info
 
@@ -628,7 +629,7 @@ def run_partitioned(args, wl):
             "unpartitioned_same_state": {"value": att_u / (ms_u * 1e-3), "unit": "attempts/s",
                                          "ms_per_step": ms_u / args.steps},
             "partition_cost": (ms / args.steps) / (ms_u / args.steps),
-            "clocks": clk, "status": status, "gpu_launches": (11 * n_parts + 1) * args.steps}
+            "clocks": clk, "status": status, "gpu_launches": (12 * n_parts + 1) * args.steps}
 
 
 def run_batch(args, wl):

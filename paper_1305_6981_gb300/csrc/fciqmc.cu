@@ -127,7 +127,7 @@ Layout layout_of(const Sizes &z, int n_orb) {
     L.heavy = take(sizeof(fq::DetView<2>) * z.heavy_cap);
     L.heavy_base = take(sizeof(unsigned) * z.heavy_cap);
     L.heavy_att = take(sizeof(unsigned) * z.heavy_cap);
-    L.partial = take(sizeof(double) * kMaxGrid);
+    L.partial = take(sizeof(double) * (std::max<long long>((z.cap + fq::kTile - 1) / fq::kTile, kMaxGrid) + fq::kTileSums));
     L.hist = take(sizeof(fciqmc_row) * z.hist_cap);
     L.ref_pinfo = take(sizeof(unsigned) * std::max(z.npairs, 1));
     L.ref_off2 = take(sizeof(unsigned) * std::max<long long>((long long)z.npairs * z.n_so, 1));
@@ -242,6 +242,7 @@ void launch_heavy(fciqmc_handle *h, cudaStream_t s) {
 template <int W>
 void launch_spawning(fciqmc_handle *h, cudaStream_t s) {
     launch_sweep<W>(h, s);
+    fq::k_tile_sum<<<fq::kTileSums, 256, 0, s>>>(h->P);
     launch_heavy<W>(h, s);
 }
 
@@ -506,6 +507,7 @@ int fciqmc_create(const double *h1, const double *eri_s8, double e_core, int n_e
     P.heavy_cap = z.heavy_cap;
     P.rcpf = at<float>(h, L.rcpf);
     P.partial = at<double>(h, L.partial);
+    P.tiles_cap = std::max<long long>((z.cap + fq::kTile - 1) / fq::kTile, kMaxGrid);
     P.hist = at<fciqmc_row>(h, L.hist);
     P.hist_cap = z.hist_cap;
     P.st = at<DevState>(h, L.state);
@@ -749,7 +751,10 @@ int fciqmc_profile(fciqmc_handle *h, int32_t n_iterations, double *kernel_ms) {
                         break;
                     case 2: fq::k_index_fill<1><<<h->small_grid, 256, 0, s>>>(P, 0); break;
                     case 3: fq::k_compact_finish<<<1, 32, 0, s>>>(P); break;
-                    case 4: launch_sweep<1>(h, s); break;
+                    case 4:
+                        launch_sweep<1>(h, s);
+                        fq::k_tile_sum<<<fq::kTileSums, 256, 0, s>>>(P);
+                        break;
                     case 5: launch_heavy<1>(h, s); break;
                     case 6:
                         fq::k_annihilate<1><<<h->ann_grid, 256, 0, s>>>(P);
@@ -768,7 +773,10 @@ int fciqmc_profile(fciqmc_handle *h, int32_t n_iterations, double *kernel_ms) {
                         break;
                     case 2: fq::k_index_fill<2><<<h->small_grid, 256, 0, s>>>(P, 0); break;
                     case 3: fq::k_compact_finish<<<1, 32, 0, s>>>(P); break;
-                    case 4: launch_sweep<2>(h, s); break;
+                    case 4:
+                        launch_sweep<2>(h, s);
+                        fq::k_tile_sum<<<fq::kTileSums, 256, 0, s>>>(P);
+                        break;
                     case 5: launch_heavy<2>(h, s); break;
                     case 6:
                         fq::k_annihilate<2><<<h->ann_grid, 256, 0, s>>>(P);
@@ -1188,8 +1196,7 @@ int fciqmc_group_create(fciqmc_handle *const *parts, int32_t n_partitions, int64
         links[r].st = P.st;
         links[r].outbox = P.outbox;
         links[r].ob_cap = P.ob_cap;
-        links[r].partial = P.partial;
-        links[r].sweep_grid = P.sweep_grid;
+        links[r].partial = P.partial + P.tiles_cap;
         links[r].hist = P.hist;
         links[r].hist_cap = P.hist_cap;
         links[r].cap = P.cap;

@@ -263,23 +263,40 @@ __device__ __forceinline__ void commit_list(DevState *st, long long nd_out, long
     st->c0_in = 0;
     st->d_nw = st->d_nd = 0;
     st->n_new = 0;
+    st->sweep_next = 0;
     for (int k = 0; k < NCNT; ++k) st->cnt[k] = 0;
     for (int k = 0; k < MAXPARTS; ++k) st->ob_n[k] = 0;
 }
 
-// Eq. 2 numerator of one list: its sweep blocks' partials summed by one warp in a fixed order (lane k takes
-// blocks k, k + 32, ..., then a fixed shuffle tree), so the sum is the same in every run; lane 0 holds it.
-__device__ __forceinline__ double list_numerator(const double *partial, int n_blocks) {
+// Range sums of the sweep tiles' numerators (after k_sweep): block b adds the tiles of its fixed range
+// [b n / kTileSums, (b + 1) n / kTileSums) in a fixed order (thread t takes tiles t, t + 256, ... of the range,
+// then the block's fixed tree), so the run's numerator is the same in every run; the FP64 adds are spread
+// over kTileSums SMs.
+__global__ void __launch_bounds__(256) k_tile_sum(Params P) {
+    __shared__ double s_red[256 / 32];
+    DevState *st = P.st;
+    if (st->status) return;
+    const long long n = (st->list_len + kTile - 1) / kTile;
+    const long long lo = n * blockIdx.x / kTileSums, hi = n * (blockIdx.x + 1) / kTileSums;
+    double v = 0.0;
+    for (long long t = lo + threadIdx.x; t < hi; t += blockDim.x) v = __dadd_rn(v, P.partial[t]);
+    const double bs = block_sum_f64<256>(v, s_red);
+    if (threadIdx.x == 0) P.partial[P.tiles_cap + blockIdx.x] = bs;
+}
+
+// Eq. 2 numerator of one list: the kTileSums range sums added by one warp in a fixed order (lane k takes sum
+// k, then a fixed shuffle tree); lane 0 holds it.
+__device__ __forceinline__ double list_numerator(const double *range_sums) {
     const int lane = threadIdx.x & 31;
     double part = 0.0;
-    for (int b = lane; b < n_blocks; b += 32) part = __dadd_rn(part, partial[b]);
+    for (int b = lane; b < kTileSums; b += 32) part = __dadd_rn(part, range_sums[b]);
     return warp_sum_f64(part);
 }
 
 __global__ void k_finish(Params P) {
     DevState *st = P.st;
     if (st->status) return;
-    const double num = list_numerator(P.partial, P.sweep_grid);
+    const double num = list_numerator(P.partial + P.tiles_cap);
     if (threadIdx.x != 0) return;
     const fciqmc_row row = list_row(st, num);
     P.hist[st->hist_n % P.hist_cap] = row;
@@ -294,8 +311,7 @@ struct PartLink {
     DevState *st;
     unsigned long long *outbox;  // [n_parts][ob_cap] entries
     long long ob_cap;
-    const double *partial;       // sweep partials of the numerator
-    int sweep_grid;
+    const double *partial;       // range sums of the sweep tiles' numerators (kTileSums)
     fciqmc_row *hist;            // the partition's own rows (its list's counters)
     long long hist_cap, cap;
 };
@@ -347,7 +363,7 @@ __global__ void k_group_finish(const PartLink *links, int n_parts, GroupDev *g, 
         return;
     }
     double nums[MAXPARTS];
-    for (int r = 0; r < n_parts; ++r) nums[r] = list_numerator(links[r].partial, links[r].sweep_grid);
+    for (int r = 0; r < n_parts; ++r) nums[r] = list_numerator(links[r].partial);
     if (threadIdx.x != 0) return;
     fciqmc_row tot = list_row(links[0].st, nums[0]);
     for (int r = 0; r < n_parts; ++r) {

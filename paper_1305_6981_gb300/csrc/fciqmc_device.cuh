@@ -52,6 +52,7 @@ struct DevState {
     double est_num;
     int check_bad;             // set by the check of a list being loaded
     unsigned long long n_new;  // determinants placed in new slots this iteration (diagonal elements pending)
+    unsigned long long sweep_next;  // next sweep tile to hand out (tiles are taken dynamically by the blocks)
     unsigned long long ob_n[MAXPARTS];  // partitioned runs: spawns routed to each other partition this iteration
 };
 
@@ -77,7 +78,9 @@ struct Params {
     float serr_f;                          // relative error bound of the float single-excitation element
     double d53_d;                          // (double)d53, exact
     int period;
-    int sweep_grid;                        // blocks of k_sweep (number of partial sums)
+    int sweep_grid;                        // blocks of k_sweep
+    long long tiles_cap;                   // partial[0, tiles_cap): the Eq. 2 numerator of each sweep tile;
+                                           // partial[tiles_cap, + kTileSums): their fixed-order range sums
     int idx_stride;                        // 64-bit words per index entry
     long long target;
     // read-only tables

@@ -17,6 +17,7 @@
 namespace fq {
 
 constexpr int kTile = 256;          // determinants per sweep tile = threads per sweep block
+constexpr int kTileSums = 32;       // range sums of the per-tile numerators (blocks of k_tile_sum)
 #ifndef FQ_SWEEP_MIN_BLOCKS
 #define FQ_SWEEP_MIN_BLOCKS 4          // resident sweep blocks per SM the register budget is sized for
 #endif
@@ -1090,13 +1091,20 @@ __global__ void __launch_bounds__(kTile, FQ_SWEEP_MIN_BLOCKS) k_sweep(Params P) 
     unsigned long long acc[NCNT + 4];  // counters, then nw, nd, d_nw, d_nd
 #pragma unroll
     for (int k = 0; k < NCNT + 4; ++k) acc[k] = 0;
-    double num = 0.0;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     SpawnQueue<W> &sq = reinterpret_cast<SpawnQueue<W> *>(s_queue)[warp];
     if (lane == 0) sq.n = 0;
     __syncwarp();
 
-    for (long long tb = (long long)blockIdx.x * kTile; tb < len; tb += (long long)gridDim.x * kTile) {
+    // tiles are handed out dynamically (one atomic per tile): per-tile costs vary with the populations, and a
+    // static assignment left the blocks' last tiles as a tail
+    __shared__ long long s_tile;
+    for (;;) {
+        if (tid == 0) s_tile = (long long)atomicAdd(&st->sweep_next, 1ull) * kTile;
+        __syncthreads();
+        const long long tb = s_tile;
+        if (tb >= len) break;
+        double num = 0.0;  // this tile's share of the Eq. 2 numerator
         const long long s = tb + tid;
         unsigned att = 0;
         if (s < len) {
@@ -1200,6 +1208,10 @@ __global__ void __launch_bounds__(kTile, FQ_SWEEP_MIN_BLOCKS) k_sweep(Params P) 
             spawn_attempt<W, false, MODE>(P, T, s_dv[lo], nullptr, s_rcpf, act, k - s_off[lo], iter, acc, sq);
             flush_queue<W>(P, sq, false, T.map1);
         }
+        // the tile's numerator, summed in a fixed order, so the run's total does not depend on which block
+        // took which tile
+        const double bs = block_sum_f64<kTile>(num, s_redf);
+        if (tid == 0 && FQ_CHECK(tb / kTile < P.tiles_cap, P.st)) P.partial[tb / kTile] = bs;
         __syncthreads();
     }
     flush_queue<W>(P, sq, true, T.map1);
@@ -1207,8 +1219,6 @@ __global__ void __launch_bounds__(kTile, FQ_SWEEP_MIN_BLOCKS) k_sweep(Params P) 
                                                &st->cnt[5], &st->cnt[6], &st->cnt[7], &st->cnt[8], &st->cnt[9],
                                                &st->nw_in, &st->nd_in, &st->d_nw, &st->d_nd};
     flush_counters<kTile, NCNT + 4>(acc, dst, s_red);
-    double bs = block_sum_f64<kTile>(num, s_redf);
-    if (threadIdx.x == 0) P.partial[blockIdx.x] = bs;
 }
 
 // Attempts of heavily populated determinants, split into chunks of kChunk attempts: each warp takes a
