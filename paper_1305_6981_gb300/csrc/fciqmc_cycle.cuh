@@ -264,6 +264,7 @@ __device__ __forceinline__ void commit_list(DevState *st, long long nd_out, long
     st->d_nw = st->d_nd = 0;
     st->n_new = 0;
     st->sweep_next = 0;
+    st->heavy_next = 0;
     for (int k = 0; k < NCNT; ++k) st->cnt[k] = 0;
     for (int k = 0; k < MAXPARTS; ++k) st->ob_n[k] = 0;
 }

@@ -53,6 +53,7 @@ struct DevState {
     int check_bad;             // set by the check of a list being loaded
     unsigned long long n_new;  // determinants placed in new slots this iteration (diagonal elements pending)
     unsigned long long sweep_next;  // next sweep tile to hand out (tiles are taken dynamically by the blocks)
+    unsigned long long heavy_next;  // next batch of heavy chunks to hand out (taken dynamically by the warps)
     unsigned long long ob_n[MAXPARTS];  // partitioned runs: spawns routed to each other partition this iteration
 };
 

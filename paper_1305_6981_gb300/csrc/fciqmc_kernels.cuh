@@ -29,6 +29,7 @@ constexpr int kHeavy = FQ_HEAVY_THRESHOLD;  // |C_i| above this: attempts go to 
 #define FQ_HEAVY_CHUNK 512
 #endif
 constexpr int kChunk = FQ_HEAVY_CHUNK;  // attempts per heavy chunk (one warp task; 512 measured against 128 to 2048)
+constexpr int kChunkBatch = 4;          // consecutive chunks a warp takes at a time (handed out dynamically)
 constexpr unsigned long long kSaltMerge = 0x5851F42D4C957F2Dull;
 constexpr unsigned long long kSaltIndex = 0x14057B7EF767814Full;
 constexpr unsigned long long kFlagUnit = 1ull << 40;  // merge payload: (#initiator spawns << 40) + amount
@@ -1221,9 +1222,9 @@ __global__ void __launch_bounds__(kTile, FQ_SWEEP_MIN_BLOCKS) k_sweep(Params P) 
     flush_counters<kTile, NCNT + 4>(acc, dst, s_red);
 }
 
-// Attempts of heavily populated determinants, split into chunks of kChunk attempts: each warp takes a
-// contiguous range of chunks (so it meets few determinants) and builds a determinant's tables once
-// when it reaches it.
+// Attempts of heavily populated determinants, split into chunks of kChunk attempts: warps take batches of
+// kChunkBatch consecutive chunks from a counter (so a warp meets few determinants) and build a
+// determinant's tables once when they reach it.
 template <int W, int MODE>
 __global__ void __launch_bounds__(kTile, 4) k_heavy(Params P) {
     DevState *st = P.st;
@@ -1247,19 +1248,29 @@ __global__ void __launch_bounds__(kTile, 4) k_heavy(Params P) {
     for (int k = 0; k < NCNT; ++k) cnt[k] = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const unsigned long long gw = (unsigned long long)blockIdx.x * NW + warp;
-    const unsigned long long nwarps = (unsigned long long)gridDim.x * NW;
-    const unsigned long long q0 = nch * gw / nwarps, q1 = nch * (gw + 1) / nwarps;
     long long cur = -1;
     DetView<W> &v = s_v[warp];
     HeavyTab &tab = s_tab[warp];
     SpawnQueue<W> &sq = reinterpret_cast<SpawnQueue<W> *>(s_queue)[warp];
     if (lane == 0) sq.n = 0;
     __syncwarp();
-    for (unsigned long long q = q0; q < q1; ++q) {
-        // record holding chunk q: last record whose first chunk is <= q
+    // warps take kChunkBatch consecutive chunks at a time from a counter: consecutive chunks mostly belong to
+    // one determinant, so a warp still builds few tables, and no warp is left with a tail of work
+    unsigned long long q = 0, qend = 0;
+    for (;;) {
+        bool fresh = false;
+        if (q >= qend) {
+            unsigned long long b = 0;
+            if (lane == 0) b = atomicAdd(&st->heavy_next, (unsigned long long)kChunkBatch);
+            b = __shfl_sync(0xFFFFFFFFu, b, 0);
+            if (b >= nch) break;
+            q = b;
+            qend = min(b + (unsigned long long)kChunkBatch, nch);
+            fresh = true;
+        }
+        // record holding chunk q: last record whose first chunk is <= q (searched at the start of a batch)
         long long r;
-        if (cur < 0) {
+        if (cur < 0 || fresh) {
             long long lo = 0, hi = nh - 1;
             while (lo < hi) {
                 const long long mid = (lo + hi + 1) >> 1;
@@ -1287,6 +1298,7 @@ __global__ void __launch_bounds__(kTile, 4) k_heavy(Params P) {
             flush_queue<W>(P, sq, false, T.map1);
         }
         __syncwarp();
+        ++q;
     }
     flush_queue<W>(P, sq, true, T.map1);
     unsigned long long *const dst[NCNT] = {&st->cnt[0], &st->cnt[1], &st->cnt[2], &st->cnt[3], &st->cnt[4],
