@@ -29,7 +29,10 @@ constexpr int kHeavy = FQ_HEAVY_THRESHOLD;  // |C_i| above this: attempts go to 
 #define FQ_HEAVY_CHUNK 512
 #endif
 constexpr int kChunk = FQ_HEAVY_CHUNK;  // attempts per heavy chunk (one warp task; 512 measured against 128 to 2048)
-constexpr int kChunkBatch = 4;          // consecutive chunks a warp takes at a time (handed out dynamically)
+#ifndef FQ_CHUNK_BATCH
+#define FQ_CHUNK_BATCH 4
+#endif
+constexpr int kChunkBatch = FQ_CHUNK_BATCH;  // consecutive chunks a warp takes at a time (handed out dynamically)
 constexpr unsigned long long kSaltMerge = 0x5851F42D4C957F2Dull;
 constexpr unsigned long long kSaltIndex = 0x14057B7EF767814Full;
 constexpr unsigned long long kFlagUnit = 1ull << 40;  // merge payload: (#initiator spawns << 40) + amount
