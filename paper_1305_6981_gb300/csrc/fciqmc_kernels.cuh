@@ -30,9 +30,9 @@ constexpr int kHeavy = FQ_HEAVY_THRESHOLD;  // |C_i| above this: attempts go to 
 #endif
 constexpr int kChunk = FQ_HEAVY_CHUNK;  // attempts per heavy chunk (one warp task; 512 measured against 128 to 2048)
 #ifndef FQ_CHUNK_BATCH
-#define FQ_CHUNK_BATCH 4
+#define FQ_CHUNK_BATCH 32
 #endif
-constexpr int kChunkBatch = FQ_CHUNK_BATCH;  // consecutive chunks a warp takes at a time (handed out dynamically)
+constexpr int kChunkBatch = FQ_CHUNK_BATCH;  // most consecutive chunks a warp takes at a time (guided, see k_heavy)
 constexpr unsigned long long kSaltMerge = 0x5851F42D4C957F2Dull;
 constexpr unsigned long long kSaltIndex = 0x14057B7EF767814Full;
 constexpr unsigned long long kFlagUnit = 1ull << 40;  // merge payload: (#initiator spawns << 40) + amount
@@ -1226,8 +1226,8 @@ __global__ void __launch_bounds__(kTile, FQ_SWEEP_MIN_BLOCKS) k_sweep(Params P) 
 }
 
 // Attempts of heavily populated determinants, split into chunks of kChunk attempts: warps take batches of
-// kChunkBatch consecutive chunks from a counter (so a warp meets few determinants) and build a
-// determinant's tables once when they reach it.
+// consecutive chunks from a counter (guided: a share of what is left, at most kChunkBatch), so a warp meets
+// few determinants, and build a determinant's tables once when they reach it.
 template <int W, int MODE>
 __global__ void __launch_bounds__(kTile, 4) k_heavy(Params P) {
     DevState *st = P.st;
@@ -1257,18 +1257,24 @@ __global__ void __launch_bounds__(kTile, 4) k_heavy(Params P) {
     SpawnQueue<W> &sq = reinterpret_cast<SpawnQueue<W> *>(s_queue)[warp];
     if (lane == 0) sq.n = 0;
     __syncwarp();
-    // warps take kChunkBatch consecutive chunks at a time from a counter: consecutive chunks mostly belong to
-    // one determinant, so a warp still builds few tables, and no warp is left with a tail of work
+    // warps take batches of consecutive chunks from a counter: consecutive chunks mostly belong to one
+    // determinant, so a warp still builds few tables, and no warp is left with a tail of work
     unsigned long long q = 0, qend = 0;
     for (;;) {
         bool fresh = false;
         if (q >= qend) {
+            // guided self-scheduling: a share of what is left, so batches are long while much is left (few
+            // determinant switches) and single chunks at the end (no tail)
+            const unsigned long long taken = *(volatile unsigned long long *)&st->heavy_next;
+            const unsigned long long nwarps = (unsigned long long)gridDim.x * NW;
+            const unsigned long long size =
+                taken >= nch ? 1ull : max(1ull, min((unsigned long long)kChunkBatch, (nch - taken) / (2ull * nwarps)));
             unsigned long long b = 0;
-            if (lane == 0) b = atomicAdd(&st->heavy_next, (unsigned long long)kChunkBatch);
+            if (lane == 0) b = atomicAdd(&st->heavy_next, size);
             b = __shfl_sync(0xFFFFFFFFu, b, 0);
             if (b >= nch) break;
             q = b;
-            qend = min(b + (unsigned long long)kChunkBatch, nch);
+            qend = min(b + size, nch);
             fresh = true;
         }
         // record holding chunk q: last record whose first chunk is <= q (searched at the start of a batch)
