@@ -269,7 +269,9 @@ int fciqmc_get_walkers(fciqmc_handle *h, uint64_t *dets, int32_t *pops, double *
  * not by history). dets: n x W words (host); pops: n nonzero populations;
  * hdiag: H_ii - E0 per determinant as returned by fciqmc_get_walkers, or NULL
  * to compute it. Determinants must be distinct and carry the run's electron
- * count. Clears the history and the device status. */
+ * count. Clears the history and the device status. A rejected list (an
+ * invalid entry or a repeated determinant: FCIQMC_ERR_INVALID_ARG) leaves the
+ * run as it was. */
 int fciqmc_set_walkers(fciqmc_handle *h, const uint64_t *dets, const int32_t *pops, const double *hdiag,
                        int64_t n, const fciqmc_state *st);
 

@@ -189,6 +189,8 @@ struct fciqmc_handle {
     fciqmc_options opt;      // as created (checked when partitions are grouped)
     double tau;
     int32_t init_thr;
+    cudaStream_t aux;        // helper stream of set_walkers (created on first use), joined by events
+    cudaEvent_t ev_fork, ev_join, ev_chunk[8];
 };
 
 namespace {
@@ -298,9 +300,12 @@ void launch_prepare(fciqmc_handle *h, int b, long long n, int compute) {
     fq::k_prepare_list<W><<<(unsigned)blocks, 256, h->smem_w, h->stream>>>(h->P, b, n, compute);
 }
 
-// Loads a list into buffer b (validated on the device); on success makes it the active list with the
-// state st0: the old list's index entries are emptied (located first, or the whole index after a
-// failed step or for a dense index), the new keys inserted.
+// Loads a list into buffer b; on success makes it the active list with the state st0. The index work
+// runs on a helper stream while the list is copied in: the old list's entries are emptied (located first,
+// or the whole index for a dense index or after a failed step), then each chunk of new keys is inserted as
+// soon as it has arrived. The check of the new entries (and the float copies of given diagonal elements)
+// runs on the caller's stream. A rejected list (invalid entries, a repeated determinant) leaves the run as
+// it was: the index is rebuilt from the current list and the state is not replaced.
 template <int W>
 int load_list(fciqmc_handle *h, const DevState &cur, DevState &st0, const uint64_t *dets, const int32_t *pops,
               const double *hdiag, long long n) {
@@ -308,32 +313,60 @@ int load_list(fciqmc_handle *h, const DevState &cur, DevState &st0, const uint64
     const Params &P = h->P;
     const int b = cur.lb ^ 1;
     const unsigned blocks = (unsigned)std::max<long long>(1, std::min<long long>((n + 255) / 256, h->small_grid));
+    const bool sparse = cur.status == 0 && cur.list_len >= 0 && cur.list_len * 16 <= h->z.idx_cap &&
+                        h->z.idx_cap <= (1LL << 31);  // positions held as int
+    int *pos = P.pop[cur.lb][cur.pp ^ 1];  // the old list's idle population buffer
+    const unsigned ob = (unsigned)std::max<long long>(1, std::min<long long>((cur.list_len + 255) / 256, h->small_grid));
+    if (!h->aux) {
+        FQ_CUDA(cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking));
+        FQ_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+        FQ_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+        for (cudaEvent_t &e : h->ev_chunk) FQ_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    cudaStream_t a = h->aux;
+    FQ_CUDA(cudaMemsetAsync(&P.st->check_bad, 0, sizeof(int), s));
+    FQ_CUDA(cudaEventRecord(h->ev_fork, s));
+    FQ_CUDA(cudaStreamWaitEvent(a, h->ev_fork, 0));
+    if (sparse && cur.list_len > 0) {
+        fq::k_index_locate<W><<<ob, 256, 0, a>>>(P, cur.lb, cur.list_len, pos);
+        fq::k_index_clear_at<W><<<ob, 256, 0, a>>>(P, pos, cur.list_len);
+    } else if (!sparse) {
+        fq::k_index_clear<<<h->small_grid, 256, 0, a>>>(P, 1);
+    }
+    const int nchunk = (int)std::min<long long>(8, std::max<long long>(1, n >> 20));  // >= 2^20 keys a chunk
+    for (int k = 0; k < nchunk; ++k) {
+        const long long lo = n * k / nchunk, hi = n * (k + 1) / nchunk;
+        if (hi > lo) {
+            FQ_CUDA(cudaMemcpyAsync(P.det[b] + W * lo, dets + W * lo, sizeof(uint64_t) * W * (hi - lo),
+                                    cudaMemcpyHostToDevice, s));
+            FQ_CUDA(cudaEventRecord(h->ev_chunk[k], s));
+            FQ_CUDA(cudaStreamWaitEvent(a, h->ev_chunk[k], 0));
+            const unsigned ib = (unsigned)std::max<long long>(1, std::min<long long>((hi - lo + 255) / 256, h->small_grid));
+            fq::k_index_insert<W><<<ib, 256, 0, a>>>(P, b, lo, hi);
+        }
+    }
+    FQ_CUDA(cudaGetLastError());
+    FQ_CUDA(cudaEventRecord(h->ev_join, a));
     if (n > 0) {
-        FQ_CUDA(cudaMemcpyAsync(P.det[b], dets, sizeof(uint64_t) * W * n, cudaMemcpyHostToDevice, s));
         FQ_CUDA(cudaMemcpyAsync(P.pop[b][0], pops, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
         if (hdiag) FQ_CUDA(cudaMemcpyAsync(P.hd[b], hdiag, sizeof(double) * n, cudaMemcpyHostToDevice, s));
     }
-    FQ_CUDA(cudaMemsetAsync(&P.st->check_bad, 0, sizeof(int), s));
-    fq::k_check_list<W><<<blocks, 256, 0, s>>>(P, b, n);
+    fq::k_check_list<W><<<blocks, 256, 0, s>>>(P, b, n, hdiag ? 1 : 0);
+    FQ_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
     int bad = 0;
     FQ_CUDA(cudaMemcpyAsync(&bad, &P.st->check_bad, sizeof(int), cudaMemcpyDeviceToHost, s));
     FQ_CUDA(cudaStreamSynchronize(s));
-    if (bad) return FCIQMC_ERR_INVALID_ARG;  // the active list and the index are untouched
+    if (bad) {  // the current list's index back as it was (keys to slots), the state untouched
+        fq::k_index_clear<<<h->small_grid, 256, 0, s>>>(P, 1);
+        fq::k_index_fill<W><<<h->small_grid, 256, 0, s>>>(P, 1);
+        FQ_CUDA(cudaGetLastError());
+        FQ_CUDA(cudaStreamSynchronize(s));
+        return bad == 3 ? FCIQMC_ERR_CAPACITY : FCIQMC_ERR_INVALID_ARG;
+    }
     st0.lb = b;
     st0.pp = 0;
     FQ_CUDA(cudaMemcpyAsync(P.st, &st0, sizeof(st0), cudaMemcpyHostToDevice, s));
-    const bool sparse = cur.status == 0 && cur.list_len >= 0 && cur.list_len * 16 <= h->z.idx_cap &&
-                        h->z.idx_cap <= (1LL << 31);  // positions held as int
-    if (sparse && cur.list_len > 0) {
-        const unsigned ob = (unsigned)std::max<long long>(1, std::min<long long>((cur.list_len + 255) / 256, h->small_grid));
-        int *pos = P.pop[cur.lb][cur.pp ^ 1];  // the old list's idle population buffer
-        fq::k_index_locate<W><<<ob, 256, 0, s>>>(P, cur.lb, cur.list_len, pos);
-        fq::k_index_clear_at<W><<<ob, 256, 0, s>>>(P, pos, cur.list_len);
-    } else if (!sparse) {
-        fq::k_index_clear<<<h->small_grid, 256, 0, s>>>(P, 1);
-    }
-    launch_prepare<W>(h, b, n, hdiag ? 0 : 1);
-    fq::k_index_fill<W><<<h->small_grid, 256, 0, s>>>(P, 1);
+    if (!hdiag) launch_prepare<W>(h, b, n, 1);
     // a failed step may have left claimed entries in the spawn table
     if (cur.status != 0) fq::k_mt_clear<<<h->small_grid, 256, 0, s>>>(P, W);
     FQ_CUDA(cudaGetLastError());
@@ -944,6 +977,13 @@ int fciqmc_get_info(const fciqmc_handle *h, fciqmc_info *info) {
 void fciqmc_destroy(fciqmc_handle *h) {
     if (!h) return;
     cudaStreamSynchronize(h->stream);
+    if (h->aux) {
+        cudaStreamSynchronize(h->aux);
+        cudaStreamDestroy(h->aux);
+        cudaEventDestroy(h->ev_fork);
+        cudaEventDestroy(h->ev_join);
+        for (cudaEvent_t e : h->ev_chunk) cudaEventDestroy(e);
+    }
     if (h->graph_ready) cudaGraphExecDestroy(h->graph);
     if (h->graph_tmpl) cudaGraphDestroy(h->graph_tmpl);
     delete h;

@@ -426,11 +426,11 @@ __device__ __forceinline__ bool sparse_index_clear(const Params &P, const DevSta
     return st->list_len * 16 <= P.idx_cap && P.idx_cap <= (1LL << 31);
 }
 
-// Empties the whole index: forced (a rebuild), or for a due compaction whose list is too long for the
-// sparse clear below.
+// Empties the whole index: forced (a rebuild, whatever the run's status), or for a due compaction whose
+// list is too long for the sparse clear below.
 __global__ void k_index_clear(Params P, int force) {
     DevState *st = P.st;
-    if (st->status || (!force && (!st->compact_pending || sparse_index_clear(P, st)))) return;
+    if (!force && (st->status || !st->compact_pending || sparse_index_clear(P, st))) return;
     const long long nwords = P.idx_cap * (P.idx_stride);
     ulonglong2 *p = reinterpret_cast<ulonglong2 *>(P.idx);
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < nwords / 2; k += (long long)gridDim.x * blockDim.x)
@@ -482,12 +482,13 @@ __global__ void k_index_clear_old(Params P) {
     }
 }
 
-// Inserts slots [0, n) of a list buffer into the (cleared) index. force: rebuild the active list
-// (after set_walkers); otherwise the compacted list in the other buffer.
+// Inserts slots [0, n) of a list buffer into the (cleared) index. force: rebuild the active list (at
+// creation, or restoring it after a rejected set_walkers), whatever the run's status; otherwise the
+// compacted list in the other buffer.
 template <int W>
 __global__ void k_index_fill(Params P, int force) {
     DevState *st = P.st;
-    if (st->status || (!force && !st->compact_pending)) return;
+    if (!force && (st->status || !st->compact_pending)) return;
     constexpr int S = Stride<W>::v;
     const int buf = force ? st->lb : (st->lb ^ 1);
     const long long n = force ? st->list_len : (long long)st->new_len;
@@ -510,6 +511,33 @@ __global__ void k_index_fill(Params P, int force) {
             h = (h + 1ull) & imask;
         }
         if (!done) set_status(st, FCIQMC_ERR_CAPACITY);
+    }
+}
+
+// Inserts slots [lo, hi) of list buffer b (a list being loaded) into the index, the old list's entries
+// already emptied: a key already present (a repeated determinant) sets check_bad to 2, a full table to 3.
+template <int W>
+__global__ void k_index_insert(Params P, int b, long long lo, long long hi) {
+    constexpr int S = Stride<W>::v;
+    const unsigned long long imask = (unsigned long long)P.idx_cap - 1ull;
+    for (long long s = lo + (long long)blockIdx.x * blockDim.x + threadIdx.x; s < hi; s += (long long)gridDim.x * blockDim.x) {
+        unsigned long long key[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) key[w] = P.det[b][s * W + w];
+        unsigned long long h = table_hash<W>(key, kSaltIndex) >> (64 - P.idx_bits);
+        bool done = false;
+        for (long long probe = 0; probe < P.idx_cap; ++probe) {
+            unsigned long long *x = P.idx + h * S;
+            bool claimed;
+            if (claim_key<W>(x, key, claimed)) {
+                if (!claimed) atomicExch(&P.st->check_bad, 2);
+                else x[W] = (unsigned long long)s;
+                done = true;
+                break;
+            }
+            h = (h + 1ull) & imask;
+        }
+        if (!done) atomicExch(&P.st->check_bad, 3);
     }
 }
 
@@ -598,9 +626,10 @@ __global__ void k_gather(Params P) {
 
 // Checks slots [0, n) of list buffer b as loaded: n_elec occupied spin orbitals, none at or above n_so,
 // inside the permitted space, owned by this partition, population neither 0 nor INT32_MIN. A failure sets
-// st->check_bad.
+// st->check_bad. With convert, also the nearest float of each given diagonal element (the buffer is not
+// the active one, so a failed check leaves nothing of the run changed).
 template <int W>
-__global__ void k_check_list(Params P, int b, long long n) {
+__global__ void k_check_list(Params P, int b, long long n, int convert) {
     for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
         int cnt = 0;
         bool ok = true;
@@ -627,6 +656,7 @@ __global__ void k_check_list(Params P, int b, long long n) {
             ok = false;  // a determinant of another partition
         const int c = P.pop[b][0][s];
         if (!ok || cnt != P.n_elec || c == 0 || c == (-2147483647 - 1)) atomicExch(&P.st->check_bad, 1);
+        if (convert) P.hdf[b][s] = __double2float_rn(P.hd[b][s]);
     }
 }
 

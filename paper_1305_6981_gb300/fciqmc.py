@@ -166,7 +166,7 @@ class Fciqmc:
             hd_ptr = _ptr(hd, ctypes.c_double)
         st = None
         if iteration is not None:
-            cur = self.state()
+            cur = self.state() if shift is None or vary is None else {}
             st = State(int(iteration), float(cur["shift"] if shift is None else shift),
                        int(cur["vary_shift"] if vary is None else vary), int(shift_counter), int(nw_last_update))
         rc = self._L.fciqmc_set_walkers(self.handle, _ptr(dets, ctypes.c_uint64), _ptr(pops, ctypes.c_int32),

@@ -3,7 +3,8 @@ tau 0.001) grown on the GPU and settled to the steady state the benchmark times 
 determinants), in its launch configuration (its workload table: 2e8-slot main list, 2^27-entry spawn table). From the grown list, one iteration
 on the GPU and one in the oracle: diagonal elements of the loaded list bit-identical, walker lists
 identical, every integer counter identical, the shift bit-identical, the projected-energy numerator within
-1e-11 relative. The oracle's iteration takes a minute or two on the host cores. The same for the
+1e-11 relative; the list loaded back through set_walkers gives the same iteration again. The oracle's
+iteration takes a minute or two on the host cores. The same for the
 active-space and spin-coupled workloads at 1e7 target walkers."""
 from __future__ import annotations
 
@@ -39,6 +40,15 @@ def one_iteration(workload: str, target: int = 0):
     g.step(1)
     rows_g = g.history(1)
     after = g.walkers()
+    # the same list loaded back through set_walkers (the copy in chunks, each chunk's keys inserted into the
+    # index as it arrives): the same iteration again, with the same result
+    g.set_walkers(d, p, h, iteration=st["iteration"], shift=st["shift"], vary=st["vary_shift"],
+                  shift_counter=st["shift_counter"], nw_last_update=st["nw_last_update"])
+    g.step(1)
+    again = g.history(1)
+    compare_rows(again, [dict(r, iter=r["iteration"]) for r in rows_g])
+    assert again[0]["heavy_attempts"] == rows_g[0]["heavy_attempts"]
+    assert same_lists(g.walkers(), after)
     g.close()
 
     q = Oracle(wl["system"](), tau=wl["tau"], initiator_threshold=wl["thr"], target_walkers=target or wl["target"],

@@ -144,12 +144,27 @@ def test_snapshot_roundtrip_and_windows():
     g.close()
 
 
-def test_reloads_and_invalid_lists():
-    """Repeated set_walkers (the old list's index entries are located and emptied before the new keys go in):
-    after loading list A, running, and loading a different list B, both sides advance identically from B.
-    Invalid lists (wrong electron count, a bit beyond the basis, a zero population) are rejected on the
-    device and leave the current list untouched."""
+def _rejects_invalid_lists(g, dB, pB):
+    """Invalid lists (wrong electron count, a bit beyond the basis, a zero population, a repeated
+    determinant) are rejected on the device and leave the run's list as it was."""
     from paper_1305_6981_gb300._native import FciqmcError
+    before = g.walkers()
+    assert len(pB) > 8 and 2 * g.info()["n_orb"] < 64
+    wrong_count, beyond_basis, zero_pop, repeated = dB.copy(), dB.copy(), pB.copy(), dB.copy()
+    wrong_count[3, 0] ^= np.uint64(1 << 40)  # one electron more or fewer
+    beyond_basis[5, 0] |= np.uint64(1 << 63)  # spin orbital 63 of a 48-spin-orbital basis
+    zero_pop[7] = 0
+    repeated[2] = repeated[len(pB) - 1]
+    for dd, pp in ((wrong_count, pB), (beyond_basis, pB), (dB, zero_pop), (repeated, pB)):
+        with pytest.raises(FciqmcError):
+            g.set_walkers(dd, pp)
+    assert same_lists(g.walkers(), before)
+
+
+def test_reloads_and_invalid_lists():
+    """Repeated set_walkers (the old list's index entries are located and emptied one by one before the new
+    keys go in): after loading list A, running, and loading a different list B, both sides advance
+    identically from B. Rejected lists leave the run as it was: the next iterations are the oracle's."""
     s = synth.init_12e24o()
     g, q = make_pair(s, 0.005, 3, initial_population=2000, initial_shift=0.8, seed=23, main_capacity=1 << 16)
     q.iterate(40)
@@ -161,16 +176,29 @@ def test_reloads_and_invalid_lists():
     st = q.state()
     g.set_walkers(dB, pB, hB, iteration=st["iteration"], shift=st["shift"], vary=st["vary"],
                   shift_counter=st["n_since"], nw_last_update=st["nw_prev"])
-    before = g.walkers()
-    assert len(pB) > 8 and 2 * s.n_orb < 64
-    wrong_count, beyond_basis, zero_pop = dB.copy(), dB.copy(), pB.copy()
-    wrong_count[3, 0] ^= np.uint64(1 << 40)  # one electron more or fewer
-    beyond_basis[5, 0] |= np.uint64(1 << 63)  # spin orbital 63 of a 48-spin-orbital basis
-    zero_pop[7] = 0
-    for dd, pp in ((wrong_count, pB), (beyond_basis, pB), (dB, zero_pop)):
-        with pytest.raises(FciqmcError):
-            g.set_walkers(dd, pp)
-    assert same_lists(g.walkers(), before)
+    _rejects_invalid_lists(g, dB, pB)
+    rows_q = q.iterate(25)
+    g.step(25)
+    compare_rows(g.history(25), rows_q)
+    assert same_lists(g.walkers(), q.walkers())
+    g.close()
+
+
+def test_reloads_and_invalid_lists_dense_index():
+    """The same with lists long against the index (more than 1/16 of its entries), where loading empties the
+    whole index instead of the old list's entries one by one: synthetic lists of 1.9e3 and 2.6e3
+    determinants, an index of 2^13 entries."""
+    s = synth.init_12e24o()
+    g, q = make_pair(s, 0.005, 3, seed=23, main_capacity=1 << 12)
+    assert g.info()["index_capacity"] == 1 << 13
+    dA, pA = synth.walker_snapshot(s, 6000, seed=3)
+    g.set_walkers(dA, pA, iteration=10, shift=0.0, vary=0)
+    g.step(5)
+    dB, pB = synth.walker_snapshot(s, 8000, seed=4)
+    assert len(pA) * 16 > 1 << 13 and len(pB) * 16 > 1 << 13
+    g.set_walkers(dB, pB, iteration=20, shift=0.0, vary=0)
+    q.set_walkers(dB, pB, iteration=20, shift=0.0)
+    _rejects_invalid_lists(g, dB, pB)
     rows_q = q.iterate(25)
     g.step(25)
     compare_rows(g.history(25), rows_q)
