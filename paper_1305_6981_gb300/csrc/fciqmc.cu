@@ -900,25 +900,34 @@ int fciqmc_get_walkers(fciqmc_handle *h, uint64_t *dets, int32_t *pops, double *
     if (!h || !n || cap < 0 || (cap > 0 && (!dets || !pops))) return FCIQMC_ERR_INVALID_ARG;
     NvtxRange range("fciqmc_get_walkers");
     DevState *st = h->P.st;
-    FQ_CUDA(cudaMemsetAsync(&st->new_len, 0, sizeof(unsigned long long), h->stream));
-    if (h->z.W == 1) fq::k_gather<1><<<h->small_grid, 256, 0, h->stream>>>(h->P);
-    else fq::k_gather<2><<<h->small_grid, 256, 0, h->stream>>>(h->P);
-    FQ_CUDA(cudaGetLastError());
-    DevState s;
-    int rc = read_state(h, s);
+    const Params &P = h->P;
+    DevState s0;
+    int rc = read_state(h, s0);
     if (rc != FCIQMC_OK) return rc;
-    const long long cnt = (long long)s.new_len;
+    // the occupied entries gathered into the idle list buffer, then copied out (a gather writing page-locked
+    // host memory itself was slower than the copy engines)
+    const int other = s0.lb ^ 1;
+    unsigned long long *od = P.det[other];
+    int *op = P.pop[other][s0.pp];
+    double *oh = P.hd[other];
+    FQ_CUDA(cudaMemsetAsync(&st->new_len, 0, sizeof(unsigned long long), h->stream));
+    if (h->z.W == 1) fq::k_gather<1><<<h->small_grid, 256, 0, h->stream>>>(P, od, op, oh, h->z.cap);
+    else fq::k_gather<2><<<h->small_grid, 256, 0, h->stream>>>(P, od, op, oh, h->z.cap);
+    FQ_CUDA(cudaGetLastError());
+    unsigned long long cnt_u = 0;
+    FQ_CUDA(cudaMemcpyAsync(&cnt_u, &st->new_len, sizeof(cnt_u), cudaMemcpyDeviceToHost, h->stream));
+    FQ_CUDA(cudaStreamSynchronize(h->stream));
+    const long long cnt = (long long)cnt_u;
     *n = cnt;
     if (cnt > cap) {
         FQ_CUDA(cudaMemsetAsync(&st->new_len, 0, sizeof(unsigned long long), h->stream));
         FQ_CUDA(cudaStreamSynchronize(h->stream));
         return FCIQMC_ERR_CAPACITY;
     }
-    const int other = s.lb ^ 1;
     if (cnt > 0) {
-        FQ_CUDA(cudaMemcpyAsync(dets, h->P.det[other], sizeof(uint64_t) * h->z.W * cnt, cudaMemcpyDeviceToHost, h->stream));
-        FQ_CUDA(cudaMemcpyAsync(pops, h->P.pop[other][s.pp], sizeof(int32_t) * cnt, cudaMemcpyDeviceToHost, h->stream));
-        if (hdiag) FQ_CUDA(cudaMemcpyAsync(hdiag, h->P.hd[other], sizeof(double) * cnt, cudaMemcpyDeviceToHost, h->stream));
+        FQ_CUDA(cudaMemcpyAsync(dets, od, sizeof(uint64_t) * h->z.W * cnt, cudaMemcpyDeviceToHost, h->stream));
+        FQ_CUDA(cudaMemcpyAsync(pops, op, sizeof(int32_t) * cnt, cudaMemcpyDeviceToHost, h->stream));
+        if (hdiag) FQ_CUDA(cudaMemcpyAsync(hdiag, oh, sizeof(double) * cnt, cudaMemcpyDeviceToHost, h->stream));
     }
     FQ_CUDA(cudaMemsetAsync(&st->new_len, 0, sizeof(unsigned long long), h->stream));
     FQ_CUDA(cudaStreamSynchronize(h->stream));

@@ -605,9 +605,10 @@ __global__ void k_estimate_finish(Params P, int nblocks) {
     P.st->est_num = num;
 }
 
-// Copies the occupied entries of the active list to the other buffer (for read-back), count in new_len.
+// Copies the occupied entries of the active list to od / op / oh (oh may be null; the idle list buffer for
+// a read-back), count in new_len; entries past cap are counted but not written.
 template <int W>
-__global__ void k_gather(Params P) {
+__global__ void k_gather(Params P, unsigned long long *od, int *op, double *oh, long long cap) {
     DevState *st = P.st;
     const int lb = st->lb, pp = st->pp;
     const long long len = st->list_len;
@@ -615,11 +616,11 @@ __global__ void k_gather(Params P) {
         const long long s = s0 + threadIdx.x;
         int c = s < len ? P.pop[lb][pp][s] : 0;
         const long long ns = warp_append(&st->new_len, c != 0);
-        if (c != 0) {
+        if (c != 0 && ns < cap) {
 #pragma unroll
-            for (int w = 0; w < W; ++w) P.det[lb ^ 1][ns * W + w] = P.det[lb][s * W + w];
-            P.hd[lb ^ 1][ns] = P.hd[lb][s];
-            P.pop[lb ^ 1][pp][ns] = c;
+            for (int w = 0; w < W; ++w) od[ns * W + w] = P.det[lb][s * W + w];
+            if (oh) oh[ns] = P.hd[lb][s];
+            op[ns] = c;
         }
     }
 }

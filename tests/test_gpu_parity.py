@@ -206,6 +206,38 @@ def test_reloads_and_invalid_lists_dense_index():
     g.close()
 
 
+def test_read_back_into_pinned_host_arrays():
+    """get_walkers into page-locked host arrays (the benchmark's host-buffer path) gives the list read into
+    pageable arrays, with or without the diagonal elements; arrays too small for the list give CAPACITY."""
+    from paper_1305_6981_gb300._native import FciqmcError
+    s = synth.init_12e24o()
+    g, q = make_pair(s, 0.005, 3, seed=29, main_capacity=1 << 14)
+    d0, p0 = synth.walker_snapshot(s, 8000, seed=4)
+    g.set_walkers(d0, p0, iteration=5, shift=0.2, vary=0)
+    q.set_walkers(d0, p0, iteration=5, shift=0.2)
+    g.step(10)
+    q.iterate(10)
+    d, p, h = g.walkers()
+    n = len(p)
+    assert n > 1000
+    W = d.shape[1]
+    pd = torch.empty((n + 7, W), dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
+    pp = torch.empty(n + 7, dtype=torch.int32, pin_memory=True).numpy()
+    ph = torch.empty(n + 7, dtype=torch.float64, pin_memory=True).numpy()
+    assert g.walkers_into(pd, pp, ph) == n
+    a, b = canonical(pd[:n], pp[:n], ph[:n]), canonical(d, p, h)
+    assert all(np.array_equal(x, y) for x, y in zip(a, b))
+    assert same_lists((pd[:n], pp[:n]), q.walkers())
+    pp[:] = 0
+    assert g.walkers_into(pd, pp) == n
+    assert same_lists((pd[:n], pp[:n]), (d, p))
+    with pytest.raises(FciqmcError) as err:
+        g.walkers_into(pd[: n - 1], pp[: n - 1], ph[: n - 1])
+    assert err.value.status == -2
+    assert same_lists(g.walkers(), (d, p))  # reading changes nothing
+    g.close()
+
+
 def test_duplicate_determinants_rejected():
     from paper_1305_6981_gb300._native import FciqmcError
     s = synth.tiny_8e8o()
