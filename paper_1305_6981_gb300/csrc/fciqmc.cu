@@ -300,16 +300,12 @@ void launch_prepare(fciqmc_handle *h, int b, long long n, int compute) {
     fq::k_prepare_list<W><<<(unsigned)blocks, 256, h->smem_w, h->stream>>>(h->P, b, n, compute);
 }
 
-// Loads a list into buffer b; on success makes it the active list with the state st0. The index work
-// runs on a helper stream while the list is copied in: the old list's entries are emptied (located first,
-// or the whole index for a dense index or after a failed step), then each chunk of new keys is inserted as
-// soon as it has arrived. The check of the new entries (and the float copies of given diagonal elements)
-// runs on the caller's stream. A rejected list (invalid entries, a repeated determinant) leaves the run as
-// it was: the index is rebuilt from the current list and the state is not replaced.
+// Copy, check and index work of load_list, up to the join of the helper stream; bad receives the verdict
+// of the check and of the inserts (1 invalid entry, 2 repeated determinant, 3 index full).
 template <int W>
-int load_list(fciqmc_handle *h, const DevState &cur, DevState &st0, const uint64_t *dets, const int32_t *pops,
-              const double *hdiag, long long n) {
-    cudaStream_t s = h->stream;
+int load_stage(fciqmc_handle *h, const DevState &cur, const uint64_t *dets, const int32_t *pops,
+               const double *hdiag, long long n, int &bad) {
+    cudaStream_t s = h->stream, a = h->aux;
     const Params &P = h->P;
     const int b = cur.lb ^ 1;
     const unsigned blocks = (unsigned)std::max<long long>(1, std::min<long long>((n + 255) / 256, h->small_grid));
@@ -317,13 +313,6 @@ int load_list(fciqmc_handle *h, const DevState &cur, DevState &st0, const uint64
                         h->z.idx_cap <= (1LL << 31);  // positions held as int
     int *pos = P.pop[cur.lb][cur.pp ^ 1];  // the old list's idle population buffer
     const unsigned ob = (unsigned)std::max<long long>(1, std::min<long long>((cur.list_len + 255) / 256, h->small_grid));
-    if (!h->aux) {
-        FQ_CUDA(cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking));
-        FQ_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
-        FQ_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
-        for (cudaEvent_t &e : h->ev_chunk) FQ_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-    }
-    cudaStream_t a = h->aux;
     FQ_CUDA(cudaMemsetAsync(&P.st->check_bad, 0, sizeof(int), s));
     FQ_CUDA(cudaEventRecord(h->ev_fork, s));
     FQ_CUDA(cudaStreamWaitEvent(a, h->ev_fork, 0));
@@ -352,17 +341,43 @@ int load_list(fciqmc_handle *h, const DevState &cur, DevState &st0, const uint64
         if (hdiag) FQ_CUDA(cudaMemcpyAsync(P.hd[b], hdiag, sizeof(double) * n, cudaMemcpyHostToDevice, s));
     }
     fq::k_check_list<W><<<blocks, 256, 0, s>>>(P, b, n, hdiag ? 1 : 0);
+    FQ_CUDA(cudaGetLastError());
     FQ_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
-    int bad = 0;
     FQ_CUDA(cudaMemcpyAsync(&bad, &P.st->check_bad, sizeof(int), cudaMemcpyDeviceToHost, s));
     FQ_CUDA(cudaStreamSynchronize(s));
-    if (bad) {  // the current list's index back as it was (keys to slots), the state untouched
+    return FCIQMC_OK;
+}
+
+// Loads a list into buffer b; on success makes it the active list with the state st0. The index work
+// runs on a helper stream while the list is copied in: the old list's entries are emptied (located first,
+// or the whole index for a dense index or after a failed step), then each chunk of new keys is inserted as
+// soon as it has arrived. The check of the new entries (and the float copies of given diagonal elements)
+// runs on the caller's stream. A rejected list (invalid entries, a repeated determinant) or a failed copy
+// leaves the run as it was: the index is rebuilt from the current list and the state is not replaced.
+template <int W>
+int load_list(fciqmc_handle *h, const DevState &cur, DevState &st0, const uint64_t *dets, const int32_t *pops,
+              const double *hdiag, long long n) {
+    cudaStream_t s = h->stream;
+    const Params &P = h->P;
+    if (!h->aux) {
+        FQ_CUDA(cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking));
+        FQ_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+        FQ_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+        for (cudaEvent_t &e : h->ev_chunk) FQ_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    int bad = 0;
+    const int rc = load_stage<W>(h, cur, dets, pops, hdiag, n, bad);
+    if (rc != FCIQMC_OK || bad) {
+        cudaStreamSynchronize(h->aux);
+        cudaStreamSynchronize(s);
         fq::k_index_clear<<<h->small_grid, 256, 0, s>>>(P, 1);
         fq::k_index_fill<W><<<h->small_grid, 256, 0, s>>>(P, 1);
         FQ_CUDA(cudaGetLastError());
         FQ_CUDA(cudaStreamSynchronize(s));
+        if (rc != FCIQMC_OK) return rc;
         return bad == 3 ? FCIQMC_ERR_CAPACITY : FCIQMC_ERR_INVALID_ARG;
     }
+    const int b = cur.lb ^ 1;
     st0.lb = b;
     st0.pp = 0;
     FQ_CUDA(cudaMemcpyAsync(P.st, &st0, sizeof(st0), cudaMemcpyHostToDevice, s));
