@@ -212,8 +212,11 @@ int configure_kernels(fciqmc_handle *h) {
     h->sweep_grid = std::min(kMaxGrid, std::max(1, sms * std::max(per_sm, 1)));
     FQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fq::k_annihilate<W>, 256, 0));
     h->ann_grid = std::min(kMaxGrid, std::max(1, sms * std::max(per_sm, 1)));
-    // k_new_diag: one block per SM (its blocks with no new slot return before loading the pair terms)
-    h->diag_grid = sms;
+    // k_new_diag: as many blocks as fit at once (one new slot per thread up to that many; each thread's H_ii
+    // is a long chain of dependent FP64 adds, so more resident warps hide its latency; blocks with no new
+    // slot return before loading the pair terms)
+    FQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fq::k_new_diag<W>, 256, h->smem_w));
+    h->diag_grid = std::min(kMaxGrid, std::max(1, sms * std::max(per_sm, 1)));
     h->heavy_grid = std::min(kMaxGrid, sms * 4);
     if (h->grid_request > 0) {
         const int g = std::min(kMaxGrid, h->grid_request);
@@ -300,7 +303,7 @@ void launch_prepare(fciqmc_handle *h, int b, long long n, int compute) {
     fq::k_prepare_list<W><<<(unsigned)blocks, 256, h->smem_w, h->stream>>>(h->P, b, n, compute);
 }
 
-// Copy, check and index work of load_list, up to the join of the helper stream; bad receives the verdict
+// Copy, check and index work of load_list, up to the join of the helper stream; bad receives the outcome
 // of the check and of the inserts (1 invalid entry, 2 repeated determinant, 3 index full).
 template <int W>
 int load_stage(fciqmc_handle *h, const DevState &cur, const uint64_t *dets, const int32_t *pops,
