@@ -1072,11 +1072,10 @@ __global__ void __launch_bounds__(kTile, FQ_SWEEP_MIN_BLOCKS) k_sweep(Params P) 
     extern __shared__ __align__(16) unsigned char s_queue[];  // one SpawnQueue per warp
     __shared__ Tables T;
     __shared__ DetView<W> s_dv[kTile];
-    __shared__ unsigned s_off[kTile + 1];
+    __shared__ unsigned s_off[kTile];
     __shared__ unsigned s_wsum[kTile / 32];
     __shared__ float s_rcpf[2 * MAXSO + 2];
     __shared__ unsigned long long s_red[(kTile / 32) * (NCNT + 4)];
-    __shared__ double s_redf[kTile / 32];
     load_tables(P, T);
     load_rcpf(P, s_rcpf);
     const int lb = st->lb, pp = st->pp;
@@ -1101,12 +1100,15 @@ __global__ void __launch_bounds__(kTile, FQ_SWEEP_MIN_BLOCKS) k_sweep(Params P) 
     __syncwarp();
 
     // tiles are handed out dynamically (one atomic per tile): per-tile costs vary with the populations, and a
-    // static assignment left the blocks' last tiles as a tail
-    __shared__ long long s_tile;
-    for (;;) {
-        if (tid == 0) s_tile = (long long)atomicAdd(&st->sweep_next, 1ull) * kTile;
-        __syncthreads();
-        const long long tb = s_tile;
+    // static assignment left the blocks' last tiles as a tail. The next tile is claimed while this one is
+    // worked on (two slots), so a tile takes three block barriers: after the per-determinant work, after the
+    // attempt offsets, and after the attempts.
+    __shared__ long long s_tile[2];
+    __shared__ double s_numw[kTile / 32];
+    if (tid == 0) s_tile[0] = (long long)atomicAdd(&st->sweep_next, 1ull) * kTile;
+    __syncthreads();
+    for (int slot = 0;; slot ^= 1) {
+        const long long tb = s_tile[slot];
         if (tb >= len) break;
         double num = 0.0;  // this tile's share of the Eq. 2 numerator
         const long long s = tb + tid;
@@ -1176,28 +1178,34 @@ __global__ void __launch_bounds__(kTile, FQ_SWEEP_MIN_BLOCKS) k_sweep(Params P) 
                 }
             }
         }
-        // exclusive scan of attempts over the tile
+        // exclusive scan of attempts over the tile: within each warp, then every thread adds the totals of the
+        // warps before its own; the tile's numerator from the warps' sums added in warp order
         unsigned x = att;
         for (int o = 1; o < 32; o <<= 1) {
             unsigned y = __shfl_up_sync(0xFFFFFFFFu, x, o);
             if (lane >= o) x += y;
         }
+        const double wnum = warp_sum_f64(num);
         if (lane == 31) s_wsum[warp] = x;
+        if (lane == 0) s_numw[warp] = wnum;
+        if (tid == 0) s_tile[slot ^ 1] = (long long)atomicAdd(&st->sweep_next, 1ull) * kTile;
         __syncthreads();
-        if (warp == 0) {
-            unsigned ws = lane < kTile / 32 ? s_wsum[lane] : 0u;
-            unsigned wx = ws;
-            for (int o = 1; o < 32; o <<= 1) {
-                unsigned y = __shfl_up_sync(0xFFFFFFFFu, wx, o);
-                if (lane >= o) wx += y;
-            }
-            if (lane < kTile / 32) s_wsum[lane] = wx - ws;
-            if (lane == kTile / 32 - 1) s_off[kTile] = wx;
+        unsigned woff = 0, total = 0;
+#pragma unroll
+        for (int w = 0; w < kTile / 32; ++w) {
+            const unsigned ws = s_wsum[w];
+            woff += w < warp ? ws : 0u;
+            total += ws;
+        }
+        s_off[tid] = x - att + woff;
+        if (tid == 0) {
+            // the tile's numerator, summed in a fixed order, so the run's total does not depend on which block
+            // took which tile
+            double bs = 0.0;
+            for (int w = 0; w < kTile / 32; ++w) bs = __dadd_rn(bs, s_numw[w]);
+            if (FQ_CHECK(tb / kTile < P.tiles_cap, P.st)) P.partial[tb / kTile] = bs;
         }
         __syncthreads();
-        s_off[tid] = x - att + s_wsum[warp];
-        __syncthreads();
-        const unsigned total = s_off[kTile];
         for (unsigned base = 0; base < total; base += kTile) {
             const unsigned k = base + tid;
             const bool act = k < total;
@@ -1212,11 +1220,7 @@ __global__ void __launch_bounds__(kTile, FQ_SWEEP_MIN_BLOCKS) k_sweep(Params P) 
             spawn_attempt<W, false, MODE>(P, T, s_dv[lo], nullptr, s_rcpf, act, k - s_off[lo], iter, acc, sq);
             flush_queue<W>(P, sq, false, T.map1);
         }
-        // the tile's numerator, summed in a fixed order, so the run's total does not depend on which block
-        // took which tile
-        const double bs = block_sum_f64<kTile>(num, s_redf);
-        if (tid == 0 && FQ_CHECK(tb / kTile < P.tiles_cap, P.st)) P.partial[tb / kTile] = bs;
-        __syncthreads();
+        __syncthreads();  // the tile's views and offsets are free again; the next tile's index is visible
     }
     flush_queue<W>(P, sq, true, T.map1);
     unsigned long long *const dst[NCNT + 4] = {&st->cnt[0], &st->cnt[1], &st->cnt[2], &st->cnt[3], &st->cnt[4],
@@ -1264,14 +1268,18 @@ __global__ void __launch_bounds__(kTile, 4) k_heavy(Params P) {
         bool fresh = false;
         if (q >= qend) {
             // guided self-scheduling: a share of what is left, so batches are long while much is left (few
-            // determinant switches) and single chunks at the end (no tail)
-            const unsigned long long taken = *(volatile unsigned long long *)&st->heavy_next;
-            const unsigned long long nwarps = (unsigned long long)gridDim.x * NW;
-            const unsigned long long size =
-                taken >= nch ? 1ull : max(1ull, min((unsigned long long)kChunkBatch, (nch - taken) / (2ull * nwarps)));
-            unsigned long long b = 0;
-            if (lane == 0) b = atomicAdd(&st->heavy_next, size);
+            // determinant switches) and single chunks at the end (no tail); lane 0 decides, so every lane of
+            // the warp holds the same batch
+            unsigned long long b = 0, size = 1;
+            if (lane == 0) {
+                const unsigned long long taken = *(volatile unsigned long long *)&st->heavy_next;
+                const unsigned long long nwarps = (unsigned long long)gridDim.x * NW;
+                if (taken < nch)
+                    size = max(1ull, min((unsigned long long)kChunkBatch, (nch - taken) / (2ull * nwarps)));
+                b = atomicAdd(&st->heavy_next, size);
+            }
             b = __shfl_sync(0xFFFFFFFFu, b, 0);
+            size = __shfl_sync(0xFFFFFFFFu, size, 0);
             if (b >= nch) break;
             q = b;
             qend = min(b + size, nch);
