@@ -84,7 +84,7 @@ bool sizes_of(int n_elec, int n_orb, const fciqmc_options &o, Sizes &z) {
 
 struct Layout {
     size_t state, h, h_f, eri, eri_f, wpair, map1, cmask, unionm, irrep, pairs, recip, rcpf, ref_occ, facts, e0;
-    size_t det[2], hd[2], hdf[2], pop[2][2], idx, mt, merged, heavy, heavy_base, heavy_att, partial, hist;
+    size_t det[2], hd[2], hdf[2], pop[2][2], idx, mt, merged, heavy, heavy_occ, heavy_base, heavy_att, partial, hist;
     size_t ref_pinfo, ref_off2, ref_exc, outbox;
     size_t total;
 };
@@ -125,6 +125,7 @@ Layout layout_of(const Sizes &z, int n_orb) {
     L.mt = take(sizeof(unsigned long long) * stride * z.mt_cap);
     L.merged = take(sizeof(unsigned) * z.mt_cap);
     L.heavy = take(sizeof(fq::DetView<2>) * z.heavy_cap);
+    L.heavy_occ = take((size_t)fq::MAXN * z.heavy_cap);
     L.heavy_base = take(sizeof(unsigned) * z.heavy_cap);
     L.heavy_att = take(sizeof(unsigned) * z.heavy_cap);
     L.partial = take(sizeof(double) * (std::max<long long>((z.cap + fq::kTile - 1) / fq::kTile, kMaxGrid) + fq::kTileSums));
@@ -208,7 +209,7 @@ int configure_kernels(fciqmc_handle *h) {
     int dev = 0, sms = 0, per_sm = 0;
     FQ_CUDA(cudaGetDevice(&dev));
     FQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    FQ_CUDA(W == 1 ? fq::sweep_occupancy_w1(&per_sm) : fq::sweep_occupancy_w2(&per_sm));
+    FQ_CUDA(W == 1 ? fq::sweep_occupancy_w1(h->P.n_elec, &per_sm) : fq::sweep_occupancy_w2(h->P.n_elec, &per_sm));
     h->sweep_grid = std::min(kMaxGrid, std::max(1, sms * std::max(per_sm, 1)));
     FQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fq::k_annihilate<W>, 256, 0));
     h->ann_grid = std::min(kMaxGrid, std::max(1, sms * std::max(per_sm, 1)));
@@ -553,6 +554,7 @@ int fciqmc_create(const double *h1, const double *eri_s8, double e_core, int n_e
     P.mt_bits = log2_exact(z.mt_cap);
     P.merged = at<unsigned>(h, L.merged);
     P.heavy = h->ws + L.heavy;
+    P.heavy_occ = at<unsigned char>(h, L.heavy_occ);
     P.heavy_base = at<unsigned>(h, L.heavy_base);
     P.heavy_att = at<unsigned>(h, L.heavy_att);
     P.heavy_cap = z.heavy_cap;

@@ -793,6 +793,7 @@ __global__ void __launch_bounds__(256) k_ref_table(Params P, unsigned *pinfo, un
                                                    long long cap, long long *out) {
     __shared__ Tables T;
     __shared__ DetView<W> v;
+    __shared__ unsigned char occ[MAXN];
     __shared__ unsigned s_g[MAXPAIRS], s_go[MAXPAIRS], s_eo[MAXPAIRS];
     __shared__ int s_ok;
     load_tables(P, T);
@@ -800,14 +801,14 @@ __global__ void __launch_bounds__(256) k_ref_table(Params P, unsigned *pinfo, un
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int w = 0; w < W; ++w) v.d[w] = P.ref[w];
-        prepare_det<W>(P, T, v, 1);
+        prepare_det<W>(P, T, v, occ, 1);
     }
     __syncthreads();
     const int np = P.npairs;
     // G and the number of (a, b) choices of every pair
     for (int k = threadIdx.x; k < np; k += blockDim.x) {
         const unsigned short pr = T.pairs[k];
-        const int i = v.occ[pr & 0xFF], j = v.occ[pr >> 8];
+        const int i = occ[pr & 0xFF], j = occ[pr >> 8];
         const int si = i & 1, sj = j & 1, gij = T.irrep[i >> 1] ^ T.irrep[j >> 1];
         unsigned long long gm[W];
         const unsigned G = (unsigned)good_set<W>(P, v, si, sj, gij, gm);
@@ -838,7 +839,7 @@ __global__ void __launch_bounds__(256) k_ref_table(Params P, unsigned *pinfo, un
     if (!s_ok) return;
     for (int k = threadIdx.x; k < np; k += blockDim.x) {
         const unsigned short pr = T.pairs[k];
-        const int i = v.occ[pr & 0xFF], j = v.occ[pr >> 8];
+        const int i = occ[pr & 0xFF], j = occ[pr >> 8];
         const int si = i & 1, sj = j & 1, gij = T.irrep[i >> 1] ^ T.irrep[j >> 1];
         unsigned long long gm[W];
         const unsigned G = (unsigned)good_set<W>(P, v, si, sj, gij, gm);

@@ -127,6 +127,7 @@ struct Params {
     int mt_bits;
     unsigned *merged;
     void *heavy;                      // DetView records of heavily populated determinants
+    unsigned char *heavy_occ;         // their occupied lists (MAXN bytes each)
     unsigned *heavy_base;             // first chunk of each (nondecreasing in the record index)
     unsigned *heavy_att;              // attempts of each
     long long heavy_cap;

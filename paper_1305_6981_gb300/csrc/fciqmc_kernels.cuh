@@ -19,7 +19,7 @@ namespace fq {
 constexpr int kTile = 256;          // determinants per sweep tile = threads per sweep block
 constexpr int kTileSums = 32;       // range sums of the per-tile numerators (blocks of k_tile_sum)
 #ifndef FQ_SWEEP_MIN_BLOCKS
-#define FQ_SWEEP_MIN_BLOCKS 4          // resident sweep blocks per SM the register budget is sized for
+#define FQ_SWEEP_MIN_BLOCKS 5          // resident sweep blocks per SM the register budget is sized for
 #endif
 #ifndef FQ_HEAVY_THRESHOLD
 #define FQ_HEAVY_THRESHOLD 256
@@ -39,7 +39,8 @@ constexpr unsigned long long kFlagUnit = 1ull << 40;  // merge payload: (#initia
 
 enum { C_ATTEMPTS = 0, C_NULLS, C_EVENTS, C_SPAWNED, C_DEATH, C_CLONE, C_MERGED, C_ABORTED, C_INSERTED, C_HEAVY };
 
-// Per-determinant data used by every attempt from it, kept in shared memory.
+// Per-determinant data used by every attempt from it, kept in shared memory (its occupied list separately, so
+// the sweep's tile of views takes only the bytes the run's electron count needs).
 template <int W>
 struct DetView {
     unsigned long long d[W];
@@ -51,8 +52,26 @@ struct DetView {
     unsigned char nok;          // electrons with at least one symmetry-allowed single (N - delta_s)
     unsigned char flag;         // initiator
     unsigned char isref;        // the reference determinant
-    unsigned char occ[MAXN];
-};
+};  // the occupied spin orbitals (ascending) are kept beside the view, n_elec bytes
+
+// Occupied spin orbitals of d in ascending order (for the exact FP64 paths, which run rarely); returns their
+// number.
+template <int W>
+__device__ __forceinline__ int decode_occ(const unsigned long long (&d)[W], unsigned char *occ) {
+    int n = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        unsigned long long m = d[w];
+        while (m && n < MAXN) {
+            occ[n++] = (unsigned char)(64 * w + __ffsll((long long)m) - 1);
+            m &= m - 1;
+        }
+    }
+    return n;
+}
+
+// Bytes of one occupied list in the sweep's tile (the electron count rounded up to 4).
+__host__ __device__ constexpr int occ_stride(int n_elec) { return (n_elec + 3) & ~3; }
 
 struct Tables {
     unsigned long long map1[MAXSO];
@@ -132,7 +151,8 @@ __device__ __forceinline__ unsigned nonzero_bytes(unsigned long long x) {
 // spin orbitals in ascending order gives the occupied list, the electrons with an allowed single (an
 // electron's class keeps an unoccupied orbital) and the fingerprint of Algorithm 1.
 template <int W>
-__device__ __forceinline__ void prepare_det(const Params &P, const Tables &T, DetView<W> &v, int c) {
+__device__ __forceinline__ void prepare_det(const Params &P, const Tables &T, DetView<W> &v, unsigned char *occ,
+                                            int c) {
     unsigned long long cb0 = 0, cb1 = 0;
     for (int g = 0; g < P.n_irrep_used; ++g) {
         int u0 = 0, u1 = 0;
@@ -164,7 +184,7 @@ __device__ __forceinline__ void prepare_det(const Params &P, const Tables &T, De
             const int b = __ffsll((long long)m) - 1;
             const int k = 64 * w + b;
             if (!FQ_CHECK(n < MAXN, P.st)) break;
-            v.occ[n] = (unsigned char)k;
+            occ[n] = (unsigned char)k;
             okm |= ((ok[w] >> b) & 1ull) << n;
             h = 1099511628211ull * h + T.map1[k] * (unsigned long long)(n + 1);
             ++n;
@@ -266,6 +286,7 @@ struct HeavyTab {
     unsigned char glist[24][MAXSO + 4];
     unsigned char ulist[NCLASS][MAXSO / 2 + 4];
     unsigned char urank[MAXSO];
+    unsigned char occ[MAXN];  // the determinant's occupied spin orbitals, ascending
     unsigned short G[24];
 };
 
@@ -417,8 +438,10 @@ __device__ double hphf_hij(const Params &P, const DetView<W> &v, const unsigned 
     flip_spins<W>(a, ab);
     flip_spins<W>(b, bb);
     const bool a_open = !det_same<W>(a, ab), b_open = !det_same<W>(b, bb);
-    const double hab = hij_any<W>(P, a, v.occ, b);
-    if (a_open && b_open) return __dadd_rn(hab, __dmul_rn(pair_sign(n_open<W>(b)), hij_any<W>(P, a, v.occ, bb)));
+    unsigned char occ[MAXN];
+    decode_occ<W>(v.d, occ);
+    const double hab = hij_any<W>(P, a, occ, b);
+    if (a_open && b_open) return __dadd_rn(hab, __dmul_rn(pair_sign(n_open<W>(b)), hij_any<W>(P, a, occ, bb)));
     if (a_open || b_open) return __dmul_rn(hab, kSqrt2);
     return hab;
 }
@@ -573,7 +596,7 @@ __device__ void hphf_attempt_end(const Params &P, const DetView<W> &v, const Hea
 // selected (electron i, virtual ao) and returned pending (true) for the warp to evaluate its element.
 template <int W, bool TAB, int MODE>
 __device__ __forceinline__ bool attempt_begin(const Params &P, const Tables &T, const DetView<W> &v,
-                                              const HeavyTab *tab, const float *rcpf, unsigned a, unsigned iter,
+                                              const unsigned char *occ, const HeavyTab *tab, const float *rcpf, unsigned a, unsigned iter,
                                               unsigned long long pol, unsigned long long *cnt, SpawnQueue<W> &out,
                                               int &i_out, int &a_out, unsigned &mallow_out, unsigned long long &q_out,
                                               int &i1_out, int &a1_out, int &i2_out, int &a2_out, bool rtab) {
@@ -585,7 +608,7 @@ __device__ __forceinline__ bool attempt_begin(const Params &P, const Tables &T, 
         // single excitation (Sec. VI A): i uniform over the N - delta_s electrons with M_allow > 0, a
         // uniform over the unoccupied spin orbitals of i's class
         if (v.nok == 0) { cnt[C_NULLS]++; return false; }
-        const int i = v.occ[select64(v.okm, (int)rank_next(rh, rl, v.nok))];
+        const int i = occ[select64(v.okm, (int)rank_next(rh, rl, v.nok))];
         const int ci = T.irrep[i >> 1] * 2 + (i & 1);
         const unsigned mallow = v.cnt[ci];
         const int k2 = (int)rank_next(rh, rl, mallow);
@@ -691,7 +714,7 @@ __device__ __forceinline__ bool attempt_begin(const Params &P, const Tables &T, 
         return false;
     }
     const unsigned short pr = T.pairs[rank_next(rh, rl, (unsigned)P.npairs)];
-    const int i = v.occ[pr & 0xFF], j = v.occ[pr >> 8];
+    const int i = occ[pr & 0xFF], j = occ[pr >> 8];
     const int si = i & 1, sj = j & 1;
     const int gij = T.irrep[i >> 1] ^ T.irrep[j >> 1];
     unsigned G;
@@ -797,20 +820,20 @@ __device__ __forceinline__ bool attempt_begin(const Params &P, const Tables &T, 
 // delta_spin (ij|ja)] (without the parity sign) for every lane with a pending single, each evaluated by
 // the whole warp: lane x takes electrons x, x + 32. Called by all 32 lanes.
 template <int W>
-__device__ __forceinline__ void single_elements_warp(const Params &P, const DetView<W> *vp, bool pend, int i, int a,
-                                                     unsigned long long pol, float &hs, float &hab) {
+__device__ __forceinline__ void single_elements_warp(const Params &P, const unsigned char *occp, bool pend, int i,
+                                                     int a, unsigned long long pol, float &hs, float &hab) {
     unsigned need = __ballot_sync(0xFFFFFFFFu, pend);
     const int lane = threadIdx.x & 31;
     while (need) {
         const int src = __ffs(need) - 1;
         need &= need - 1;
-        const DetView<W> *sv = reinterpret_cast<const DetView<W> *>(
-            __shfl_sync(0xFFFFFFFFu, reinterpret_cast<unsigned long long>(vp), src));
+        const unsigned char *so = reinterpret_cast<const unsigned char *>(
+            __shfl_sync(0xFFFFFFFFu, reinterpret_cast<unsigned long long>(occp), src));
         const int ii = __shfl_sync(0xFFFFFFFFu, i, src), aa = __shfl_sync(0xFFFFFFFFu, a, src);
         const int I = ii >> 1, A = aa >> 1;
         float s = 0.f, b = 0.f;
         for (int x = lane; x < P.n_elec; x += 32) {
-            const int j = sv->occ[x];
+            const int j = so[x];
             if (j != ii) {
                 const int J = j >> 1;
                 const float u = eri_f(P, I, A, J, J, pol);
@@ -844,7 +867,8 @@ __device__ __forceinline__ void single_elements_warp(const Params &P, const DetV
 // Completes a pending single i -> ao: |H - hs| <= hab serr (float sum of at most 2N - 1 rounded terms,
 // and the FP64 sum), so most decisions need no FP64; the rest evaluate H in FP64.
 template <int W>
-__device__ __forceinline__ void attempt_single_end(const Params &P, const DetView<W> &v, int i, int ao, unsigned mallow,
+__device__ __forceinline__ void attempt_single_end(const Params &P, const DetView<W> &v, const unsigned char *occ,
+                                                   int i, int ao, unsigned mallow,
                                                    unsigned long long q, float hs, float hab, unsigned long long *cnt,
                                                    SpawnQueue<W> &out) {
     const float eh = fmaf(hab, P.serr_f, 1e-30f);
@@ -858,7 +882,7 @@ __device__ __forceinline__ void attempt_single_end(const Params &P, const DetVie
         if (count_between<W>(v.d, i, ao) & 1) sgn_h = -sgn_h;
     } else {
         atomicAdd(&P.st->exact_spawn, 1ull);
-        const double hv = hij_single<W>(P, v.d, v.occ, i, ao);
+        const double hv = hij_single<W>(P, v.d, occ, i, ao);
         if (hv == 0.0) return;
         // p = (|H| (tau / P_single)) (M_allow (N - delta_s))
         const double p = __dmul_rn(__dmul_rn(fabs(hv), P.cs), (double)((long long)mallow * (long long)v.nok));
@@ -957,7 +981,7 @@ __device__ __forceinline__ void hphf_single_end(const Params &P, const DetView<W
 // One spawning attempt per lane (active lanes only); called by all 32 lanes of a warp.
 template <int W, bool TAB, int MODE>
 __device__ __forceinline__ void spawn_attempt(const Params &P, const Tables &T, const DetView<W> &v,
-                                              const HeavyTab *tab, const float *rcpf, bool active, unsigned a,
+                                              const unsigned char *occ, const HeavyTab *tab, const float *rcpf, bool active, unsigned a,
                                               unsigned iter, unsigned long long *cnt, SpawnQueue<W> &out,
                                               bool rtab = false) {
     const unsigned long long pol = keep_policy();
@@ -966,16 +990,16 @@ __device__ __forceinline__ void spawn_attempt(const Params &P, const Tables &T, 
     unsigned long long q = 0;
     bool pend = false;
     if (active)
-        pend = attempt_begin<W, TAB, MODE>(P, T, v, tab, rcpf, a, iter, pol, cnt, out, i, ao, mallow, q, i1, a1, i2, a2,
+        pend = attempt_begin<W, TAB, MODE>(P, T, v, occ, tab, rcpf, a, iter, pol, cnt, out, i, ao, mallow, q, i1, a1, i2, a2,
                                            rtab);
     float hs = 0.f, hab = 0.f;
-    single_elements_warp<W>(P, &v, pend, i1, a1, pol, hs, hab);
+    single_elements_warp<W>(P, occ, pend, i1, a1, pol, hs, hab);
     if (MODE & 2) {
         float hs2 = 0.f, hab2 = 0.f;
-        single_elements_warp<W>(P, &v, pend && i2 >= 0, i2, a2, pol, hs2, hab2);
+        single_elements_warp<W>(P, occ, pend && i2 >= 0, i2, a2, pol, hs2, hab2);
         if (pend) hphf_single_end<W>(P, v, tab, i, ao, i1, a1, i2, a2, mallow, q, hs, hab, hs2, hab2, cnt, out);
     } else if (pend) {
-        attempt_single_end<W>(P, v, i, ao, mallow, q, hs, hab, cnt, out);
+        attempt_single_end<W>(P, v, occ, i, ao, mallow, q, hs, hab, cnt, out);
     }
 }
 
@@ -1069,7 +1093,10 @@ template <int W, int MODE>
 __global__ void __launch_bounds__(kTile, FQ_SWEEP_MIN_BLOCKS) k_sweep(Params P) {
     DevState *st = P.st;
     if (st->status) return;
-    extern __shared__ __align__(16) unsigned char s_queue[];  // one SpawnQueue per warp
+    // dynamic: one SpawnQueue per warp, then the tile's occupied lists (occ_stride bytes each)
+    extern __shared__ __align__(16) unsigned char s_queue[];
+    unsigned char *const s_occ = s_queue + sizeof(SpawnQueue<W>) * (kTile / 32);
+    const int ostride = occ_stride(P.n_elec);
     __shared__ Tables T;
     __shared__ DetView<W> s_dv[kTile];
     __shared__ unsigned s_off[kTile];
@@ -1127,7 +1154,8 @@ __global__ void __launch_bounds__(kTile, FQ_SWEEP_MIN_BLOCKS) k_sweep(Params P) 
                     v.d[0] = __ldcs(det + s);
                 }
                 const float hf = __ldcs(hdf + s);
-                prepare_det<W>(P, T, v, c);
+                unsigned char *occ = s_occ + tid * ostride;
+                prepare_det<W>(P, T, v, occ, c);
                 const unsigned ac = (unsigned)(c < 0 ? -c : c);
                 acc[NCNT] += ac;
                 acc[NCNT + 1] += 1;
@@ -1170,6 +1198,7 @@ __global__ void __launch_bounds__(kTile, FQ_SWEEP_MIN_BLOCKS) k_sweep(Params P) 
                         set_status(st, FCIQMC_ERR_CAPACITY);
                     } else {
                         heavy[hidx] = v;
+                        for (int k = 0; k < P.n_elec; ++k) P.heavy_occ[hidx * MAXN + k] = occ[k];
                         P.heavy_base[hidx] = (unsigned)(old & ((1ull << 40) - 1ull));
                         P.heavy_att[hidx] = natt;
                     }
@@ -1217,7 +1246,8 @@ __global__ void __launch_bounds__(kTile, FQ_SWEEP_MIN_BLOCKS) k_sweep(Params P) 
                     if (s_off[mid] <= k) lo = mid; else hi = mid - 1;
                 }
             }
-            spawn_attempt<W, false, MODE>(P, T, s_dv[lo], nullptr, s_rcpf, act, k - s_off[lo], iter, acc, sq);
+            spawn_attempt<W, false, MODE>(P, T, s_dv[lo], s_occ + lo * ostride, nullptr, s_rcpf, act, k - s_off[lo],
+                                          iter, acc, sq);
             flush_queue<W>(P, sq, false, T.map1);
         }
         __syncthreads();  // the tile's views and offsets are free again; the next tile's index is visible
@@ -1302,6 +1332,7 @@ __global__ void __launch_bounds__(kTile, 4) k_heavy(Params P) {
             const unsigned long long *src = reinterpret_cast<const unsigned long long *>(heavy + r);
             unsigned long long *dstv = reinterpret_cast<unsigned long long *>(&v);
             for (int k = lane; k < (int)(sizeof(DetView<W>) / 8); k += 32) dstv[k] = src[k];
+            for (int k = lane; k < P.n_elec; k += 32) tab.occ[k] = P.heavy_occ[r * MAXN + k];
             __syncwarp();
             build_heavy_tab<W>(P, T, v, tab, lane);
             cur = r;
@@ -1311,7 +1342,7 @@ __global__ void __launch_bounds__(kTile, 4) k_heavy(Params P) {
         const bool rtab = P.ref_tab && v.isref;
         for (unsigned base = a0; base < a1; base += 32) {
             const unsigned a = base + lane;
-            spawn_attempt<W, true, MODE>(P, T, v, &tab, s_rcpf, a < a1, a, iter, cnt, sq, rtab);
+            spawn_attempt<W, true, MODE>(P, T, v, tab.occ, &tab, s_rcpf, a < a1, a, iter, cnt, sq, rtab);
             flush_queue<W>(P, sq, false, T.map1);
         }
         __syncwarp();

@@ -11,9 +11,9 @@ struct Params;
 
 void launch_sweep_w1(int mode, int grid, cudaStream_t s, const Params &P);
 void launch_heavy_w1(int mode, int grid, cudaStream_t s, const Params &P);
-cudaError_t sweep_occupancy_w1(int *blocks_per_sm);  // also sets the kernels' shared-memory limits
+cudaError_t sweep_occupancy_w1(int n_elec, int *blocks_per_sm);  // also sets the kernels' shared-memory limits
 void launch_sweep_w2(int mode, int grid, cudaStream_t s, const Params &P);
 void launch_heavy_w2(int mode, int grid, cudaStream_t s, const Params &P);
-cudaError_t sweep_occupancy_w2(int *blocks_per_sm);
+cudaError_t sweep_occupancy_w2(int n_elec, int *blocks_per_sm);
 
 }  // namespace fq
