@@ -226,6 +226,7 @@ int configure_kernels(fciqmc_handle *h) {
         h->diag_grid = std::min(h->diag_grid, g);
         h->heavy_grid = std::min(h->heavy_grid, g);
     }
+    h->P.heavy_warps = (long long)h->heavy_grid * (fq::kTile / 32);
     h->small_grid = std::min(kMaxGrid, sms * 8);
     h->info.num_sms = sms;
     h->info.grid_blocks = h->sweep_grid;
@@ -1269,6 +1270,8 @@ int fciqmc_group_create(fciqmc_handle *const *parts, int32_t n_partitions, int64
         links[r].hist = P.hist;
         links[r].hist_cap = P.hist_cap;
         links[r].cap = P.cap;
+        links[r].heavy_warps = P.heavy_warps;
+        links[r].frac_bits = P.frac_bits;
     }
     int rc = FCIQMC_OK;
     cudaStream_t cs = nullptr;

@@ -247,9 +247,20 @@ __device__ __forceinline__ void shift_update(DevState *st, long long nw_out, lon
     }
 }
 
+// Heavy chunk size for the next iteration from its expected attempts: kChunk doubled while every k_heavy warp
+// still gets kChunksPerWarp chunks, up to kChunkGrowth kChunk (larger chunks: fewer table builds and batch
+// claims; small ones when the walkers are few, so that every warp has work).
+__device__ __forceinline__ unsigned next_chunk(long long attempts, long long warps) {
+    unsigned c = kChunk;
+    while (c < (unsigned)(kChunkGrowth * kChunk) && attempts >= 2ll * c * kChunksPerWarp * warps) c *= 2u;
+    return c;
+}
+
 // Makes the iteration's list the current one (new slots included, populations' parity flipped), decides a
-// compaction for the next iteration and clears the per-iteration counters.
-__device__ __forceinline__ void commit_list(DevState *st, long long nd_out, long long cap) {
+// compaction and the heavy chunk size for the next iteration (attempts: its expected spawning attempts) and
+// clears the per-iteration counters.
+__device__ __forceinline__ void commit_list(DevState *st, long long nd_out, long long cap, long long attempts,
+                                            long long heavy_warps) {
     const long long new_len = (long long)st->claim;
     st->list_len = new_len;
     st->pp ^= 1;
@@ -265,6 +276,7 @@ __device__ __forceinline__ void commit_list(DevState *st, long long nd_out, long
     st->n_new = 0;
     st->sweep_next = 0;
     st->heavy_next = 0;
+    st->heavy_chunk = next_chunk(attempts, heavy_warps);
     for (int k = 0; k < NCNT; ++k) st->cnt[k] = 0;
     for (int k = 0; k < MAXPARTS; ++k) st->ob_n[k] = 0;
 }
@@ -303,7 +315,7 @@ __global__ void k_finish(Params P) {
     P.hist[st->hist_n % P.hist_cap] = row;
     st->hist_n++;
     shift_update(st, row.nw_out, P.target, P.period, P.c_shift);
-    commit_list(st, row.nd_out, P.cap);
+    commit_list(st, row.nd_out, P.cap, row.nw_out >> P.frac_bits, P.heavy_warps);
 }
 
 // ---------------------------------------------------------------------------- hash-partitioned runs
@@ -315,6 +327,8 @@ struct PartLink {
     const double *partial;       // range sums of the sweep tiles' numerators (kTileSums)
     fciqmc_row *hist;            // the partition's own rows (its list's counters)
     long long hist_cap, cap;
+    long long heavy_warps;       // warps of the partition's k_heavy launch
+    int frac_bits;               // hybrid walkers: populations in units of 2^-frac_bits
 };
 struct GroupDev {
     long long hist_n;            // rows written to hist
@@ -395,7 +409,9 @@ __global__ void k_group_finish(const PartLink *links, int n_parts, GroupDev *g, 
     for (int r = 0; r < n_parts; ++r) {
         DevState *st = links[r].st;
         shift_update(st, tot.nw_out, target, period, c_shift);  // the same state and input in every partition
-        commit_list(st, (long long)st->nd_in + (long long)st->d_nd, links[r].cap);
+        const long long nw_part = (long long)st->nw_in + (long long)st->d_nw;
+        commit_list(st, (long long)st->nd_in + (long long)st->d_nd, links[r].cap, nw_part >> links[r].frac_bits,
+                    links[r].heavy_warps);
     }
 }
 

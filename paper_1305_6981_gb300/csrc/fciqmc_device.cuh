@@ -54,6 +54,7 @@ struct DevState {
     unsigned long long n_new;  // determinants placed in new slots this iteration (diagonal elements pending)
     unsigned long long sweep_next;  // next sweep tile to hand out (tiles are taken dynamically by the blocks)
     unsigned long long heavy_next;  // next batch of heavy chunks to hand out (taken dynamically by the warps)
+    unsigned heavy_chunk;           // attempts per heavy chunk this iteration (0: the smallest size)
     unsigned long long ob_n[MAXPARTS];  // partitioned runs: spawns routed to each other partition this iteration
 };
 
@@ -131,6 +132,7 @@ struct Params {
     unsigned *heavy_base;             // first chunk of each (nondecreasing in the record index)
     unsigned *heavy_att;              // attempts of each
     long long heavy_cap;
+    long long heavy_warps;            // warps of a k_heavy launch (chooses the chunk size)
     double *partial;
     fciqmc_row *hist;
     long long hist_cap;

@@ -28,7 +28,12 @@ constexpr int kHeavy = FQ_HEAVY_THRESHOLD;  // |C_i| above this: attempts go to 
 #ifndef FQ_HEAVY_CHUNK
 #define FQ_HEAVY_CHUNK 512
 #endif
-constexpr int kChunk = FQ_HEAVY_CHUNK;  // attempts per heavy chunk (one warp task; 512 measured against 128 to 2048)
+constexpr int kChunk = FQ_HEAVY_CHUNK;  // smallest heavy chunk in attempts (one warp task)
+#ifndef FQ_CHUNK_GROWTH
+#define FQ_CHUNK_GROWTH 4
+#endif
+constexpr int kChunkGrowth = FQ_CHUNK_GROWTH;  // chunks grow to at most kChunkGrowth kChunk with the walkers
+constexpr int kChunksPerWarp = 12;       // the chunk size keeps at least this many chunks per k_heavy warp
 #ifndef FQ_CHUNK_BATCH
 #define FQ_CHUNK_BATCH 32
 #endif
@@ -1116,6 +1121,7 @@ __global__ void __launch_bounds__(kTile, FQ_SWEEP_MIN_BLOCKS) k_sweep(Params P) 
     const int *pop_in = P.pop[lb][pp];
     int *pop_out = P.pop[lb][pp ^ 1];
     DetView<W> *heavy = reinterpret_cast<DetView<W> *>(P.heavy);
+    const unsigned chunk = st->heavy_chunk ? st->heavy_chunk : (unsigned)kChunk;
     __syncthreads();
 
     unsigned long long acc[NCNT + 4];  // counters, then nw, nd, d_nw, d_nd
@@ -1187,11 +1193,11 @@ __global__ void __launch_bounds__(kTile, FQ_SWEEP_MIN_BLOCKS) k_sweep(Params P) 
                 }
                 acc[C_ATTEMPTS] += natt;
                 if (natt > (unsigned)kHeavy) {
-                    // heavily populated determinant: a record for k_heavy, whose warps take chunks of kChunk
+                    // heavily populated determinant: a record for k_heavy, whose warps take chunks of `chunk`
                     // attempts; record index and first chunk are claimed by one atomic, so the first
                     // chunks are nondecreasing in the record index
                     acc[C_HEAVY] += natt;
-                    const unsigned nch = (natt + kChunk - 1) / kChunk;
+                    const unsigned nch = (natt + chunk - 1) / chunk;
                     const unsigned long long old = atomicAdd(&st->heavy_packed, (1ull << 40) | nch);
                     const unsigned long long hidx = old >> 40;
                     if (hidx >= (unsigned long long)P.heavy_cap) {
@@ -1279,6 +1285,7 @@ __global__ void __launch_bounds__(kTile, 4) k_heavy(Params P) {
     const long long nh = min((long long)(packed >> 40), P.heavy_cap);
     const unsigned long long nch = nh > 0 ? (packed & ((1ull << 40) - 1ull)) : 0ull;
     const unsigned iter = (unsigned)st->iter;
+    const unsigned chunk = st->heavy_chunk ? st->heavy_chunk : (unsigned)kChunk;
     const DetView<W> *heavy = reinterpret_cast<const DetView<W> *>(P.heavy);
     unsigned long long cnt[NCNT];
 #pragma unroll
@@ -1337,8 +1344,8 @@ __global__ void __launch_bounds__(kTile, 4) k_heavy(Params P) {
             build_heavy_tab<W>(P, T, v, tab, lane);
             cur = r;
         }
-        const unsigned a0 = (unsigned)(q - P.heavy_base[r]) * kChunk;
-        const unsigned a1 = min(a0 + (unsigned)kChunk, P.heavy_att[r]);
+        const unsigned a0 = (unsigned)(q - P.heavy_base[r]) * chunk;
+        const unsigned a1 = min(a0 + chunk, P.heavy_att[r]);
         const bool rtab = P.ref_tab && v.isref;
         for (unsigned base = a0; base < a1; base += 32) {
             const unsigned a = base + lane;
