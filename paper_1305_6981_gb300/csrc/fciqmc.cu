@@ -249,8 +249,10 @@ void launch_heavy(fciqmc_handle *h, cudaStream_t s) {
 template <int W>
 void launch_spawning(fciqmc_handle *h, cudaStream_t s) {
     launch_sweep<W>(h, s);
-    fq::k_tile_sum<<<fq::kTileSums, 256, 0, s>>>(h->P);
     launch_heavy<W>(h, s);
+    // the sweep tiles' numerators are summed after k_heavy, which does not need them: the 32-block sum then
+    // does not sit between the two spawning kernels
+    fq::k_tile_sum<<<fq::kTileSums, 256, 0, s>>>(h->P);
 }
 
 template <int W>
