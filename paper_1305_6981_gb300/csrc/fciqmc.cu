@@ -307,6 +307,27 @@ void launch_prepare(fciqmc_handle *h, int b, long long n, int compute) {
     fq::k_prepare_list<W><<<(unsigned)blocks, 256, h->smem_w, h->stream>>>(h->P, b, n, compute);
 }
 
+// The helper stream of set_walkers and its events, created together (nothing is kept if one fails).
+int create_helper_stream(fciqmc_handle *h) {
+    static_assert(sizeof(fciqmc_handle::ev_chunk) == 8 * sizeof(cudaEvent_t), "eight chunk events");
+    cudaStream_t a = nullptr;
+    cudaEvent_t ev[10] = {};
+    bool ok = cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking) == cudaSuccess;
+    for (cudaEvent_t &e : ev) ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+        if (a) cudaStreamDestroy(a);
+        cudaGetLastError();
+        return FCIQMC_ERR_CUDA;
+    }
+    h->ev_fork = ev[0];
+    h->ev_join = ev[1];
+    for (int k = 0; k < 8; ++k) h->ev_chunk[k] = ev[2 + k];
+    h->aux = a;
+    return FCIQMC_OK;
+}
+
 // Copy, check and index work of load_list, up to the join of the helper stream; bad receives the outcome
 // of the check and of the inserts (1 invalid entry, 2 repeated determinant, 3 index full).
 template <int W>
@@ -366,12 +387,7 @@ int load_list(fciqmc_handle *h, const DevState &cur, DevState &st0, const uint64
               const double *hdiag, long long n) {
     cudaStream_t s = h->stream;
     const Params &P = h->P;
-    if (!h->aux) {
-        FQ_CUDA(cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking));
-        FQ_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
-        FQ_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
-        for (cudaEvent_t &e : h->ev_chunk) FQ_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-    }
+    if (!h->aux && create_helper_stream(h) != FCIQMC_OK) return FCIQMC_ERR_CUDA;
     int bad = 0;
     const int rc = load_stage<W>(h, cur, dets, pops, hdiag, n, bad);
     if (rc != FCIQMC_OK || bad) {
