@@ -52,7 +52,7 @@ int log2_exact(long long x) {
 }
 
 struct Sizes {
-    int W, n_so, npairs, n_parts, part;
+    int W, n_so, npairs, n_parts, part, ostride;
     long long n_eri, cap, idx_cap, mt_cap, hist_cap, heavy_cap, ref_cap, ob_cap;
 };
 
@@ -60,6 +60,7 @@ bool sizes_of(int n_elec, int n_orb, const fciqmc_options &o, Sizes &z) {
     if (n_orb < 1 || n_orb > 64 || n_elec < 1 || n_elec > fq::MAXN || n_elec >= 2 * n_orb) return false;
     z.W = (2 * n_orb + 63) / 64;
     z.n_so = 2 * n_orb;
+    z.ostride = fq::occ_stride(n_elec);
     z.npairs = n_elec * (n_elec - 1) / 2;
     long long npair = (long long)n_orb * (n_orb + 1) / 2;
     z.n_eri = npair * (npair + 1) / 2;
@@ -84,7 +85,7 @@ bool sizes_of(int n_elec, int n_orb, const fciqmc_options &o, Sizes &z) {
 
 struct Layout {
     size_t state, h, h_f, eri, eri_f, wpair, map1, cmask, unionm, irrep, pairs, recip, rcpf, ref_occ, facts, e0;
-    size_t det[2], hd[2], hdf[2], pop[2][2], idx, mt, merged, heavy, heavy_occ, heavy_base, heavy_att, partial, hist;
+    size_t det[2], hd[2], hdf[2], pop[2][2], pre[2], occa[2], idx, mt, merged, heavy, heavy_occ, heavy_base, heavy_att, partial, hist;
     size_t ref_pinfo, ref_off2, ref_exc, outbox;
     size_t total;
 };
@@ -119,6 +120,8 @@ Layout layout_of(const Sizes &z, int n_orb) {
         L.hdf[b] = take(sizeof(float) * z.cap);
         L.pop[b][0] = take(sizeof(int) * z.cap);
         L.pop[b][1] = take(sizeof(int) * z.cap);
+        L.pre[b] = take(sizeof(unsigned long long) * fq::PRE_WORDS * z.cap);
+        L.occa[b] = take((size_t)z.ostride * z.cap);
     }
     const int stride = z.W == 1 ? 2 : 4;
     L.idx = take(sizeof(unsigned long long) * stride * z.idx_cap);
@@ -301,10 +304,10 @@ void launch_index_rebuild(fciqmc_handle *h) {
 }
 
 template <int W>
-void launch_prepare(fciqmc_handle *h, int b, long long n, int compute) {
+void launch_prepare(fciqmc_handle *h, int b, long long n, int compute) {  // slots [0, n)
     long long blocks = std::min<long long>((n + 255) / 256, h->small_grid);
     if (blocks < 1) blocks = 1;
-    fq::k_prepare_list<W><<<(unsigned)blocks, 256, h->smem_w, h->stream>>>(h->P, b, n, compute);
+    fq::k_prepare_list<W><<<(unsigned)blocks, 256, h->smem_w, h->stream>>>(h->P, b, 0, n, compute);
 }
 
 // The helper stream of set_walkers and its events, created together (nothing is kept if one fails).
@@ -360,6 +363,7 @@ int load_stage(fciqmc_handle *h, const DevState &cur, const uint64_t *dets, cons
             FQ_CUDA(cudaStreamWaitEvent(a, h->ev_chunk[k], 0));
             const unsigned ib = (unsigned)std::max<long long>(1, std::min<long long>((hi - lo + 255) / 256, h->small_grid));
             fq::k_index_insert<W><<<ib, 256, 0, a>>>(P, b, lo, hi);
+            fq::k_prepare_list<W><<<ib, 256, 0, a>>>(P, b, lo, hi, 0);  // derived words of the chunk
         }
     }
     FQ_CUDA(cudaGetLastError());
@@ -526,6 +530,7 @@ int fciqmc_create(const double *h1, const double *eri_s8, double e_core, int n_e
     Params &P = h->P;
     std::memset(&P, 0, sizeof(P));
     P.n_elec = n_elec;
+    P.ostride = z.ostride;
     P.n_orb = n_orb;
     P.n_so = z.n_so;
     P.npairs = z.npairs;
@@ -560,6 +565,8 @@ int fciqmc_create(const double *h1, const double *eri_s8, double e_core, int n_e
         P.det[b] = at<unsigned long long>(h, L.det[b]);
         P.hd[b] = at<double>(h, L.hd[b]);
         P.hdf[b] = at<float>(h, L.hdf[b]);
+        P.pre[b] = at<unsigned long long>(h, L.pre[b]);
+        P.occa[b] = at<unsigned char>(h, L.occa[b]);
         P.pop[b][0] = at<int>(h, L.pop[b][0]);
         P.pop[b][1] = at<int>(h, L.pop[b][1]);
     }

@@ -131,6 +131,8 @@ __global__ void __launch_bounds__(256) k_new_diag(Params P) {
     const long long n = (long long)st->n_new;
     if ((long long)blockIdx.x * blockDim.x >= n) return;
     const int M = P.n_orb;
+    __shared__ Tables T;
+    load_tables(P, T);
     for (int k = threadIdx.x; k < 2 * M * M; k += blockDim.x) s_w[k] = P.wpair[k];
     for (int k = threadIdx.x; k < M; k += blockDim.x) s_w[2 * M * M + k] = P.h[k * M + k];
     __syncthreads();
@@ -145,6 +147,7 @@ __global__ void __launch_bounds__(256) k_new_diag(Params P) {
         const double hdv = __dsub_rn(v, P.E0);
         P.hd[lb][s] = hdv;
         P.hdf[lb][s] = __double2float_rn(hdv);
+        store_derived<W>(P, T, lb, s, key);
     }
 }
 
@@ -432,6 +435,13 @@ __global__ void k_compact_copy(Params P) {
             P.hd[lb ^ 1][ns] = P.hd[lb][s];
             P.hdf[lb ^ 1][ns] = P.hdf[lb][s];
             P.pop[lb ^ 1][pp][ns] = c;
+            const ulonglong2 *ps = reinterpret_cast<const ulonglong2 *>(P.pre[lb] + s * PRE_WORDS);
+            ulonglong2 *pd = reinterpret_cast<ulonglong2 *>(P.pre[lb ^ 1] + ns * PRE_WORDS);
+            pd[0] = ps[0];
+            pd[1] = ps[1];
+            const unsigned *os = reinterpret_cast<const unsigned *>(P.occa[lb] + s * P.ostride);
+            unsigned *od = reinterpret_cast<unsigned *>(P.occa[lb ^ 1] + ns * P.ostride);
+            for (int k = 0; k < P.ostride / 4; ++k) od[k] = os[k];
         }
     }
 }
@@ -715,28 +725,30 @@ __global__ void k_index_clear_at(Params P, const int *pos, long long n) {
     }
 }
 
-// Diagonal elements of slots [0, n) of list buffer b: computed (compute != 0) or taken as given; the
-// float copy is the nearest float.
+// Slots [lo, n) of list buffer b as loaded: their derived words and occupied lists, and with compute their
+// diagonal elements (H_ii - E0 and its nearest float; without, the float copies are made by the check).
 template <int W>
-__global__ void __launch_bounds__(256) k_prepare_list(Params P, int b, long long n, int compute) {
+__global__ void __launch_bounds__(256) k_prepare_list(Params P, int b, long long lo, long long n, int compute) {
     extern __shared__ double s_w[];
+    __shared__ Tables T;
+    load_tables(P, T);
     const int M = P.n_orb;
-    for (int k = threadIdx.x; k < 2 * M * M; k += blockDim.x) s_w[k] = P.wpair[k];
-    for (int k = threadIdx.x; k < M; k += blockDim.x) s_w[2 * M * M + k] = P.h[k * M + k];
+    if (compute) {
+        for (int k = threadIdx.x; k < 2 * M * M; k += blockDim.x) s_w[k] = P.wpair[k];
+        for (int k = threadIdx.x; k < M; k += blockDim.x) s_w[2 * M * M + k] = P.h[k * M + k];
+    }
     __syncthreads();
-    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
-        double v;
-        if (compute) {
-            unsigned long long d[W];
+    for (long long s = lo + (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
+        unsigned long long d[W];
 #pragma unroll
-            for (int w = 0; w < W; ++w) d[w] = P.det[b][s * W + w];
-            v = __dsub_rn(P.hphf ? hphf_hdiag<W>(P, d, s_w, s_w + 2 * M * M) : hdiag<W>(P, d, s_w, s_w + 2 * M * M),
-                          P.E0);
+        for (int w = 0; w < W; ++w) d[w] = P.det[b][s * W + w];
+        store_derived<W>(P, T, b, s, d);
+        if (compute) {
+            const double v = __dsub_rn(P.hphf ? hphf_hdiag<W>(P, d, s_w, s_w + 2 * M * M) : hdiag<W>(P, d, s_w, s_w + 2 * M * M),
+                                       P.E0);
             P.hd[b][s] = v;
-        } else {
-            v = P.hd[b][s];
+            P.hdf[b][s] = __double2float_rn(v);
         }
-        P.hdf[b][s] = __double2float_rn(v);
     }
 }
 

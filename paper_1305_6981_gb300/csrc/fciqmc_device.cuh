@@ -150,6 +150,11 @@ struct Params {
     int occ_units;                    // occupation threshold in units (1: none)
     double tau_death;
     float tau_death_f;
+    // per slot of each list buffer, what the spawning kernels need of a determinant beyond its bits, derived
+    // once when it enters the list: PRE_WORDS words, and its occupied spin orbitals (ostride bytes)
+    unsigned long long *pre[2];
+    unsigned char *occa[2];
+    int ostride;
 };
 
 __device__ __forceinline__ void set_status(DevState *st, int code) { atomicCAS(&st->status, 0, code); }

@@ -152,29 +152,29 @@ __device__ __forceinline__ unsigned nonzero_bytes(unsigned long long x) {
     return (unsigned)((bits * 0x0102040810204080ull) >> 56);
 }
 
-// Class counts first (population counts against the class masks); then one pass over the occupied
-// spin orbitals in ascending order gives the occupied list, the electrons with an allowed single (an
-// electron's class keeps an unoccupied orbital) and the fingerprint of Algorithm 1.
+// What the spawning kernels need of a determinant beyond its bits, a function of the bits alone (stored per
+// slot when the determinant enters the list): PRE_FP the fingerprint of Algorithm 1, PRE_OKM bit x set when
+// electron x has an allowed single (its class keeps an unoccupied orbital), PRE_CB0 / PRE_CB1 byte g the
+// unoccupied spin orbitals of class (irrep g, spin 0 / 1); beside them the occupied list.
+enum { PRE_FP = 0, PRE_OKM, PRE_CB0, PRE_CB1, PRE_WORDS };
+
+// Class counts first (population counts against the class masks); then one pass over the occupied spin
+// orbitals in ascending order gives the occupied list, the electrons with an allowed single and the
+// fingerprint.
 template <int W>
-__device__ __forceinline__ void prepare_det(const Params &P, const Tables &T, DetView<W> &v, unsigned char *occ,
-                                            int c) {
+__device__ __forceinline__ void derive_det(const Params &P, const Tables &T, const unsigned long long (&d)[W],
+                                           unsigned long long (&pre)[PRE_WORDS], unsigned char *occ) {
     unsigned long long cb0 = 0, cb1 = 0;
     for (int g = 0; g < P.n_irrep_used; ++g) {
         int u0 = 0, u1 = 0;
 #pragma unroll
         for (int w = 0; w < W; ++w) {
-            u0 += __popcll(~v.d[w] & T.mask[(2 * g) * MAXW + w]);
-            u1 += __popcll(~v.d[w] & T.mask[(2 * g + 1) * MAXW + w]);
+            u0 += __popcll(~d[w] & T.mask[(2 * g) * MAXW + w]);
+            u1 += __popcll(~d[w] & T.mask[(2 * g + 1) * MAXW + w]);
         }
         cb0 |= (unsigned long long)u0 << (8 * g);
         cb1 |= (unsigned long long)u1 << (8 * g);
     }
-    v.cb8[0] = cb0;
-    v.cb8[1] = cb1;
-    unsigned *cw = reinterpret_cast<unsigned *>(v.cnt);
-#pragma unroll
-    for (int j = 0; j < NCLASS / 4; ++j)  // class 2g + s: bytes (g = 2j, s = 0), (2j, 1), (2j + 1, 0), (2j + 1, 1)
-        cw[j] = __byte_perm((unsigned)(cb0 >> (16 * j)), (unsigned)(cb1 >> (16 * j)), 0x5140u);
     const unsigned set0 = nonzero_bytes(cb0), set1 = nonzero_bytes(cb1);
     unsigned long long ok[W];
 #pragma unroll
@@ -184,7 +184,7 @@ __device__ __forceinline__ void prepare_det(const Params &P, const Tables &T, De
     unsigned long long okm = 0, h = 0;
 #pragma unroll
     for (int w = 0; w < W; ++w) {
-        unsigned long long m = v.d[w];
+        unsigned long long m = d[w];
         while (m) {
             const int b = __ffsll((long long)m) - 1;
             const int k = 64 * w + b;
@@ -196,14 +196,56 @@ __device__ __forceinline__ void prepare_det(const Params &P, const Tables &T, De
             m &= m - 1;
         }
     }
-    v.okm = okm;
-    v.nok = (unsigned char)__popcll(okm);
-    v.fp = h;
+    pre[PRE_FP] = h;
+    pre[PRE_OKM] = okm;
+    pre[PRE_CB0] = cb0;
+    pre[PRE_CB1] = cb1;
+}
+
+// The per-determinant view from the derived words, the population and the run's reference and initiator rule.
+template <int W>
+__device__ __forceinline__ void fill_view(const Params &P, DetView<W> &v, const unsigned long long (&pre)[PRE_WORDS],
+                                          int c) {
+    const unsigned long long cb0 = pre[PRE_CB0], cb1 = pre[PRE_CB1];
+    v.cb8[0] = cb0;
+    v.cb8[1] = cb1;
+    unsigned *cw = reinterpret_cast<unsigned *>(v.cnt);
+#pragma unroll
+    for (int j = 0; j < NCLASS / 4; ++j)  // class 2g + s: bytes (g = 2j, s = 0), (2j, 1), (2j + 1, 0), (2j + 1, 1)
+        cw[j] = __byte_perm((unsigned)(cb0 >> (16 * j)), (unsigned)(cb1 >> (16 * j)), 0x5140u);
+    v.okm = pre[PRE_OKM];
+    v.nok = (unsigned char)__popcll(pre[PRE_OKM]);
+    v.fp = pre[PRE_FP];
     v.c = c;
     int ac = c < 0 ? -c : c;
     bool is_ref = det_eq<W>(v.d, P.ref);
     v.flag = (P.init_thr < 0 || ac > P.init_thr || is_ref) ? 1 : 0;
     v.isref = is_ref ? 1 : 0;
+}
+
+// The view of v.d (its bits already set), derived on the spot.
+template <int W>
+__device__ __forceinline__ void prepare_det(const Params &P, const Tables &T, DetView<W> &v, unsigned char *occ,
+                                            int c) {
+    unsigned long long pre[PRE_WORDS];
+    derive_det<W>(P, T, v.d, pre, occ);
+    fill_view<W>(P, v, pre, c);
+}
+
+// Derived words and occupied list of slot s of list buffer b, computed and stored.
+template <int W>
+__device__ __forceinline__ void store_derived(const Params &P, const Tables &T, int b, long long s,
+                                              const unsigned long long (&d)[W]) {
+    unsigned long long pre[PRE_WORDS];
+    unsigned char occ[MAXN] = {};
+    derive_det<W>(P, T, d, pre, occ);
+    ulonglong2 *dst = reinterpret_cast<ulonglong2 *>(P.pre[b] + s * PRE_WORDS);
+    dst[0] = make_ulonglong2(pre[0], pre[1]);
+    dst[1] = make_ulonglong2(pre[2], pre[3]);
+    unsigned *od = reinterpret_cast<unsigned *>(P.occa[b] + s * P.ostride);
+    for (int k = 0; k < P.ostride / 4; ++k)
+        od[k] = (unsigned)occ[4 * k] | ((unsigned)occ[4 * k + 1] << 8) | ((unsigned)occ[4 * k + 2] << 16) |
+                ((unsigned)occ[4 * k + 3] << 24);
 }
 
 // ---------------------------------------------------------------------------- one spawning attempt
@@ -1160,8 +1202,20 @@ __global__ void __launch_bounds__(kTile, FQ_SWEEP_MIN_BLOCKS) k_sweep(Params P) 
                     v.d[0] = __ldcs(det + s);
                 }
                 const float hf = __ldcs(hdf + s);
+                // the determinant's derived words and occupied list, stored when it entered the list
                 unsigned char *occ = s_occ + tid * ostride;
-                prepare_det<W>(P, T, v, occ, c);
+                unsigned long long pre[PRE_WORDS];
+                {
+                    const ulonglong2 *ps = reinterpret_cast<const ulonglong2 *>(P.pre[lb] + s * PRE_WORDS);
+                    const ulonglong2 p0 = __ldcs(ps), p1 = __ldcs(ps + 1);
+                    pre[0] = p0.x;
+                    pre[1] = p0.y;
+                    pre[2] = p1.x;
+                    pre[3] = p1.y;
+                    const unsigned *os = reinterpret_cast<const unsigned *>(P.occa[lb] + s * ostride);
+                    for (int k = 0; k < ostride / 4; ++k) reinterpret_cast<unsigned *>(occ)[k] = __ldcs(os + k);
+                }
+                fill_view<W>(P, v, pre, c);
                 const unsigned ac = (unsigned)(c < 0 ? -c : c);
                 acc[NCNT] += ac;
                 acc[NCNT + 1] += 1;
