@@ -193,8 +193,8 @@ struct fciqmc_handle {
     fciqmc_options opt;      // as created (checked when partitions are grouped)
     double tau;
     int32_t init_thr;
-    cudaStream_t aux;        // helper stream of set_walkers (created on first use), joined by events
-    cudaEvent_t ev_fork, ev_join, ev_chunk[8];
+    cudaStream_t aux, aux2;  // helper streams of set_walkers (created on first use), joined by events
+    cudaEvent_t ev_fork, ev_join, ev_join2, ev_chunk[8];
 };
 
 namespace {
@@ -310,29 +310,33 @@ void launch_prepare(fciqmc_handle *h, int b, long long n, int compute) {  // slo
     fq::k_prepare_list<W><<<(unsigned)blocks, 256, h->smem_w, h->stream>>>(h->P, b, 0, n, compute);
 }
 
-// The helper stream of set_walkers and its events, created together (nothing is kept if one fails).
+// The helper streams of set_walkers and their events, created together (nothing is kept if one fails).
 int create_helper_stream(fciqmc_handle *h) {
     static_assert(sizeof(fciqmc_handle::ev_chunk) == 8 * sizeof(cudaEvent_t), "eight chunk events");
-    cudaStream_t a = nullptr;
-    cudaEvent_t ev[10] = {};
-    bool ok = cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking) == cudaSuccess;
+    cudaStream_t a = nullptr, a2 = nullptr;
+    cudaEvent_t ev[11] = {};
+    bool ok = cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&a2, cudaStreamNonBlocking) == cudaSuccess;
     for (cudaEvent_t &e : ev) ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
     if (!ok) {
         for (cudaEvent_t e : ev)
             if (e) cudaEventDestroy(e);
         if (a) cudaStreamDestroy(a);
+        if (a2) cudaStreamDestroy(a2);
         cudaGetLastError();
         return FCIQMC_ERR_CUDA;
     }
     h->ev_fork = ev[0];
     h->ev_join = ev[1];
-    for (int k = 0; k < 8; ++k) h->ev_chunk[k] = ev[2 + k];
+    h->ev_join2 = ev[2];
+    for (int k = 0; k < 8; ++k) h->ev_chunk[k] = ev[3 + k];
     h->aux = a;
+    h->aux2 = a2;
     return FCIQMC_OK;
 }
 
-// Copy, check and index work of load_list, up to the join of the helper stream; bad receives the outcome
-// of the check and of the inserts (1 invalid entry, 2 repeated determinant, 3 index full).
+// Copy, check, index and derived-data work of load_list, up to the join of the helper streams; bad receives
+// the outcome of the check and of the inserts (1 invalid entry, 2 repeated determinant, 3 index full).
 template <int W>
 int load_stage(fciqmc_handle *h, const DevState &cur, const uint64_t *dets, const int32_t *pops,
                const double *hdiag, long long n, int &bad) {
@@ -363,11 +367,14 @@ int load_stage(fciqmc_handle *h, const DevState &cur, const uint64_t *dets, cons
             FQ_CUDA(cudaStreamWaitEvent(a, h->ev_chunk[k], 0));
             const unsigned ib = (unsigned)std::max<long long>(1, std::min<long long>((hi - lo + 255) / 256, h->small_grid));
             fq::k_index_insert<W><<<ib, 256, 0, a>>>(P, b, lo, hi);
-            fq::k_prepare_list<W><<<ib, 256, 0, a>>>(P, b, lo, hi, 0);  // derived words of the chunk
+            // the chunk's derived words on the second helper stream, beside the index work
+            FQ_CUDA(cudaStreamWaitEvent(h->aux2, h->ev_chunk[k], 0));
+            fq::k_prepare_list<W><<<ib, 256, 0, h->aux2>>>(P, b, lo, hi, 0);
         }
     }
     FQ_CUDA(cudaGetLastError());
     FQ_CUDA(cudaEventRecord(h->ev_join, a));
+    FQ_CUDA(cudaEventRecord(h->ev_join2, h->aux2));
     if (n > 0) {
         FQ_CUDA(cudaMemcpyAsync(P.pop[b][0], pops, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
         if (hdiag) FQ_CUDA(cudaMemcpyAsync(P.hd[b], hdiag, sizeof(double) * n, cudaMemcpyHostToDevice, s));
@@ -375,6 +382,7 @@ int load_stage(fciqmc_handle *h, const DevState &cur, const uint64_t *dets, cons
     fq::k_check_list<W><<<blocks, 256, 0, s>>>(P, b, n, hdiag ? 1 : 0);
     FQ_CUDA(cudaGetLastError());
     FQ_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
+    FQ_CUDA(cudaStreamWaitEvent(s, h->ev_join2, 0));
     FQ_CUDA(cudaMemcpyAsync(&bad, &P.st->check_bad, sizeof(int), cudaMemcpyDeviceToHost, s));
     FQ_CUDA(cudaStreamSynchronize(s));
     return FCIQMC_OK;
@@ -383,8 +391,9 @@ int load_stage(fciqmc_handle *h, const DevState &cur, const uint64_t *dets, cons
 // Loads a list into buffer b; on success makes it the active list with the state st0. The index work
 // runs on a helper stream while the list is copied in: the old list's entries are emptied (located first,
 // or the whole index for a dense index or after a failed step), then each chunk of new keys is inserted as
-// soon as it has arrived. The check of the new entries (and the float copies of given diagonal elements)
-// runs on the caller's stream. A rejected list (invalid entries, a repeated determinant) or a failed copy
+// soon as it has arrived; a second helper stream derives each chunk's per-slot data (fingerprint, class
+// counts, occupied list) meanwhile. The check of the new entries (and the float copies of given diagonal
+// elements) runs on the caller's stream. A rejected list (invalid entries, a repeated determinant) or a failed copy
 // leaves the run as it was: the index is rebuilt from the current list and the state is not replaced.
 template <int W>
 int load_list(fciqmc_handle *h, const DevState &cur, DevState &st0, const uint64_t *dets, const int32_t *pops,
@@ -396,6 +405,7 @@ int load_list(fciqmc_handle *h, const DevState &cur, DevState &st0, const uint64
     const int rc = load_stage<W>(h, cur, dets, pops, hdiag, n, bad);
     if (rc != FCIQMC_OK || bad) {
         cudaStreamSynchronize(h->aux);
+        cudaStreamSynchronize(h->aux2);
         cudaStreamSynchronize(s);
         fq::k_index_clear<<<h->small_grid, 256, 0, s>>>(P, 1);
         fq::k_index_fill<W><<<h->small_grid, 256, 0, s>>>(P, 1);
@@ -1034,9 +1044,12 @@ void fciqmc_destroy(fciqmc_handle *h) {
     cudaStreamSynchronize(h->stream);
     if (h->aux) {
         cudaStreamSynchronize(h->aux);
+        cudaStreamSynchronize(h->aux2);
         cudaStreamDestroy(h->aux);
+        cudaStreamDestroy(h->aux2);
         cudaEventDestroy(h->ev_fork);
         cudaEventDestroy(h->ev_join);
+        cudaEventDestroy(h->ev_join2);
         for (cudaEvent_t e : h->ev_chunk) cudaEventDestroy(e);
     }
     if (h->graph_ready) cudaGraphExecDestroy(h->graph);
