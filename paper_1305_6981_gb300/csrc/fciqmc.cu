@@ -393,8 +393,9 @@ int load_stage(fciqmc_handle *h, const DevState &cur, const uint64_t *dets, cons
 // or the whole index for a dense index or after a failed step), then each chunk of new keys is inserted as
 // soon as it has arrived; a second helper stream derives each chunk's per-slot data (fingerprint, class
 // counts, occupied list) meanwhile. The check of the new entries (and the float copies of given diagonal
-// elements) runs on the caller's stream. A rejected list (invalid entries, a repeated determinant) or a failed copy
-// leaves the run as it was: the index is rebuilt from the current list and the state is not replaced.
+// elements) runs on the caller's stream. A rejected list (invalid entries, a repeated determinant) or a
+// failed copy leaves the run as it was: the index is rebuilt from the current list and the state is not
+// replaced.
 template <int W>
 int load_list(fciqmc_handle *h, const DevState &cur, DevState &st0, const uint64_t *dets, const int32_t *pops,
               const double *hdiag, long long n) {
