@@ -81,6 +81,9 @@ __host__ __device__ constexpr int occ_stride(int n_elec) { return (n_elec + 3) &
 struct Tables {
     unsigned long long map1[MAXSO];
     unsigned long long mask[NCLASS * MAXW];
+    // spin orbitals of spin s in the irreps of a 4-bit set, for irreps 0..3 (half 0) and 4..7 (half 1):
+    // uh[((s * 2 + half) * 16 + set) * MAXW + w]
+    unsigned long long uh[2 * 2 * 16 * MAXW];
     unsigned char irrep[MAXSO / 2];
     unsigned short pairs[MAXPAIRS];
 };
@@ -88,6 +91,13 @@ struct Tables {
 __device__ __forceinline__ void load_tables(const Params &P, Tables &T) {
     for (int k = threadIdx.x; k < P.n_so; k += blockDim.x) T.map1[k] = P.map1[k];
     for (int k = threadIdx.x; k < NCLASS * MAXW; k += blockDim.x) T.mask[k] = P.cmask[k];
+    for (int k = threadIdx.x; k < 2 * 2 * 16 * MAXW; k += blockDim.x) {
+        const int w = k % MAXW, set = (k / MAXW) % 16, half = (k / (16 * MAXW)) % 2, s = k / (32 * MAXW);
+        unsigned long long u = 0ull;
+        for (int b = 0; b < 4; ++b)
+            if ((set >> b) & 1) u |= P.cmask[((4 * half + b) * 2 + s) * MAXW + w];
+        T.uh[k] = u;
+    }
     for (int k = threadIdx.x; k < P.n_orb; k += blockDim.x) T.irrep[k] = P.irrep[k];
     for (int k = threadIdx.x; k < P.npairs; k += blockDim.x) T.pairs[k] = P.pairs[k];
 }
@@ -364,6 +374,39 @@ __device__ __forceinline__ unsigned good_set(const Params &P, const DetView<W> &
         const unsigned set = (unsigned)((bits * 0x0102040810204080ull) >> 56);
 #pragma unroll
         for (int w = 0; w < W; ++w) gm[w] |= __ldg(P.unionm + ((sa * 256 + set) * MAXW + w));
+    }
+#pragma unroll
+    for (int w = 0; w < W; ++w) gm[w] &= ~v.d[w];
+    return G;
+}
+
+// good_set with the union of the good classes' orbitals from the block's shared tables (two 4-irrep halves)
+// instead of the global 8-bit-set table.
+template <int W>
+__device__ __forceinline__ unsigned good_set_t(const Tables &T, const DetView<W> &v, int si, int sj, int gij,
+                                               unsigned long long (&gm)[W]) {
+    constexpr unsigned long long kOnes = 0x0101010101010101ull, kHigh = 0x8080808080808080ull;
+    unsigned G = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) gm[w] = 0ull;
+#pragma unroll
+    for (int sa = 0; sa < 2; ++sa) {
+        if (si == sj && sa != si) continue;
+        const int sb = si + sj - sa;
+        const unsigned long long A = v.cb8[sa];
+        unsigned long long B = v.cb8[sb];
+        if (gij & 4) B = (B >> 32) | (B << 32);
+        const unsigned sel = 0x3210u ^ (0x1111u * (unsigned)(gij & 3));  // byte g <- byte g ^ (gij & 3)
+        B = ((unsigned long long)__byte_perm((unsigned)(B >> 32), 0u, sel) << 32) | __byte_perm((unsigned)B, 0u, sel);
+        const unsigned long long need = (sa == sb && gij == 0) ? 2ull : 1ull;  // a and b from one class
+        const unsigned long long cond = (A + 0x7F * kOnes) & (B + (0x80 - need) * kOnes) & kHigh;
+        const unsigned long long bits = cond >> 7;
+        G += (unsigned)(((A & (bits * 0xFFull)) * kOnes) >> 56);
+        const unsigned set = (unsigned)((bits * 0x0102040810204080ull) >> 56);
+        const unsigned long long *lo = T.uh + ((sa * 2) * 16 + (set & 15u)) * MAXW;
+        const unsigned long long *hi = T.uh + ((sa * 2 + 1) * 16 + (set >> 4)) * MAXW;
+#pragma unroll
+        for (int w = 0; w < W; ++w) gm[w] |= lo[w] | hi[w];
     }
 #pragma unroll
     for (int w = 0; w < W; ++w) gm[w] &= ~v.d[w];
@@ -775,7 +818,7 @@ __device__ __forceinline__ bool attempt_begin(const Params &P, const Tables &T, 
         ao = tab->glist[e][k2];
     } else {
         unsigned long long gm[W];
-        G = good_set<W>(P, v, si, sj, gij, gm);
+        G = good_set_t<W>(T, v, si, sj, gij, gm);
         if (G == 0) { cnt[C_NULLS]++; return false; }
         ao = select_bit<W>(gm, (int)rank_next(rh, rl, G));
     }
