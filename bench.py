@@ -46,10 +46,10 @@ METRIC = "spawn attempts/s at 1e8 walkers (24e/60o, initiator, tau 0.001)"
 # the medium case first (--ncu-case --target 5000000); multi-pass sets (--set full) stay on that medium case,
 # one kernel and one launch. The commands are in the profile summary named in WARP_INST_SOURCE. The figures
 # must be re-measured whenever those kernels change.
-WARP_INST_PER_ATTEMPT = {"heavy": 12.53, "sweep": 26.92}
+WARP_INST_PER_ATTEMPT = {"heavy": 12.53, "sweep": 27.10}
 WARP_INST_SOURCE = "profiles/counters_24e60o_steady.txt (full size, steady state, one-pass capture)"
 # DRAM bytes (read + write) per launch at the full workload, from the same capture.
-DRAM_BYTES_PER_LAUNCH = {"heavy": 35_800_000, "sweep": 563_000_000, "annihilate": 87_700_000}
+DRAM_BYTES_PER_LAUNCH = {"heavy": 35_700_000, "sweep": 562_900_000, "annihilate": 87_700_000}
 ISSUE_PER_CLK_PER_SM = 4  # warp instructions: 4 schedulers per SM, one issue each per clock
 N_SMS = 152
 
