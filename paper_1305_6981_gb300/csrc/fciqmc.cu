@@ -230,6 +230,7 @@ int configure_kernels(fciqmc_handle *h) {
         h->heavy_grid = std::min(h->heavy_grid, g);
     }
     h->P.heavy_warps = (long long)h->heavy_grid * (fq::kTile / 32);
+    h->P.sweep_blocks = h->sweep_grid;
     h->small_grid = std::min(kMaxGrid, sms * 8);
     h->info.num_sms = sms;
     h->info.grid_blocks = h->sweep_grid;
@@ -1310,6 +1311,7 @@ int fciqmc_group_create(fciqmc_handle *const *parts, int32_t n_partitions, int64
         links[r].hist_cap = P.hist_cap;
         links[r].cap = P.cap;
         links[r].heavy_warps = P.heavy_warps;
+        links[r].sweep_blocks = P.sweep_blocks;
         links[r].frac_bits = P.frac_bits;
     }
     int rc = FCIQMC_OK;

@@ -263,7 +263,7 @@ __device__ __forceinline__ unsigned next_chunk(long long attempts, long long war
 // compaction and the heavy chunk size for the next iteration (attempts: its expected spawning attempts) and
 // clears the per-iteration counters.
 __device__ __forceinline__ void commit_list(DevState *st, long long nd_out, long long cap, long long attempts,
-                                            long long heavy_warps) {
+                                            long long heavy_warps, long long sweep_blocks) {
     const long long new_len = (long long)st->claim;
     st->list_len = new_len;
     st->pp ^= 1;
@@ -280,6 +280,9 @@ __device__ __forceinline__ void commit_list(DevState *st, long long nd_out, long
     st->sweep_next = 0;
     st->heavy_next = 0;
     st->heavy_chunk = next_chunk(attempts, heavy_warps);
+    // a short list leaves most sweep blocks without a tile, and each tile's light attempts run in one block:
+    // then the heavy path, whose chunks spread over every warp, takes determinants from 32 walkers on
+    st->heavy_thr = (new_len + kTile - 1) / kTile * 4 < sweep_blocks ? (unsigned)kHeavyShort : (unsigned)kHeavy;
     for (int k = 0; k < NCNT; ++k) st->cnt[k] = 0;
     for (int k = 0; k < MAXPARTS; ++k) st->ob_n[k] = 0;
 }
@@ -318,7 +321,7 @@ __global__ void k_finish(Params P) {
     P.hist[st->hist_n % P.hist_cap] = row;
     st->hist_n++;
     shift_update(st, row.nw_out, P.target, P.period, P.c_shift);
-    commit_list(st, row.nd_out, P.cap, row.nw_out >> P.frac_bits, P.heavy_warps);
+    commit_list(st, row.nd_out, P.cap, row.nw_out >> P.frac_bits, P.heavy_warps, P.sweep_blocks);
 }
 
 // ---------------------------------------------------------------------------- hash-partitioned runs
@@ -331,6 +334,7 @@ struct PartLink {
     fciqmc_row *hist;            // the partition's own rows (its list's counters)
     long long hist_cap, cap;
     long long heavy_warps;       // warps of the partition's k_heavy launch
+    long long sweep_blocks;      // blocks of the partition's k_sweep launch
     int frac_bits;               // hybrid walkers: populations in units of 2^-frac_bits
 };
 struct GroupDev {
@@ -414,7 +418,7 @@ __global__ void k_group_finish(const PartLink *links, int n_parts, GroupDev *g, 
         shift_update(st, tot.nw_out, target, period, c_shift);  // the same state and input in every partition
         const long long nw_part = (long long)st->nw_in + (long long)st->d_nw;
         commit_list(st, (long long)st->nd_in + (long long)st->d_nd, links[r].cap, nw_part >> links[r].frac_bits,
-                    links[r].heavy_warps);
+                    links[r].heavy_warps, links[r].sweep_blocks);
     }
 }
 

@@ -55,6 +55,7 @@ struct DevState {
     unsigned long long sweep_next;  // next sweep tile to hand out (tiles are taken dynamically by the blocks)
     unsigned long long heavy_next;  // next batch of heavy chunks to hand out (taken dynamically by the warps)
     unsigned heavy_chunk;           // attempts per heavy chunk this iteration (0: the smallest size)
+    unsigned heavy_thr;             // attempts above which a determinant takes the heavy path (0: kHeavy)
     unsigned long long ob_n[MAXPARTS];  // partitioned runs: spawns routed to each other partition this iteration
 };
 
@@ -133,6 +134,7 @@ struct Params {
     unsigned *heavy_att;              // attempts of each
     long long heavy_cap;
     long long heavy_warps;            // warps of a k_heavy launch (chooses the chunk size)
+    long long sweep_blocks;           // blocks of a k_sweep launch (chooses the heavy threshold)
     double *partial;
     fciqmc_row *hist;
     long long hist_cap;

@@ -25,6 +25,7 @@ constexpr int kTileSums = 32;       // range sums of the per-tile numerators (bl
 #define FQ_HEAVY_THRESHOLD 256
 #endif
 constexpr int kHeavy = FQ_HEAVY_THRESHOLD;  // |C_i| above this: attempts go to the chunked heavy path
+constexpr int kHeavyShort = 32;  // the threshold for lists with fewer tiles than a quarter of the sweep's blocks
 #ifndef FQ_HEAVY_CHUNK
 #define FQ_HEAVY_CHUNK 512
 #endif
@@ -1207,6 +1208,7 @@ __global__ void __launch_bounds__(kTile, FQ_SWEEP_MIN_BLOCKS) k_sweep(Params P) 
     int *pop_out = P.pop[lb][pp ^ 1];
     DetView<W> *heavy = reinterpret_cast<DetView<W> *>(P.heavy);
     const unsigned chunk = st->heavy_chunk ? st->heavy_chunk : (unsigned)kChunk;
+    const unsigned heavy_thr = st->heavy_thr ? st->heavy_thr : (unsigned)kHeavy;
     __syncthreads();
 
     unsigned long long acc[NCNT + 4];  // counters, then nw, nd, d_nw, d_nd
@@ -1289,7 +1291,7 @@ __global__ void __launch_bounds__(kTile, FQ_SWEEP_MIN_BLOCKS) k_sweep(Params P) 
                     }
                 }
                 acc[C_ATTEMPTS] += natt;
-                if (natt > (unsigned)kHeavy) {
+                if (natt > heavy_thr) {
                     // heavily populated determinant: a record for k_heavy, whose warps take chunks of `chunk`
                     // attempts; record index and first chunk are claimed by one atomic, so the first
                     // chunks are nondecreasing in the record index
