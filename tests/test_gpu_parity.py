@@ -206,6 +206,29 @@ def test_reloads_and_invalid_lists_dense_index():
     g.close()
 
 
+@pytest.mark.parametrize("n_walkers,scale", [(30_000, 20), (900_000, 1)])
+def test_short_and_long_lists_every_iteration(n_walkers, scale):
+    """A list shorter than a quarter of the sweep's blocks in tiles (9.5e3 determinants with ~60 walkers each,
+    so from the second iteration on the heavy path takes every determinant above 32 walkers) and a long one
+    (2.9e5 determinants, threshold 256): both in lockstep with the oracle for 8 iterations."""
+    s = synth.init_12e24o()
+    g, q = make_pair(s, 0.005, 3, seed=31, main_capacity=1 << 21)
+    d, p = synth.walker_snapshot(s, n_walkers, seed=6)
+    p = (p.astype(np.int64) * scale).astype(np.int32)
+    g.set_walkers(d, p, iteration=3, shift=0.3, vary=0)
+    q.set_walkers(d, p, iteration=3, shift=0.3)
+    rows_q = []
+    for k in range(8):
+        g.step(1)
+        rows_q += q.iterate(1)
+        assert same_lists(g.walkers(), q.walkers()), f"iteration {k + 1}"
+    rows = g.history(8)
+    compare_rows(rows, rows_q)
+    if scale > 1:  # the lowered threshold sends most attempts to the heavy path after the first iteration
+        assert rows[1]["heavy_attempts"] > 2 * rows[0]["heavy_attempts"]
+    g.close()
+
+
 def test_read_back_into_pinned_host_arrays():
     """get_walkers into page-locked host arrays (the benchmark's host-buffer path) gives the list read into
     pageable arrays, with or without the diagonal elements; arrays too small for the list give CAPACITY."""
