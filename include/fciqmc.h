@@ -152,8 +152,8 @@ typedef struct {
     int64_t merged_entries;   /* distinct determinants spawned onto */
     int64_t aborted_walkers;  /* spawned walkers discarded by the initiator rule */
     int64_t inserted_dets;    /* determinants newly occupied by spawning */
-    int64_t heavy_attempts;   /* attempts from determinants with more than 256 walkers, which the
-                                 chunked spawning kernel (k_heavy) carries out */
+    int64_t heavy_attempts;   /* attempts from determinants with more than 256 walkers (32 for lists
+                                 of few tiles), which the chunked spawning kernel (k_heavy) carries out */
 } fciqmc_row;
 
 /* Estimators of the current list (Sec. II, Eq. 2). Energies include e_core. */
